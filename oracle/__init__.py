@@ -1,0 +1,194 @@
+"""ctypes front end of the CSS ORACLE (plain FP64 C in css_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the test-suite, the smoke check and the benchmark's CPU-baseline
+leg may import this package; the library's product path never does.  It shares no code with
+the CUDA library.  Every function takes and returns host numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "css_oracle.c"
+_LIB = _HERE / "libcss_oracle.so"
+
+SYMMETRIZE = 1
+REORTH_LOCAL = 4
+SIGNS_ONES = 1
+
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with the host C compiler (gcc, OpenMP, no fp contraction)."""
+    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _LIB.with_suffix(f".{os.getpid()}.tmp.so")
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-o", str(tmp), str(_SRC), "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = C.CDLL(str(_LIB))
+        p = C.c_void_p
+        i32, i64, u64, f64 = C.c_int32, C.c_int64, C.c_uint64, C.c_double
+        lib.css_ref_hash.restype = u64
+        lib.css_ref_hash.argtypes = [u64, u64]
+        lib.css_ref_fermi.restype = f64
+        lib.css_ref_fermi.argtypes = [f64, f64, f64]
+        lib.css_ref_neighbours.argtypes = [i32, p, f64, f64, p, C.POINTER(C.c_void_p)]
+        lib.css_ref_free.argtypes = [p]
+        lib.css_ref_color_graph.argtypes = [i32, p, p, u64, p, p]
+        lib.css_ref_color.argtypes = [i32, p, f64, f64, u64, p, p]
+        lib.css_ref_probes.argtypes = [p, i32, i32, u64, C.c_int, p]
+        lib.css_ref_eigh.argtypes = [i32, p, p]
+        lib.css_ref_lanczos.argtypes = [i32, i32, p, p, p, p, p, i32, i32, C.c_int, p, p, p]
+        lib.css_ref_density.argtypes = [i32, i32, i32, p, p, p, p, p, i32, f64, f64, f64, C.c_int, i32,
+                                        C.c_int, p, i32, p, p, p, p, p]
+        lib.css_ref_ritz.argtypes = [i32, i32, p, p, p, p, p, i32, i32, C.c_int, p, p, p]
+        lib.css_ref_num_threads.restype = C.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _chk(st, what):
+    if st != 0:
+        raise RuntimeError(f"oracle {what} failed with status {st}")
+
+
+def hash64(seed: int, x: int) -> int:
+    return int(_load().css_ref_hash(seed, x))
+
+
+def fermi(x: float, mu: float, kT: float) -> float:
+    return float(_load().css_ref_fermi(x, mu, kT))
+
+
+def neighbours(xyz, box: float, r_col: float):
+    """Colour-graph adjacency (CSR) by brute force in int64 fixed point."""
+    lib = _load()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    n = xyz.shape[0]
+    ptr = np.zeros(n + 1, dtype=np.int32)
+    adj = C.c_void_p()
+    _chk(lib.css_ref_neighbours(n, _ptr(xyz), box, r_col, _ptr(ptr), C.byref(adj)), "neighbours")
+    m = int(ptr[-1])
+    out = np.ctypeslib.as_array(C.cast(adj, C.POINTER(C.c_int32)), shape=(max(m, 1),))[:m].copy()
+    lib.css_ref_free(adj)
+    return ptr, out
+
+
+def color_graph(adj_ptr, adj, seed: int):
+    lib = _load()
+    adj_ptr = np.ascontiguousarray(adj_ptr, dtype=np.int32)
+    adj = np.ascontiguousarray(adj, dtype=np.int32)
+    n = adj_ptr.shape[0] - 1
+    col = np.empty(n, dtype=np.int32)
+    nc = np.zeros(1, dtype=np.int32)
+    _chk(lib.css_ref_color_graph(n, _ptr(adj_ptr), _ptr(adj), seed, _ptr(col), _ptr(nc)), "color_graph")
+    return col, int(nc[0])
+
+
+def color(xyz, box: float, r_col: float, seed: int):
+    lib = _load()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    n = xyz.shape[0]
+    col = np.empty(n, dtype=np.int32)
+    nc = np.zeros(1, dtype=np.int32)
+    _chk(lib.css_ref_color(n, _ptr(xyz), box, r_col, seed, _ptr(col), _ptr(nc)), "color")
+    return col, int(nc[0])
+
+
+def probes(colour, b: int, sign_seed: int, flags: int = 0):
+    lib = _load()
+    colour = np.ascontiguousarray(colour, dtype=np.int32)
+    n = colour.shape[0]
+    s = np.empty(n * b, dtype=np.int8)
+    _chk(lib.css_ref_probes(_ptr(colour), n, b, sign_seed, flags, _ptr(s)), "probes")
+    return s
+
+
+def eigh(A):
+    """Eigen-decomposition of a symmetric matrix: (w ascending, U columns)."""
+    A = np.array(A, dtype=np.float64, order="C", copy=True)
+    n = A.shape[0]
+    w = np.empty(n)
+    _chk(_load().css_ref_eigh(n, _ptr(A), _ptr(w)), "eigh")
+    return w, A
+
+
+def _h(H):
+    return (H.n_brow, H.b, _ptr(np.ascontiguousarray(H.row_ptr, dtype=np.int32)),
+            _ptr(np.ascontiguousarray(H.col_idx, dtype=np.int32)),
+            _ptr(np.ascontiguousarray(H.val, dtype=np.float64)))
+
+
+def lanczos(H, colour, sign, c: int, m: int, flags: int = 0, want_q: bool = False):
+    """Projected block-tridiagonal matrix T (n_used x n_used) of colour c, and Q if asked."""
+    colour = np.ascontiguousarray(colour, dtype=np.int32)
+    sign = np.ascontiguousarray(sign, dtype=np.int8)
+    nmax = m * H.b
+    T = np.zeros((nmax, nmax))
+    Q = np.zeros((H.n, nmax)) if want_q else None
+    nb = np.zeros(1, dtype=np.int32)
+    refs = (np.ascontiguousarray(H.row_ptr, dtype=np.int32), np.ascontiguousarray(H.col_idx, dtype=np.int32),
+            np.ascontiguousarray(H.val, dtype=np.float64))
+    _chk(_load().css_ref_lanczos(H.n_brow, H.b, _ptr(refs[0]), _ptr(refs[1]), _ptr(refs[2]), _ptr(colour),
+                                 _ptr(sign), c, m, flags, _ptr(T), _ptr(Q), _ptr(nb)), "lanczos")
+    n = int(nb[0]) * H.b
+    T = T[:n, :n].copy()
+    return (T, Q[:, :n].copy()) if want_q else T
+
+
+def ritz(H, colour, sign, n_colours: int, m: int, flags: int = 0):
+    """Per-colour Ritz values and weights: list of (lam, w) arrays."""
+    colour = np.ascontiguousarray(colour, dtype=np.int32)
+    sign = np.ascontiguousarray(sign, dtype=np.int8)
+    nmax = m * H.b
+    lam = np.zeros((n_colours, nmax)); wgt = np.zeros((n_colours, nmax))
+    nper = np.zeros(n_colours, dtype=np.int32)
+    rp = np.ascontiguousarray(H.row_ptr, dtype=np.int32); ci = np.ascontiguousarray(H.col_idx, dtype=np.int32)
+    vv = np.ascontiguousarray(H.val, dtype=np.float64)
+    _chk(_load().css_ref_ritz(H.n_brow, H.b, _ptr(rp), _ptr(ci), _ptr(vv), _ptr(colour), _ptr(sign),
+                              n_colours, m, flags, _ptr(lam), _ptr(wgt), _ptr(nper)), "ritz")
+    return [(lam[c, :nper[c]].copy(), wgt[c, :nper[c]].copy()) for c in range(n_colours)]
+
+
+def density(H, colour, sign, n_colours: int, *, mu: float = 0.0, kT: float = 0.05, n_elec: float = 0.0,
+            solve_mu: bool = True, m: int = 30, flags: int = SYMMETRIZE, colour_subset=None, P_init=None):
+    """CSS density matrix on H's pattern.
+
+    Returns dict(P=(nnzb, b, b), trP, trPH, mu, n_breakdown)."""
+    colour = np.ascontiguousarray(colour, dtype=np.int32)
+    sign = np.ascontiguousarray(sign, dtype=np.int8)
+    P = np.zeros((H.nnzb, H.b, H.b)) if P_init is None else np.array(P_init, dtype=np.float64, order="C")
+    sub = None if colour_subset is None else np.ascontiguousarray(colour_subset, dtype=np.int32)
+    out = np.zeros(3)
+    nb = np.zeros(1, dtype=np.int32)
+    rp = np.ascontiguousarray(H.row_ptr, dtype=np.int32); ci = np.ascontiguousarray(H.col_idx, dtype=np.int32)
+    vv = np.ascontiguousarray(H.val, dtype=np.float64)
+    st = _load().css_ref_density(
+        H.n_brow, H.b, H.nnzb, _ptr(rp), _ptr(ci), _ptr(vv), _ptr(colour), _ptr(sign), n_colours,
+        mu, kT, n_elec, int(bool(solve_mu)), m, flags, _ptr(sub), 0 if sub is None else sub.shape[0],
+        _ptr(P), _ptr(out[0:1]), _ptr(out[1:2]), _ptr(out[2:3]), _ptr(nb))
+    _chk(st, "density")
+    return {"P": P, "trP": float(out[0]), "trPH": float(out[1]), "mu": float(out[2]),
+            "n_breakdown": int(nb[0])}
+
+
+def num_threads() -> int:
+    return int(_load().css_ref_num_threads())

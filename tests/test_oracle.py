@@ -1,0 +1,414 @@
+"""Pins of the CPU oracle against things other than itself (no GPU needed).
+
+Each test fixes part of the oracle with a published value, a closed form, LAPACK on a dense
+matrix, brute force on a tiny input or an invariant of the method, chosen so that a dropped
+term, a wrong sign or index, or a transposed operand in the oracle fails at least one.
+"""
+import json
+import math
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from paper_2605_20918_gb300 import synth
+from tests.dense_truth import Dense, fermi, probe_matrix, symmetrize
+
+GOLDEN = Path(__file__).resolve().parent / "golden"
+
+
+@pytest.fixture(scope="module")
+def O(oracle_lib):
+    return oracle_lib
+
+
+# ------------------------------------------------------------------ hash and probes
+def test_splitmix64_published_outputs(O):
+    g = json.loads((GOLDEN / "splitmix64.json").read_text())
+    got = [O.hash64(g["seed"], i) for i in range(len(g["outputs"]))]
+    assert got == [int(x) for x in g["outputs"]]
+
+
+def test_probe_signs_and_structure(O):
+    g = synth.water_box(64)
+    col, nc = O.color(g.pos, g.box, 8.0, 1004)
+    b = 6
+    s = O.probes(col, b, 1005)
+    assert set(np.unique(s)) == {-1, 1}
+    frac = (s == -1).mean()
+    assert abs(frac - 0.5) < 4 * math.sqrt(0.25 / s.size)
+    R = probe_matrix(col, s, b, nc)
+    counts = np.bincount(col, minlength=nc)
+    # R_c^T R_c = |c| I and probe blocks of different colours are orthogonal
+    assert np.array_equal(R.T @ R, np.diag(np.repeat(counts, b)).astype(float))
+    # every orbital sits in exactly one probe column
+    assert np.array_equal((R != 0).sum(axis=1), np.ones(64 * b))
+    ones = O.probes(col, b, 1005, flags=O.SIGNS_ONES)
+    assert np.all(ones == 1)
+    assert np.array_equal(O.probes(col, b, 1005), s)
+    assert not np.array_equal(O.probes(col, b, 1006), s)
+
+
+# ------------------------------------------------------------------- colouring
+def _min_image_dist(p, q, L):
+    d = p - q
+    d -= L * np.round(d / L)
+    return float(np.sqrt((d * d).sum()))
+
+
+def test_neighbours_match_float_distances(O):
+    rng = np.random.default_rng(7)
+    L, R = 20.0, 6.5
+    x = rng.uniform(-3, 23, size=(120, 3))
+    ptr, adj = O.neighbours(x, L, R)
+    for i in range(len(x)):
+        mine = set(adj[ptr[i]:ptr[i + 1]].tolist())
+        for j in range(len(x)):
+            if i == j:
+                continue
+            d = _min_image_dist(x[i], x[j], L)
+            if abs(d - R) < 1e-5:
+                continue
+            assert (j in mine) == (d < R), (i, j, d)
+
+
+def test_neighbours_strict_cutoff_fixed_point(O):
+    # exactly R apart (representable in 2^-20 A) is NOT an edge; a hair closer is
+    x = np.array([[1.0, 1.0, 1.0], [9.0, 1.0, 1.0], [1.0, 1.0, 8.999999]])
+    ptr, adj = O.neighbours(x, 100.0, 8.0)
+    assert adj[ptr[0]:ptr[1]].tolist() == [2]
+    # minimum image across the boundary
+    y = np.array([[0.5, 0.5, 0.5], [9.5, 0.5, 0.5]])
+    ptr, adj = O.neighbours(y, 10.0, 1.5)
+    assert adj.tolist() == [1, 0]
+
+
+def _check_greedy(O, ptr, adj, col, seed):
+    n = len(ptr) - 1
+    deg = np.diff(ptr)
+    key = [O.hash64(seed, i) for i in range(n)]
+    prio = lambda v: (int(deg[v]), key[v], -v)  # larger = earlier
+    for v in range(n):
+        nb = adj[ptr[v]:ptr[v + 1]]
+        assert all(col[u] != col[v] for u in nb), "monochromatic edge"
+        higher = [u for u in nb if prio(u) > prio(v)]
+        hc = {int(col[u]) for u in higher}
+        # greedy in priority order <=> every smaller colour is taken by a higher-priority neighbour
+        assert all(c in hc for c in range(int(col[v]))), (v, col[v], hc)
+
+
+def _random_graph(n, p, rng):
+    A = np.triu(rng.random((n, n)) < p, 1)
+    A = A | A.T
+    ptr = np.concatenate([[0], np.cumsum(A.sum(1))]).astype(np.int32)
+    adj = np.concatenate([np.nonzero(A[i])[0] for i in range(n)]).astype(np.int32)
+    return ptr, adj
+
+
+@pytest.mark.parametrize("n,p", [(1, 0.0), (10, 0.0), (30, 0.2), (60, 0.5), (40, 1.0)])
+def test_greedy_colouring_characterisation(O, n, p):
+    rng = np.random.default_rng(n)
+    ptr, adj = _random_graph(n, p, rng)
+    col, nc = O.color_graph(ptr, adj, 1004)
+    assert nc == (col.max() + 1 if n else 0)
+    _check_greedy(O, ptr, adj, col, 1004)
+    if p == 1.0:
+        assert nc == n
+    if p == 0.0:
+        assert nc == 1
+
+
+def test_hand_checked_graphs(O):
+    # star K_{1,5}: hub (degree 5) first -> colour 0, leaves -> colour 1
+    ptr = np.array([0, 5, 6, 7, 8, 9, 10], np.int32)
+    adj = np.array([1, 2, 3, 4, 5, 0, 0, 0, 0, 0], np.int32)
+    col, nc = O.color_graph(ptr, adj, 99)
+    assert col.tolist() == [0, 1, 1, 1, 1, 1] and nc == 2
+    # complete bipartite K_{3,5}: the degree-5 side is coloured first and takes colour 0
+    A = np.zeros((8, 8), bool)
+    A[:3, 3:] = True
+    A = A | A.T
+    ptr = np.concatenate([[0], np.cumsum(A.sum(1))]).astype(np.int32)
+    adj = np.concatenate([np.nonzero(A[i])[0] for i in range(8)]).astype(np.int32)
+    col, nc = O.color_graph(ptr, adj, 5)
+    assert col.tolist() == [0, 0, 0, 1, 1, 1, 1, 1] and nc == 2
+
+
+def test_lattice_colouring_valid_and_greedy(O):
+    g = synth.water_box(216)
+    ptr, adj = O.neighbours(g.pos, g.box, 8.0)
+    col, nc = O.color(g.pos, g.box, 8.0, 1004)
+    _check_greedy(O, ptr, adj, col, 1004)
+    col2, _ = O.color(g.pos, g.box, 8.0, 1004)
+    assert np.array_equal(col, col2)
+
+
+# ------------------------------------------------------------------- eigensolver
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 120])
+def test_eigh_against_lapack(O, n):
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n))
+    A = A + A.T
+    w, U = O.eigh(A)
+    ref = np.linalg.eigvalsh(A)
+    scale = max(1.0, abs(ref).max())
+    assert np.abs(w - ref).max() <= 1e-13 * scale * n
+    assert np.abs(U.T @ U - np.eye(n)).max() <= 1e-13 * n
+    assert np.abs(U @ np.diag(w) @ U.T - A).max() <= 1e-13 * scale * n
+
+
+def test_eigh_degenerate_and_banded(O):
+    # repeated eigenvalues
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+    lam = np.repeat([-3.0, 1.0, 2.5, 7.0], 10)
+    A = (Q * lam) @ Q.T
+    A = 0.5 * (A + A.T)
+    w, U = O.eigh(A)
+    assert np.abs(w - np.sort(lam)).max() < 1e-12
+    assert np.abs(U @ np.diag(w) @ U.T - A).max() < 1e-12
+    # diagonal input (already reduced)
+    d = np.array([3.0, -1.0, 2.0])
+    w, U = O.eigh(np.diag(d))
+    assert np.array_equal(w, np.sort(d))
+
+
+# --------------------------------------------------------------------- Lanczos
+def test_block_lanczos_definition(O):
+    g = synth.water_box(27)
+    H = synth.hamiltonian(g)
+    col, nc = O.color(g.pos, g.box, 6.0, 1004)
+    s = O.probes(col, H.b, 1005)
+    c = int(col[0])
+    m = 5
+    T, Q = O.lanczos(H, col, s, c, m, want_q=True)
+    D = H.dense()
+    n = T.shape[0]
+    assert n == m * H.b
+    assert np.abs(Q.T @ Q - np.eye(n)).max() < 1e-12           # orthonormal basis
+    assert np.abs(Q.T @ D @ Q - T).max() < 1e-11               # projected Hamiltonian
+    R = probe_matrix(col, s, H.b, nc)[:, c * H.b:(c + 1) * H.b]
+    cnt = (col == c).sum()
+    assert np.abs(Q[:, :H.b] - R / math.sqrt(cnt)).max() < 1e-15
+    b = H.b
+    for j in range(m - 1):                                      # block tridiagonal, B_j upper, diag >= 0
+        Bj = T[(j + 1) * b:(j + 2) * b, j * b:(j + 1) * b]
+        assert np.abs(np.tril(Bj, -1)).max() == 0.0
+        assert np.all(np.diag(Bj) > 0)
+        if j + 2 < m:
+            assert np.abs(T[(j + 2) * b:, j * b:(j + 1) * b]).max() == 0.0
+    # span: the Krylov blocks [R, HR, H^2 R, ...] lie in range(Q)
+    K = [R]
+    for _ in range(m - 1):
+        K.append(D @ K[-1])
+    K = np.concatenate(K, axis=1)
+    resid = K - Q @ (Q.T @ K)
+    assert np.linalg.norm(resid) / np.linalg.norm(K) < 1e-9
+
+
+def test_ritz_weights_sum_to_probe_norm(O):
+    g = synth.water_box(64)
+    H = synth.hamiltonian(g)
+    col, nc = O.color(g.pos, g.box, 8.0, 1004)
+    s = O.probes(col, H.b, 1005)
+    rz = O.ritz(H, col, s, nc, m=6)
+    cnt = np.bincount(col, minlength=nc)
+    for c, (lam, w) in enumerate(rz):
+        assert abs(w.sum() - H.b * cnt[c]) < 1e-11 * H.b * cnt[c]
+        assert np.all(np.diff(lam) >= 0)
+
+
+# --------------------------------------------------------------------- density
+def _pattern_err(A, B):
+    return float(np.abs(A - B).max())
+
+
+def test_degenerate_colouring_full_krylov_is_f_of_H(O):
+    """Every molecule its own colour and m b >= N: P equals f(H) on the pattern."""
+    g = synth.water_box(8)
+    H = synth.hamiltonian(g)
+    col, nc = O.color(g.pos, g.box, 100.0, 1004)
+    assert nc == 8
+    s = O.probes(col, H.b, 1005)
+    ne = synth.n_electrons(8)
+    r = O.density(H, col, s, nc, kT=0.05, n_elec=ne, m=8)
+    dn = Dense(H)
+    mu = dn.mu_exact(ne, 0.05)
+    assert _pattern_err(r["P"], dn.on_pattern(dn.f(mu, 0.05))) < 1e-10
+    assert abs(r["trP"] - ne / 2) < 1e-9
+
+
+def test_contaminated_projection_full_krylov(O):
+    """Shared colours and a Krylov space that spans everything: P~ = extract(f(H) R) (Eq. 2)."""
+    g = synth.water_box(12, box=9.0)
+    H = synth.hamiltonian(g, r_cut=5.0)
+    col, nc = O.color(g.pos, g.box, 4.0, 1004)
+    assert nc < 12
+    s = O.probes(col, H.b, 1005)
+    ne = synth.n_electrons(12)
+    dn = Dense(H)
+    R = probe_matrix(col, s, H.b, nc)
+    mu = dn.mu_projected(R, ne, 0.05, nc, H.b)
+    Pt = dn.css_extract(mu, 0.05, col, s, nc)
+    r = O.density(H, col, s, nc, kT=0.05, n_elec=ne, m=12, flags=0)
+    assert _pattern_err(r["P"], Pt) < 1e-10
+    r2 = O.density(H, col, s, nc, kT=0.05, n_elec=ne, m=12)
+    assert _pattern_err(r2["P"], symmetrize(H, Pt)) < 1e-10
+    # symmetrisation leaves the traces unchanged
+    assert abs(r["trP"] - r2["trP"]) < 1e-10 and abs(r["trPH"] - r2["trPH"]) < 1e-9
+    # the traces against the dense truth
+    assert abs(r["trP"] - ne / 2) < 1e-9
+    assert abs(r2["trPH"] - float((Pt * H.val).sum())) < 1e-9
+
+
+def test_fixed_mu_matches_dense(O):
+    g = synth.water_box(12, box=9.0)
+    H = synth.hamiltonian(g, r_cut=5.0)
+    col, nc = O.color(g.pos, g.box, 4.0, 1004)
+    s = O.probes(col, H.b, 1005)
+    dn = Dense(H)
+    for mu, kT in [(-4.0, 0.05), (-10.5, 0.3), (1.7, 0.5)]:
+        r = O.density(H, col, s, nc, mu=mu, kT=kT, solve_mu=False, m=12, flags=0)
+        assert _pattern_err(r["P"], dn.css_extract(mu, kT, col, s, nc)) < 1e-10
+        assert r["mu"] == mu
+
+
+def test_zero_coupling_blocks(O):
+    """Block-diagonal H: P_II = U f(D) U^T exactly and no off-diagonal density."""
+    g = synth.water_box(27)
+    H = synth.hamiltonian(g, coupling=0.0)
+    col, nc = O.color(g.pos, g.box, 6.0, 1004)
+    s = O.probes(col, H.b, 1005)
+    ne = synth.n_electrons(27)
+    r = O.density(H, col, s, nc, kT=0.05, n_elec=ne, m=10)
+    assert r["n_breakdown"] > 0
+    rows = H.rows()
+    for k in range(H.nnzb):
+        I, J = rows[k], H.col_idx[k]
+        if I == J:
+            w, V = np.linalg.eigh(H.val[k])
+            ref = (V * fermi(w, r["mu"], 0.05)) @ V.T
+            assert np.abs(r["P"][k] - ref).max() < 1e-11
+        else:
+            assert np.abs(r["P"][k]).max() < 1e-11
+    assert abs(r["trP"] - ne / 2) < 1e-9
+
+
+def test_single_molecule(O):
+    g = synth.water_box(1)
+    H = synth.hamiltonian(g, "dzp")
+    col = np.zeros(1, np.int32)
+    s = O.probes(col, H.b, 1005)
+    r = O.density(H, col, s, 1, kT=0.05, n_elec=8.0, m=3)
+    w, V = np.linalg.eigh(H.val[0])
+    mu = r["mu"]
+    assert np.abs(r["P"][0] - (V * fermi(w, mu, 0.05)) @ V.T).max() < 1e-11
+    assert abs(r["trP"] - 4.0) < 1e-9
+
+
+def test_two_level_closed_form(O):
+    """b = 1, two coupled sites: f(H) from the closed-form 2x2 eigen-decomposition."""
+    a, d, t = -1.3, 0.4, 0.7
+    H = synth.BSR(n_brow=2, b=1, row_ptr=np.array([0, 2, 4], np.int32), col_idx=np.array([0, 1, 0, 1], np.int32),
+                  val=np.array([a, t, t, d], dtype=float).reshape(4, 1, 1))
+    col = np.array([0, 1], np.int32)
+    s = np.array([1, -1], np.int8)
+    mu, kT = -0.2, 0.25
+    r = O.density(H, col, s, 2, mu=mu, kT=kT, solve_mu=False, m=2)
+    h = math.sqrt(((a - d) / 2) ** 2 + t * t)
+    lp, lm = (a + d) / 2 + h, (a + d) / 2 - h
+    vp = np.array([t, lp - a]); vp /= np.linalg.norm(vp)
+    vm = np.array([t, lm - a]); vm /= np.linalg.norm(vm)
+    fp = 1.0 / (1.0 + math.exp((lp - mu) / kT))
+    fm = 1.0 / (1.0 + math.exp((lm - mu) / kT))
+    F = fp * np.outer(vp, vp) + fm * np.outer(vm, vm)
+    assert np.abs(r["P"].ravel() - F.ravel()).max() < 1e-14
+    assert abs(r["trP"] - (fp + fm)) < 1e-14
+    assert abs(r["trPH"] - (lp * fp + lm * fm)) < 1e-14
+
+
+def test_trace_identity_and_bisection(O):
+    """Tr of the unsymmetrised extraction equals the Ritz quadrature sum_j f w (Eq. 6-7)."""
+    g = synth.water_box(64)
+    H = synth.hamiltonian(g)
+    col, nc = O.color(g.pos, g.box, 8.0, 1004)
+    s = O.probes(col, H.b, 1005)
+    ne = synth.n_electrons(64)
+    r = O.density(H, col, s, nc, kT=0.05, n_elec=ne, m=6, flags=0)
+    rz = O.ritz(H, col, s, nc, m=6)
+    quad = sum(float((fermi(l, r["mu"], 0.05) * w).sum()) for l, w in rz)
+    assert abs(r["trP"] - quad) < 1e-9
+    assert abs(quad - ne / 2) < 1e-6
+
+
+def test_idempotent_as_kT_vanishes(O):
+    g = synth.water_box(8)
+    H = synth.hamiltonian(g)
+    col, nc = O.color(g.pos, g.box, 100.0, 1004)
+    s = O.probes(col, H.b, 1005)
+    r = O.density(H, col, s, nc, kT=1e-3, n_elec=64.0, m=8)
+    dn = Dense(H)
+    P = np.zeros_like(dn.D)
+    b = H.b
+    rows = H.rows()
+    for k in range(H.nnzb):
+        P[rows[k] * b:(rows[k] + 1) * b, H.col_idx[k] * b:(H.col_idx[k] + 1) * b] = r["P"][k]
+    assert H.nnzb == 64  # the tiny box couples every pair: P is the full matrix
+    assert np.abs(P @ P - P).max() < 1e-10
+    assert np.abs(P - P.T).max() == 0.0
+
+
+def test_convergence_in_krylov_depth(O):
+    g = synth.water_box(64)
+    H = synth.hamiltonian(g)
+    col, nc = O.color(g.pos, g.box, 8.0, 1004)
+    s = O.probes(col, H.b, 1005)
+    dn = Dense(H)
+    mu = -4.0
+    ref = dn.css_extract(mu, 0.05, col, s, nc)
+    errs = [_pattern_err(O.density(H, col, s, nc, mu=mu, kT=0.05, solve_mu=False, m=m, flags=0)["P"], ref)
+            for m in (2, 4, 8, 16, 24, 40)]
+    assert all(a > b for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-9
+
+
+def test_decay_with_distance(O):
+    """|P_IJ| decays with the molecule distance (nearsightedness behind Eq. 2)."""
+    g = synth.water_box(216)
+    H = synth.hamiltonian(g)
+    rows = H.rows()
+    dist = np.array([_min_image_dist(g.pos[rows[k]], g.pos[H.col_idx[k]], g.box) for k in range(H.nnzb)])
+    bins = [(2.0, 3.0), (3.0, 4.0), (4.0, 5.0), (5.0, 6.1)]
+    for r_col, stat in [(8.0, np.median), (12.0, np.max)]:
+        # at R_col = 8 A < 2 x 6 A same-colour contamination lifts single far blocks, so the
+        # envelope is taken on the median; at 12 A the maximum itself decays
+        col, nc = O.color(g.pos, g.box, r_col, 1004)
+        s = O.probes(col, H.b, 1005)
+        r = O.density(H, col, s, nc, kT=0.05, n_elec=synth.n_electrons(216), m=10)
+        amax = np.abs(r["P"]).max(axis=(1, 2))
+        env = [stat(amax[(dist >= lo) & (dist < hi)]) for lo, hi in bins]
+        assert all(a > b for a, b in zip(env, env[1:])), (r_col, env)
+
+
+def test_local_reorth_agrees(O):
+    g = synth.water_box(64)
+    H = synth.hamiltonian(g)
+    col, nc = O.color(g.pos, g.box, 8.0, 1004)
+    s = O.probes(col, H.b, 1005)
+    a = O.density(H, col, s, nc, mu=-4.0, solve_mu=False, m=10, flags=0)
+    b = O.density(H, col, s, nc, mu=-4.0, solve_mu=False, m=10, flags=O.REORTH_LOCAL)
+    assert _pattern_err(a["P"], b["P"]) < 1e-9
+
+
+def test_colour_subset_equals_full_columns(O):
+    g = synth.water_box(64)
+    H = synth.hamiltonian(g)
+    col, nc = O.color(g.pos, g.box, 8.0, 1004)
+    s = O.probes(col, H.b, 1005)
+    full = O.density(H, col, s, nc, mu=-4.0, solve_mu=False, m=6, flags=0)
+    sub = [1, 3]
+    part = O.density(H, col, s, nc, mu=-4.0, solve_mu=False, m=6, flags=0, colour_subset=sub,
+                     P_init=np.full((H.nnzb, H.b, H.b), np.nan))
+    sel = np.isin(col[H.col_idx], sub)
+    assert np.array_equal(part["P"][sel], full["P"][sel])
+    assert np.all(np.isnan(part["P"][~sel]))
