@@ -1,0 +1,182 @@
+/*
+ * css.h — C-ABI of the GB300 (sm_103a) chromatic-superposition-state (CSS) density-matrix
+ * library: graph colouring, CSS probe blocks and the block-Lanczos projection that returns
+ * the sparse Kohn-Sham density matrix P = f(H) on H's sparsity pattern.
+ *
+ * Paper: Jiang, Xiao, Tang, Li, Sun, Xia, Ke, "High-performance linear-scaling electronic
+ * structure method via chromatic superposition states" (arXiv 2605.20918).
+ *
+ * Conventions for every entry point
+ *   - Plain C types only.  Array arguments are DEVICE pointers (cudaMalloc'd or from any
+ *     CUDA allocator, e.g. torch) unless a comment says "host".  The caller owns every input
+ *     and output buffer; the library never frees them.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  All device
+ *     work is ordered on it.  Calls that return a scalar through a host pointer synchronise
+ *     that stream before returning; the others are asynchronous unless stated.
+ *   - The context owns device workspace.  It grows on demand (cudaMalloc) and is reused;
+ *     once a call has run with a given shape, repeating it allocates nothing.
+ *   - No C++ exception crosses this interface.  Errors are returned as css_status; a
+ *     CUDA error is reported as CSS_ERR_CUDA and the message is kept for css_last_error().
+ *   - Orthogonal basis: S = I, so H' = H in the paper's Eq. 4.
+ */
+#ifndef CSS_H
+#define CSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CSS_API __attribute__((visibility("default")))
+#else
+#define CSS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CSS_OK = 0,
+  CSS_ERR_INVALID_ARG = 1, /* a size, pointer, flag or value is out of range          */
+  CSS_ERR_NOMEM = 2,       /* device workspace could not be allocated                  */
+  CSS_ERR_CUDA = 3,        /* a CUDA runtime call or kernel failed                      */
+  CSS_ERR_TIMEOUT = 4,     /* a bounded device wait ran out (grid barrier)              */
+  CSS_ERR_NUMERIC = 5,     /* NaN/Inf in the result or a non-convergent eigen-step      */
+  CSS_WARN_BREAKDOWN = 6,  /* some colour's Krylov space became invariant early; result valid */
+  CSS_ERR_UNSUPPORTED = 7  /* a shape the build does not support (b > 32)              */
+} css_status;
+
+typedef enum {
+  CSS_FP64 = 0,       /* everything in FP64                                               */
+  CSS_MIXED_FP32 = 1  /* H*V, Krylov vectors and block products in FP32 (FP32 accumulate); */
+                      /* recurrence coefficients, Cholesky, eigensolve, mu, Z and P in FP64 */
+} css_precision;
+
+/* css_density flags */
+#define CSS_SYMMETRIZE 1u   /* P = (P~ + P~^T)/2 on the pattern (default in the Python binding)   */
+#define CSS_TWO_PASS 2u     /* regenerate the Krylov basis instead of storing its sampled rows  */
+#define CSS_REORTH_LOCAL 4u /* one more orthogonalisation pass of each new block against Q_j, Q_j-1 */
+#define CSS_HOST_IO 8u      /* css_pbuild only: every array argument is HOST memory            */
+/* css_probes flags */
+#define CSS_SIGNS_ONES 1u   /* all probe entries +1 instead of seeded random signs             */
+
+typedef struct css_ctx css_ctx;
+
+/* Molecule centres in a periodic cubic box.  xyz: n_mol x 3 doubles (Angstrom). */
+typedef struct {
+  int32_t n_mol;
+  const double* xyz;
+  double box;
+} css_geom;
+
+/* Symmetric block-sparse-row matrix with b x b blocks (b <= 32).
+ * row_ptr[n_brow+1], col_idx[nnzb] (sorted within a row, diagonal present, pattern
+ * structurally symmetric), val[nnzb*b*b] row-major inside each block, FP64. */
+typedef struct {
+  int32_t n_brow, b, nnzb;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const double* val;
+} css_bsr;
+
+/* Fermi-Dirac occupation f(x) = 1/(1+exp((x-mu)/kT)) (paper, Eq. 1); kT = 0 is the step
+ * function.  solve_mu != 0: mu is found by bisection so that the Ritz quadrature of Tr P
+ * equals n_elec/2 (P per spin); otherwise `mu` is used as given. */
+typedef struct {
+  double mu, kT, n_elec;
+  int32_t solve_mu;
+} css_fermi;
+
+/* Per-call diagnostics (host struct filled by css_get_info). */
+typedef struct {
+  int32_t n_colours, n_pairs, n_breakdown, m;
+  int64_t workspace_bytes;
+  double ms_color, ms_probes, ms_setup, ms_lanczos, ms_spmm, ms_eigen, ms_mu, ms_extract, ms_total;
+  int64_t spmm_launches; /* H*V launches of the last css_density call                       */
+  double spmm_flops;     /* algorithmic flops of one H*V launch: 2 nnzb b^2 w               */
+  double spmm_bytes;     /* algorithmic bytes of one H*V launch: H once, V in, W out        */
+} css_info;
+
+/* ------------------------------------------------------------------ context */
+/* Create a context bound to CUDA device `device`.  *ctx receives the handle. */
+CSS_API css_status css_create(css_ctx** ctx, int device);
+/* Free the context and its workspace (synchronises the device first). */
+CSS_API void css_destroy(css_ctx* ctx);
+/* Static string for a status code. */
+CSS_API const char* css_status_str(css_status s);
+/* Message of the last CUDA/argument error seen by this context ("" if none). */
+CSS_API const char* css_last_error(const css_ctx* ctx);
+/* Diagnostics of the last call (host pointer).  Phase times are taken with CUDA events
+ * only when the environment variable CSS_TIMING=1 was set at css_create. */
+CSS_API css_status css_get_info(const css_ctx* ctx, css_info* info);
+
+/* ---------------------------------------------------------------- colouring */
+/* Greedy multicolouring of molecules (paper: CSS construction paragraph after Eq. 2; greedy
+ * order after Welsh-Powell): molecules whose minimum-image centre distance is < r_col get
+ * different colours.  Distances are exact: coordinates are rounded to int64 multiples of
+ * 2^-20 A (llrint(x*2^20)) and compared as squared integers, strictly below
+ * llrint(r_col*2^20)^2.  The order is degree descending, then SplitMix64(seed, id)
+ * descending, then id ascending; each molecule takes the smallest colour not used by a
+ * neighbour earlier in that order (Jones-Plassmann rounds on the GPU give exactly that
+ * colouring).
+ *   geom      host struct; geom->xyz is a DEVICE array of n_mol*3 doubles
+ *   colour    device int32[n_mol], written
+ *   n_colours host int32*, written (the call synchronises `stream`)
+ * Errors: INVALID_ARG for n_mol < 1, box <= 0, r_col < 0 or box > 1000 A. */
+CSS_API css_status css_color(css_ctx* ctx, const css_geom* geom, double r_col, uint64_t seed, int32_t* colour,
+                     int32_t* n_colours, void* stream);
+
+/* Same colouring rule on an explicit graph: device CSR adj_ptr[n+1], adj[adj_ptr[n]]
+ * (symmetric, no self loops; neighbour order irrelevant). */
+CSS_API css_status css_color_graph(css_ctx* ctx, int32_t n, const int32_t* adj_ptr, const int32_t* adj, uint64_t seed,
+                           int32_t* colour, int32_t* n_colours, void* stream);
+
+/* ------------------------------------------------------------------- probes */
+/* CSS probe signs (paper: same paragraph, Fig. 1c): column k of colour c's probe block holds
+ * sign[J*b+k] = +-1 on orbital k of every molecule J of colour c, 0 elsewhere.  sign is -1
+ * exactly when bit 0 of SplitMix64(sign_seed, J*b+k) is set (all +1 with CSS_SIGNS_ONES).
+ *   colour  device int32[n_mol] (not read; the probes are implicit in colour + sign)
+ *   sign    device int8[n_mol*b], written.  Asynchronous. */
+CSS_API css_status css_probes(css_ctx* ctx, const int32_t* colour, int32_t n_mol, int32_t b, uint64_t sign_seed,
+                      uint32_t flags, int8_t* sign, void* stream);
+
+/* ------------------------------------------------------------------ density */
+/* CSS density matrix (paper, Eq. 2 and Eq. 5-7): for every colour c a block-Lanczos
+ * recurrence of depth m on R_c (block width b), the projected block-tridiagonal matrix
+ * diagonalised exactly in FP64, f applied to its eigenvalues, and
+ *   P~_IJ = [Q_c Z_c]_I diag(s_J),  c = colour(J),  Z_c = U f(Lambda) U^T E_1 B_0
+ * written on H's pattern only; P = (P~ + P~^T)/2 with CSS_SYMMETRIZE.
+ *   H          host struct of device arrays (see css_bsr)
+ *   colour     device int32[n_brow] in [0, n_colours)
+ *   sign       device int8[n_brow*b] (from css_probes)
+ *   fermi      host struct
+ *   m          Lanczos block steps (projected matrix of size m*b per colour), 1 <= m, m*b <= 4096
+ *   P_val      device double[nnzb*b*b], written (same block order as H->val)
+ *   trP, trPH, mu_out   host doubles, written (Tr P, Tr(P H), chemical potential); may be NULL
+ * Returns CSS_WARN_BREAKDOWN when a colour's recurrence stopped early (invariant Krylov
+ * space: the result is exact for that colour).  Synchronises `stream`. */
+CSS_API css_status css_density(css_ctx* ctx, const css_bsr* H, const int32_t* colour, const int8_t* sign, int32_t n_colours,
+                       const css_fermi* fermi, int32_t m, css_precision prec, uint32_t flags, double* P_val,
+                       double* trP, double* trPH, double* mu_out, void* stream);
+
+/* Many independent systems in one call (MD snapshots of uneven size).  Arrays of n_sys
+ * host structs / host arrays of device pointers; mu is solved per system (fermi[s]).
+ * Outputs per system: P_val[s] (device), trP[s], trPH[s], mu_out[s] (host arrays). */
+CSS_API css_status css_density_batch(css_ctx* ctx, int32_t n_sys, const css_bsr* H, const int32_t* const* colour,
+                             const int8_t* const* sign, const int32_t* n_colours, const css_fermi* fermi, int32_t m,
+                             css_precision prec, uint32_t flags, double* const* P_val, double* trP, double* trPH,
+                             double* mu_out, void* stream);
+
+/* One whole P build from a geometry and H: css_color + css_probes + css_density.  With
+ * CSS_HOST_IO every array (geom->xyz, H arrays, P_val) is HOST memory and the library copies
+ * in and out on `stream`; otherwise they are device arrays.  colour_out (n_mol int32,
+ * same memory kind) may be NULL. */
+CSS_API css_status css_pbuild(css_ctx* ctx, const css_geom* geom, const css_bsr* H, double r_col, uint64_t colour_seed,
+                      uint64_t sign_seed, const css_fermi* fermi, int32_t m, css_precision prec, uint32_t flags,
+                      double* P_val, int32_t* colour_out, int32_t* n_colours, double* trP, double* trPH,
+                      double* mu_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSS_H */

@@ -1,0 +1,905 @@
+// CSS density matrix on H's pattern (paper, Eq. 2 and Eq. 5-7): set-up of the sampled
+// (row, colour) pairs, the block-Lanczos passes, the eigensolve, the chemical potential, the
+// reconstruction X_c = Q_c Z_c on the sampled rows and the extraction
+//     P~_IJ = X_{c(J)}[I] diag(s_J),  P = (P~ + P~^T) / 2,  Tr P,  Tr(P H).
+//
+// "Pairs": for every block row I the distinct colours of its pattern columns.  X is needed
+// exactly on those (I, c) pairs; they are stored sorted by colour, so the pairs of a colour
+// batch are one contiguous range.
+#include <cmath>
+
+#include "css_eigen.cuh"
+#include "css_lanczos.cuh"
+
+css_status css_scan_i32(css_ctx* ctx, const int32_t* in, int32_t* out, int64_t n, cudaStream_t st, int depth = 0);
+
+namespace {
+
+constexpr int ERR_PATTERN = 1;     // pattern not structurally symmetric / diagonal missing
+constexpr int ERR_COLOUR = 2;      // colour out of range
+
+// ----------------------------------------------------------------------- set-up
+__global__ void k_concat_rowptr(int32_t n, const int32_t* __restrict__ src, int32_t row_off, int32_t blk_off,
+                                int32_t* __restrict__ dst) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= n) dst[row_off + i] = src[i] + blk_off;
+}
+
+__global__ void k_offset_i32(int64_t n, const int32_t* __restrict__ src, int32_t off, int32_t* __restrict__ dst) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i] + off;
+}
+
+__global__ void k_rows(int32_t n_brow, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                       const int32_t* __restrict__ colour, int32_t n_col, int32_t* __restrict__ brow,
+                       int32_t* __restrict__ trans, int32_t* __restrict__ cnt, int32_t* __restrict__ maxrow,
+                       int32_t* __restrict__ err) {
+  int32_t I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n_brow) return;
+  const int32_t s = row_ptr[I], e = row_ptr[I + 1];
+  atomicMax(maxrow, e - s);
+  const int32_t cI = colour[I];
+  if (cI < 0 || cI >= n_col) atomicOr(err, ERR_COLOUR);
+  else atomicAdd(&cnt[cI], 1);
+  bool diag = false;
+  for (int32_t k = s; k < e; ++k) {
+    brow[k] = I;
+    const int32_t J = col_idx[k];
+    if (J == I) diag = true;
+    if (J < 0 || J >= n_brow) {
+      atomicOr(err, ERR_PATTERN);
+      trans[k] = k;
+      continue;
+    }
+    // binary search for column I in row J
+    int32_t lo = row_ptr[J], hi = row_ptr[J + 1] - 1, f = -1;
+    while (lo <= hi) {
+      int32_t mid = (lo + hi) >> 1, v = col_idx[mid];
+      if (v == I) {
+        f = mid;
+        break;
+      }
+      if (v < I) lo = mid + 1;
+      else hi = mid - 1;
+    }
+    if (f < 0) {
+      atomicOr(err, ERR_PATTERN);
+      f = k;
+    }
+    trans[k] = f;
+  }
+  if (!diag) atomicOr(err, ERR_PATTERN);
+}
+
+// empty colours are finished from the start (no blocks, no Ritz pairs)
+__global__ void k_inv_sqrt(int32_t n_col, const int32_t* __restrict__ cnt, double* __restrict__ isq,
+                           int32_t* __restrict__ nblk, int32_t* __restrict__ done, int32_t m) {
+  int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_col) return;
+  isq[c] = cnt[c] > 0 ? 1.0 / sqrt((double)cnt[c]) : 0.0;
+  nblk[c] = cnt[c] > 0 ? m : 0;
+  done[c] = cnt[c] > 0 ? 0 : 1;
+}
+
+// distinct colours among row I's pattern columns
+__global__ void k_pair_count(int32_t n_brow, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                             const int32_t* __restrict__ colour, int32_t* __restrict__ pcount) {
+  int32_t I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n_brow) return;
+  const int32_t s = row_ptr[I], e = row_ptr[I + 1];
+  int32_t n = 0;
+  for (int32_t k = s; k < e; ++k) {
+    const int32_t c = colour[col_idx[k]];
+    bool seen = false;
+    for (int32_t k2 = s; k2 < k; ++k2)
+      if (colour[col_idx[k2]] == c) {
+        seen = true;
+        break;
+      }
+    n += !seen;
+  }
+  pcount[I] = n;
+}
+
+__global__ void k_pair_fill(int32_t n_brow, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                            const int32_t* __restrict__ colour, const int32_t* __restrict__ pstart,
+                            int32_t* __restrict__ pr_c, int32_t* __restrict__ bpr, int32_t* __restrict__ ccount) {
+  int32_t I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n_brow) return;
+  const int32_t s = row_ptr[I], e = row_ptr[I + 1];
+  int32_t n = 0;
+  const int32_t base = pstart[I];
+  for (int32_t k = s; k < e; ++k) {
+    const int32_t c = colour[col_idx[k]];
+    int32_t found = -1;
+    for (int32_t t = 0; t < n; ++t)
+      if (pr_c[base + t] == c) {
+        found = t;
+        break;
+      }
+    if (found < 0) {
+      found = n++;
+      pr_c[base + found] = c;
+      atomicAdd(&ccount[c], 1);
+    }
+    bpr[k] = base + found;
+  }
+}
+
+// row-grouped pair q -> colour-sorted slot (order inside a colour is by arrival)
+__global__ void k_pair_place(int32_t n_brow, const int32_t* __restrict__ pstart, const int32_t* __restrict__ pr_c,
+                             const int32_t* __restrict__ coff, int32_t* __restrict__ cfill, int32_t* __restrict__ perm,
+                             int32_t* __restrict__ pair_I, int32_t* __restrict__ pair_c) {
+  int32_t I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n_brow) return;
+  for (int32_t q = pstart[I]; q < pstart[I + 1]; ++q) {
+    const int32_t c = pr_c[q];
+    const int32_t pos = coff[c] + atomicAdd(&cfill[c], 1);
+    perm[q] = pos;
+    pair_I[pos] = I;
+    pair_c[pos] = c;
+  }
+}
+
+__global__ void k_pob(int32_t nnzb, const int32_t* __restrict__ bpr, const int32_t* __restrict__ perm,
+                      int32_t* __restrict__ pob) {
+  int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nnzb) pob[k] = perm[bpr[k]];
+}
+
+__global__ void k_to_f32(int64_t n, const double* __restrict__ src, float* __restrict__ dst) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (float)src[i];
+}
+
+// ----------------------------------------------------------- chemical potential
+// Bounded grid barrier (generation counter): every wait gives up after ~2^24 polls, sets
+// *err and returns false, so the kernel always terminates.
+__device__ bool grid_sync(unsigned* count, unsigned* gen, unsigned nb, int32_t* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vg = gen;
+    const unsigned g = *vg;
+    __threadfence();
+    const unsigned arrived = atomicAdd(count, 1u) + 1u;
+    ok = 1;
+    if (arrived == nb) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vg == g) {
+        if (++spins > (1ll << 24) || *(volatile int32_t*)err) {
+          atomicOr(err, 4);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+constexpr int MU_T = 256;
+constexpr int MU_MAXSYS = 1024;
+
+// Bisection of g_s(mu) = sum_{c in s} sum_k f(lam_ck; mu) w_ck - N_e,s / 2 for every system
+// s at once (one persistent cooperative launch).  Each CTA sums a fixed range of colours in
+// a fixed order; all CTAs then reduce the per-CTA partials in the same order, so every CTA
+// holds identical brackets and the result is deterministic.
+__global__ void __launch_bounds__(MU_T) k_mu(int32_t n_sys, int32_t n_col, int32_t nmax, const int32_t* __restrict__ nblk,
+                                             int32_t b, const int32_t* __restrict__ sys_of_colour,
+                                             const double* __restrict__ lam, const double* __restrict__ wgt,
+                                             const double* __restrict__ kT, const double* __restrict__ half_ne,
+                                             const int32_t* __restrict__ solve, const double* __restrict__ mu_in,
+                                             double* __restrict__ mu_out, double* __restrict__ part,
+                                             unsigned* __restrict__ bar, int32_t* __restrict__ err) {
+  __shared__ double acc[MU_MAXSYS];
+  __shared__ double lo[MU_MAXSYS], hi[MU_MAXSYS];
+  __shared__ int conv[MU_MAXSYS];
+  __shared__ double red[MU_T / 32];
+  __shared__ int all_done;
+  const unsigned G = gridDim.x;
+  const int32_t per = (int32_t)((n_col + G - 1) / G);
+  const int32_t c0 = blockIdx.x * per, c1 = min(n_col, c0 + per);
+  double* pbuf[2] = {part, part + (size_t)2 * n_sys * G};
+  // phase 0: spectrum bounds per system
+  for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) {
+    lo[s] = 1e300;
+    hi[s] = -1e300;
+  }
+  __syncthreads();
+  for (int32_t c = c0; c < c1; ++c) {
+    const int32_t n = nblk[c] * b;
+    double mn = 1e300, mx = -1e300;
+    for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
+      const double x = lam[(size_t)c * nmax + k];
+      mn = fmin(mn, x);
+      mx = fmax(mx, x);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 1e300;
+      for (int i = 0; i < MU_T / 32; ++i) t = fmin(t, red[i]);
+      lo[sys_of_colour[c]] = fmin(lo[sys_of_colour[c]], t);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = -1e300;
+      for (int i = 0; i < MU_T / 32; ++i) t = fmax(t, red[i]);
+      hi[sys_of_colour[c]] = fmax(hi[sys_of_colour[c]], t);
+    }
+    __syncthreads();
+  }
+  for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) {
+    pbuf[0][(size_t)s * G + blockIdx.x] = lo[s];
+    pbuf[0][(size_t)(n_sys + s) * G + blockIdx.x] = hi[s];
+  }
+  if (!grid_sync(bar, bar + 1, G, err)) return;
+  for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) {
+    double a = 1e300, z = -1e300;
+    for (unsigned g = 0; g < G; ++g) {
+      a = fmin(a, __ldcg(&pbuf[0][(size_t)s * G + g]));
+      z = fmax(z, __ldcg(&pbuf[0][(size_t)(n_sys + s) * G + g]));
+    }
+    lo[s] = a - 1.0;
+    hi[s] = z + 1.0;
+    conv[s] = solve[s] ? 0 : 1;
+  }
+  __syncthreads();
+  for (int it = 0; it < 200; ++it) {
+    for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) acc[s] = 0.0;
+    __syncthreads();
+    for (int32_t c = c0; c < c1; ++c) {
+      const int32_t s = sys_of_colour[c];
+      if (conv[s]) continue;
+      const double mid = 0.5 * (lo[s] + hi[s]);
+      const double t_ = kT[s];
+      const int32_t n = nblk[c] * b;
+      double v = 0.0;
+      for (int32_t k = threadIdx.x; k < n; k += blockDim.x)
+        v += css_fermi_dirac(lam[(size_t)c * nmax + k], mid, t_) * wgt[(size_t)c * nmax + k];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < MU_T / 32; ++i) t += red[i];
+        acc[s] += t;
+      }
+      __syncthreads();
+    }
+    double* pb = pbuf[(it + 1) & 1];
+    for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) pb[(size_t)s * G + blockIdx.x] = acc[s];
+    if (!grid_sync(bar, bar + 1, G, err)) return;
+    if (threadIdx.x == 0) all_done = 1;
+    __syncthreads();
+    for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) {
+      if (conv[s]) continue;
+      double g = 0.0;
+      for (unsigned q = 0; q < G; ++q) g += __ldcg(&pb[(size_t)s * G + q]);
+      g -= half_ne[s];
+      const double mid = 0.5 * (lo[s] + hi[s]);
+      if (g > 0.0) hi[s] = mid;
+      else lo[s] = mid;
+      if (hi[s] - lo[s] <= 1e-13 * fmax(1.0, fabs(mid))) conv[s] = 1;
+      else all_done = 0;
+    }
+    __syncthreads();
+    if (all_done) break;
+  }
+  if (blockIdx.x == 0)
+    for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) mu_out[s] = solve[s] ? 0.5 * (lo[s] + hi[s]) : mu_in[s];
+}
+
+// --------------------------------------------------------- reconstruction on pairs
+__global__ void k_zsplit(int64_t n, const double* __restrict__ Z, float* __restrict__ zh, float* __restrict__ zl) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double z = Z[i];
+  const float h = (float)z;
+  zh[i] = h;
+  zl[i] = (float)(z - (double)h);
+}
+
+// X[p][a][kk] = sum_j sum_l Qs[p][j][a][l] Z_c[j b + l][kk]; FP64 rows, or FP32 rows with a
+// two-term FP32 split of Z and FP64 accumulation over the blocks j
+template <typename T>
+__global__ void k_xcompute(int64_t n_pairs, int32_t b, int32_t m, int32_t nmax, const int32_t* __restrict__ pair_c,
+                           const int32_t* __restrict__ nblk, const T* __restrict__ Qs, const double* __restrict__ Z,
+                           const float* __restrict__ zh, const float* __restrict__ zl, double* __restrict__ X) {
+  const int32_t bb = b * b;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t p = t / bb;
+  if (p >= n_pairs) return;
+  const int32_t e = (int32_t)(t % bb), a = e / b, kk = e % b;
+  const int32_t c = pair_c[p];
+  const int32_t nb = nblk[c];
+  const T* q = Qs + (size_t)p * m * bb + (size_t)a * b;
+  double acc = 0.0;
+  if (sizeof(T) == 8) {
+    const double* z = Z + (size_t)c * nmax * b + kk;
+    for (int32_t j = 0; j < nb; ++j)
+      for (int32_t l = 0; l < b; ++l) acc = fma((double)q[(size_t)j * bb + l], z[(size_t)(j * b + l) * b], acc);
+  } else {
+    const float* h = zh + (size_t)c * nmax * b + kk;
+    const float* lw = zl + (size_t)c * nmax * b + kk;
+    for (int32_t j = 0; j < nb; ++j) {
+      float sh = 0.f, sl = 0.f;
+      for (int32_t l = 0; l < b; ++l) {
+        const float qv = (float)q[(size_t)j * bb + l];
+        sh = fmaf(qv, h[(size_t)(j * b + l) * b], sh);
+        sl = fmaf(qv, lw[(size_t)(j * b + l) * b], sl);
+      }
+      acc += (double)sh + (double)sl;
+    }
+  }
+  X[(size_t)p * bb + e] = acc;
+}
+
+// P_val and trace partials of one system's blocks [k0, k1)
+constexpr int EX_T = 256;
+__global__ void __launch_bounds__(EX_T) k_extract(int32_t k0, int32_t k1, int32_t b, int32_t blk_off,
+                                                  const int32_t* __restrict__ brow, const int32_t* __restrict__ col_idx,
+                                                  const int32_t* __restrict__ trans, const int32_t* __restrict__ pob,
+                                                  const int8_t* __restrict__ sign, const double* __restrict__ X,
+                                                  const double* __restrict__ Hval, int sym, double* __restrict__ P,
+                                                  double* __restrict__ part) {
+  __shared__ double r1[EX_T / 32], r2[EX_T / 32];
+  const int32_t bb = b * b;
+  const int64_t t = (int64_t)k0 * bb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double tp = 0.0, tph = 0.0;
+  if (t < (int64_t)k1 * bb) {
+    const int32_t k = (int32_t)(t / bb), e = (int32_t)(t % bb), a = e / b, kk = e % b;
+    const int32_t I = brow[k], J = col_idx[k];
+    double v = X[(size_t)pob[k] * bb + e] * (double)sign[(size_t)J * b + kk];
+    if (sym) {
+      const int32_t kt = trans[k];
+      const double w = X[(size_t)pob[kt] * bb + kk * b + a] * (double)sign[(size_t)I * b + a];
+      v = 0.5 * (v + w);
+    }
+    P[(size_t)(k - blk_off) * bb + e] = v;
+    if (I == J && a == kk) tp = v;
+    tph = v * Hval[(size_t)k * bb + e];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    tp += __shfl_xor_sync(0xffffffffu, tp, o);
+    tph += __shfl_xor_sync(0xffffffffu, tph, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    r1[threadIdx.x >> 5] = tp;
+    r2[threadIdx.x >> 5] = tph;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, z = 0.0;
+    for (int i = 0; i < EX_T / 32; ++i) {
+      a += r1[i];
+      z += r2[i];
+    }
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = z;
+  }
+}
+
+__global__ void k_trace_sum(int32_t nparts, const double* __restrict__ part, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double a = 0.0, z = 0.0;
+    for (int32_t i = 0; i < nparts; ++i) {
+      a += part[2 * i];
+      z += part[2 * i + 1];
+    }
+    out[0] = a;
+    out[1] = z;
+  }
+}
+
+__global__ void k_count_breakdown(int32_t n_col, int32_t m, const int32_t* __restrict__ nblk,
+                                  const int32_t* __restrict__ cnt, int32_t* __restrict__ out) {
+  int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n_col && cnt[c] > 0 && nblk[c] < m) atomicAdd(out, 1);
+}
+
+template <typename Tp>
+css_status ws_get(css_ctx* ctx, const char* name, size_t count, Tp** p) {
+  return css_ws(ctx, name, count * sizeof(Tp), (void**)p);
+}
+
+struct Timer {
+  css_ctx* ctx;
+  cudaStream_t st;
+  cudaEvent_t ev[16];
+  int n = 0;
+  bool on;
+  Timer(css_ctx* c, cudaStream_t s) : ctx(c), st(s), on(c->timing) {}
+  void mark() {
+    if (!on || n >= 16) return;
+    cudaEventCreate(&ev[n]);
+    cudaEventRecord(ev[n], st);
+    ++n;
+  }
+  double ms(int a, int b) {
+    float t = 0.f;
+    if (on && a < n && b < n) cudaEventElapsedTime(&t, ev[a], ev[b]);
+    return t;
+  }
+  ~Timer() {
+    for (int i = 0; i < n; ++i) cudaEventDestroy(ev[i]);
+  }
+};
+
+}  // namespace
+
+css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys, int32_t m, css_precision prec,
+                            uint32_t flags, double* trP, double* trPH, double* mu_out, cudaStream_t st) {
+  // ------------------------------------------------------------ validation
+  if (n_sys < 1 || n_sys > MU_MAXSYS) return css_set_arg_error(ctx, "css_density: n_sys out of range");
+  if (prec != CSS_FP64 && prec != CSS_MIXED_FP32) return css_set_arg_error(ctx, "css_density: unknown precision");
+  if (flags & ~(CSS_SYMMETRIZE | CSS_TWO_PASS | CSS_REORTH_LOCAL))
+    return css_set_arg_error(ctx, "css_density: unknown flag");
+  const int32_t b = sys[0].H.b;
+  if (b < 1) return css_set_arg_error(ctx, "css_density: b < 1");
+  if (b > CSS_MAX_B) {
+    ctx->last_error = "css_density: b > 32 is not supported";
+    return CSS_ERR_UNSUPPORTED;
+  }
+  if (m < 1 || (int64_t)m * b > 4096) return css_set_arg_error(ctx, "css_density: need 1 <= m and m*b <= 4096");
+  int64_t nb_tot = 0, nnz_tot = 0, nc_tot = 0;
+  for (int32_t s = 0; s < n_sys; ++s) {
+    const css_sys_desc& d = sys[s];
+    if (d.H.b != b) return css_set_arg_error(ctx, "css_density_batch: all systems need the same b");
+    if (d.H.n_brow < 1 || d.H.nnzb < d.H.n_brow || !d.H.row_ptr || !d.H.col_idx || !d.H.val || !d.colour ||
+        !d.sign || !d.P_val || d.n_colours < 1)
+      return css_set_arg_error(ctx, "css_density: bad H, colour, sign or P_val argument");
+    if (!(d.fermi.kT >= 0.0) || !std::isfinite(d.fermi.kT) || !std::isfinite(d.fermi.mu) ||
+        !std::isfinite(d.fermi.n_elec))
+      return css_set_arg_error(ctx, "css_density: kT must be finite and >= 0, mu and n_elec finite");
+    nb_tot += d.H.n_brow;
+    nnz_tot += d.H.nnzb;
+    nc_tot += d.n_colours;
+  }
+  if (nb_tot > (1ll << 30) || nnz_tot > (1ll << 30) || nc_tot > (1 << 24) || nnz_tot * b * b > (1ll << 40))
+    return css_set_arg_error(ctx, "css_density: problem too large for 32-bit block indices");
+  const int32_t n_brow = (int32_t)nb_tot, nnzb = (int32_t)nnz_tot, n_col = (int32_t)nc_tot;
+  const int64_t N = (int64_t)n_brow * b;
+  const int32_t bb = b * b, nmax = m * b;
+  const bool f32 = prec == CSS_MIXED_FP32;
+  const bool two_pass = (flags & CSS_TWO_PASS) != 0;
+  const int T = 256;
+  Timer tm(ctx, st);
+  tm.mark();  // 0
+
+  // -------------------------------------------------- combined system (batch)
+  const int32_t *row_ptr, *col_idx, *colour;
+  const int8_t* sign;
+  const double* Hval;
+  double* Pout;
+  int32_t *sys_of_colour, *row_off_dev;
+  std::vector<int32_t> row_off(n_sys + 1), blk_off(n_sys + 1), col_off(n_sys + 1);
+  row_off[0] = blk_off[0] = col_off[0] = 0;
+  for (int32_t s = 0; s < n_sys; ++s) {
+    row_off[s + 1] = row_off[s] + sys[s].H.n_brow;
+    blk_off[s + 1] = blk_off[s] + sys[s].H.nnzb;
+    col_off[s + 1] = col_off[s] + sys[s].n_colours;
+  }
+  CSS_TRY(ws_get(ctx, "sys_of_colour", n_col, &sys_of_colour));
+  CSS_TRY(ws_get(ctx, "row_off", n_sys + 1, &row_off_dev));
+  {
+    std::vector<int32_t> soc(n_col);
+    for (int32_t s = 0; s < n_sys; ++s)
+      for (int32_t c = col_off[s]; c < col_off[s + 1]; ++c) soc[c] = s;
+    int32_t* hp;
+    CSS_TRY(css_pinned(ctx, sizeof(int32_t) * (n_col + n_sys + 1) + 256, (void**)&hp));
+    memcpy(hp, soc.data(), sizeof(int32_t) * n_col);
+    CSS_CU(ctx, cudaMemcpyAsync(sys_of_colour, hp, sizeof(int32_t) * n_col, cudaMemcpyHostToDevice, st));
+    CSS_CU(ctx, cudaStreamSynchronize(st));
+  }
+  if (n_sys == 1) {
+    row_ptr = sys[0].H.row_ptr;
+    col_idx = sys[0].H.col_idx;
+    colour = sys[0].colour;
+    sign = sys[0].sign;
+    Hval = sys[0].H.val;
+    Pout = sys[0].P_val;
+  } else {
+    int32_t *rp, *ci, *co;
+    int8_t* sg;
+    double* hv;
+    CSS_TRY(ws_get(ctx, "b_rowptr", n_brow + 1, &rp));
+    CSS_TRY(ws_get(ctx, "b_colidx", nnzb, &ci));
+    CSS_TRY(ws_get(ctx, "b_colour", n_brow, &co));
+    CSS_TRY(ws_get(ctx, "b_sign", N, &sg));
+    CSS_TRY(ws_get(ctx, "b_hval", (size_t)nnzb * bb, &hv));
+    for (int32_t s = 0; s < n_sys; ++s) {
+      const css_sys_desc& d = sys[s];
+      k_concat_rowptr<<<(unsigned)css_ceil_div(d.H.n_brow + 1, T), T, 0, st>>>(d.H.n_brow, d.H.row_ptr, row_off[s],
+                                                                                blk_off[s], rp);
+      CSS_LAUNCHED(ctx);
+      k_offset_i32<<<(unsigned)css_ceil_div(d.H.nnzb, T), T, 0, st>>>(d.H.nnzb, d.H.col_idx, row_off[s],
+                                                                       ci + blk_off[s]);
+      CSS_LAUNCHED(ctx);
+      k_offset_i32<<<(unsigned)css_ceil_div(d.H.n_brow, T), T, 0, st>>>(d.H.n_brow, d.colour, col_off[s],
+                                                                         co + row_off[s]);
+      CSS_LAUNCHED(ctx);
+      CSS_CU(ctx, cudaMemcpyAsync(sg + (size_t)row_off[s] * b, d.sign, (size_t)d.H.n_brow * b, cudaMemcpyDeviceToDevice,
+                                  st));
+      CSS_CU(ctx, cudaMemcpyAsync(hv + (size_t)blk_off[s] * bb, d.H.val, (size_t)d.H.nnzb * bb * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, st));
+    }
+    row_ptr = rp;
+    col_idx = ci;
+    colour = co;
+    sign = sg;
+    Hval = hv;
+    Pout = nullptr;  // each system's blocks are written straight into its own P_val
+  }
+
+  // ------------------------------------------------------------------ set-up
+  int32_t *brow, *trans, *cnt, *nblk, *done, *misc, *pcount, *pstart, *bpr, *pr_c, *ccount, *coff, *cfill;
+  double* isq;
+  CSS_TRY(ws_get(ctx, "brow", nnzb, &brow));
+  CSS_TRY(ws_get(ctx, "trans", nnzb, &trans));
+  CSS_TRY(ws_get(ctx, "cnt", n_col, &cnt));
+  CSS_TRY(ws_get(ctx, "nblk", n_col, &nblk));
+  CSS_TRY(ws_get(ctx, "done", n_col, &done));
+  CSS_TRY(ws_get(ctx, "isq", n_col, &isq));
+  CSS_TRY(ws_get(ctx, "misc", 64, &misc));
+  CSS_TRY(ws_get(ctx, "pcount", n_brow + 1, &pcount));
+  CSS_TRY(ws_get(ctx, "pstart", n_brow + 1, &pstart));
+  CSS_TRY(ws_get(ctx, "bpr", nnzb, &bpr));
+  CSS_TRY(ws_get(ctx, "ccount", n_col + 1, &ccount));
+  CSS_TRY(ws_get(ctx, "coff", n_col + 1, &coff));
+  CSS_TRY(ws_get(ctx, "cfill", n_col + 1, &cfill));
+  CSS_CU(ctx, cudaMemsetAsync(misc, 0, 64 * sizeof(int32_t), st));
+  CSS_CU(ctx, cudaMemsetAsync(cnt, 0, n_col * sizeof(int32_t), st));
+  CSS_CU(ctx, cudaMemsetAsync(done, 0, n_col * sizeof(int32_t), st));
+  CSS_CU(ctx, cudaMemsetAsync(ccount, 0, (n_col + 1) * sizeof(int32_t), st));
+  CSS_CU(ctx, cudaMemsetAsync(cfill, 0, (n_col + 1) * sizeof(int32_t), st));
+  const unsigned gb = (unsigned)css_ceil_div(n_brow, T);
+  k_rows<<<gb, T, 0, st>>>(n_brow, row_ptr, col_idx, colour, n_col, brow, trans, cnt, misc + 1, misc);
+  CSS_LAUNCHED(ctx);
+  k_inv_sqrt<<<(unsigned)css_ceil_div(n_col, T), T, 0, st>>>(n_col, cnt, isq, nblk, done, m);
+  CSS_LAUNCHED(ctx);
+  k_pair_count<<<gb, T, 0, st>>>(n_brow, row_ptr, col_idx, colour, pcount);
+  CSS_LAUNCHED(ctx);
+  CSS_TRY(css_scan_i32(ctx, pcount, pstart, n_brow, st));
+  int32_t* hb;
+  CSS_TRY(css_pinned(ctx, sizeof(int64_t) * (n_col + 8) + 256, (void**)&hb));
+  CSS_CU(ctx, cudaMemcpyAsync(hb, misc, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CSS_CU(ctx, cudaMemcpyAsync(hb + 2, pstart + n_brow, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CSS_CU(ctx, cudaStreamSynchronize(st));
+  if (hb[0] & ERR_COLOUR) return css_set_arg_error(ctx, "css_density: colour outside [0, n_colours)");
+  if (hb[0] & ERR_PATTERN)
+    return css_set_arg_error(ctx, "css_density: pattern not symmetric, column out of range or diagonal missing");
+  const int32_t max_row = hb[1];
+  const int64_t n_pairs = hb[2];
+  int32_t *pair_I, *pair_c, *perm, *pob;
+  CSS_TRY(ws_get(ctx, "pr_c", n_pairs + 1, &pr_c));
+  CSS_TRY(ws_get(ctx, "perm", n_pairs + 1, &perm));
+  CSS_TRY(ws_get(ctx, "pair_I", n_pairs + 1, &pair_I));
+  CSS_TRY(ws_get(ctx, "pair_c", n_pairs + 1, &pair_c));
+  CSS_TRY(ws_get(ctx, "pob", nnzb, &pob));
+  k_pair_fill<<<gb, T, 0, st>>>(n_brow, row_ptr, col_idx, colour, pstart, pr_c, bpr, ccount);
+  CSS_LAUNCHED(ctx);
+  CSS_TRY(css_scan_i32(ctx, ccount, coff, n_col, st));
+  k_pair_place<<<gb, T, 0, st>>>(n_brow, pstart, pr_c, coff, cfill, perm, pair_I, pair_c);
+  CSS_LAUNCHED(ctx);
+  k_pob<<<(unsigned)css_ceil_div(nnzb, T), T, 0, st>>>(nnzb, bpr, perm, pob);
+  CSS_LAUNCHED(ctx);
+  std::vector<int64_t> pair_off_h(n_col + 1);
+  {
+    CSS_CU(ctx, cudaMemcpyAsync(hb, coff, sizeof(int32_t) * (n_col + 1), cudaMemcpyDeviceToHost, st));
+    CSS_CU(ctx, cudaStreamSynchronize(st));
+    for (int32_t c = 0; c <= n_col; ++c) pair_off_h[c] = hb[c];
+  }
+  const void* Hv = Hval;
+  if (f32) {
+    float* hf;
+    CSS_TRY(ws_get(ctx, "h_f32", (size_t)nnzb * bb, &hf));
+    k_to_f32<<<(unsigned)css_ceil_div((int64_t)nnzb * bb, T), T, 0, st>>>((int64_t)nnzb * bb, Hval, hf);
+    CSS_LAUNCHED(ctx);
+    Hv = hf;
+  }
+  tm.mark();  // 1
+
+  // ----------------------------------------------------------- memory plan
+  const size_t s_vec = f32 ? 4 : 8;
+  double *Ablk, *Bblk, *Bprev, *X;
+  CSS_TRY(ws_get(ctx, "Ablk", (size_t)n_col * m * bb, &Ablk));
+  CSS_TRY(ws_get(ctx, "Bblk", (size_t)n_col * m * bb, &Bblk));
+  CSS_TRY(ws_get(ctx, "Bprev", (size_t)n_col * bb, &Bprev));
+  CSS_TRY(ws_get(ctx, "X", (size_t)n_pairs * bb, &X));
+  void* Qs = nullptr;
+  if (!two_pass) CSS_TRY(css_ws(ctx, "Qs", (size_t)n_pairs * m * bb * s_vec, &Qs));
+  // eigen workspace (all colours at once)
+  EigArgs ea;
+  ea.n_col = n_col;
+  ea.b = b;
+  ea.m = m;
+  ea.Ablk = Ablk;
+  ea.Bblk = Bblk;
+  ea.nblk = nblk;
+  ea.cnt = cnt;
+  ea.rcap = nmax * (nmax / b + 2);
+  CSS_TRY(ws_get(ctx, "e_AB", (size_t)n_col * nmax * (2 * b + 1), &ea.AB));
+  CSS_TRY(ws_get(ctx, "e_RV", (size_t)n_col * ea.rcap * b, &ea.RV));
+  CSS_TRY(ws_get(ctx, "e_RT", (size_t)n_col * ea.rcap, &ea.RT));
+  CSS_TRY(ws_get(ctx, "e_RR0", (size_t)n_col * ea.rcap, &ea.RR0));
+  CSS_TRY(ws_get(ctx, "e_so", (size_t)n_col * (nmax + 1), &ea.sweep_off));
+  CSS_TRY(ws_get(ctx, "e_d", (size_t)n_col * nmax, &ea.d));
+  CSS_TRY(ws_get(ctx, "e_e", (size_t)n_col * nmax, &ea.e));
+  CSS_TRY(ws_get(ctx, "e_l32", (size_t)n_col * nmax, &ea.lam32));
+  CSS_TRY(ws_get(ctx, "e_tn", (size_t)n_col, &ea.tnorm));
+  CSS_TRY(ws_get(ctx, "e_U", (size_t)n_col * nmax * nmax, &ea.U));
+  CSS_TRY(ws_get(ctx, "e_F", (size_t)n_col * 5 * nmax * nmax, &ea.F));
+  CSS_TRY(ws_get(ctx, "e_lam", (size_t)n_col * nmax, &ea.lam));
+  CSS_TRY(ws_get(ctx, "e_X0", (size_t)n_col * nmax * b, &ea.X0));
+  CSS_TRY(ws_get(ctx, "e_Y", (size_t)n_col * nmax * b, &ea.Y));
+  CSS_TRY(ws_get(ctx, "e_w", (size_t)n_col * nmax, &ea.wgt));
+  CSS_TRY(ws_get(ctx, "e_st", (size_t)n_col, &ea.status));
+  double* Z;
+  CSS_TRY(ws_get(ctx, "Z", (size_t)n_col * nmax * b, &Z));
+  // Krylov vectors: as many colours per batch as memory allows
+  size_t free_b = 0, total_b = 0;
+  CSS_CU(ctx, cudaMemGetInfo(&free_b, &total_b));
+  int32_t ncb = n_col;
+  auto vec_need = [&](int32_t k) -> size_t {
+    const int32_t ws = (int32_t)css_ceil_div((int64_t)k * b, 8) * 8;
+    return 3 * (size_t)N * ws * s_vec + css_lanczos_part_doubles(N, b, k) * 8 * 2 + css_lanczos_small_doubles(b, k) * 8;
+  };
+  const size_t reserve = (size_t)2 << 30;
+  while (ncb > 1 && vec_need(ncb) + reserve > free_b) ncb = (ncb + 1) / 2;
+  const int32_t ws = (int32_t)css_ceil_div((int64_t)ncb * b, 8) * 8;
+  void *Q0, *Q1, *Wv;
+  double *part, *small;
+  CSS_TRY(css_ws(ctx, "Q0", (size_t)N * ws * s_vec, &Q0));
+  CSS_TRY(css_ws(ctx, "Q1", (size_t)N * ws * s_vec, &Q1));
+  CSS_TRY(css_ws(ctx, "W", (size_t)N * ws * s_vec, &Wv));
+  CSS_TRY(ws_get(ctx, "lz_part", css_lanczos_part_doubles(N, b, ncb) * 2, &part));
+  CSS_TRY(ws_get(ctx, "lz_small", css_lanczos_small_doubles(b, ncb), &small));
+
+  LzArgs la;
+  la.fp32 = f32;
+  la.n_brow = n_brow;
+  la.b = b;
+  la.m = m;
+  la.row_ptr = row_ptr;
+  la.col_idx = col_idx;
+  la.Hval = Hv;
+  la.max_row_blocks = max_row;
+  la.colour = colour;
+  la.sign = sign;
+  la.inv_sqrt_cnt = isq;
+  la.Q0 = Q0;
+  la.Q1 = Q1;
+  la.W = Wv;
+  la.ws = ws;
+  la.Ablk = Ablk;
+  la.Bblk = Bblk;
+  la.Bblk_prev = Bprev;
+  la.nblk = nblk;
+  la.done = done;
+  la.part = part;
+  la.small = small;
+  la.tau = f32 ? 1e-5 : 1e-10;
+  la.flags = flags;
+  la.Qs = Qs;
+  la.X = X;
+  la.Z = Z;
+  la.ldz = nmax;
+  la.pair_I = pair_I;
+  la.pair_c = pair_c;
+  la.pair_off_h = pair_off_h.data();
+  std::vector<cudaEvent_t> evs;
+  int64_t n_spmm = 0;
+  if (ctx->timing) {
+    evs.resize(2 * (size_t)m);
+    for (auto& e : evs) cudaEventCreate(&e);
+  }
+  double spmm_ms = 0.0;
+  auto run_batches = [&](int mode) -> css_status {
+    la.mode = mode;
+    for (int32_t cb0 = 0; cb0 < n_col; cb0 += ncb) {
+      la.cb0 = cb0;
+      la.ncb = min(ncb, n_col - cb0);
+      la.w = la.ncb * b;
+      la.ev_spmm = ctx->timing ? evs.data() : nullptr;
+      CSS_TRY(css_lanczos_pass(ctx, la, st));
+      if (ctx->timing) {
+        CSS_CU(ctx, cudaStreamSynchronize(st));
+        for (int32_t j = 0; j < m; ++j) {
+          float t = 0.f;
+          if (cudaEventElapsedTime(&t, evs[2 * j], evs[2 * j + 1]) == cudaSuccess) {
+            spmm_ms += t;
+            ++n_spmm;
+          }
+        }
+      }
+    }
+    return CSS_OK;
+  };
+  CSS_TRY(run_batches(two_pass ? 0 : 1));
+  tm.mark();  // 2
+
+  // ---------------------------------------------------------- eigen + mu + Z
+  CSS_TRY(css_eigen_ritz(ctx, ea, st));
+  tm.mark();  // 3
+  double *dmu, *dkT, *dhalf, *dmu_in, *mupart;
+  int32_t* dsolve;
+  unsigned* bar;
+  CSS_TRY(ws_get(ctx, "mu", n_sys, &dmu));
+  CSS_TRY(ws_get(ctx, "kT", n_sys, &dkT));
+  CSS_TRY(ws_get(ctx, "half_ne", n_sys, &dhalf));
+  CSS_TRY(ws_get(ctx, "mu_in", n_sys, &dmu_in));
+  CSS_TRY(ws_get(ctx, "solve", n_sys, &dsolve));
+  CSS_TRY(ws_get(ctx, "bar", 8, &bar));
+  {
+    double* hp;
+    CSS_TRY(css_pinned(ctx, sizeof(double) * 4 * n_sys + 256, (void**)&hp));
+    for (int32_t s = 0; s < n_sys; ++s) {
+      hp[s] = sys[s].fermi.kT;
+      hp[n_sys + s] = 0.5 * sys[s].fermi.n_elec;
+      hp[2 * n_sys + s] = sys[s].fermi.mu;
+      ((int32_t*)(hp + 3 * n_sys))[s] = sys[s].fermi.solve_mu ? 1 : 0;
+    }
+    CSS_CU(ctx, cudaMemcpyAsync(dkT, hp, sizeof(double) * n_sys, cudaMemcpyHostToDevice, st));
+    CSS_CU(ctx, cudaMemcpyAsync(dhalf, hp + n_sys, sizeof(double) * n_sys, cudaMemcpyHostToDevice, st));
+    CSS_CU(ctx, cudaMemcpyAsync(dmu_in, hp + 2 * n_sys, sizeof(double) * n_sys, cudaMemcpyHostToDevice, st));
+    CSS_CU(ctx, cudaMemcpyAsync(dsolve, hp + 3 * n_sys, sizeof(int32_t) * n_sys, cudaMemcpyHostToDevice, st));
+    CSS_CU(ctx, cudaMemsetAsync(bar, 0, 8 * sizeof(unsigned), st));
+    CSS_CU(ctx, cudaStreamSynchronize(st));  // the pinned staging is reused below
+  }
+  int occ = 0;
+  CSS_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mu, MU_T, 0));
+  unsigned G = (unsigned)std::max(1, std::min(ctx->n_sm * std::max(occ, 1), std::max(n_col, 1)));
+  if (G > (unsigned)ctx->n_sm) G = (unsigned)ctx->n_sm;
+  CSS_TRY(ws_get(ctx, "mu_part", (size_t)4 * n_sys * G + 16, &mupart));
+  {
+    int32_t n_sys_ = n_sys, n_col_ = n_col, nmax_ = nmax, b_ = b;
+    const int32_t* nblk_ = nblk;
+    const int32_t* soc_ = sys_of_colour;
+    const double* lam_ = ea.lam;
+    const double* w_ = ea.wgt;
+    const double* kT_ = dkT;
+    const double* h_ = dhalf;
+    const int32_t* sv_ = dsolve;
+    const double* mi_ = dmu_in;
+    double* mo_ = dmu;
+    double* pp_ = mupart;
+    unsigned* bar_ = bar;
+    int32_t* err_ = misc + 8;
+    void* args[] = {&n_sys_, &n_col_, &nmax_, &nblk_, &b_, &soc_, &lam_, &w_, &kT_, &h_, &sv_, &mi_, &mo_, &pp_,
+                    &bar_, &err_};
+    CSS_CU(ctx, cudaLaunchCooperativeKernel((void*)k_mu, dim3(G), dim3(MU_T), args, 0, st));
+  }
+  tm.mark();  // 4
+  CSS_TRY(css_eigen_z(ctx, ea, sys_of_colour, dmu, dkT, Z, st));
+
+  // --------------------------------------------------------- reconstruction
+  if (two_pass) {
+    CSS_CU(ctx, cudaMemsetAsync(X, 0, (size_t)n_pairs * bb * sizeof(double), st));
+    CSS_CU(ctx, cudaMemsetAsync(done, 0, n_col * sizeof(int32_t), st));
+    k_inv_sqrt<<<(unsigned)css_ceil_div(n_col, T), T, 0, st>>>(n_col, cnt, isq, nblk, done, m);
+    CSS_LAUNCHED(ctx);
+    CSS_TRY(run_batches(2));
+  } else {
+    float *zh = nullptr, *zl = nullptr;
+    if (f32) {
+      CSS_TRY(ws_get(ctx, "zh", (size_t)n_col * nmax * b, &zh));
+      CSS_TRY(ws_get(ctx, "zl", (size_t)n_col * nmax * b, &zl));
+      k_zsplit<<<(unsigned)css_ceil_div((int64_t)n_col * nmax * b, T), T, 0, st>>>((int64_t)n_col * nmax * b, Z, zh,
+                                                                                   zl);
+      CSS_LAUNCHED(ctx);
+      k_xcompute<float><<<(unsigned)css_ceil_div(n_pairs * bb, T), T, 0, st>>>(n_pairs, b, m, nmax, pair_c, nblk,
+                                                                                (const float*)Qs, Z, zh, zl, X);
+    } else {
+      k_xcompute<double><<<(unsigned)css_ceil_div(n_pairs * bb, T), T, 0, st>>>(n_pairs, b, m, nmax, pair_c, nblk,
+                                                                                 (const double*)Qs, Z, nullptr,
+                                                                                 nullptr, X);
+    }
+    CSS_LAUNCHED(ctx);
+  }
+  tm.mark();  // 5
+  // ------------------------------------------------------------- extraction
+  const int sym = (flags & CSS_SYMMETRIZE) ? 1 : 0;
+  double* tpart;
+  double* tout;
+  const int64_t max_parts = css_ceil_div((int64_t)nnzb * bb, EX_T) + n_sys;
+  CSS_TRY(ws_get(ctx, "tr_part", 2 * (size_t)max_parts, &tpart));
+  CSS_TRY(ws_get(ctx, "tr_out", 2 * (size_t)n_sys + 2, &tout));
+  for (int32_t s = 0; s < n_sys; ++s) {
+    const int32_t k0 = blk_off[s], k1 = blk_off[s + 1];
+    const int64_t nth = (int64_t)(k1 - k0) * bb;
+    const unsigned blocks = (unsigned)css_ceil_div(nth, EX_T);
+    double* out_p = (n_sys == 1) ? Pout : sys[s].P_val;
+    k_extract<<<blocks, EX_T, 0, st>>>(k0, k1, b, k0, brow, col_idx, trans, pob, sign, X, Hval, sym, out_p, tpart);
+    CSS_LAUNCHED(ctx);
+    k_trace_sum<<<1, 32, 0, st>>>((int32_t)blocks, tpart, tout + 2 * s);
+    CSS_LAUNCHED(ctx);
+  }
+  k_count_breakdown<<<(unsigned)css_ceil_div(n_col, T), T, 0, st>>>(n_col, m, nblk, cnt, misc + 16);
+  CSS_LAUNCHED(ctx);
+  tm.mark();  // 6
+  // ------------------------------------------------------------ read back
+  double* hres;
+  CSS_TRY(css_pinned(ctx, sizeof(double) * (3 * n_sys + 16), (void**)&hres));
+  CSS_CU(ctx, cudaMemcpyAsync(hres, tout, sizeof(double) * 2 * n_sys, cudaMemcpyDeviceToHost, st));
+  CSS_CU(ctx, cudaMemcpyAsync(hres + 2 * n_sys, dmu, sizeof(double) * n_sys, cudaMemcpyDeviceToHost, st));
+  CSS_CU(ctx, cudaMemcpyAsync(hres + 3 * n_sys, misc + 8, sizeof(int32_t) * 16, cudaMemcpyDeviceToHost, st));
+  CSS_CU(ctx, cudaStreamSynchronize(st));
+  const int32_t* hmisc = (const int32_t*)(hres + 3 * n_sys);
+  const int32_t mu_err = hmisc[0];
+  const int32_t n_break = hmisc[8];
+  bool finite = true;
+  for (int32_t s = 0; s < n_sys; ++s) {
+    if (trP) trP[s] = hres[2 * s];
+    if (trPH) trPH[s] = hres[2 * s + 1];
+    if (mu_out) mu_out[s] = hres[2 * n_sys + s];
+    finite = finite && std::isfinite(hres[2 * s]) && std::isfinite(hres[2 * s + 1]) &&
+             std::isfinite(hres[2 * n_sys + s]);
+  }
+  ctx->info.n_colours = n_col;
+  ctx->info.n_pairs = (int32_t)n_pairs;
+  ctx->info.n_breakdown = n_break;
+  ctx->info.m = m;
+  ctx->info.spmm_launches = n_spmm;
+  const int64_t wcols = (int64_t)std::min(ncb, n_col) * b;
+  ctx->info.spmm_flops = 2.0 * nnzb * (double)bb * (double)wcols;
+  ctx->info.spmm_bytes = (double)nnzb * bb * s_vec + 2.0 * (double)N * wcols * s_vec;
+  ctx->info.ms_spmm = n_spmm ? spmm_ms / n_spmm : 0.0;
+  if (ctx->timing) {
+    ctx->info.ms_setup = tm.ms(0, 1);
+    ctx->info.ms_lanczos = tm.ms(1, 2);
+    ctx->info.ms_eigen = tm.ms(2, 3);
+    ctx->info.ms_mu = tm.ms(3, 4);
+    ctx->info.ms_extract = tm.ms(4, 6);
+    ctx->info.ms_total = tm.ms(0, 6);
+    for (auto& e : evs) cudaEventDestroy(e);
+  }
+  if (mu_err) {
+    ctx->last_error = "css_density: grid barrier of the mu bisection timed out";
+    return CSS_ERR_TIMEOUT;
+  }
+  if (!finite) {
+    ctx->last_error = "css_density: non-finite trace or mu";
+    return CSS_ERR_NUMERIC;
+  }
+  return n_break > 0 ? CSS_WARN_BREAKDOWN : CSS_OK;
+}
+
+extern "C" {
+
+css_status css_density(css_ctx* ctx, const css_bsr* H, const int32_t* colour, const int8_t* sign, int32_t n_colours,
+                       const css_fermi* fermi, int32_t m, css_precision prec, uint32_t flags, double* P_val,
+                       double* trP, double* trPH, double* mu_out, void* stream) {
+  if (!ctx || !H || !fermi) return css_set_arg_error(ctx, "css_density: null pointer");
+  CSS_CU(ctx, cudaSetDevice(ctx->device));
+  css_sys_desc d{*H, colour, sign, n_colours, *fermi, P_val};
+  return css_density_impl(ctx, 1, &d, m, prec, flags, trP, trPH, mu_out, (cudaStream_t)stream);
+}
+
+css_status css_density_batch(css_ctx* ctx, int32_t n_sys, const css_bsr* H, const int32_t* const* colour,
+                             const int8_t* const* sign, const int32_t* n_colours, const css_fermi* fermi, int32_t m,
+                             css_precision prec, uint32_t flags, double* const* P_val, double* trP, double* trPH,
+                             double* mu_out, void* stream) {
+  if (!ctx || !H || !colour || !sign || !n_colours || !fermi || !P_val || n_sys < 1)
+    return css_set_arg_error(ctx, "css_density_batch: null pointer or n_sys < 1");
+  CSS_CU(ctx, cudaSetDevice(ctx->device));
+  std::vector<css_sys_desc> d(n_sys);
+  for (int32_t s = 0; s < n_sys; ++s) d[s] = css_sys_desc{H[s], colour[s], sign[s], n_colours[s], fermi[s], P_val[s]};
+  return css_density_impl(ctx, n_sys, d.data(), m, prec, flags, trP, trPH, mu_out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,611 @@
+// FP64 eigen-decomposition of the projected block-tridiagonal matrices, one per colour, and
+// the subspace matrix function Z = U f(Lambda) U^T E_1 B_0 (paper, Eq. 5-7: exact
+// diagonalisation of the Krylov-projected Hamiltonian).
+//
+// GB300 runs FP64 at about 1/64 of the FP32 rate and a dependent FP64 sqrt + divide costs
+// ~0.6 us, so no stage here is a long sequential FP64 chain:
+//   1. band -> tridiagonal by Householder bulge chasing (reflectors of length <= b; a sweep's
+//      reflectors touch disjoint rows, so their action on b-column blocks is applied sweep by
+//      sweep with all of a sweep's reflectors in parallel);
+//   2. eigenvalues of the tridiagonal by Sturm-count bisection in FP32 (one thread per
+//      eigenvalue), used only as shifts;
+//   3. FP64 Rayleigh-quotient inverse iteration per eigenvalue (one thread per cluster of
+//      close shifts, Gram-Schmidt inside the cluster and a Rayleigh-Ritz step on it), which
+//      gives eigenvalues and eigenvectors to FP64 accuracy;
+//   4. Y = U^T (Q_band^T E_1 B_0), weights w = ||Y_k||^2, and after mu is known
+//      Z = Q_band U f(Lambda) Y.
+#include "css_eigen.cuh"
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------------ band storage
+// AB[col * LDB + d] = T[col + d][col], d in [0, LDB), LDB = 2 kd + 1 (room for the bulge)
+__global__ void k_band_build(int32_t b, int32_t m, int32_t nmax, int32_t ldb, const double* __restrict__ Ablk,
+                             const double* __restrict__ Bblk, const int32_t* __restrict__ nblk,
+                             double* __restrict__ AB) {
+  const int32_t c = blockIdx.x;
+  const int32_t n = nblk[c] * b;
+  double* ab = AB + (size_t)c * nmax * ldb;
+  for (int32_t t = threadIdx.x; t < nmax * ldb; t += blockDim.x) {
+    int32_t col = t / ldb, d = t % ldb, row = col + d;
+    double v = 0.0;
+    if (col < n && row < n && d <= b) {
+      int32_t jc = col / b, kc = col % b, jr = row / b, kr = row % b;
+      if (jr == jc) v = Ablk[(((size_t)c * m + jc) * b + kr) * b + kc];
+      else if (jr == jc + 1 && kr <= kc) v = Bblk[(((size_t)c * m + jc) * b + kr) * b + kc];
+    }
+    ab[t] = v;
+  }
+}
+
+struct Band {
+  double* ab;
+  int32_t ldb;
+  // lower-stored symmetric access, r >= c
+  __device__ __forceinline__ double& at(int32_t r, int32_t c) const { return ab[(size_t)c * ldb + (r - c)]; }
+};
+
+// Householder vector of x[0..L) held one element per lane of warp 0: H x = beta e_0.
+// Textbook construction (Golub & Van Loan, Alg. 5.1.1): v[0] = 1, tau = 2 v0^2/(sigma+v0^2).
+__device__ void warp_house(double x, int32_t L, double* sv, double* stau, double* sbeta) {
+  const int lane = threadIdx.x & 31;
+  double x0 = __shfl_sync(0xffffffffu, x, 0);
+  double sig = warp_sum((lane >= 1 && lane < L) ? x * x : 0.0);
+  if (sig == 0.0) {
+    if (lane < 32) sv[lane] = (lane == 0) ? 1.0 : 0.0;
+    if (lane == 0) {
+      *stau = 0.0;
+      *sbeta = x0;
+    }
+    return;
+  }
+  double mu = sqrt(x0 * x0 + sig);
+  double v0 = (x0 <= 0.0) ? x0 - mu : -sig / (x0 + mu);
+  double inv = 1.0 / v0;
+  sv[lane] = (lane == 0) ? 1.0 : ((lane < L) ? x * inv : 0.0);
+  if (lane == 0) {
+    *stau = 2.0 * v0 * v0 / (sig + v0 * v0);
+    *sbeta = mu;
+  }
+}
+
+// D <- H D H on the symmetric L x L diagonal block starting at r0 (H = I - tau v v^T).
+// 1024 threads: warp p owns row p, lane q owns column q.
+__device__ void two_sided(const Band& A, int32_t r0, int32_t L, const double* v, double tau, double* sp,
+                          double* salpha) {
+  const int32_t p = threadIdx.x >> 5, q = threadIdx.x & 31;
+  if (tau == 0.0) return;
+  double prod = 0.0;
+  if (p < L && q < L) prod = (p >= q ? A.at(r0 + p, r0 + q) : A.at(r0 + q, r0 + p)) * v[q];
+  prod = warp_sum(prod);
+  if (q == 0 && p < 32) sp[p] = (p < L) ? tau * prod : 0.0;
+  __syncthreads();
+  if (p == 0) {
+    double t = warp_sum(q < L ? sp[q] * v[q] : 0.0);
+    if (q == 0) *salpha = -0.5 * tau * t;
+  }
+  __syncthreads();
+  const double alpha = *salpha;
+  if (p < L && q <= p) {
+    double wp = sp[p] + alpha * v[p], wq = sp[q] + alpha * v[q];
+    A.at(r0 + p, r0 + q) -= v[p] * wq + wp * v[q];
+  }
+  __syncthreads();
+}
+
+// Band -> tridiagonal (one CTA of 1024 threads per colour), reflectors recorded in order
+__global__ void __launch_bounds__(1024) k_band_to_tri(int32_t kd, int32_t nmax, int32_t ldb, int32_t rcap,
+                                                      const int32_t* __restrict__ nblk, double* __restrict__ AB,
+                                                      double* __restrict__ RV, double* __restrict__ RT,
+                                                      int32_t* __restrict__ RR0, int32_t* __restrict__ sweep_off,
+                                                      double* __restrict__ dd, double* __restrict__ ee) {
+  __shared__ double sv[32], sv2[32], sy[32], sp[32];
+  __shared__ double stau, stau2, sbeta, salpha;
+  const int32_t c = blockIdx.x;
+  const int32_t n = nblk[c] * kd;
+  Band A{AB + (size_t)c * nmax * ldb, ldb};
+  double* rv = RV + (size_t)c * rcap * kd;
+  double* rt = RT + (size_t)c * rcap;
+  int32_t* rr = RR0 + (size_t)c * rcap;
+  int32_t* so = sweep_off + (size_t)c * (nmax + 1);
+  const int32_t p = threadIdx.x >> 5, q = threadIdx.x & 31;
+  int32_t cnt = 0;
+  auto record = [&](int32_t r0, const double* v, double tau) {
+    if (threadIdx.x < kd) rv[(size_t)cnt * kd + threadIdx.x] = v[threadIdx.x];
+    if (threadIdx.x == 0) {
+      rt[cnt] = tau;
+      rr[cnt] = r0;
+    }
+    ++cnt;
+  };
+  for (int32_t i = 0; i + 2 < n; ++i) {
+    if (threadIdx.x == 0) so[i] = cnt;
+    const int32_t r0 = i + 1;
+    const int32_t L = min(kd, n - 1 - i);
+    // type 1: annihilate column i below the sub-diagonal
+    if (p == 0) {
+      double x = (q < L) ? A.at(r0 + q, i) : 0.0;
+      warp_house(x, L, sv, &stau, &sbeta);
+    }
+    __syncthreads();
+    if (threadIdx.x < L) A.at(r0 + threadIdx.x, i) = (threadIdx.x == 0) ? sbeta : 0.0;
+    __syncthreads();
+    two_sided(A, r0, L, sv, stau, sp, &salpha);
+    record(r0, sv, stau);
+    int32_t p0 = r0, Lp = L;
+    double* v = sv;
+    double* vn = sv2;
+    double tau = stau;
+    for (;;) {
+      const int32_t q0 = p0 + Lp;
+      if (q0 > n - 1) break;
+      const int32_t Lq = min(kd, n - q0);
+      // type 2a: B = A[q0.., p0..] <- B (I - tau v v^T)
+      if (tau != 0.0) {
+        double prod = (p < Lq && q < Lp) ? A.at(q0 + p, p0 + q) * v[q] : 0.0;
+        prod = warp_sum(prod);
+        if (q == 0) sy[p] = prod;
+        __syncthreads();
+        if (p < Lq && q < Lp) A.at(q0 + p, p0 + q) -= tau * sy[p] * v[q];
+        __syncthreads();
+      }
+      if (Lq < 2) break;
+      // type 2b: new reflector from the bulge's first column, applied from the left
+      if (p == 0) {
+        double x = (q < Lq) ? A.at(q0 + q, p0) : 0.0;
+        warp_house(x, Lq, vn, &stau2, &sbeta);
+      }
+      __syncthreads();
+      const double tau2 = stau2;
+      if (tau2 != 0.0) {
+        // z[col] = v^T B[:, col] for col >= 1: warp col, lane row
+        double prod = (p >= 1 && p < Lp && q < Lq) ? vn[q] * A.at(q0 + q, p0 + p) : 0.0;
+        prod = warp_sum(prod);
+        if (q == 0) sy[p] = prod;
+        __syncthreads();
+        if (q >= 1 && q < Lp && p < Lq) A.at(q0 + p, p0 + q) -= tau2 * vn[p] * sy[q];
+      }
+      if (threadIdx.x < Lq) A.at(q0 + threadIdx.x, p0) = (threadIdx.x == 0) ? sbeta : 0.0;
+      __syncthreads();
+      // type 3: two-sided on the next diagonal block
+      two_sided(A, q0, Lq, vn, tau2, sp, &salpha);
+      record(q0, vn, tau2);
+      double* t = v;
+      v = vn;
+      vn = t;
+      tau = tau2;
+      p0 = q0;
+      Lp = Lq;
+    }
+    __syncthreads();
+  }
+  for (int32_t i = max(0, n - 2); i <= n; ++i)
+    if (threadIdx.x == 0) so[i] = cnt;
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    dd[(size_t)c * nmax + i] = A.at(i, i);
+    ee[(size_t)c * nmax + i] = (i + 1 < n) ? A.at(i + 1, i) : 0.0;
+  }
+}
+
+// Apply the recorded reflectors to an n x b block X ([c][nmax][b]): FWD applies them in
+// generation order (X <- Q^T X), otherwise in reverse (X <- Q X).  A sweep's reflectors act
+// on disjoint rows, so one thread per (reflector of the sweep, column) works in parallel.
+template <bool FWD>
+__global__ void k_apply_refl(int32_t kd, int32_t b, int32_t nmax, int32_t rcap, const int32_t* __restrict__ nblk,
+                             const double* __restrict__ RV, const double* __restrict__ RT,
+                             const int32_t* __restrict__ RR0, const int32_t* __restrict__ sweep_off,
+                             double* __restrict__ X) {
+  const int32_t c = blockIdx.x;
+  const int32_t n = nblk[c] * kd;
+  const double* rv = RV + (size_t)c * rcap * kd;
+  const double* rt = RT + (size_t)c * rcap;
+  const int32_t* rr = RR0 + (size_t)c * rcap;
+  const int32_t* so = sweep_off + (size_t)c * (nmax + 1);
+  double* x = X + (size_t)c * nmax * b;
+  const int32_t nsweep = n > 2 ? n - 2 : 0;
+  for (int32_t s = 0; s < nsweep; ++s) {
+    const int32_t i = FWD ? s : nsweep - 1 - s;
+    const int32_t t0 = so[i], t1 = so[i + 1];
+    for (int32_t t = threadIdx.x; t < (t1 - t0) * b; t += blockDim.x) {
+      const int32_t r = t0 + t / b, col = t % b;
+      const double tau = rt[r];
+      if (tau == 0.0) continue;
+      const int32_t r0 = rr[r];
+      const int32_t L = min(kd, n - r0);
+      const double* v = rv + (size_t)r * kd;
+      double s2 = 0.0;
+      for (int32_t l = 0; l < L; ++l) s2 += v[l] * x[(size_t)(r0 + l) * b + col];
+      s2 *= tau;
+      for (int32_t l = 0; l < L; ++l) x[(size_t)(r0 + l) * b + col] -= s2 * v[l];
+    }
+    __syncthreads();
+  }
+}
+
+// X0 = E_1 B_0 = sqrt|c| [I_b; 0]
+__global__ void k_x0(int32_t b, int32_t nmax, const int32_t* __restrict__ cnt, double* __restrict__ X) {
+  const int32_t c = blockIdx.x;
+  const double s = sqrt((double)cnt[c]);
+  for (int32_t t = threadIdx.x; t < nmax * b; t += blockDim.x) {
+    int32_t i = t / b, k = t % b;
+    X[(size_t)c * nmax * b + t] = (i == k) ? s : 0.0;
+  }
+}
+
+// ------------------------------------------------------------- FP32 bisection
+__device__ __forceinline__ int32_t sturm32(const float* d, const float* e2, int32_t n, float x, float pivmin) {
+  float qv = d[0] - x;
+  int32_t cnt = qv < 0.f;
+  for (int32_t i = 1; i < n; ++i) {
+    if (fabsf(qv) < pivmin) qv = -pivmin;
+    qv = (d[i] - x) - __fdividef(e2[i - 1], qv);
+    cnt += qv < 0.f;
+  }
+  return cnt;
+}
+
+__global__ void k_bisect32(int32_t kd, int32_t nmax, const int32_t* __restrict__ nblk, const double* __restrict__ dd,
+                           const double* __restrict__ ee, float* __restrict__ lam32, double* __restrict__ tnorm) {
+  extern __shared__ float sh32[];
+  const int32_t c = blockIdx.x;
+  const int32_t n = nblk[c] * kd;
+  float* d = sh32;
+  float* e2 = sh32 + nmax;
+  __shared__ double red_lo[32], red_hi[32];
+  double lo = 1e300, hi = -1e300, emax = 0.0;
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double di = dd[(size_t)c * nmax + i];
+    double el = i > 0 ? fabs(ee[(size_t)c * nmax + i - 1]) : 0.0;
+    double er = i + 1 < n ? fabs(ee[(size_t)c * nmax + i]) : 0.0;
+    lo = fmin(lo, di - el - er);
+    hi = fmax(hi, di + el + er);
+    d[i] = (float)di;
+    double e = i + 1 < n ? ee[(size_t)c * nmax + i] : 0.0;
+    e2[i] = (float)(e * e);
+    emax = fmax(emax, e * e);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red_lo[threadIdx.x >> 5] = lo;
+    red_hi[threadIdx.x >> 5] = fmax(hi, -1e300);
+  }
+  __shared__ double semax[32];
+  if ((threadIdx.x & 31) == 0) semax[threadIdx.x >> 5] = emax;
+  __syncthreads();
+  double glo = 1e300, ghi = -1e300, gem = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+    glo = fmin(glo, red_lo[i]);
+    ghi = fmax(ghi, red_hi[i]);
+    gem = fmax(gem, semax[i]);
+  }
+  const double span = fmax(fabs(glo), fabs(ghi));
+  if (threadIdx.x == 0) tnorm[c] = fmax(span, 1e-100);
+  const float flo = (float)(glo - 1e-3 * span - 1e-30), fhi = (float)(ghi + 1e-3 * span + 1e-30);
+  const float pivmin = (float)fmax(1e-30, 1e-30 * gem);
+  for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
+    float a = flo, z = fhi;
+    for (int it = 0; it < 80; ++it) {
+      float mid = 0.5f * (a + z);
+      if (!(mid > a && mid < z)) break;
+      if (sturm32(d, e2, n, mid, pivmin) <= k) a = mid;
+      else z = mid;
+    }
+    lam32[(size_t)c * nmax + k] = 0.5f * (a + z);
+  }
+}
+
+// ------------------------------------------------- FP64 inverse iteration
+constexpr int kMaxCluster = 16;
+
+__device__ __forceinline__ double hash_unit(uint64_t a, uint64_t b) {
+  uint64_t z = css_splitmix64(a * 0x9E3779B97F4A7C15ull + 0x5851F42D4C957F2Dull, b);
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// One thread per cluster of close shifts.  Column k of U and five scratch columns of F are
+// owned by the thread handling eigenvalue k.  Layout [c][row][col] so threads with
+// neighbouring k touch neighbouring addresses.
+__global__ void k_inviter(int32_t kd, int32_t nmax, const int32_t* __restrict__ nblk, const double* __restrict__ dd,
+                          const double* __restrict__ ee, const float* __restrict__ lam32,
+                          const double* __restrict__ tnorm, double rel_cluster, double* __restrict__ U,
+                          double* __restrict__ F, double* __restrict__ lam, int32_t* __restrict__ status) {
+  const int32_t c = blockIdx.x;
+  const int32_t n = nblk[c] * kd;
+  const double* d = dd + (size_t)c * nmax;
+  const double* e = ee + (size_t)c * nmax;
+  const float* l32 = lam32 + (size_t)c * nmax;
+  double* u = U + (size_t)c * nmax * nmax;
+  double* f_l = F + (size_t)c * 5 * nmax * nmax;
+  double* f_u0 = f_l + (size_t)nmax * nmax;
+  double* f_u1 = f_u0 + (size_t)nmax * nmax;
+  double* f_u2 = f_u1 + (size_t)nmax * nmax;
+  double* f_x = f_u2 + (size_t)nmax * nmax;
+  const double tn = tnorm[c];
+  const double tol = rel_cluster * tn;
+  const double pivmin = 2.2e-16 * tn;
+  for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
+    // cluster starts where the gap to the previous shift exceeds tol (and every 16 members)
+    int32_t s = k;
+    while (s > 0 && (double)l32[s] - (double)l32[s - 1] <= tol) --s;
+    if ((k - s) % kMaxCluster != 0) continue;
+    const int32_t k0 = k;
+    int32_t k1 = k;
+    while (k1 + 1 < n && (double)l32[k1 + 1] - (double)l32[k1] <= tol && k1 + 1 - k0 < kMaxCluster) ++k1;
+    auto U_ = [&](int32_t i, int32_t col) -> double& { return u[(size_t)i * nmax + col]; };
+    auto F_ = [&](double* base, int32_t i, int32_t col) -> double& { return base[(size_t)i * nmax + col]; };
+    for (int32_t kk = k0; kk <= k1; ++kk) {
+      double sigma = (double)l32[kk];
+      // start vector
+      double nrm = 0.0;
+      for (int32_t i = 0; i < n; ++i) {
+        double x = hash_unit((uint64_t)c * 1000003ull + kk, (uint64_t)i);
+        F_(f_x, i, kk) = x;
+        nrm += x * x;
+      }
+      nrm = 1.0 / sqrt(nrm);
+      for (int32_t i = 0; i < n; ++i) F_(f_x, i, kk) *= nrm;
+      for (int it = 0; it < 5; ++it) {
+        // LU with partial pivoting of T - sigma I (rows: sub e_{i-1}, diag d_i - sigma, sup e_i)
+        double cd = d[0] - sigma, cs = n > 1 ? e[0] : 0.0;
+        for (int32_t i = 0; i + 1 < n; ++i) {
+          const double sub = e[i], dg = d[i + 1] - sigma, sup = (i + 2 < n) ? e[i + 1] : 0.0;
+          if (fabs(cd) >= fabs(sub)) {
+            if (fabs(cd) < pivmin) cd = cd >= 0 ? pivmin : -pivmin;
+            const double l = sub / cd;
+            F_(f_l, i, kk) = l;
+            F_(f_u0, i, kk) = cd;
+            F_(f_u1, i, kk) = cs;
+            F_(f_u2, i, kk) = 0.0;  // no interchange
+            cd = dg - l * cs;
+            cs = sup;
+          } else {
+            // rows i and i+1 interchanged; |l| <= 1, so l + 4 in [3, 5] marks the interchange
+            const double l = cd / sub;
+            F_(f_l, i, kk) = l + 4.0;
+            F_(f_u0, i, kk) = sub;
+            F_(f_u1, i, kk) = dg;
+            F_(f_u2, i, kk) = sup;
+            const double ncd = cs - l * dg;
+            cs = -l * sup;
+            cd = ncd;
+          }
+        }
+        if (fabs(cd) < pivmin) cd = cd >= 0 ? pivmin : -pivmin;
+        F_(f_u0, n - 1, kk) = cd;
+        // forward: P and L
+        for (int32_t i = 0; i + 1 < n; ++i) {
+          double l = F_(f_l, i, kk);
+          double xi = F_(f_x, i, kk), xn = F_(f_x, i + 1, kk);
+          if (l >= 3.0) {  // interchange
+            l -= 4.0;
+            F_(f_x, i, kk) = xn;
+            F_(f_x, i + 1, kk) = xi - l * xn;
+          } else {
+            F_(f_x, i + 1, kk) = xn - l * xi;
+          }
+        }
+        // backward: U y = x
+        double y2 = 0.0, y1 = 0.0;
+        for (int32_t i = n - 1; i >= 0; --i) {
+          double r = F_(f_x, i, kk);
+          if (i + 1 < n) r -= F_(f_u1, i, kk) * y1;
+          if (i + 2 < n) r -= F_(f_u2, i, kk) * y2;
+          double y = r / F_(f_u0, i, kk);
+          F_(f_x, i, kk) = y;
+          y2 = y1;
+          y1 = y;
+        }
+        // Gram-Schmidt against the cluster's finished vectors, twice
+        for (int rep = 0; rep < 2; ++rep)
+          for (int32_t pq = k0; pq < kk; ++pq) {
+            double dot = 0.0;
+            for (int32_t i = 0; i < n; ++i) dot += U_(i, pq) * F_(f_x, i, kk);
+            for (int32_t i = 0; i < n; ++i) F_(f_x, i, kk) -= dot * U_(i, pq);
+          }
+        nrm = 0.0;
+        for (int32_t i = 0; i < n; ++i) nrm += F_(f_x, i, kk) * F_(f_x, i, kk);
+        const double growth = sqrt(nrm);
+        nrm = 1.0 / growth;
+        // Rayleigh quotient x^T T x of the normalised vector
+        double rq = 0.0, prev = 0.0;
+        for (int32_t i = 0; i < n; ++i) {
+          double xi = F_(f_x, i, kk) * nrm;
+          F_(f_x, i, kk) = xi;
+          rq += xi * (d[i] * xi + 2.0 * (i > 0 ? e[i - 1] * prev : 0.0));
+          prev = xi;
+        }
+        const bool conv = it >= 1 && growth * pivmin > 1.0;
+        sigma = rq;
+        if (conv) break;
+      }
+      for (int32_t i = 0; i < n; ++i) U_(i, kk) = F_(f_x, i, kk);
+      lam[(size_t)c * nmax + kk] = sigma;
+    }
+    if (k1 > k0) {
+      // Rayleigh-Ritz inside the cluster: C = U_c^T T U_c, cyclic Jacobi, U_c <- U_c V
+      const int32_t kc = k1 - k0 + 1;
+      double C[kMaxCluster][kMaxCluster], V[kMaxCluster][kMaxCluster];
+      for (int32_t a = 0; a < kc; ++a)
+        for (int32_t bq = 0; bq < kc; ++bq) {
+          double s2 = 0.0;
+          for (int32_t i = 0; i < n; ++i) {
+            double tu = d[i] * U_(i, k0 + bq);
+            if (i > 0) tu += e[i - 1] * U_(i - 1, k0 + bq);
+            if (i + 1 < n) tu += e[i] * U_(i + 1, k0 + bq);
+            s2 += U_(i, k0 + a) * tu;
+          }
+          C[a][bq] = s2;
+          V[a][bq] = (a == bq) ? 1.0 : 0.0;
+        }
+      for (int32_t a = 0; a < kc; ++a)
+        for (int32_t bq = a + 1; bq < kc; ++bq) {
+          double t = 0.5 * (C[a][bq] + C[bq][a]);
+          C[a][bq] = t;
+          C[bq][a] = t;
+        }
+      for (int sweep = 0; sweep < 30; ++sweep) {
+        double off = 0.0, on = 0.0;
+        for (int32_t a = 0; a < kc; ++a)
+          for (int32_t bq = 0; bq < kc; ++bq) (a == bq ? on : off) += C[a][bq] * C[a][bq];
+        if (off <= 1e-32 * on || off == 0.0) break;
+        for (int32_t a = 0; a < kc; ++a)
+          for (int32_t bq = a + 1; bq < kc; ++bq) {
+            if (C[a][bq] == 0.0) continue;
+            double theta = (C[bq][bq] - C[a][a]) / (2.0 * C[a][bq]);
+            double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+            for (int32_t r = 0; r < kc; ++r) {
+              double ca = C[r][a], cb = C[r][bq];
+              C[r][a] = cs * ca - sn * cb;
+              C[r][bq] = sn * ca + cs * cb;
+            }
+            for (int32_t r = 0; r < kc; ++r) {
+              double ca = C[a][r], cb = C[bq][r];
+              C[a][r] = cs * ca - sn * cb;
+              C[bq][r] = sn * ca + cs * cb;
+            }
+            for (int32_t r = 0; r < kc; ++r) {
+              double va = V[r][a], vb = V[r][bq];
+              V[r][a] = cs * va - sn * vb;
+              V[r][bq] = sn * va + cs * vb;
+            }
+          }
+      }
+      double row[kMaxCluster];
+      for (int32_t i = 0; i < n; ++i) {
+        for (int32_t a = 0; a < kc; ++a) {
+          double s2 = 0.0;
+          for (int32_t bq = 0; bq < kc; ++bq) s2 += U_(i, k0 + bq) * V[bq][a];
+          row[a] = s2;
+        }
+        for (int32_t a = 0; a < kc; ++a) U_(i, k0 + a) = row[a];
+      }
+      for (int32_t a = 0; a < kc; ++a) lam[(size_t)c * nmax + k0 + a] = C[a][a];
+    }
+  }
+  (void)status;
+}
+
+// Y[k][col] = sum_i U[i][k] X[i][col], w[k] = ||Y[k]||^2 (one thread per k)
+__global__ void k_ritz_y(int32_t kd, int32_t b, int32_t nmax, const int32_t* __restrict__ nblk,
+                         const double* __restrict__ U, const double* __restrict__ X, double* __restrict__ Y,
+                         double* __restrict__ wgt) {
+  extern __shared__ double shx[];
+  const int32_t c = blockIdx.y;
+  const int32_t n = nblk[c] * kd;
+  const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  const double* u = U + (size_t)c * nmax * nmax;
+  const double* x = X + (size_t)c * nmax * b;
+  double acc[CSS_MAX_B];
+#pragma unroll
+  for (int a = 0; a < CSS_MAX_B; ++a) acc[a] = 0.0;
+  const int32_t CH = 64;
+  for (int32_t i0 = 0; i0 < n; i0 += CH) {
+    const int32_t ie = min(n, i0 + CH);
+    __syncthreads();
+    for (int32_t t = threadIdx.x; t < (ie - i0) * b; t += blockDim.x) shx[t] = x[(size_t)i0 * b + t];
+    __syncthreads();
+    if (k < n)
+      for (int32_t i = i0; i < ie; ++i) {
+        const double uk = u[(size_t)i * nmax + k];
+#pragma unroll
+        for (int a = 0; a < CSS_MAX_B; ++a)
+          if (a < b) acc[a] = fma(uk, shx[(i - i0) * b + a], acc[a]);
+      }
+  }
+  if (k < n) {
+    double w = 0.0;
+#pragma unroll
+    for (int a = 0; a < CSS_MAX_B; ++a)
+      if (a < b) {
+        Y[((size_t)c * nmax + k) * b + a] = acc[a];
+        w = fma(acc[a], acc[a], w);
+      }
+    wgt[(size_t)c * nmax + k] = w;
+  } else if (k < nmax) {
+    wgt[(size_t)c * nmax + k] = 0.0;
+  }
+}
+
+// Zt[i][col] = sum_k U[i][k] f(lam_k) Y[k][col] (one thread per row i)
+__global__ void k_zt(int32_t kd, int32_t b, int32_t nmax, const int32_t* __restrict__ nblk,
+                     const int32_t* __restrict__ sys_of_colour, const double* __restrict__ mu,
+                     const double* __restrict__ kT, const double* __restrict__ U, const double* __restrict__ lam,
+                     const double* __restrict__ Y, double* __restrict__ Z) {
+  extern __shared__ double shy[];
+  const int32_t c = blockIdx.y;
+  const int32_t n = nblk[c] * kd;
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double* u = U + (size_t)c * nmax * nmax;
+  const int32_t s = sys_of_colour[c];
+  const double m_ = mu[s], t_ = kT[s];
+  double acc[CSS_MAX_B];
+#pragma unroll
+  for (int a = 0; a < CSS_MAX_B; ++a) acc[a] = 0.0;
+  const int32_t CH = 64;
+  for (int32_t k0 = 0; k0 < n; k0 += CH) {
+    const int32_t ke = min(n, k0 + CH);
+    __syncthreads();
+    for (int32_t t = threadIdx.x; t < (ke - k0) * b; t += blockDim.x) {
+      const int32_t kk = k0 + t / b;
+      shy[t] = css_fermi_dirac(lam[(size_t)c * nmax + kk], m_, t_) * Y[((size_t)c * nmax) * b + (size_t)k0 * b + t];
+    }
+    __syncthreads();
+    if (i < n)
+      for (int32_t kk = k0; kk < ke; ++kk) {
+        const double uk = u[(size_t)i * nmax + kk];
+#pragma unroll
+        for (int a = 0; a < CSS_MAX_B; ++a)
+          if (a < b) acc[a] = fma(uk, shy[(kk - k0) * b + a], acc[a]);
+      }
+  }
+  if (i < nmax) {
+#pragma unroll
+    for (int a = 0; a < CSS_MAX_B; ++a)
+      if (a < b) Z[((size_t)c * nmax + i) * b + a] = (i < n) ? acc[a] : 0.0;
+  }
+}
+
+}  // namespace
+
+css_status css_eigen_ritz(css_ctx* ctx, const EigArgs& a, cudaStream_t st) {
+  const int32_t nc = a.n_col, b = a.b, nmax = a.m * b, ldb = 2 * b + 1;
+  k_band_build<<<nc, 256, 0, st>>>(b, a.m, nmax, ldb, a.Ablk, a.Bblk, a.nblk, a.AB);
+  CSS_LAUNCHED(ctx);
+  k_band_to_tri<<<nc, 1024, 0, st>>>(b, nmax, ldb, a.rcap, a.nblk, a.AB, a.RV, a.RT, a.RR0, a.sweep_off, a.d, a.e);
+  CSS_LAUNCHED(ctx);
+  k_x0<<<nc, 256, 0, st>>>(b, nmax, a.cnt, a.X0);
+  CSS_LAUNCHED(ctx);
+  k_apply_refl<true><<<nc, 1024, 0, st>>>(b, b, nmax, a.rcap, a.nblk, a.RV, a.RT, a.RR0, a.sweep_off, a.X0);
+  CSS_LAUNCHED(ctx);
+  const size_t sh = 2 * (size_t)nmax * sizeof(float);
+  if (sh > 48 * 1024) CSS_CU(ctx, cudaFuncSetAttribute(k_bisect32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+  k_bisect32<<<nc, 256, sh, st>>>(b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm);
+  CSS_LAUNCHED(ctx);
+  k_inviter<<<nc, 128, 0, st>>>(b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm, 1e-4, a.U, a.F, a.lam, a.status);
+  CSS_LAUNCHED(ctx);
+  dim3 g((unsigned)css_ceil_div(nmax, 128), (unsigned)nc);
+  k_ritz_y<<<g, 128, 64 * b * sizeof(double), st>>>(b, b, nmax, a.nblk, a.U, a.X0, a.Y, a.wgt);
+  CSS_LAUNCHED(ctx);
+  return CSS_OK;
+}
+
+css_status css_eigen_z(css_ctx* ctx, const EigArgs& a, const int32_t* sys_of_colour, const double* mu,
+                       const double* kT, double* Z, cudaStream_t st) {
+  const int32_t nc = a.n_col, b = a.b, nmax = a.m * b;
+  dim3 g((unsigned)css_ceil_div(nmax, 128), (unsigned)nc);
+  k_zt<<<g, 128, 64 * b * sizeof(double), st>>>(b, b, nmax, a.nblk, sys_of_colour, mu, kT, a.U, a.lam, a.Y, Z);
+  CSS_LAUNCHED(ctx);
+  k_apply_refl<false><<<nc, 1024, 0, st>>>(b, b, nmax, a.rcap, a.nblk, a.RV, a.RT, a.RR0, a.sweep_off, Z);
+  CSS_LAUNCHED(ctx);
+  return CSS_OK;
+}

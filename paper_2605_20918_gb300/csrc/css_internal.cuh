@@ -1,0 +1,80 @@
+// Internal declarations shared by the CUDA translation units of the CSS library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "css.h"
+
+#define CSS_MAX_B 32
+
+// ---------------------------------------------------------------- error handling
+#define CSS_TRY(expr)                       \
+  do {                                      \
+    css_status _st = (expr);                \
+    if (_st != CSS_OK) return _st;          \
+  } while (0)
+
+#define CSS_CU(ctx, call)                                                             \
+  do {                                                                                \
+    cudaError_t _e = (call);                                                          \
+    if (_e != cudaSuccess) return css_set_cuda_error((ctx), _e, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define CSS_LAUNCHED(ctx) CSS_CU(ctx, cudaGetLastError())
+
+struct css_buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct css_ctx {
+  int device = 0;
+  int n_sm = 0;
+  bool timing = false;
+  std::string last_error;
+  css_info info{};
+  // named, grow-only device workspace
+  std::vector<std::pair<std::string, css_buf>> bufs;
+  int64_t ws_bytes = 0;
+  // pinned host staging for scalars read back at the end of a call
+  void* host_pinned = nullptr;
+  size_t host_pinned_bytes = 0;
+};
+
+css_status css_set_cuda_error(css_ctx* ctx, cudaError_t e, const char* what, const char* file, int line);
+css_status css_set_arg_error(css_ctx* ctx, const char* what);
+// Device buffer `name` with at least `bytes` bytes (grow-only; contents not preserved on growth).
+css_status css_ws(css_ctx* ctx, const char* name, size_t bytes, void** out);
+css_status css_pinned(css_ctx* ctx, size_t bytes, void** out);
+
+// SplitMix64 output for state seed + (x + 1) * gamma (Steele, Lea & Flood 2014).
+__host__ __device__ __forceinline__ uint64_t css_splitmix64(uint64_t seed, uint64_t x) {
+  uint64_t z = seed + (x + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ int64_t css_ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ----------------------------------------------------------- internal entry points
+// colouring (css_color.cu)
+css_status css_color_impl(css_ctx* ctx, int32_t n, const double* xyz, double box, double r_col, uint64_t seed,
+                          const int32_t* adj_ptr_in, const int32_t* adj_in, int32_t* colour, int32_t* n_colours,
+                          cudaStream_t st);
+// density (css_density.cu)
+struct css_sys_desc {
+  css_bsr H;
+  const int32_t* colour;
+  const int8_t* sign;
+  int32_t n_colours;
+  css_fermi fermi;
+  double* P_val;
+};
+css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys, int32_t m, css_precision prec,
+                            uint32_t flags, double* trP, double* trPH, double* mu_out, cudaStream_t st);

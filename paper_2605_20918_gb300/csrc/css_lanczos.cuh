@@ -1,0 +1,40 @@
+// Host-side interface of the block-Lanczos pass (css_lanczos.cu).
+#pragma once
+#include "css_internal.cuh"
+
+struct LzArgs {
+  bool fp32 = false;                 // Krylov vectors and H*V in FP32 (else FP64)
+  int32_t n_brow = 0, b = 0, m = 0;  // molecules, block width, block steps
+  int32_t w = 0, ws = 0;             // columns of the batch (b * ncb) and row stride
+  const int32_t* row_ptr = nullptr;
+  const int32_t* col_idx = nullptr;
+  const void* Hval = nullptr;        // [nnzb][b][b] in the vector precision
+  int32_t max_row_blocks = 0;        // largest block count of a row
+  const int32_t* colour = nullptr;   // global colour of each molecule
+  const int8_t* sign = nullptr;      // probe signs [n_brow * b]
+  const double* inv_sqrt_cnt = nullptr;  // 1/sqrt|c| per global colour
+  int32_t cb0 = 0, ncb = 0;          // batch = global colours [cb0, cb0 + ncb)
+  void *Q0 = nullptr, *Q1 = nullptr, *W = nullptr;  // N x ws vectors
+  double* Ablk = nullptr;            // [colour][m][b][b] projected diagonal blocks
+  double* Bblk = nullptr;            // [colour][m][b][b] projected sub-diagonal blocks (upper)
+  double* Bblk_prev = nullptr;       // [colour][b][b] scratch: B_{j-1} of the running step
+  int32_t* nblk = nullptr;           // [colour] blocks used (m unless breakdown)
+  int32_t* done = nullptr;           // [colour] recurrence stopped
+  double* part = nullptr;            // per-chunk partial products
+  double* small = nullptr;           // per-colour small matrices of the batch
+  double tau = 1e-10;                // breakdown threshold relative to ||H Q_j||_F
+  uint32_t flags = 0;
+  int mode = 0;                      // 0 none, 1 store sampled rows into Qs, 2 accumulate X
+  void* Qs = nullptr;                // [pair][m][b][b] in the vector precision
+  double* X = nullptr;               // [pair][b][b]
+  const double* Z = nullptr;         // [colour][ldz][b]
+  int32_t ldz = 0;
+  const int32_t* pair_I = nullptr;   // pairs sorted by colour
+  const int32_t* pair_c = nullptr;
+  const int64_t* pair_off_h = nullptr;  // host: first pair of each colour (n_colours + 1)
+  cudaEvent_t* ev_spmm = nullptr;    // when set: 2 events per step bracket each H*V launch
+};
+
+css_status css_lanczos_pass(css_ctx* ctx, const LzArgs& a, cudaStream_t st);
+size_t css_lanczos_part_doubles(int64_t N, int32_t b, int32_t ncb);
+size_t css_lanczos_small_doubles(int32_t b, int32_t ncb);

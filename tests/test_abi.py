@@ -1,0 +1,51 @@
+"""The CUDA library builds for sm_103a and exports every entry point declared in include/css.h.
+
+No compute call is made here (no GPU needed)."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2605_20918_gb300 import build
+    return build.build()
+
+
+def declared_symbols():
+    names = set()
+    for h in (ROOT / "include").glob("*.h"):
+        text = h.read_text()
+        names |= set(re.findall(r"CSS_API[^;(]*?\b(css_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for want in ("css_create", "css_destroy", "css_color", "css_color_graph", "css_probes", "css_density",
+                 "css_density_batch", "css_pbuild", "css_get_info", "css_status_str", "css_last_error"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(str(lib_path))
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu(lib_path):
+    lib = ctypes.CDLL(str(lib_path))
+    lib.css_status_str.restype = ctypes.c_char_p
+    lib.css_status_str.argtypes = [ctypes.c_int]
+    assert lib.css_status_str(0) == b"CSS_OK"
+    assert lib.css_status_str(6) == b"CSS_WARN_BREAKDOWN"
+
+
+def test_binding_refuses_missing_library(tmp_path):
+    import paper_2605_20918_gb300 as css
+    with pytest.raises(RuntimeError, match="not found"):
+        css.load_library(tmp_path / "nope.so")
