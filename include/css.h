@@ -80,10 +80,13 @@ typedef struct {
 } css_bsr;
 
 /* Fermi-Dirac occupation f(x) = 1/(1+exp((x-mu)/kT)) (paper, Eq. 1); kT = 0 is the step
- * function.  solve_mu != 0: mu is found by bisection so that the Ritz quadrature of Tr P
- * equals n_elec/2 (P per spin); otherwise `mu` is used as given. */
+ * function.  solve_mu != 0: mu is taken from the Ritz quadrature N(mu) = sum_c sum_k
+ * f(lambda_ck) w_ck of Tr P (P per spin): it is the midpoint of the set of mu where
+ * |N(mu) - n_elec/2| <= ne_tol (each end by bisection), i.e. the root for a metal and
+ * mid-gap for an insulator; ne_tol <= 0 selects 1e-6 * n_elec/2.  Otherwise `mu` is used
+ * as given. */
 typedef struct {
-  double mu, kT, n_elec;
+  double mu, kT, n_elec, ne_tol;
   int32_t solve_mu;
 } css_fermi;
 

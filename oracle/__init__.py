@@ -53,7 +53,7 @@ def _load():
         lib.css_ref_probes.argtypes = [p, i32, i32, u64, C.c_int, p]
         lib.css_ref_eigh.argtypes = [i32, p, p]
         lib.css_ref_lanczos.argtypes = [i32, i32, p, p, p, p, p, i32, i32, C.c_int, p, p, p]
-        lib.css_ref_density.argtypes = [i32, i32, i32, p, p, p, p, p, i32, f64, f64, f64, C.c_int, i32,
+        lib.css_ref_density.argtypes = [i32, i32, i32, p, p, p, p, p, i32, f64, f64, f64, f64, C.c_int, i32,
                                         C.c_int, p, i32, p, p, p, p, p]
         lib.css_ref_ritz.argtypes = [i32, i32, p, p, p, p, p, i32, i32, C.c_int, p, p, p]
         lib.css_ref_num_threads.restype = C.c_int
@@ -169,9 +169,11 @@ def ritz(H, colour, sign, n_colours: int, m: int, flags: int = 0):
 
 
 def density(H, colour, sign, n_colours: int, *, mu: float = 0.0, kT: float = 0.05, n_elec: float = 0.0,
-            solve_mu: bool = True, m: int = 30, flags: int = SYMMETRIZE, colour_subset=None, P_init=None):
+            solve_mu: bool = True, m: int = 30, flags: int = SYMMETRIZE, colour_subset=None, P_init=None,
+            ne_tol: float = 0.0):
     """CSS density matrix on H's pattern.
 
+    ne_tol: electron-count tolerance of the mu rule (<= 0: 1e-6 N_e/2).
     Returns dict(P=(nnzb, b, b), trP, trPH, mu, n_breakdown)."""
     colour = np.ascontiguousarray(colour, dtype=np.int32)
     sign = np.ascontiguousarray(sign, dtype=np.int8)
@@ -183,7 +185,7 @@ def density(H, colour, sign, n_colours: int, *, mu: float = 0.0, kT: float = 0.0
     vv = np.ascontiguousarray(H.val, dtype=np.float64)
     st = _load().css_ref_density(
         H.n_brow, H.b, H.nnzb, _ptr(rp), _ptr(ci), _ptr(vv), _ptr(colour), _ptr(sign), n_colours,
-        mu, kT, n_elec, int(bool(solve_mu)), m, flags, _ptr(sub), 0 if sub is None else sub.shape[0],
+        mu, kT, n_elec, ne_tol, int(bool(solve_mu)), m, flags, _ptr(sub), 0 if sub is None else sub.shape[0],
         _ptr(P), _ptr(out[0:1]), _ptr(out[1:2]), _ptr(out[2:3]), _ptr(nb))
     _chk(st, "density")
     return {"P": P, "trP": float(out[0]), "trPH": float(out[1]), "mu": float(out[2]),

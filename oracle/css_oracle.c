@@ -24,9 +24,11 @@
  *     h = SplitMix64 (Steele, Lea & Flood 2014);
  *   - probe signs s[J*b+k] = -1 if bit 0 of h(sign_seed, J*b+k) is set, else +1;
  *   - Fermi-Dirac f(x) = (1 - tanh((x - mu) / (2 kT))) / 2, step function at kT = 0;
- *   - mu by bisection of sum_c sum_j f(lambda_cj) w_cj = N_e / 2 on
- *     [min lambda - 1, max lambda + 1], stop when hi - lo <= 1e-13 max(1, |mid|) or after
- *     200 halvings, mu = midpoint of the last bracket;
+ *   - mu: the Ritz quadrature N(mu) = sum_c sum_j f(lambda_cj) w_cj of Tr P must match N_e/2;
+ *     mu is the midpoint of the set where |N(mu) - N_e/2| <= ne_tol (default 1e-6 N_e/2),
+ *     each end found by bisection on [min lambda - 1, max lambda + 1] until
+ *     hi - lo <= 1e-13 max(1, |mid|) or 200 halvings (mid-gap for an insulator, the root for
+ *     a metal; the paper works at T = 0 and does not state how mu is fixed);
  *   - breakdown: stop the colour's recurrence at step j when min_k R_kk of the QR of the
  *     new block is <= 1e-10 ||H Q_j||_F; its projected matrix then has j blocks;
  *   - no reorthogonalisation unless CSS_REF_REORTH_LOCAL (one more pass against Q_j, Q_j-1);
@@ -545,12 +547,13 @@ static int ref_colour_eigen(const ref_h* H, const int32_t* colour, const int8_t*
  * in the subset are written).  Returns REF_OK; *n_breakdown counts truncated colours. */
 int css_ref_density(int32_t n_brow, int32_t b, int32_t nnzb, const int32_t* row_ptr, const int32_t* col_idx,
                     const double* val, const int32_t* colour, const int8_t* sign, int32_t n_colours,
-                    double mu, double kT, double n_elec, int solve_mu, int32_t m, int flags,
+                    double mu, double kT, double n_elec, double ne_tol, int solve_mu, int32_t m, int flags,
                     const int32_t* colour_subset, int32_t n_subset, double* P_val, double* trP,
                     double* trPH, double* mu_out, int32_t* n_breakdown) {
   if (n_brow < 1 || b < 1 || m < 1 || n_colours < 1 || nnzb < n_brow || !P_val) return REF_ERR_ARG;
   if (colour_subset && solve_mu) return REF_ERR_ARG;
   if (kT < 0.0) return REF_ERR_ARG;
+  if (!(ne_tol > 0.0)) ne_tol = 1e-6 * fmax(1.0, 0.5 * n_elec);
   ref_h H = {n_brow, b, row_ptr, col_idx, val};
   const int64_t N = (int64_t)n_brow * b;
   const int32_t nmax = m * b;
@@ -583,29 +586,43 @@ int css_ref_density(int32_t n_brow, int32_t b, int32_t nnzb, const int32_t* row_
     free(U);
   }
   if (status != REF_OK) return status;
-  /* chemical potential by bisection on the Ritz quadrature of Tr P */
+  /* chemical potential from the Ritz quadrature N(mu) = sum_c sum_j f(lambda_cj; mu) w_cj:
+   * mu is the midpoint of the interval where |N(mu) - N_e/2| <= ne_tol, found by two
+   * bisections (lower end: smallest mu with N - N_e/2 >= -ne_tol; upper end: largest mu with
+   * N - N_e/2 <= +ne_tol).  For a metal both ends meet at the root; for an insulator the
+   * interval is the gap and mu lands mid-gap instead of at a band edge. */
   if (solve_mu) {
-    double lo = INFINITY, hi = -INFINITY;
+    double lo0 = INFINITY, hi0 = -INFINITY;
     for (int32_t t = 0; t < nwork; ++t)
       for (int32_t j = 0; j < nj[t]; ++j) {
         double x = lam[(size_t)t * nmax + j];
-        if (x < lo) lo = x;
-        if (x > hi) hi = x;
+        if (x < lo0) lo0 = x;
+        if (x > hi0) hi0 = x;
       }
-    lo -= 1.0;
-    hi += 1.0;
-    for (int it = 0; it < 200; ++it) {
-      double mid = 0.5 * (lo + hi);
-      double g = 0.0;
-      for (int32_t t = 0; t < nwork; ++t)
-        for (int32_t j = 0; j < nj[t]; ++j)
-          g += ref_fermi(lam[(size_t)t * nmax + j], mid, kT) * wgt[(size_t)t * nmax + j];
-      g -= 0.5 * n_elec;
-      if (g > 0.0) hi = mid;
-      else lo = mid;
-      if (hi - lo <= 1e-13 * fmax(1.0, fabs(mid))) break;
+    lo0 -= 1.0;
+    hi0 += 1.0;
+    double ends[2];
+    for (int side = 0; side < 2; ++side) {
+      double lo = lo0, hi = hi0;
+      for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        double g = 0.0;
+        for (int32_t t = 0; t < nwork; ++t)
+          for (int32_t j = 0; j < nj[t]; ++j)
+            g += ref_fermi(lam[(size_t)t * nmax + j], mid, kT) * wgt[(size_t)t * nmax + j];
+        g -= 0.5 * n_elec;
+        if (side == 0) {
+          if (g >= -ne_tol) hi = mid;
+          else lo = mid;
+        } else {
+          if (g <= ne_tol) lo = mid;
+          else hi = mid;
+        }
+        if (hi - lo <= 1e-13 * fmax(1.0, fabs(mid))) break;
+      }
+      ends[side] = 0.5 * (lo + hi);
     }
-    mu = 0.5 * (lo + hi);
+    mu = 0.5 * (ends[0] + ends[1]);
   }
   if (mu_out) *mu_out = mu;
   /* pass 2: rebuild each colour's basis, X_c = Q_c Z_c with Z_c = U f(Lambda) U^T E_1 B_0,

@@ -45,7 +45,8 @@ class _BSR(C.Structure):
 
 
 class _Fermi(C.Structure):
-    _fields_ = [("mu", C.c_double), ("kT", C.c_double), ("n_elec", C.c_double), ("solve_mu", C.c_int32)]
+    _fields_ = [("mu", C.c_double), ("kT", C.c_double), ("n_elec", C.c_double), ("ne_tol", C.c_double),
+                ("solve_mu", C.c_int32)]
 
 
 class _Info(C.Structure):
@@ -211,17 +212,17 @@ def css_probes(ctx, colour, b: int, sign_seed: int, sign, flags: int = 0, stream
            "css_probes")
 
 
-def _fermi(mu, kT, n_elec, solve_mu):
-    return _Fermi(float(mu), float(kT), float(n_elec), 1 if solve_mu else 0)
+def _fermi(mu, kT, n_elec, solve_mu, ne_tol=0.0):
+    return _Fermi(float(mu), float(kT), float(n_elec), float(ne_tol), 1 if solve_mu else 0)
 
 
 def css_density(ctx, H: DeviceBSR, colour, sign, n_colours: int, P, *, mu=0.0, kT=0.05, n_elec=0.0,
-                solve_mu=True, m=30, precision=CSS_FP64, flags=CSS_SYMMETRIZE, stream=None) -> dict:
+                solve_mu=True, ne_tol=0.0, m=30, precision=CSS_FP64, flags=CSS_SYMMETRIZE, stream=None) -> dict:
     """CSS density matrix on H's pattern into P (device float64 [nnzb, b, b])."""
     torch = _torch()
     lib = load_library()
     hb = H._c()
-    f = _fermi(mu, kT, n_elec, solve_mu)
+    f = _fermi(mu, kT, n_elec, solve_mu, ne_tol)
     tp, tph, mo = C.c_double(), C.c_double(), C.c_double()
     st = _check(lib, ctx, lib.css_density(ctx, C.byref(hb), _dev(colour, torch.int32, "colour"),
                                           _dev(sign, torch.int8, "sign"), int(n_colours), C.byref(f), int(m),
@@ -240,8 +241,8 @@ def css_density_batch(ctx, Hs, colours, signs, n_colours, Ps, fermis, *, m=30, p
     cp = (C.c_void_p * n)(*[_dev(c, torch.int32, "colour") for c in colours])
     sp = (C.c_void_p * n)(*[_dev(s, torch.int8, "sign") for s in signs])
     nc = (C.c_int32 * n)(*[int(x) for x in n_colours])
-    fr = (_Fermi * n)(*[_fermi(f.get("mu", 0.0), f.get("kT", 0.05), f.get("n_elec", 0.0), f.get("solve_mu", True))
-                        for f in fermis])
+    fr = (_Fermi * n)(*[_fermi(f.get("mu", 0.0), f.get("kT", 0.05), f.get("n_elec", 0.0), f.get("solve_mu", True),
+                               f.get("ne_tol", 0.0)) for f in fermis])
     pp = (C.c_void_p * n)(*[_dev(p, torch.float64, "P") for p in Ps])
     tp, tph, mo = (C.c_double * n)(), (C.c_double * n)(), (C.c_double * n)()
     st = _check(lib, ctx, lib.css_density_batch(ctx, n, hb, cp, sp, nc, fr, int(m), int(precision), int(flags), pp,
@@ -250,7 +251,7 @@ def css_density_batch(ctx, Hs, colours, signs, n_colours, Ps, fermis, *, m=30, p
 
 
 def css_pbuild(ctx, xyz, box, H, P, *, r_col, colour_seed=1004, sign_seed=1005, mu=0.0, kT=0.05, n_elec=0.0,
-               solve_mu=True, m=30, precision=CSS_FP64, flags=CSS_SYMMETRIZE, colour_out=None, stream=None) -> dict:
+               solve_mu=True, ne_tol=0.0, m=30, precision=CSS_FP64, flags=CSS_SYMMETRIZE, colour_out=None, stream=None) -> dict:
     """Whole P build.  With CSS_HOST_IO in flags, xyz / H (synth.BSR) / P / colour_out are host
     numpy arrays and the copies happen inside the call; otherwise torch CUDA tensors."""
     lib = load_library()
@@ -274,7 +275,7 @@ def css_pbuild(ctx, xyz, box, H, P, *, r_col, colour_seed=1004, sign_seed=1005, 
         pp = _dev(P, torch.float64, "P")
         cop = _dev(colour_out, torch.int32, "colour_out") if colour_out is not None else C.c_void_p(0)
         keep = ()
-    f = _fermi(mu, kT, n_elec, solve_mu)
+    f = _fermi(mu, kT, n_elec, solve_mu, ne_tol)
     nc = C.c_int32()
     tp, tph, mo = C.c_double(), C.c_double(), C.c_double()
     st = _check(lib, ctx, lib.css_pbuild(ctx, C.byref(g), C.byref(hb), float(r_col), C.c_uint64(colour_seed),

@@ -151,6 +151,11 @@ css_status css_scan_i32(css_ctx* ctx, const int32_t* in, int32_t* out, int64_t n
     return CSS_OK;
   }
   int64_t nb = css_ceil_div(n, 1024);
+  if (nb == 1) {  // one block: its total is the grand total
+    k_scan_block<<<1, 1024, 0, st>>>(in, out, n, out + n);
+    CSS_LAUNCHED(ctx);
+    return CSS_OK;
+  }
   char name[32];
   snprintf(name, sizeof(name), "scan_sums_%d", depth);
   int32_t* sums = nullptr;

@@ -152,6 +152,18 @@ __global__ void k_to_f32(int64_t n, const double* __restrict__ src, float* __res
   if (i < n) dst[i] = (float)src[i];
 }
 
+// FP32 remainder of every diagonal block: lo = fl32(H_II - fl32(H_II))
+__global__ void k_diag_lo(int32_t n_brow, int32_t bb, const int32_t* __restrict__ row_ptr,
+                          const int32_t* __restrict__ col_idx, const double* __restrict__ src, float* __restrict__ lo) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n_brow * bb) return;
+  const int32_t I = (int32_t)(t / bb), e = (int32_t)(t % bb);
+  int32_t k = row_ptr[I];
+  while (k < row_ptr[I + 1] && col_idx[k] != I) ++k;
+  const double h = src[(size_t)k * bb + e];
+  lo[t] = (float)(h - (double)(float)h);
+}
+
 // ----------------------------------------------------------- chemical potential
 // Bounded grid barrier (generation counter): every wait gives up after ~2^24 polls, sets
 // *err and returns false, so the kernel always terminates.
@@ -186,23 +198,27 @@ __device__ bool grid_sync(unsigned* count, unsigned* gen, unsigned nb, int32_t* 
 }
 
 constexpr int MU_T = 256;
-constexpr int MU_MAXSYS = 1024;
+constexpr int MU_MAXSYS = 512;
 
-// Bisection of g_s(mu) = sum_{c in s} sum_k f(lam_ck; mu) w_ck - N_e,s / 2 for every system
-// s at once (one persistent cooperative launch).  Each CTA sums a fixed range of colours in
-// a fixed order; all CTAs then reduce the per-CTA partials in the same order, so every CTA
-// holds identical brackets and the result is deterministic.
+// Chemical potential of every system s from its Ritz quadrature
+//     g_s(mu) = sum_{c in s} sum_k f(lam_ck; mu) w_ck - N_e,s / 2:
+// mu_s is the midpoint of {mu : |g_s(mu)| <= tol_s}; its lower end (smallest mu with
+// g >= -tol) and upper end (largest mu with g <= +tol) are bisected together in one
+// persistent cooperative launch.  Each CTA sums a fixed range of colours in a fixed order;
+// all CTAs then reduce the per-CTA partials in the same order, so every CTA holds identical
+// brackets and the result is deterministic.
 __global__ void __launch_bounds__(MU_T) k_mu(int32_t n_sys, int32_t n_col, int32_t nmax, const int32_t* __restrict__ nblk,
                                              int32_t b, const int32_t* __restrict__ sys_of_colour,
                                              const double* __restrict__ lam, const double* __restrict__ wgt,
                                              const double* __restrict__ kT, const double* __restrict__ half_ne,
-                                             const int32_t* __restrict__ solve, const double* __restrict__ mu_in,
-                                             double* __restrict__ mu_out, double* __restrict__ part,
-                                             unsigned* __restrict__ bar, int32_t* __restrict__ err) {
-  __shared__ double acc[MU_MAXSYS];
-  __shared__ double lo[MU_MAXSYS], hi[MU_MAXSYS];
+                                             const double* __restrict__ tol, const int32_t* __restrict__ solve,
+                                             const double* __restrict__ mu_in, double* __restrict__ mu_out,
+                                             double* __restrict__ part, unsigned* __restrict__ bar,
+                                             int32_t* __restrict__ err) {
+  __shared__ double acc[2][MU_MAXSYS];
+  __shared__ double lo[2][MU_MAXSYS], hi[2][MU_MAXSYS];
   __shared__ int conv[MU_MAXSYS];
-  __shared__ double red[MU_T / 32];
+  __shared__ double red[2][MU_T / 32];
   __shared__ int all_done;
   const unsigned G = gridDim.x;
   const int32_t per = (int32_t)((n_col + G - 1) / G);
@@ -210,8 +226,8 @@ __global__ void __launch_bounds__(MU_T) k_mu(int32_t n_sys, int32_t n_col, int32
   double* pbuf[2] = {part, part + (size_t)2 * n_sys * G};
   // phase 0: spectrum bounds per system
   for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) {
-    lo[s] = 1e300;
-    hi[s] = -1e300;
+    lo[0][s] = 1e300;
+    hi[0][s] = -1e300;
   }
   __syncthreads();
   for (int32_t c = c0; c < c1; ++c) {
@@ -226,26 +242,26 @@ __global__ void __launch_bounds__(MU_T) k_mu(int32_t n_sys, int32_t n_col, int32
       mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
       mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     }
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mn;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 1e300;
-      for (int i = 0; i < MU_T / 32; ++i) t = fmin(t, red[i]);
-      lo[sys_of_colour[c]] = fmin(lo[sys_of_colour[c]], t);
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = mn;
+      red[1][threadIdx.x >> 5] = mx;
     }
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-    __syncthreads();
     if (threadIdx.x == 0) {
-      double t = -1e300;
-      for (int i = 0; i < MU_T / 32; ++i) t = fmax(t, red[i]);
-      hi[sys_of_colour[c]] = fmax(hi[sys_of_colour[c]], t);
+      double t0 = 1e300, t1 = -1e300;
+      for (int i = 0; i < MU_T / 32; ++i) {
+        t0 = fmin(t0, red[0][i]);
+        t1 = fmax(t1, red[1][i]);
+      }
+      const int32_t s = sys_of_colour[c];
+      lo[0][s] = fmin(lo[0][s], t0);
+      hi[0][s] = fmax(hi[0][s], t1);
     }
     __syncthreads();
   }
   for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) {
-    pbuf[0][(size_t)s * G + blockIdx.x] = lo[s];
-    pbuf[0][(size_t)(n_sys + s) * G + blockIdx.x] = hi[s];
+    pbuf[0][(size_t)s * G + blockIdx.x] = lo[0][s];
+    pbuf[0][(size_t)(n_sys + s) * G + blockIdx.x] = hi[0][s];
   }
   if (!grid_sync(bar, bar + 1, G, err)) return;
   for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) {
@@ -254,54 +270,79 @@ __global__ void __launch_bounds__(MU_T) k_mu(int32_t n_sys, int32_t n_col, int32
       a = fmin(a, __ldcg(&pbuf[0][(size_t)s * G + g]));
       z = fmax(z, __ldcg(&pbuf[0][(size_t)(n_sys + s) * G + g]));
     }
-    lo[s] = a - 1.0;
-    hi[s] = z + 1.0;
+    lo[0][s] = lo[1][s] = a - 1.0;
+    hi[0][s] = hi[1][s] = z + 1.0;
     conv[s] = solve[s] ? 0 : 1;
   }
   __syncthreads();
   for (int it = 0; it < 200; ++it) {
-    for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) acc[s] = 0.0;
+    for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) acc[0][s] = acc[1][s] = 0.0;
     __syncthreads();
     for (int32_t c = c0; c < c1; ++c) {
       const int32_t s = sys_of_colour[c];
       if (conv[s]) continue;
-      const double mid = 0.5 * (lo[s] + hi[s]);
+      const double m0 = 0.5 * (lo[0][s] + hi[0][s]), m1 = 0.5 * (lo[1][s] + hi[1][s]);
       const double t_ = kT[s];
       const int32_t n = nblk[c] * b;
-      double v = 0.0;
-      for (int32_t k = threadIdx.x; k < n; k += blockDim.x)
-        v += css_fermi_dirac(lam[(size_t)c * nmax + k], mid, t_) * wgt[(size_t)c * nmax + k];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+      double v0 = 0.0, v1 = 0.0;
+      for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
+        const double x = lam[(size_t)c * nmax + k], w = wgt[(size_t)c * nmax + k];
+        v0 += css_fermi_dirac(x, m0, t_) * w;
+        v1 += css_fermi_dirac(x, m1, t_) * w;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+      }
+      if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = v0;
+        red[1][threadIdx.x >> 5] = v1;
+      }
       __syncthreads();
       if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < MU_T / 32; ++i) t += red[i];
-        acc[s] += t;
+        double t0 = 0.0, t1 = 0.0;
+        for (int i = 0; i < MU_T / 32; ++i) {
+          t0 += red[0][i];
+          t1 += red[1][i];
+        }
+        acc[0][s] += t0;
+        acc[1][s] += t1;
       }
       __syncthreads();
     }
     double* pb = pbuf[(it + 1) & 1];
-    for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) pb[(size_t)s * G + blockIdx.x] = acc[s];
+    for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) {
+      pb[(size_t)s * G + blockIdx.x] = acc[0][s];
+      pb[(size_t)(n_sys + s) * G + blockIdx.x] = acc[1][s];
+    }
     if (!grid_sync(bar, bar + 1, G, err)) return;
     if (threadIdx.x == 0) all_done = 1;
     __syncthreads();
     for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) {
       if (conv[s]) continue;
-      double g = 0.0;
-      for (unsigned q = 0; q < G; ++q) g += __ldcg(&pb[(size_t)s * G + q]);
-      g -= half_ne[s];
-      const double mid = 0.5 * (lo[s] + hi[s]);
-      if (g > 0.0) hi[s] = mid;
-      else lo[s] = mid;
-      if (hi[s] - lo[s] <= 1e-13 * fmax(1.0, fabs(mid))) conv[s] = 1;
+      double g0 = 0.0, g1 = 0.0;
+      for (unsigned q = 0; q < G; ++q) {
+        g0 += __ldcg(&pb[(size_t)s * G + q]);
+        g1 += __ldcg(&pb[(size_t)(n_sys + s) * G + q]);
+      }
+      g0 -= half_ne[s];
+      g1 -= half_ne[s];
+      const double m0 = 0.5 * (lo[0][s] + hi[0][s]), m1 = 0.5 * (lo[1][s] + hi[1][s]);
+      if (g0 >= -tol[s]) hi[0][s] = m0;
+      else lo[0][s] = m0;
+      if (g1 <= tol[s]) lo[1][s] = m1;
+      else hi[1][s] = m1;
+      const bool d0 = hi[0][s] - lo[0][s] <= 1e-13 * fmax(1.0, fabs(m0));
+      const bool d1 = hi[1][s] - lo[1][s] <= 1e-13 * fmax(1.0, fabs(m1));
+      if (d0 && d1) conv[s] = 1;
       else all_done = 0;
     }
     __syncthreads();
     if (all_done) break;
   }
   if (blockIdx.x == 0)
-    for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) mu_out[s] = solve[s] ? 0.5 * (lo[s] + hi[s]) : mu_in[s];
+    for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x)
+      mu_out[s] = solve[s] ? 0.5 * (0.5 * (lo[0][s] + hi[0][s]) + 0.5 * (lo[1][s] + hi[1][s])) : mu_in[s];
 }
 
 // --------------------------------------------------------- reconstruction on pairs
@@ -464,7 +505,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
         !d.sign || !d.P_val || d.n_colours < 1)
       return css_set_arg_error(ctx, "css_density: bad H, colour, sign or P_val argument");
     if (!(d.fermi.kT >= 0.0) || !std::isfinite(d.fermi.kT) || !std::isfinite(d.fermi.mu) ||
-        !std::isfinite(d.fermi.n_elec))
+        !std::isfinite(d.fermi.n_elec) || !std::isfinite(d.fermi.ne_tol))
       return css_set_arg_error(ctx, "css_density: kT must be finite and >= 0, mu and n_elec finite");
     nb_tot += d.H.n_brow;
     nnz_tot += d.H.nnzb;
@@ -605,12 +646,18 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     for (int32_t c = 0; c <= n_col; ++c) pair_off_h[c] = hb[c];
   }
   const void* Hv = Hval;
+  const void* Hlo = nullptr;
   if (f32) {
     float* hf;
     CSS_TRY(ws_get(ctx, "h_f32", (size_t)nnzb * bb, &hf));
     k_to_f32<<<(unsigned)css_ceil_div((int64_t)nnzb * bb, T), T, 0, st>>>((int64_t)nnzb * bb, Hval, hf);
     CSS_LAUNCHED(ctx);
     Hv = hf;
+    float* hlo;
+    CSS_TRY(ws_get(ctx, "h_lo", (size_t)n_brow * bb, &hlo));
+    k_diag_lo<<<(unsigned)css_ceil_div((int64_t)n_brow * bb, T), T, 0, st>>>(n_brow, bb, row_ptr, col_idx, Hval, hlo);
+    CSS_LAUNCHED(ctx);
+    Hlo = hlo;
   }
   tm.mark();  // 1
 
@@ -678,6 +725,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   la.row_ptr = row_ptr;
   la.col_idx = col_idx;
   la.Hval = Hv;
+  la.Hlo_diag = Hlo;
   la.max_row_blocks = max_row;
   la.colour = colour;
   la.sign = sign;
@@ -736,24 +784,28 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   // ---------------------------------------------------------- eigen + mu + Z
   CSS_TRY(css_eigen_ritz(ctx, ea, st));
   tm.mark();  // 3
-  double *dmu, *dkT, *dhalf, *dmu_in, *mupart;
+  double *dmu, *dkT, *dhalf, *dmu_in, *dtol, *mupart;
   int32_t* dsolve;
   unsigned* bar;
   CSS_TRY(ws_get(ctx, "mu", n_sys, &dmu));
   CSS_TRY(ws_get(ctx, "kT", n_sys, &dkT));
   CSS_TRY(ws_get(ctx, "half_ne", n_sys, &dhalf));
   CSS_TRY(ws_get(ctx, "mu_in", n_sys, &dmu_in));
+  CSS_TRY(ws_get(ctx, "ne_tol", n_sys, &dtol));
   CSS_TRY(ws_get(ctx, "solve", n_sys, &dsolve));
   CSS_TRY(ws_get(ctx, "bar", 8, &bar));
   {
     double* hp;
-    CSS_TRY(css_pinned(ctx, sizeof(double) * 4 * n_sys + 256, (void**)&hp));
+    CSS_TRY(css_pinned(ctx, sizeof(double) * 5 * n_sys + 256, (void**)&hp));
     for (int32_t s = 0; s < n_sys; ++s) {
       hp[s] = sys[s].fermi.kT;
       hp[n_sys + s] = 0.5 * sys[s].fermi.n_elec;
       hp[2 * n_sys + s] = sys[s].fermi.mu;
       ((int32_t*)(hp + 3 * n_sys))[s] = sys[s].fermi.solve_mu ? 1 : 0;
+      const double tl = sys[s].fermi.ne_tol;
+      hp[4 * n_sys + s] = tl > 0.0 ? tl : 1e-6 * std::max(1.0, 0.5 * sys[s].fermi.n_elec);
     }
+    CSS_CU(ctx, cudaMemcpyAsync(dtol, hp + 4 * n_sys, sizeof(double) * n_sys, cudaMemcpyHostToDevice, st));
     CSS_CU(ctx, cudaMemcpyAsync(dkT, hp, sizeof(double) * n_sys, cudaMemcpyHostToDevice, st));
     CSS_CU(ctx, cudaMemcpyAsync(dhalf, hp + n_sys, sizeof(double) * n_sys, cudaMemcpyHostToDevice, st));
     CSS_CU(ctx, cudaMemcpyAsync(dmu_in, hp + 2 * n_sys, sizeof(double) * n_sys, cudaMemcpyHostToDevice, st));
@@ -765,7 +817,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   CSS_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mu, MU_T, 0));
   unsigned G = (unsigned)std::max(1, std::min(ctx->n_sm * std::max(occ, 1), std::max(n_col, 1)));
   if (G > (unsigned)ctx->n_sm) G = (unsigned)ctx->n_sm;
-  CSS_TRY(ws_get(ctx, "mu_part", (size_t)4 * n_sys * G + 16, &mupart));
+  CSS_TRY(ws_get(ctx, "mu_part", (size_t)4 * n_sys * G + 16, &mupart));  // two buffers of [2][n_sys][G]
   {
     int32_t n_sys_ = n_sys, n_col_ = n_col, nmax_ = nmax, b_ = b;
     const int32_t* nblk_ = nblk;
@@ -774,13 +826,14 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     const double* w_ = ea.wgt;
     const double* kT_ = dkT;
     const double* h_ = dhalf;
+    const double* tl_ = dtol;
     const int32_t* sv_ = dsolve;
     const double* mi_ = dmu_in;
     double* mo_ = dmu;
     double* pp_ = mupart;
     unsigned* bar_ = bar;
     int32_t* err_ = misc + 8;
-    void* args[] = {&n_sys_, &n_col_, &nmax_, &nblk_, &b_, &soc_, &lam_, &w_, &kT_, &h_, &sv_, &mi_, &mo_, &pp_,
+    void* args[] = {&n_sys_, &n_col_, &nmax_, &nblk_, &b_, &soc_, &lam_, &w_, &kT_, &h_, &tl_, &sv_, &mi_, &mo_, &pp_,
                     &bar_, &err_};
     CSS_CU(ctx, cudaLaunchCooperativeKernel((void*)k_mu, dim3(G), dim3(MU_T), args, 0, st));
   }

@@ -23,7 +23,7 @@ template <typename T, int BM, int TC>
 __global__ void __launch_bounds__(128) k_spmm(int32_t b, const int32_t* __restrict__ row_ptr,
                                               const int32_t* __restrict__ col_idx, const T* __restrict__ Hv,
                                               const T* __restrict__ V, T* __restrict__ W, int32_t ws, int32_t w,
-                                              int32_t chunk) {
+                                              int32_t chunk, const T* __restrict__ Hlo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Hs = reinterpret_cast<T*>(smem_raw);
   const int32_t I = blockIdx.x;
@@ -64,6 +64,32 @@ __global__ void __launch_bounds__(128) k_spmm(int32_t b, const int32_t* __restri
           for (int u = 0; u < TC; ++u) acc[a][u] = fma(h, v[k][u], acc[a][u]);
         }
     }
+  }
+  if (Hlo) {
+    // low part of the diagonal block (FP32 mode: H_II = hi + lo, both FP32), W_I += lo V_I
+    __syncthreads();
+    for (int32_t e = threadIdx.x; e < BM * BM; e += blockDim.x) {
+      int32_t a = e / BM, k = e % BM;
+      Hs[e] = (a < b && k < b) ? Hlo[(size_t)I * bb + a * b + k] : T(0);
+    }
+    __syncthreads();
+    const T* Vr = V + (size_t)I * b * ws;
+    T v[BM][TC];
+#pragma unroll
+    for (int k = 0; k < BM; ++k)
+#pragma unroll
+      for (int u = 0; u < TC; ++u) {
+        const int32_t col = col0 + 128 * u;
+        v[k][u] = (k < b && col < w) ? __ldg(Vr + (size_t)k * ws + col) : T(0);
+      }
+#pragma unroll
+    for (int a = 0; a < BM; ++a)
+#pragma unroll
+      for (int k = 0; k < BM; ++k) {
+        const T h = Hs[a * BM + k];
+#pragma unroll
+        for (int u = 0; u < TC; ++u) acc[a][u] = fma(h, v[k][u], acc[a][u]);
+      }
   }
   T* Wr = W + (size_t)I * b * ws;
 #pragma unroll
@@ -445,7 +471,8 @@ css_status launch_spmm_t(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaSt
   auto kern = k_spmm<T, BM, TC>;
   CSS_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((unsigned)a.n_brow, (unsigned)css_ceil_div(a.w, 128 * TC));
-  kern<<<grid, 128, smem, st>>>(a.b, a.row_ptr, a.col_idx, (const T*)a.Hval, V, W, a.ws, a.w, chunk);
+  kern<<<grid, 128, smem, st>>>(a.b, a.row_ptr, a.col_idx, (const T*)a.Hval, V, W, a.ws, a.w, chunk,
+                                (const T*)a.Hlo_diag);
   CSS_LAUNCHED(ctx);
   return CSS_OK;
 }

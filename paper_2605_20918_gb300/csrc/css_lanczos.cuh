@@ -9,6 +9,7 @@ struct LzArgs {
   const int32_t* row_ptr = nullptr;
   const int32_t* col_idx = nullptr;
   const void* Hval = nullptr;        // [nnzb][b][b] in the vector precision
+  const void* Hlo_diag = nullptr;    // FP32 mode: [n_brow][b][b] low parts of the diagonal blocks
   int32_t max_row_blocks = 0;        // largest block count of a row
   const int32_t* colour = nullptr;   // global colour of each molecule
   const int8_t* sign = nullptr;      // probe signs [n_brow * b]

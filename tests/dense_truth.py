@@ -36,17 +36,26 @@ class Dense:
     def f(self, mu, kT):
         return (self.V * fermi(self.w, mu, kT)) @ self.V.T
 
-    def mu_exact(self, n_elec, kT):
-        """mu with Tr f(H) = N_e / 2."""
-        return so.brentq(lambda m: fermi(self.w, m, kT).sum() - 0.5 * n_elec,
-                         self.w.min() - 5, self.w.max() + 5, xtol=1e-15, rtol=1e-15, maxiter=500)
+    @staticmethod
+    def _mid_of_tolerance_set(g, lo, hi, ne_tol):
+        """Midpoint of {mu : |g(mu)| <= ne_tol} for increasing g (both ends by brentq)."""
+        a = so.brentq(lambda m: g(m) + ne_tol, lo, hi, xtol=1e-15, rtol=1e-15, maxiter=500)
+        z = so.brentq(lambda m: g(m) - ne_tol, lo, hi, xtol=1e-15, rtol=1e-15, maxiter=500)
+        return 0.5 * (a + z)
 
-    def mu_projected(self, R, n_elec, kT, n_colours, b):
-        """mu with sum_c tr(R_c^T f(H) R_c) = N_e / 2 (the quadrature the CSS method solves)."""
+    def mu_exact(self, n_elec, kT, ne_tol=None):
+        """mu with Tr f(H) = N_e / 2 (midpoint of the set matching it within ne_tol)."""
+        tol = 1e-6 * max(1.0, 0.5 * n_elec) if ne_tol is None else ne_tol
+        return self._mid_of_tolerance_set(lambda m: fermi(self.w, m, kT).sum() - 0.5 * n_elec,
+                                          self.w.min() - 5, self.w.max() + 5, tol)
+
+    def mu_projected(self, R, n_elec, kT, n_colours, b, ne_tol=None):
+        """mu for the quadrature sum_c tr(R_c^T f(H) R_c) = N_e / 2 the CSS method solves."""
         A = self.V.T @ R                         # eigenbasis components of every probe column
         wts = (A * A).sum(axis=1)                # sum over all probe columns
-        return so.brentq(lambda m: (fermi(self.w, m, kT) * wts).sum() - 0.5 * n_elec,
-                         self.w.min() - 5, self.w.max() + 5, xtol=1e-15, rtol=1e-15, maxiter=500)
+        tol = 1e-6 * max(1.0, 0.5 * n_elec) if ne_tol is None else ne_tol
+        return self._mid_of_tolerance_set(lambda m: (fermi(self.w, m, kT) * wts).sum() - 0.5 * n_elec,
+                                          self.w.min() - 5, self.w.max() + 5, tol)
 
     def on_pattern(self, M):
         """Blocks of a dense N x N matrix on H's pattern, (nnzb, b, b)."""

@@ -191,12 +191,14 @@ def test_bitwise_repeatable(torch, css, ctx):
 
 
 # ------------------------------------------------------------------------ mixed
-@pytest.mark.parametrize("n,kind,r_col,m", [(64, "minimal", 8.0, 30), (125, "dzp", 10.0, 8), (343, "minimal", 10.0, 20)])
-def test_density_mixed_within_tolerance(torch, css, ctx, n, kind, r_col, m):
+@pytest.mark.parametrize("n,kind,r_col,m,solve", [(64, "minimal", 8.0, 30, True), (343, "minimal", 10.0, 20, True),
+                                                   (125, "dzp", 10.0, 40, True), (125, "dzp", 10.0, 8, False)])
+def test_density_mixed_within_tolerance(torch, css, ctx, n, kind, r_col, m, solve):
     g, H, col, s, nc = _system(n, kind, r_col)
     ne = synth.n_electrons(n)
-    ref = oracle.density(H, col, s, nc, kT=0.05, n_elec=ne, m=m)
-    got = gpu_density(torch, css, ctx, H, col, s, nc, kT=0.05, n_elec=ne, m=m, precision=css.CSS_MIXED_FP32)
+    ref = oracle.density(H, col, s, nc, kT=0.05, n_elec=ne, m=m, mu=-4.0, solve_mu=solve)
+    got = gpu_density(torch, css, ctx, H, col, s, nc, kT=0.05, n_elec=ne, m=m, mu=-4.0, solve_mu=solve,
+                      precision=css.CSS_MIXED_FP32)
     dP = float(np.abs(got["P"] - ref["P"]).max())
     dE = abs(2 * got["trPH"] - 2 * ref["trPH"]) / n
     assert dP < MIXED_P_TOL, dP

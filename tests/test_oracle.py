@@ -235,7 +235,7 @@ def test_degenerate_colouring_full_krylov_is_f_of_H(O):
     dn = Dense(H)
     mu = dn.mu_exact(ne, 0.05)
     assert _pattern_err(r["P"], dn.on_pattern(dn.f(mu, 0.05))) < 1e-10
-    assert abs(r["trP"] - ne / 2) < 1e-9
+    assert abs(r["trP"] - ne / 2) <= 1e-6 * ne / 2
 
 
 def test_contaminated_projection_full_krylov(O):
@@ -257,7 +257,7 @@ def test_contaminated_projection_full_krylov(O):
     # symmetrisation leaves the traces unchanged
     assert abs(r["trP"] - r2["trP"]) < 1e-10 and abs(r["trPH"] - r2["trPH"]) < 1e-9
     # the traces against the dense truth
-    assert abs(r["trP"] - ne / 2) < 1e-9
+    assert abs(r["trP"] - ne / 2) <= 1e-6 * ne / 2
     assert abs(r2["trPH"] - float((Pt * H.val).sum())) < 1e-9
 
 
@@ -291,7 +291,7 @@ def test_zero_coupling_blocks(O):
             assert np.abs(r["P"][k] - ref).max() < 1e-11
         else:
             assert np.abs(r["P"][k]).max() < 1e-11
-    assert abs(r["trP"] - ne / 2) < 1e-9
+    assert abs(r["trP"] - ne / 2) <= 1e-6 * ne / 2
 
 
 def test_single_molecule(O):
@@ -303,7 +303,10 @@ def test_single_molecule(O):
     w, V = np.linalg.eigh(H.val[0])
     mu = r["mu"]
     assert np.abs(r["P"][0] - (V * fermi(w, mu, 0.05)) @ V.T).max() < 1e-11
-    assert abs(r["trP"] - 4.0) < 1e-9
+    assert abs(r["trP"] - 4.0) <= 4e-6
+    # the single molecule has a gap between levels 4 and 5: mu is its midpoint
+    lv = np.sort(w)
+    assert abs(mu - 0.5 * (lv[3] + lv[4])) < 0.3 * (lv[4] - lv[3])
 
 
 def test_two_level_closed_form(O):
@@ -338,7 +341,7 @@ def test_trace_identity_and_bisection(O):
     rz = O.ritz(H, col, s, nc, m=6)
     quad = sum(float((fermi(l, r["mu"], 0.05) * w).sum()) for l, w in rz)
     assert abs(r["trP"] - quad) < 1e-9
-    assert abs(quad - ne / 2) < 1e-6
+    assert abs(quad - ne / 2) <= 1e-6 * ne / 2 * (1 + 1e-9)
 
 
 def test_idempotent_as_kT_vanishes(O):
