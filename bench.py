@@ -1,0 +1,337 @@
+"""Benchmark: CSS density-matrix P build time per geometry, 10,000 water-like molecules.
+
+Workload (synthetic, seeded): 10,000 molecules in a 66.9 A periodic box, 23 orbitals per
+molecule (N = 230,000), 6 A coupling cut-off, colouring radius R_col = 10 A, block-Lanczos
+depth m = 40, Fermi-Dirac kT = 0.05 eV, mu from the Ritz quadrature of Tr P = N_e/2; an
+MD-like sequence of 20 geometries (Gaussian steps of 0.02 A) with H rebuilt per geometry.
+One step = one P build = css_color + css_probes + css_density on the next geometry, with H
+and the positions already resident in HBM (H: 1.17 GB in FP64, larger than L2).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+                  [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank builds P for its own geometries (independent problems, no
+data-path collective); the time is the maximum over ranks and `value` is that time divided
+by the P builds of all ranks.  `--impl reference` times the CPU oracle on a bounded sample
+(one colour of the P build, both Lanczos passes, scaled to all colours) on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+FP32_PEAK_NOTE = "FP32 FFMA peak derived from 152 SMs x 128 lanes x 2 flop x 2070 MHz max SM clock"
+FP64_PEAK_NOTE = "FP64 peak: 1.25 TFLOP/s nominal GB300 FP64 rate"
+FP32_PEAK = 152 * 128 * 2 * 2070e6 / 1e12       # TFLOP/s
+FP64_PEAK = 1.25                                 # TFLOP/s
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--n-mol", type=int, default=10000)
+    ap.add_argument("--kind", default="dzp")
+    ap.add_argument("--m", type=int, default=40)
+    ap.add_argument("--r-col", type=float, default=10.0)
+    ap.add_argument("--geometries", type=int, default=20)
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(a):
+    return {"workload": f"CSS P build, {a.n_mol} water-like molecules, {23 if a.kind == 'dzp' else 6} orbitals "
+                        f"each, MD-like sequence of {a.geometries} geometries",
+            "n_mol": a.n_mol, "orbitals_per_molecule": 23 if a.kind == "dzp" else 6, "krylov_blocks_m": a.m,
+            "r_col_A": a.r_col, "coupling_cutoff_A": 6.0, "kT_eV": 0.05, "geometries": a.geometries,
+            "precision": a.precision, "l2": "inputs larger than L2 (H alone is 1.17 GB in FP64)"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def build_inputs(a, indices):
+    """Geometries of the MD-like sequence at `indices` (mod a.geometries) and their H."""
+    from paper_2605_20918_gb300 import synth
+    want = sorted({i % a.geometries for i in indices})
+    geoms, cache = {}, {}
+    for t, g in enumerate(synth.md_sequence(a.n_mol, max(want) + 1)):
+        if t in want:
+            geoms[t] = (g, synth.hamiltonian(g, a.kind, cache=cache))
+    return geoms
+
+
+def run_reference(a):
+    """Oracle on host cores, each step one colour of the P build (both Lanczos passes)."""
+    import oracle
+    from paper_2605_20918_gb300 import synth
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    oracle.build()
+    geoms = build_inputs(a, [0])
+    g, H = geoms[0]
+    col, nc = oracle.color(g.pos, g.box, a.r_col, 1004)
+    sign = oracle.probes(col, H.b, 1005)
+    threads = oracle.num_threads()
+    times = []
+    for i in range(a.warmup + a.steps):
+        c = i % nc
+        t0 = time.perf_counter()
+        oracle.density(H, col, sign, nc, mu=-4.0, kT=0.05, solve_mu=False, m=a.m, flags=0, colour_subset=[c])
+        dt = time.perf_counter() - t0
+        if i >= a.warmup:
+            times.append(dt)
+    per_colour = statistics.mean(times)
+    value = per_colour * nc
+    sample = (f"one colour of {nc} per step (both block-Lanczos passes, m={a.m}, fixed mu), geometry 0, "
+              f"scaled x{nc} to a whole P build")
+    line = {"impl": "reference", "metric": "P build s/step", "value": value, "unit": "s/P-build",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": per_colour * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(a),
+            "cpu_baseline": {"value": value, "unit": "s/P-build", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "s/P-build", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(a, g, H):
+    import oracle
+    oracle.build()
+    col, nc = oracle.color(g.pos, g.box, a.r_col, 1004)
+    sign = oracle.probes(col, H.b, 1005)
+    t0 = time.perf_counter()
+    oracle.density(H, col, sign, nc, mu=-4.0, kT=0.05, solve_mu=False, m=a.m, flags=0, colour_subset=[0])
+    dt = time.perf_counter() - t0
+    return {"value": dt * nc, "unit": "s/P-build", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one colour of {nc} (both block-Lanczos passes, m={a.m}, fixed mu), geometry 0, "
+                      f"took {dt:.1f} s, scaled x{nc} to a whole P build"}
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    os.environ.setdefault("CSS_TIMING", "1")
+    import torch
+    import paper_2605_20918_gb300 as css
+    from paper_2605_20918_gb300 import build as cbuild
+    from paper_2605_20918_gb300 import synth
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    if rank == 0 or ws == 1:
+        cbuild.build()
+    if ws > 1:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    prec = css.CSS_MIXED_FP32 if a.precision == "mixed" else css.CSS_FP64
+    n_steps = a.warmup + a.steps
+    my = [rank + ws * i for i in range(n_steps)]
+    geoms = build_inputs(a, my)
+    # inputs resident in HBM before the timed region
+    dev_in = {}
+    for t, (g, H) in geoms.items():
+        dev_in[t] = (torch.as_tensor(g.pos, device=dev), css.DeviceBSR.from_host(H, dev))
+    g0, H0 = geoms[my[0] % a.geometries]
+    colour = torch.empty(a.n_mol, dtype=torch.int32, device=dev)
+    sign = torch.empty(a.n_mol * H0.b, dtype=torch.int8, device=dev)
+    P = {t: torch.empty((H.nnzb, H.b, H.b), dtype=torch.float64, device=dev) for t, (g, H) in geoms.items()}
+    ctx = css.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    ne = synth.n_electrons(a.n_mol)
+
+    def step(i):
+        t = my[i] % a.geometries
+        xyz, Hd = dev_in[t]
+        nc = ctx.color(xyz, geoms[t][0].box, a.r_col, 1004, colour)
+        ctx.probes(colour, Hd.b, 1005, sign)
+        r = ctx.density(Hd, colour, sign, nc, P[t], kT=0.05, n_elec=ne, m=a.m, precision=prec)
+        inf = ctx.info()
+        return r, nc, inf
+
+    for i in range(a.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    launches0 = ctx.info()["kernel_launches"]
+    spmm_ms, results = [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for i in range(a.warmup, n_steps):
+            r, nc, inf = step(i)
+            spmm_ms.append(inf["ms_spmm"])
+            results.append((r, nc, inf))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = ctx.info()["kernel_launches"] - launches0
+    if ws > 1:
+        tt = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+        dist.barrier()
+    value = elapsed / (a.steps * ws)
+    last_r, last_nc, last_inf = results[-1]
+    spmm_avg = statistics.mean(spmm_ms)
+    achieved = last_inf["spmm_flops"] / (spmm_avg * 1e-3) / 1e12
+    peak = FP32_PEAK if prec == css.CSS_MIXED_FP32 else FP64_PEAK
+    traffic = None
+    tf = ROOT / "profiles" / "spmm_traffic.json"
+    if tf.exists():
+        try:
+            d = json.loads(tf.read_text())
+            if d.get("kernel_version") == "k_spmm-ffma-v1" and d.get("precision") == a.precision:
+                traffic = d.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    line = {"metric": "P build s/step at 10k H2O", "value": value, "unit": "s/P-build", "n_gpus": ws,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": elapsed / a.steps * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == css.CSS_MIXED_FP32 else "f64",
+            "data": "synthetic", "config": workload_config(a),
+            "roofline": {"kernel": "k_spmm (H*V, all colours of the system as columns)",
+                         "bound": "alu" if prec == css.CSS_MIXED_FP32 else "alu_fp64",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": traffic,
+                         "peak_source": FP32_PEAK_NOTE if prec == css.CSS_MIXED_FP32 else FP64_PEAK_NOTE,
+                         "launch_ms": spmm_avg, "flops_per_launch": last_inf["spmm_flops"],
+                         "alg_bytes_per_launch": last_inf["spmm_bytes"]},
+            "clocks": clk.summary(), "gpu_launches": int(launches),
+            "phases_ms": {k: last_inf[k] for k in ("ms_setup", "ms_lanczos", "ms_eigen", "ms_mu", "ms_extract",
+                                                   "ms_total")},
+            "n_colours": last_nc, "trP": last_r["trP"], "mu": last_r["mu"]}
+    if rank == 0 and not a.no_fp64_compare and prec == css.CSS_MIXED_FP32:
+        # mixed against FP64 on the last geometry (the FP64 path matches the oracle to ~1e-13)
+        t = my[n_steps - 1] % a.geometries
+        xyz, Hd = dev_in[t]
+        nc = ctx.color(xyz, geoms[t][0].box, a.r_col, 1004, colour)
+        ctx.probes(colour, Hd.b, 1005, sign)
+        P64 = torch.empty_like(P[t])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r64 = ctx.density(Hd, colour, sign, nc, P64, kT=0.05, n_elec=ne, m=a.m, precision=css.CSS_FP64)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        dP = float((P64 - P[t]).abs().max().item())
+        line["fp64_compare"] = {"fp64_s_per_pbuild": t64, "mixed_s_per_pbuild": value,
+                                "speedup_mixed_vs_fp64": t64 / value, "max_abs_dP": dP,
+                                "dE_band_eV_per_molecule": abs(2 * (last_r["trPH"] - r64["trPH"])) / a.n_mol,
+                                "dTrP": last_r["trP"] - r64["trP"], "mu_fp64": r64["mu"],
+                                "note": "mixed P of the last timed geometry against the FP64 path on the same geometry"}
+    if not a.no_e2e:
+        # end to end through css_pbuild with host buffers: pinned host inputs in, P out per step
+        pin = {}
+        for i in range(a.warmup, n_steps):
+            t = my[i] % a.geometries
+            g, H = geoms[t]
+            hv = torch.empty(H.val.shape, dtype=torch.float64, pin_memory=True)
+            hv.numpy()[...] = H.val
+            pin[t] = (np.ascontiguousarray(g.pos), synth.BSR(H.n_brow, H.b, H.row_ptr, H.col_idx, hv.numpy()),
+                      torch.empty(H.val.shape, dtype=torch.float64, pin_memory=True), hv)
+        flags = css.CSS_SYMMETRIZE | css.CSS_HOST_IO
+        t0s = my[a.warmup] % a.geometries
+        ctx.pbuild(pin[t0s][0], geoms[t0s][0].box, pin[t0s][1], pin[t0s][2].numpy(), r_col=a.r_col, kT=0.05,
+                   n_elec=ne, m=a.m, precision=prec, flags=flags)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for i in range(a.warmup, n_steps):
+            t = my[i] % a.geometries
+            pos, Hh, Ph, _ = pin[t]
+            ctx.pbuild(pos, geoms[t][0].box, Hh, Ph.numpy(), r_col=a.r_col, kT=0.05, n_elec=ne, m=a.m,
+                       precision=prec, flags=flags)
+            h2d += pos.nbytes + Hh.row_ptr.nbytes + Hh.col_idx.nbytes + Hh.val.nbytes
+            d2h += Ph.numel() * 8
+        e2e_t = time.perf_counter() - t0
+        if ws > 1:
+            tt = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_t = float(tt.item())
+        line["e2e"] = {"value": e2e_t / (a.steps * ws), "unit": "s/P-build", "h2d_bytes_per_step": h2d // a.steps,
+                       "d2h_bytes_per_step": d2h // a.steps, "api": "css_pbuild(CSS_HOST_IO)"}
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        g, H = geoms[my[0] % a.geometries]
+        line["cpu_baseline"] = cpu_baseline(a, g, H)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -98,6 +98,7 @@ typedef struct {
   int64_t spmm_launches; /* H*V launches of the last css_density call                       */
   double spmm_flops;     /* algorithmic flops of one H*V launch: 2 nnzb b^2 w               */
   double spmm_bytes;     /* algorithmic bytes of one H*V launch: H once, V in, W out        */
+  int64_t kernel_launches; /* kernels launched by this context since css_create            */
 } css_info;
 
 /* ------------------------------------------------------------------ context */

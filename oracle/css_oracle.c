@@ -195,6 +195,10 @@ int css_ref_probes(const int32_t* colour, int32_t n_mol, int32_t b, uint64_t sig
 /* y (N x w) = H (BSR) x (N x w); row-major vectors with leading dimension w */
 static void ref_bsr_mul(int32_t n_brow, int32_t b, const int32_t* row_ptr, const int32_t* col_idx,
                         const double* val, const double* x, double* y, int32_t w) {
+  /* rows are independent; threads split them only when no outer parallel region is active */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) if (!omp_in_parallel())
+#endif
   for (int32_t I = 0; I < n_brow; ++I) {
     for (int32_t a = 0; a < b; ++a)
       for (int32_t k = 0; k < w; ++k) y[((size_t)I * b + a) * w + k] = 0.0;

@@ -54,7 +54,8 @@ class _Info(C.Structure):
                 ("workspace_bytes", C.c_int64)] + \
                [(k, C.c_double) for k in ("ms_color", "ms_probes", "ms_setup", "ms_lanczos", "ms_spmm", "ms_eigen",
                                           "ms_mu", "ms_extract", "ms_total")] + \
-               [("spmm_launches", C.c_int64), ("spmm_flops", C.c_double), ("spmm_bytes", C.c_double)]
+               [("spmm_launches", C.c_int64), ("spmm_flops", C.c_double), ("spmm_bytes", C.c_double),
+                ("kernel_launches", C.c_int64)]
 
 
 _lib = None

@@ -115,6 +115,7 @@ css_status css_get_info(const css_ctx* ctx, css_info* info) {
   if (!ctx || !info) return CSS_ERR_INVALID_ARG;
   *info = ctx->info;
   info->workspace_bytes = ctx->ws_bytes;
+  info->kernel_launches = ctx->kernel_launches;
   return CSS_OK;
 }
 

@@ -836,6 +836,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     void* args[] = {&n_sys_, &n_col_, &nmax_, &nblk_, &b_, &soc_, &lam_, &w_, &kT_, &h_, &tl_, &sv_, &mi_, &mo_, &pp_,
                     &bar_, &err_};
     CSS_CU(ctx, cudaLaunchCooperativeKernel((void*)k_mu, dim3(G), dim3(MU_T), args, 0, st));
+    ++ctx->kernel_launches;
   }
   tm.mark();  // 4
   CSS_TRY(css_eigen_z(ctx, ea, sys_of_colour, dmu, dkT, Z, st));

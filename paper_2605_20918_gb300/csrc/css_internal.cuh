@@ -25,7 +25,11 @@
     if (_e != cudaSuccess) return css_set_cuda_error((ctx), _e, #call, __FILE__, __LINE__); \
   } while (0)
 
-#define CSS_LAUNCHED(ctx) CSS_CU(ctx, cudaGetLastError())
+#define CSS_LAUNCHED(ctx)        \
+  do {                           \
+    ++(ctx)->kernel_launches;    \
+    CSS_CU(ctx, cudaGetLastError()); \
+  } while (0)
 
 struct css_buf {
   void* p = nullptr;
@@ -36,6 +40,7 @@ struct css_ctx {
   int device = 0;
   int n_sm = 0;
   bool timing = false;
+  int64_t kernel_launches = 0;  // kernels this context has launched (all calls)
   std::string last_error;
   css_info info{};
   // named, grow-only device workspace

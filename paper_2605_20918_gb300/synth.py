@@ -253,22 +253,45 @@ def _pairs_within(pos: np.ndarray, L: float, rc: float):
     return i[o].astype(np.int64), j[o].astype(np.int64), r[o]
 
 
+def _coupling_G(pi, pj, n, b, coupling_seed, pair_chunk):
+    """Unscaled coupling blocks G of the pairs (pi < pj), keyed by the unordered pair."""
+    bb = b * b
+    out = np.empty((pi.shape[0], b, b))
+    for s in range(0, pi.shape[0], pair_chunk):
+        e = min(pi.shape[0], s + pair_chunk)
+        key = pi[s:e].astype(np.uint64) * _U64(n) + pj[s:e].astype(np.uint64)
+        ctr = (key[:, None] * _U64(bb) + np.arange(bb, dtype=np.uint64)[None, :]).ravel()
+        out[s:e] = _normal(coupling_seed, _P_COUPLING, ctr).reshape(e - s, b, b) / math.sqrt(b)
+    return out
+
+
 def hamiltonian(geom: Geometry, kind: str = "minimal", *, r_cut: float = 6.0, coupling: float = 0.5,
                 levels: np.ndarray | None = None, onsite_seed: int = 1002, coupling_seed: int = 1003,
-                pair_chunk: int = 200_000) -> BSR:
+                pair_chunk: int = 200_000, cache: dict | None = None) -> BSR:
     """Orthogonal water-like tight-binding H in BSR form.
 
     kind: "minimal" (b = 6) or "dzp" (b = 23); `levels` (n_mol, b) overrides the spectra and
-    then fixes b.  coupling = 0 gives a block-diagonal H.
+    then fixes b.  coupling = 0 gives a block-diagonal H.  `cache` (a dict kept by the caller
+    across the geometries of one sequence) keeps the on-site blocks and the pair-keyed G
+    blocks, which do not depend on the positions, so only new pairs are drawn.
     """
     n = geom.n_mol
     lv = onsite_levels(n, kind, onsite_seed) if levels is None else np.asarray(levels, dtype=np.float64)
     if lv.shape[0] != n:
         raise ValueError("levels must have one row per molecule")
     b = lv.shape[1]
-    U = _haar_orthogonal(n, b, onsite_seed)
-    diag = np.einsum("nik,nk,njk->nij", U, lv, U)
-    diag = 0.5 * (diag + np.transpose(diag, (0, 2, 1)))
+    ckey = (n, b, kind, onsite_seed, coupling_seed, None if levels is None else lv.tobytes())
+    if cache is not None and cache.get("key") != ckey:
+        cache.clear()
+        cache["key"] = ckey
+    if cache is not None and "diag" in cache:
+        diag = cache["diag"]
+    else:
+        U = _haar_orthogonal(n, b, onsite_seed)
+        diag = np.einsum("nik,nk,njk->nij", U, lv, U)
+        diag = 0.5 * (diag + np.transpose(diag, (0, 2, 1)))
+        if cache is not None:
+            cache["diag"] = diag
 
     pi, pj, pr = _pairs_within(geom.pos, geom.box, r_cut)
     npair = pi.shape[0]
@@ -283,17 +306,29 @@ def hamiltonian(geom: Geometry, kind: str = "minimal", *, r_cut: float = 6.0, co
     inv[order] = np.arange(nnzb)
     # diagonal blocks
     val[inv[2 * npair:]] = diag
-    # coupling blocks, chunked over pairs
+    # coupling blocks t(r) G, G drawn per unordered pair (or taken from the cache)
     t = coupling * np.exp(-(pr - 2.8) / 0.5)
-    bb = b * b
-    for s in range(0, npair, pair_chunk):
-        e = min(npair, s + pair_chunk)
-        key = pi[s:e].astype(np.uint64) * _U64(n) + pj[s:e].astype(np.uint64)
-        ctr = (key[:, None] * _U64(bb) + np.arange(bb, dtype=np.uint64)[None, :]).ravel()
-        G = _normal(coupling_seed, _P_COUPLING, ctr).reshape(e - s, b, b) / math.sqrt(b)
-        blk = G * t[s:e, None, None]
-        val[inv[s:e]] = blk
-        val[inv[npair + s:npair + e]] = np.transpose(blk, (0, 2, 1))
+    if cache is None:
+        G = _coupling_G(pi, pj, n, b, coupling_seed, pair_chunk)
+    else:
+        keys = pi.astype(np.uint64) * _U64(n) + pj.astype(np.uint64)
+        ck = cache.get("gkeys", np.zeros(0, np.uint64))
+        cv = cache.get("gvals", np.zeros((0, b, b)))
+        pos = np.searchsorted(ck, keys)
+        hit = (pos < ck.shape[0]) & (ck[np.minimum(pos, max(ck.shape[0] - 1, 0))] == keys) if ck.shape[0] else \
+            np.zeros(keys.shape[0], bool)
+        G = np.empty((npair, b, b))
+        G[hit] = cv[pos[hit]]
+        miss = ~hit
+        if miss.any():
+            G[miss] = _coupling_G(pi[miss], pj[miss], n, b, coupling_seed, pair_chunk)
+            allk = np.concatenate([ck, keys[miss]])
+            allv = np.concatenate([cv, G[miss]])
+            o = np.argsort(allk, kind="stable")
+            cache["gkeys"], cache["gvals"] = allk[o], allv[o]
+    blk = G * t[:, None, None]
+    val[inv[:npair]] = blk
+    val[inv[npair:2 * npair]] = np.transpose(blk, (0, 2, 1))
     col_idx = cols[order].astype(np.int32)
     return BSR(n_brow=n, b=b, row_ptr=row_ptr.astype(np.int32), col_idx=col_idx, val=val,
                meta={"n_pairs": int(npair), "r_cut": r_cut, "box": geom.box, "kind": kind})
