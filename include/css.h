@@ -171,6 +171,35 @@ CSS_API css_status css_density_batch(css_ctx* ctx, int32_t n_sys, const css_bsr*
                              css_precision prec, uint32_t flags, double* const* P_val, double* trP, double* trPH,
                              double* mu_out, void* stream);
 
+/* Ritz data of the last css_density / css_density_batch call (paper, Eq. 7: eigenvalues of
+ * each colour's projected matrix and their weights w = ||Y_k||^2, Y = U^T E_1 B_0, whose
+ * f-weighted sum is the quadrature of Tr P).  Host arrays: lam and wgt receive, colour by
+ * colour, n_per[c] values each (n_per has n_colours entries); `capacity` is the length of
+ * lam and wgt.  *n_colours receives the colour count (all systems of a batch, in order).
+ * Errors: INVALID_ARG if nothing was computed yet or capacity is too small (then *n_colours
+ * and n_per are still written when n_per is large enough: pass n_per = NULL to query). */
+CSS_API css_status css_ritz(css_ctx* ctx, double* lam, double* wgt, int32_t* n_per, int64_t capacity,
+                            int32_t* n_colours);
+
+/* Projected block-tridiagonal matrices of the last css_density call (the Krylov-projected
+ * Hamiltonian of Eq. 5-7): host arrays A and B of n_colours * m * b * b doubles ([c][j][b][b],
+ * B upper triangular, sub-diagonal blocks) and nblk (n_colours; blocks in use per colour).
+ * capacity = length of A and B in doubles.  INVALID_ARG if nothing was computed yet or the
+ * capacity is short. */
+CSS_API css_status css_projected(css_ctx* ctx, double* A, double* B, int32_t* nblk, int64_t capacity,
+                                 int32_t* n_colours, int32_t* m, int32_t* b);
+
+/* The exact-diagonalisation stage on its own (paper, Eq. 7): for each of n_col
+ * block-tridiagonal projected matrices T_c (diagonal blocks A[c][j], sub-diagonal blocks
+ * B[c][j] upper triangular, j < nblk[c] <= m, b x b row-major, FP64) return the eigenvalues
+ * lam[c][k], the weights wgt[c][k] = |c| sum_{i<b} U[i][k]^2 (U the eigenvectors, |c| =
+ * cnt[c]) and, when Z is not NULL, Z_c = U f(Lambda) U^T E_1 sqrt|c| for the given mu, kT.
+ * All arrays are device arrays laid out [c][m*b] (lam, wgt) and [c][m*b][b] (Z); entries
+ * beyond nblk[c]*b are zero.  Synchronises `stream`. */
+CSS_API css_status css_eigen_blocks(css_ctx* ctx, int32_t n_col, int32_t b, int32_t m, const double* A, const double* B,
+                                    const int32_t* nblk, const int32_t* cnt, double mu, double kT, double* lam,
+                                    double* wgt, double* Z, void* stream);
+
 /* One whole P build from a geometry and H: css_color + css_probes + css_density.  With
  * CSS_HOST_IO every array (geom->xyz, H arrays, P_val) is HOST memory and the library copies
  * in and out on `stream`; otherwise they are device arrays.  colour_out (n_mol int32,

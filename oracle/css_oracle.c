@@ -576,7 +576,7 @@ int css_ref_density(int32_t n_brow, int32_t b, int32_t nnzb, const int32_t* row_
   }
   int status = REF_OK;
   /* pass 1: Lanczos + exact diagonalisation per colour -> Ritz values and weights */
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel for schedule(dynamic, 1) if (nwork > 1)
   for (int32_t t = 0; t < nwork; ++t) {
     int32_t c = todo[t];
     if (cnt[c] == 0) { nj[t] = 0; continue; }
@@ -637,7 +637,7 @@ int css_ref_density(int32_t n_brow, int32_t b, int32_t nnzb, const int32_t* row_
   double* Pt = (double*)malloc(sizeof(double) * (size_t)nnzb * b * b);
   if (!brow || !Pt) return REF_ERR_NOMEM;
   for (size_t i = 0; i < (size_t)nnzb * b * b; ++i) Pt[i] = P_val[i];
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel for schedule(dynamic, 1) if (nwork > 1)
   for (int32_t t = 0; t < nwork; ++t) {
     int32_t c = todo[t];
     if (cnt[c] == 0) continue;

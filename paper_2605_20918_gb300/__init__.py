@@ -17,7 +17,7 @@ import numpy as np
 
 __all__ = [
     "CSSError", "Context", "DeviceBSR", "load_library", "library_path", "css_create", "css_destroy", "css_color",
-    "css_color_graph", "css_probes", "css_density", "css_density_batch", "css_pbuild", "css_get_info",
+    "css_color_graph", "css_probes", "css_density", "css_density_batch", "css_pbuild", "css_get_info", "css_ritz", "css_projected", "css_eigen_blocks",
     "CSS_OK", "CSS_WARN_BREAKDOWN", "CSS_FP64", "CSS_MIXED_FP32", "CSS_SYMMETRIZE", "CSS_TWO_PASS",
     "CSS_REORTH_LOCAL", "CSS_HOST_IO", "CSS_SIGNS_ONES",
 ]
@@ -99,6 +99,13 @@ def load_library(path: str | Path | None = None):
     lib.css_pbuild.argtypes = [v, C.POINTER(_Geom), C.POINTER(_BSR), f64, u64, u64, C.POINTER(_Fermi), i32, st, u32,
                                v, v, C.POINTER(C.c_int32), C.POINTER(f64), C.POINTER(f64), C.POINTER(f64), v]
     lib.css_pbuild.restype = st
+    lib.css_ritz.argtypes = [v, v, v, v, C.c_int64, C.POINTER(C.c_int32)]
+    lib.css_projected.argtypes = [v, v, v, v, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_int32)]
+    lib.css_projected.restype = st
+    lib.css_eigen_blocks.argtypes = [v, i32, i32, i32, v, v, v, v, f64, f64, v, v, v, v]
+    lib.css_eigen_blocks.restype = st
+    lib.css_ritz.restype = st
     _lib = lib
     return lib
 
@@ -287,6 +294,56 @@ def css_pbuild(ctx, xyz, box, H, P, *, r_col, colour_seed=1004, sign_seed=1005, 
     return {"n_colours": nc.value, "trP": tp.value, "trPH": tph.value, "mu": mo.value, "status": st}
 
 
+def css_ritz(ctx):
+    """Ritz values and weights of the last density call: list of (lam, w) per colour."""
+    lib = load_library()
+    nc = C.c_int32()
+    _check(lib, ctx, lib.css_ritz(ctx, None, None, None, 0, C.byref(nc)), "css_ritz")
+    n_per = np.zeros(nc.value, np.int32)
+    # sizes first: with capacity 0 the call fills n_per and reports INVALID_ARG
+    lib.css_ritz(ctx, None, None, n_per.ctypes.data_as(C.c_void_p), 0, C.byref(nc))
+    total = int(n_per.sum())
+    lam = np.zeros(max(total, 1)); wgt = np.zeros(max(total, 1))
+    _check(lib, ctx, lib.css_ritz(ctx, lam.ctypes.data_as(C.c_void_p), wgt.ctypes.data_as(C.c_void_p),
+                                  n_per.ctypes.data_as(C.c_void_p), total, C.byref(nc)), "css_ritz")
+    out, o = [], 0
+    for k in n_per:
+        out.append((lam[o:o + k].copy(), wgt[o:o + k].copy()))
+        o += k
+    return out
+
+
+def css_projected(ctx):
+    """Projected block-tridiagonal matrices of the last density call: (A, B, nblk) with A, B of
+    shape [n_colours, m, b, b]."""
+    lib = load_library()
+    nc, m, b = C.c_int32(), C.c_int32(), C.c_int32()
+    lib.css_projected(ctx, None, None, None, 0, C.byref(nc), C.byref(m), C.byref(b))
+    shape = (nc.value, m.value, b.value, b.value)
+    A = np.zeros(shape); B = np.zeros(shape); nb = np.zeros(nc.value, np.int32)
+    _check(lib, ctx, lib.css_projected(ctx, A.ctypes.data_as(C.c_void_p), B.ctypes.data_as(C.c_void_p),
+                                       nb.ctypes.data_as(C.c_void_p), A.size, C.byref(nc), C.byref(m), C.byref(b)),
+           "css_projected")
+    return A, B, nb
+
+
+def css_eigen_blocks(ctx, A, B, nblk, cnt, *, mu=0.0, kT=0.05, want_z=True, stream=None):
+    """Eigen stage alone.  A, B: float64 CUDA tensors [n_col, m, b, b]; nblk, cnt: int32 CUDA
+    tensors [n_col].  Returns (lam [n_col, m b], wgt [n_col, m b], Z [n_col, m b, b] or None)."""
+    torch = _torch()
+    lib = load_library()
+    n_col, m, b = int(A.shape[0]), int(A.shape[1]), int(A.shape[2])
+    lam = torch.zeros((n_col, m * b), dtype=torch.float64, device=A.device)
+    wgt = torch.zeros_like(lam)
+    Z = torch.zeros((n_col, m * b, b), dtype=torch.float64, device=A.device) if want_z else None
+    _check(lib, ctx, lib.css_eigen_blocks(ctx, n_col, b, m, _dev(A, torch.float64, "A"), _dev(B, torch.float64, "B"),
+                                          _dev(nblk, torch.int32, "nblk"), _dev(cnt, torch.int32, "cnt"), float(mu),
+                                          float(kT), _dev(lam, torch.float64, "lam"), _dev(wgt, torch.float64, "wgt"),
+                                          _dev(Z, torch.float64, "Z") if want_z else C.c_void_p(0), _stream(stream)),
+           "css_eigen_blocks")
+    return lam, wgt, Z
+
+
 class Context:
     """Owns a css_ctx (device workspace) for one GPU."""
 
@@ -330,3 +387,12 @@ class Context:
 
     def info(self):
         return css_get_info(self.handle)
+
+    def ritz(self):
+        return css_ritz(self.handle)
+
+    def projected(self):
+        return css_projected(self.handle)
+
+    def eigen_blocks(self, *a, **k):
+        return css_eigen_blocks(self.handle, *a, **k)

@@ -742,6 +742,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   la.part = part;
   la.small = small;
   la.tau = f32 ? 1e-5 : 1e-10;
+  la.shift_rel = f32 ? 1e-5 : 1e-12;
   la.flags = flags;
   la.Qs = Qs;
   la.X = X;
@@ -904,6 +905,15 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     finite = finite && std::isfinite(hres[2 * s]) && std::isfinite(hres[2 * s + 1]) &&
              std::isfinite(hres[2 * n_sys + s]);
   }
+  ctx->last_lam = ea.lam;
+  ctx->last_wgt = ea.wgt;
+  ctx->last_nblk = nblk;
+  ctx->last_ncol = n_col;
+  ctx->last_b = b;
+  ctx->last_nmax = nmax;
+  ctx->last_A = Ablk;
+  ctx->last_B = Bblk;
+  ctx->last_m = m;
   ctx->info.n_colours = n_col;
   ctx->info.n_pairs = (int32_t)n_pairs;
   ctx->info.n_breakdown = n_break;
@@ -934,6 +944,99 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
 }
 
 extern "C" {
+
+css_status css_ritz(css_ctx* ctx, double* lam, double* wgt, int32_t* n_per, int64_t capacity, int32_t* n_colours) {
+  if (!ctx || !n_colours) return css_set_arg_error(ctx, "css_ritz: null pointer");
+  if (!ctx->last_lam) return css_set_arg_error(ctx, "css_ritz: no density has been computed");
+  CSS_CU(ctx, cudaSetDevice(ctx->device));
+  const int32_t nc = ctx->last_ncol, nmax = ctx->last_nmax;
+  *n_colours = nc;
+  if (!n_per) return CSS_OK;
+  std::vector<int32_t> nb(nc);
+  CSS_CU(ctx, cudaDeviceSynchronize());
+  CSS_CU(ctx, cudaMemcpy(nb.data(), ctx->last_nblk, sizeof(int32_t) * nc, cudaMemcpyDeviceToHost));
+  int64_t total = 0;
+  for (int32_t c = 0; c < nc; ++c) {
+    n_per[c] = nb[c] * ctx->last_b;
+    total += n_per[c];
+  }
+  if (!lam || !wgt || capacity < total) return css_set_arg_error(ctx, "css_ritz: capacity too small");
+  int64_t o = 0;
+  for (int32_t c = 0; c < nc; ++c) {
+    if (n_per[c] == 0) continue;
+    CSS_CU(ctx, cudaMemcpy(lam + o, ctx->last_lam + (size_t)c * nmax, sizeof(double) * n_per[c], cudaMemcpyDeviceToHost));
+    CSS_CU(ctx, cudaMemcpy(wgt + o, ctx->last_wgt + (size_t)c * nmax, sizeof(double) * n_per[c], cudaMemcpyDeviceToHost));
+    o += n_per[c];
+  }
+  return CSS_OK;
+}
+
+css_status css_projected(css_ctx* ctx, double* A, double* B, int32_t* nblk, int64_t capacity, int32_t* n_colours,
+                         int32_t* m, int32_t* b) {
+  if (!ctx || !n_colours || !m || !b) return css_set_arg_error(ctx, "css_projected: null pointer");
+  if (!ctx->last_A) return css_set_arg_error(ctx, "css_projected: no density has been computed");
+  *n_colours = ctx->last_ncol;
+  *m = ctx->last_m;
+  *b = ctx->last_b;
+  const int64_t need = (int64_t)ctx->last_ncol * ctx->last_m * ctx->last_b * ctx->last_b;
+  if (!A || !B || !nblk || capacity < need) return css_set_arg_error(ctx, "css_projected: capacity too small");
+  CSS_CU(ctx, cudaSetDevice(ctx->device));
+  CSS_CU(ctx, cudaDeviceSynchronize());
+  CSS_CU(ctx, cudaMemcpy(A, ctx->last_A, sizeof(double) * need, cudaMemcpyDeviceToHost));
+  CSS_CU(ctx, cudaMemcpy(B, ctx->last_B, sizeof(double) * need, cudaMemcpyDeviceToHost));
+  CSS_CU(ctx, cudaMemcpy(nblk, ctx->last_nblk, sizeof(int32_t) * ctx->last_ncol, cudaMemcpyDeviceToHost));
+  return CSS_OK;
+}
+
+css_status css_eigen_blocks(css_ctx* ctx, int32_t n_col, int32_t b, int32_t m, const double* A, const double* B,
+                            const int32_t* nblk, const int32_t* cnt, double mu, double kT, double* lam, double* wgt,
+                            double* Z, void* stream) {
+  if (!ctx || !A || !B || !nblk || !cnt || !lam || !wgt) return css_set_arg_error(ctx, "css_eigen_blocks: null pointer");
+  if (n_col < 1 || b < 1 || b > CSS_MAX_B || m < 1 || (int64_t)m * b > 4096 || !(kT >= 0.0))
+    return css_set_arg_error(ctx, "css_eigen_blocks: bad size or kT");
+  CSS_CU(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int32_t nmax = m * b;
+  EigArgs ea;
+  ea.n_col = n_col;
+  ea.b = b;
+  ea.m = m;
+  ea.Ablk = A;
+  ea.Bblk = B;
+  ea.nblk = nblk;
+  ea.cnt = cnt;
+  ea.rcap = nmax * (nmax / b + 2);
+  CSS_TRY(ws_get(ctx, "e_AB", (size_t)n_col * nmax * (2 * b + 1), &ea.AB));
+  CSS_TRY(ws_get(ctx, "e_RV", (size_t)n_col * ea.rcap * b, &ea.RV));
+  CSS_TRY(ws_get(ctx, "e_RT", (size_t)n_col * ea.rcap, &ea.RT));
+  CSS_TRY(ws_get(ctx, "e_RR0", (size_t)n_col * ea.rcap, &ea.RR0));
+  CSS_TRY(ws_get(ctx, "e_so", (size_t)n_col * (nmax + 1), &ea.sweep_off));
+  CSS_TRY(ws_get(ctx, "e_d", (size_t)n_col * nmax, &ea.d));
+  CSS_TRY(ws_get(ctx, "e_e", (size_t)n_col * nmax, &ea.e));
+  CSS_TRY(ws_get(ctx, "e_l32", (size_t)n_col * nmax, &ea.lam32));
+  CSS_TRY(ws_get(ctx, "e_tn", (size_t)n_col, &ea.tnorm));
+  CSS_TRY(ws_get(ctx, "e_U", (size_t)n_col * nmax * nmax, &ea.U));
+  CSS_TRY(ws_get(ctx, "e_F", (size_t)n_col * 5 * nmax * nmax, &ea.F));
+  CSS_TRY(ws_get(ctx, "e_X0", (size_t)n_col * nmax * b, &ea.X0));
+  CSS_TRY(ws_get(ctx, "e_Y", (size_t)n_col * nmax * b, &ea.Y));
+  CSS_TRY(ws_get(ctx, "e_st", (size_t)n_col, &ea.status));
+  ea.lam = lam;
+  ea.wgt = wgt;
+  CSS_CU(ctx, cudaMemsetAsync(lam, 0, sizeof(double) * n_col * nmax, st));
+  CSS_TRY(css_eigen_ritz(ctx, ea, st));
+  if (Z) {
+    int32_t* soc;
+    double* par;
+    CSS_TRY(ws_get(ctx, "eb_soc", n_col, &soc));
+    CSS_TRY(ws_get(ctx, "eb_par", 2, &par));
+    CSS_CU(ctx, cudaMemsetAsync(soc, 0, sizeof(int32_t) * n_col, st));
+    double hp[2] = {mu, kT};
+    CSS_CU(ctx, cudaMemcpyAsync(par, hp, sizeof(hp), cudaMemcpyHostToDevice, st));
+    CSS_TRY(css_eigen_z(ctx, ea, soc, par, par + 1, Z, st));
+  }
+  CSS_CU(ctx, cudaStreamSynchronize(st));
+  return CSS_OK;
+}
 
 css_status css_density(css_ctx* ctx, const css_bsr* H, const int32_t* colour, const int8_t* sign, int32_t n_colours,
                        const css_fermi* fermi, int32_t m, css_precision prec, uint32_t flags, double* P_val,

@@ -342,90 +342,101 @@ __global__ void k_inviter(int32_t kd, int32_t nmax, const int32_t* __restrict__ 
     while (k1 + 1 < n && (double)l32[k1 + 1] - (double)l32[k1] <= tol && k1 + 1 - k0 < kMaxCluster) ++k1;
     auto U_ = [&](int32_t i, int32_t col) -> double& { return u[(size_t)i * nmax + col]; };
     auto F_ = [&](double* base, int32_t i, int32_t col) -> double& { return base[(size_t)i * nmax + col]; };
+    // window the refined eigenvalues must fall in: the cluster's shifts widened by a quarter of
+    // the gaps to the neighbouring shifts outside the cluster
+    const double g_lo = k0 > 0 ? (double)l32[k0] - (double)l32[k0 - 1] : tn;
+    const double g_hi = k1 + 1 < n ? (double)l32[k1 + 1] - (double)l32[k1] : tn;
+    const double win_lo = (double)l32[k0] - 0.25 * g_lo - 2e-6 * tn;
+    const double win_hi = (double)l32[k1] + 0.25 * g_hi + 2e-6 * tn;
     for (int32_t kk = k0; kk <= k1; ++kk) {
       double sigma = (double)l32[kk];
-      // start vector
-      double nrm = 0.0;
-      for (int32_t i = 0; i < n; ++i) {
-        double x = hash_unit((uint64_t)c * 1000003ull + kk, (uint64_t)i);
-        F_(f_x, i, kk) = x;
-        nrm += x * x;
-      }
-      nrm = 1.0 / sqrt(nrm);
-      for (int32_t i = 0; i < n; ++i) F_(f_x, i, kk) *= nrm;
-      for (int it = 0; it < 5; ++it) {
-        // LU with partial pivoting of T - sigma I (rows: sub e_{i-1}, diag d_i - sigma, sup e_i)
-        double cd = d[0] - sigma, cs = n > 1 ? e[0] : 0.0;
-        for (int32_t i = 0; i + 1 < n; ++i) {
-          const double sub = e[i], dg = d[i + 1] - sigma, sup = (i + 2 < n) ? e[i + 1] : 0.0;
-          if (fabs(cd) >= fabs(sub)) {
-            if (fabs(cd) < pivmin) cd = cd >= 0 ? pivmin : -pivmin;
-            const double l = sub / cd;
-            F_(f_l, i, kk) = l;
-            F_(f_u0, i, kk) = cd;
-            F_(f_u1, i, kk) = cs;
-            F_(f_u2, i, kk) = 0.0;  // no interchange
-            cd = dg - l * cs;
-            cs = sup;
-          } else {
-            // rows i and i+1 interchanged; |l| <= 1, so l + 4 in [3, 5] marks the interchange
-            const double l = cd / sub;
-            F_(f_l, i, kk) = l + 4.0;
-            F_(f_u0, i, kk) = sub;
-            F_(f_u1, i, kk) = dg;
-            F_(f_u2, i, kk) = sup;
-            const double ncd = cs - l * dg;
-            cs = -l * sup;
-            cd = ncd;
-          }
-        }
-        if (fabs(cd) < pivmin) cd = cd >= 0 ? pivmin : -pivmin;
-        F_(f_u0, n - 1, kk) = cd;
-        // forward: P and L
-        for (int32_t i = 0; i + 1 < n; ++i) {
-          double l = F_(f_l, i, kk);
-          double xi = F_(f_x, i, kk), xn = F_(f_x, i + 1, kk);
-          if (l >= 3.0) {  // interchange
-            l -= 4.0;
-            F_(f_x, i, kk) = xn;
-            F_(f_x, i + 1, kk) = xi - l * xn;
-          } else {
-            F_(f_x, i + 1, kk) = xn - l * xi;
-          }
-        }
-        // backward: U y = x
-        double y2 = 0.0, y1 = 0.0;
-        for (int32_t i = n - 1; i >= 0; --i) {
-          double r = F_(f_x, i, kk);
-          if (i + 1 < n) r -= F_(f_u1, i, kk) * y1;
-          if (i + 2 < n) r -= F_(f_u2, i, kk) * y2;
-          double y = r / F_(f_u0, i, kk);
-          F_(f_x, i, kk) = y;
-          y2 = y1;
-          y1 = y;
-        }
-        // Gram-Schmidt against the cluster's finished vectors, twice
-        for (int rep = 0; rep < 2; ++rep)
-          for (int32_t pq = k0; pq < kk; ++pq) {
-            double dot = 0.0;
-            for (int32_t i = 0; i < n; ++i) dot += U_(i, pq) * F_(f_x, i, kk);
-            for (int32_t i = 0; i < n; ++i) F_(f_x, i, kk) -= dot * U_(i, pq);
-          }
-        nrm = 0.0;
-        for (int32_t i = 0; i < n; ++i) nrm += F_(f_x, i, kk) * F_(f_x, i, kk);
-        const double growth = sqrt(nrm);
-        nrm = 1.0 / growth;
-        // Rayleigh quotient x^T T x of the normalised vector
-        double rq = 0.0, prev = 0.0;
+      for (int attempt = 0; attempt < 3; ++attempt) {
+        sigma = (double)l32[kk];
+        // start vector
+        double nrm = 0.0;
         for (int32_t i = 0; i < n; ++i) {
-          double xi = F_(f_x, i, kk) * nrm;
-          F_(f_x, i, kk) = xi;
-          rq += xi * (d[i] * xi + 2.0 * (i > 0 ? e[i - 1] * prev : 0.0));
-          prev = xi;
+          double x = hash_unit((uint64_t)c * 1000003ull + (uint64_t)kk + 7919ull * attempt, (uint64_t)i);
+          F_(f_x, i, kk) = x;
+          nrm += x * x;
         }
-        const bool conv = it >= 1 && growth * pivmin > 1.0;
-        sigma = rq;
-        if (conv) break;
+        nrm = 1.0 / sqrt(nrm);
+        for (int32_t i = 0; i < n; ++i) F_(f_x, i, kk) *= nrm;
+        // two inverse-iteration steps at the fixed FP32 shift make the target eigenvector
+        // dominate whatever the start vector; Rayleigh-quotient shifts from then on
+        for (int it = 0; it < 8; ++it) {
+          // LU with partial pivoting of T - sigma I (rows: sub e_{i-1}, diag d_i - sigma, sup e_i)
+          double cd = d[0] - sigma, cs = n > 1 ? e[0] : 0.0;
+          for (int32_t i = 0; i + 1 < n; ++i) {
+            const double sub = e[i], dg = d[i + 1] - sigma, sup = (i + 2 < n) ? e[i + 1] : 0.0;
+            if (fabs(cd) >= fabs(sub)) {
+              if (fabs(cd) < pivmin) cd = cd >= 0 ? pivmin : -pivmin;
+              const double l = sub / cd;
+              F_(f_l, i, kk) = l;
+              F_(f_u0, i, kk) = cd;
+              F_(f_u1, i, kk) = cs;
+              F_(f_u2, i, kk) = 0.0;  // no interchange
+              cd = dg - l * cs;
+              cs = sup;
+            } else {
+              // rows i and i+1 interchanged; |l| <= 1, so l + 4 in [3, 5] marks the interchange
+              const double l = cd / sub;
+              F_(f_l, i, kk) = l + 4.0;
+              F_(f_u0, i, kk) = sub;
+              F_(f_u1, i, kk) = dg;
+              F_(f_u2, i, kk) = sup;
+              const double ncd = cs - l * dg;
+              cs = -l * sup;
+              cd = ncd;
+            }
+          }
+          if (fabs(cd) < pivmin) cd = cd >= 0 ? pivmin : -pivmin;
+          F_(f_u0, n - 1, kk) = cd;
+          // forward: P and L
+          for (int32_t i = 0; i + 1 < n; ++i) {
+            double l = F_(f_l, i, kk);
+            double xi = F_(f_x, i, kk), xn = F_(f_x, i + 1, kk);
+            if (l >= 3.0) {  // interchange
+              l -= 4.0;
+              F_(f_x, i, kk) = xn;
+              F_(f_x, i + 1, kk) = xi - l * xn;
+            } else {
+              F_(f_x, i + 1, kk) = xn - l * xi;
+            }
+          }
+          // backward: U y = x
+          double y2 = 0.0, y1 = 0.0;
+          for (int32_t i = n - 1; i >= 0; --i) {
+            double r = F_(f_x, i, kk);
+            if (i + 1 < n) r -= F_(f_u1, i, kk) * y1;
+            if (i + 2 < n) r -= F_(f_u2, i, kk) * y2;
+            double y = r / F_(f_u0, i, kk);
+            F_(f_x, i, kk) = y;
+            y2 = y1;
+            y1 = y;
+          }
+          // Gram-Schmidt against the cluster's finished vectors, twice
+          for (int rep = 0; rep < 2; ++rep)
+            for (int32_t pq = k0; pq < kk; ++pq) {
+              double dot = 0.0;
+              for (int32_t i = 0; i < n; ++i) dot += U_(i, pq) * F_(f_x, i, kk);
+              for (int32_t i = 0; i < n; ++i) F_(f_x, i, kk) -= dot * U_(i, pq);
+            }
+          nrm = 0.0;
+          for (int32_t i = 0; i < n; ++i) nrm += F_(f_x, i, kk) * F_(f_x, i, kk);
+          const double growth = sqrt(nrm);
+          nrm = 1.0 / growth;
+          // Rayleigh quotient x^T T x of the normalised vector
+          double rq = 0.0, prev = 0.0;
+          for (int32_t i = 0; i < n; ++i) {
+            double xi = F_(f_x, i, kk) * nrm;
+            F_(f_x, i, kk) = xi;
+            rq += xi * (d[i] * xi + 2.0 * (i > 0 ? e[i - 1] * prev : 0.0));
+            prev = xi;
+          }
+          if (it >= 1) sigma = rq;
+          if (it >= 2 && growth * pivmin > 1.0) break;
+        }
+        if (sigma >= win_lo && sigma <= win_hi) break;  // converged to an eigenvalue of this cluster
       }
       for (int32_t i = 0; i < n; ++i) U_(i, kk) = F_(f_x, i, kk);
       lam[(size_t)c * nmax + kk] = sigma;
@@ -575,6 +586,12 @@ __global__ void k_zt(int32_t kd, int32_t b, int32_t nmax, const int32_t* __restr
   }
 }
 
+// diagnostics: copy the FP32 shifts over the eigenvalues
+__global__ void k_shifts_out(int32_t nmax, const float* __restrict__ lam32, double* __restrict__ lam) {
+  for (int32_t k = threadIdx.x; k < nmax; k += blockDim.x)
+    lam[(size_t)blockIdx.x * nmax + k] = (double)lam32[(size_t)blockIdx.x * nmax + k];
+}
+
 }  // namespace
 
 css_status css_eigen_ritz(css_ctx* ctx, const EigArgs& a, cudaStream_t st) {
@@ -593,6 +610,10 @@ css_status css_eigen_ritz(css_ctx* ctx, const EigArgs& a, cudaStream_t st) {
   CSS_LAUNCHED(ctx);
   k_inviter<<<nc, 128, 0, st>>>(b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm, 1e-4, a.U, a.F, a.lam, a.status);
   CSS_LAUNCHED(ctx);
+  if (ctx->debug_eig == 1) {
+    k_shifts_out<<<nc, 256, 0, st>>>(nmax, a.lam32, a.lam);
+    CSS_LAUNCHED(ctx);
+  }
   dim3 g((unsigned)css_ceil_div(nmax, 128), (unsigned)nc);
   k_ritz_y<<<g, 128, 64 * b * sizeof(double), st>>>(b, b, nmax, a.nblk, a.U, a.X0, a.Y, a.wgt);
   CSS_LAUNCHED(ctx);

@@ -40,7 +40,16 @@ struct css_ctx {
   int device = 0;
   int n_sm = 0;
   bool timing = false;
+  int debug_eig = 0;  // 1: eigen stage returns its FP32 shifts instead of refined eigenvalues
   int64_t kernel_launches = 0;  // kernels this context has launched (all calls)
+  // where the last density call left its Ritz data (device)
+  const double* last_lam = nullptr;
+  const double* last_wgt = nullptr;
+  const int32_t* last_nblk = nullptr;
+  const double* last_A = nullptr;
+  const double* last_B = nullptr;
+  int32_t last_m = 0;
+  int32_t last_ncol = 0, last_b = 0, last_nmax = 0;
   std::string last_error;
   css_info info{};
   // named, grow-only device workspace

@@ -328,13 +328,20 @@ __global__ void k_store_A(int32_t ncb, int32_t b, int32_t cb0, int32_t m, int32_
   A[(size_t)ncb * b * b + t] = v;
 }
 
-// Cholesky G = R^T R (R upper) and R^-1, one warp per colour; lane l owns column l.
-// PASS 1: breakdown test min_k R_kk <= tau * ||H Q_j||_F marks the colour done.
-// PASS 2: B_j = R2 R1 stored in the projected matrix.
-template <int PASS>
+// Cholesky factor and inverse of one colour's Gram matrix, one warp per colour (lane l owns
+// column l).  Three uses make shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto &
+// Yanagisawa, SIAM J. Sci. Comput. 2020), which keeps the new block orthonormal even when it
+// is nearly rank deficient (converged Ritz directions):
+//   MODE 0: R0 = chol(G + s I), s = shift_rel * trace(G)                 (regularised pass)
+//   MODE 1: R1 = chol(G); stores R10 = R1 R0 in Rprod
+//   MODE 2: R2 = chol(G); B_j = R2 R10 stored in the projected matrix; breakdown when
+//           min_k B_kk <= tau ||H Q_j||_F (same rule as a Householder QR's R_kk)
+// A colour already finished, or a failed factorisation, gives R = I and R^-1 = 0, so the
+// colour's next block is zero.
+template <int MODE>
 __global__ void k_chol(int32_t ncb, int32_t b, int32_t cb0, int32_t m, int32_t j, const double* __restrict__ G,
-                       const double* __restrict__ hq2, double tau, double* __restrict__ R /*[lc][b][b]*/,
-                       double* __restrict__ Rinv, const double* __restrict__ R1, double* __restrict__ Bblk,
+                       const double* __restrict__ hq2, double tau, double shift_rel, double* __restrict__ R,
+                       double* __restrict__ Rinv, double* __restrict__ Rprod, double* __restrict__ Bblk,
                        int32_t* __restrict__ done, int32_t* __restrict__ nblk) {
   __shared__ double sR[4][CSS_MAX_B][CSS_MAX_B + 1];
   const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -345,65 +352,92 @@ __global__ void k_chol(int32_t ncb, int32_t b, int32_t cb0, int32_t m, int32_t j
   const double* g = G + (size_t)lc * b * b;
   double* ro = R + (size_t)lc * b * b;
   double* ri = Rinv + (size_t)lc * b * b;
+  double* rp = Rprod + (size_t)lc * b * b;
   const bool was_done = done[c] != 0;
   bool broken = was_done;
   for (int32_t i = 0; i < b; ++i)
     if (lane < b) r[i][lane] = 0.0;
   __syncwarp();
+  double shift = 0.0;
+  if (MODE == 0) {
+    double t = (lane < b) ? g[lane * b + lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    shift = shift_rel * t;
+  }
   if (!broken) {
-    const double thr = PASS == 1 ? tau * tau * hq2[lc] : 0.0;
     for (int32_t k = 0; k < b && !broken; ++k) {
-      double s = 0.0;
+      double sv = 0.0;
       if (lane < b && lane >= k) {
-        s = g[k * b + lane];
-        for (int32_t i = 0; i < k; ++i) s -= r[i][k] * r[i][lane];
+        sv = g[k * b + lane] + ((lane == k) ? shift : 0.0);
+        for (int32_t i = 0; i < k; ++i) sv -= r[i][k] * r[i][lane];
       }
-      const double piv = __shfl_sync(0xffffffffu, s, k);
-      if (!(piv > thr) || !(piv > 0.0)) {
+      const double piv = __shfl_sync(0xffffffffu, sv, k);
+      if (!(piv > 0.0)) {
         broken = true;
         break;
       }
       const double inv = 1.0 / sqrt(piv);
-      if (lane < b && lane >= k) r[k][lane] = (lane == k) ? piv * inv : s * inv;
+      if (lane < b && lane >= k) r[k][lane] = sv * inv;
       __syncwarp();
     }
   }
   __syncwarp();
+  // the new sub-diagonal block and the breakdown test
+  if (MODE == 2 && !broken && lane < b) {
+    for (int32_t i = 0; i < b; ++i) {
+      double sv = 0.0;
+      for (int32_t k2 = i; k2 <= lane; ++k2) sv += r[i][k2] * rp[k2 * b + lane];
+      Bblk[(((size_t)c) * m + j) * b * b + i * b + lane] = (i <= lane) ? sv : 0.0;
+    }
+  }
+  if (MODE == 2 && !broken) {
+    double dk = 1e300;
+    if (lane < b) {
+      double sv = 0.0;
+      for (int32_t k2 = lane; k2 < b; ++k2) sv += (k2 == lane ? r[lane][lane] : 0.0) * rp[k2 * b + lane];
+      dk = sv;  // (R2 R10)_kk = R2_kk R10_kk for upper-triangular factors
+    }
+    for (int o = 16; o > 0; o >>= 1) dk = fmin(dk, __shfl_xor_sync(0xffffffffu, dk, o));
+    if (!(dk > tau * sqrt(hq2[lc]))) broken = true;
+  }
   if (broken) {
-    // breakdown (or colour already finished): identity factor, zero inverse -> zero block
     if (lane < b)
       for (int32_t i = 0; i < b; ++i) {
         ro[i * b + lane] = (i == lane) ? 1.0 : 0.0;
         ri[i * b + lane] = 0.0;
+        if (MODE == 1) rp[i * b + lane] = (i == lane) ? 1.0 : 0.0;
+        if (MODE == 2) Bblk[(((size_t)c) * m + j) * b * b + i * b + lane] = 0.0;
       }
     if (!was_done && lane == 0) {
       done[c] = 1;
       nblk[c] = j + 1;
     }
-    if (PASS == 2 && lane < b)
-      for (int32_t i = 0; i < b; ++i) Bblk[(((size_t)c) * m + j) * b * b + i * b + lane] = 0.0;
     return;
   }
   // inverse of the upper-triangular factor: lane l solves R x = e_l
   if (lane < b) {
     double x[CSS_MAX_B];
     for (int32_t i = b - 1; i >= 0; --i) {
-      double s = (i == lane) ? 1.0 : 0.0;
-      for (int32_t k2 = i + 1; k2 <= lane; ++k2) s -= r[i][k2] * x[k2];
-      x[i] = (i <= lane) ? s / r[i][i] : 0.0;
+      double sv = (i == lane) ? 1.0 : 0.0;
+      for (int32_t k2 = i + 1; k2 <= lane; ++k2) sv -= r[i][k2] * x[k2];
+      x[i] = (i <= lane) ? sv / r[i][i] : 0.0;
     }
     for (int32_t i = 0; i < b; ++i) {
       ri[i * b + lane] = (i <= lane) ? x[i] : 0.0;
       ro[i * b + lane] = r[i][lane];
     }
-    if (PASS == 2) {
-      const double* r1 = R1 + (size_t)lc * b * b;
-      for (int32_t i = 0; i < b; ++i) {
-        double s = 0.0;
-        for (int32_t k2 = i; k2 <= lane; ++k2) s += r[i][k2] * r1[k2 * b + lane];
-        Bblk[(((size_t)c) * m + j) * b * b + i * b + lane] = (i <= lane) ? s : 0.0;
-      }
+  }
+  __syncwarp();
+  if (MODE == 1 && lane < b) {
+    // R10 = R1 R0 (R0 is the factor of the previous pass, passed in Rprod's slot on entry)
+    double col[CSS_MAX_B];
+    for (int32_t i = 0; i < b; ++i) {
+      double sv = 0.0;
+      for (int32_t k2 = i; k2 <= lane; ++k2) sv += r[i][k2] * rp[k2 * b + lane];
+      col[i] = (i <= lane) ? sv : 0.0;
     }
+    __syncwarp();
+    for (int32_t i = 0; i < b; ++i) rp[i * b + lane] = col[i];
   }
 }
 
@@ -571,17 +605,26 @@ css_status run_pass(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
       k_sub<T, true><<<rgrid, RT, sm_sub, st>>>(N, b, a.ws, Qc, Qp, W, Asym, nullptr, partA);
       CSS_LAUNCHED(ctx);
     }
+    // shifted CholeskyQR3 of W: R0 from G + sI, then two plain CholeskyQR passes
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partA, sG);
     CSS_LAUNCHED(ctx);
-    k_chol<1><<<(unsigned)css_ceil_div(ncb, 4), 128, 0, st>>>(ncb, b, a.cb0, m, j, sG, sH, a.tau, sR1, sR1i, nullptr,
-                                                              nullptr, a.done, a.nblk);
+    k_chol<0><<<(unsigned)css_ceil_div(ncb, 4), 128, 0, st>>>(ncb, b, a.cb0, m, j, sG, sH, a.tau, a.shift_rel, sR1, sR1i,
+                                                              sC1, a.Bblk, a.done, a.nblk);
+    CSS_LAUNCHED(ctx);
+    CSS_CU(ctx, cudaMemcpyAsync(sC1, sR1, sizeof(double) * ncb * bb, cudaMemcpyDeviceToDevice, st));
+    k_apply<T, true><<<rgrid, RT, sm_apply, st>>>(N, b, a.ws, W, nullptr, sR1i, partA);
+    CSS_LAUNCHED(ctx);
+    k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partA, sG);
+    CSS_LAUNCHED(ctx);
+    k_chol<1><<<(unsigned)css_ceil_div(ncb, 4), 128, 0, st>>>(ncb, b, a.cb0, m, j, sG, sH, a.tau, 0.0, sR1, sR1i,
+                                                              sC1, a.Bblk, a.done, a.nblk);
     CSS_LAUNCHED(ctx);
     k_apply<T, true><<<rgrid, RT, sm_apply, st>>>(N, b, a.ws, W, nullptr, sR1i, partA);
     CSS_LAUNCHED(ctx);
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partA, sG);
     CSS_LAUNCHED(ctx);
-    k_chol<2><<<(unsigned)css_ceil_div(ncb, 4), 128, 0, st>>>(ncb, b, a.cb0, m, j, sG, sH, 0.0, sR2, sR2i, sR1,
-                                                              a.Bblk, a.done, a.nblk);
+    k_chol<2><<<(unsigned)css_ceil_div(ncb, 4), 128, 0, st>>>(ncb, b, a.cb0, m, j, sG, sH, a.tau, 0.0, sR2, sR2i,
+                                                              sC1, a.Bblk, a.done, a.nblk);
     CSS_LAUNCHED(ctx);
     // Q_{j+1} = W R2^-1 overwrites Q_{j-1}
     k_apply<T, false><<<rgrid, RT, sm_apply, st>>>(N, b, a.ws, W, Qp, sR2i, nullptr);

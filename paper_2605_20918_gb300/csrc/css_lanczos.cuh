@@ -24,6 +24,7 @@ struct LzArgs {
   double* part = nullptr;            // per-chunk partial products
   double* small = nullptr;           // per-colour small matrices of the batch
   double tau = 1e-10;                // breakdown threshold relative to ||H Q_j||_F
+  double shift_rel = 1e-12;          // shifted-CholeskyQR shift relative to trace(W^T W)
   uint32_t flags = 0;
   int mode = 0;                      // 0 none, 1 store sampled rows into Qs, 2 accumulate X
   void* Qs = nullptr;                // [pair][m][b][b] in the vector precision
