@@ -49,7 +49,8 @@ typedef enum {
 typedef enum {
   CSS_FP64 = 0,       /* everything in FP64                                               */
   CSS_MIXED_FP32 = 1  /* H*V, Krylov vectors and block products in FP32 (FP32 accumulate); */
-                      /* recurrence coefficients, Cholesky, eigensolve, mu, Z and P in FP64 */
+                      /* recurrence coefficients, Cholesky, eigensolve, mu, Z and P in FP64; */
+                      /* implies CSS_REORTH_LOCAL (it removes an FP32-level bias of Tr P)   */
 } css_precision;
 
 /* css_density flags */

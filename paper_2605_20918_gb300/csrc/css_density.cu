@@ -435,15 +435,33 @@ __global__ void __launch_bounds__(EX_T) k_extract(int32_t k0, int32_t k1, int32_
   }
 }
 
-__global__ void k_trace_sum(int32_t nparts, const double* __restrict__ part, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double a = 0.0, z = 0.0;
-    for (int32_t i = 0; i < nparts; ++i) {
-      a += part[2 * i];
-      z += part[2 * i + 1];
+// out = sum of the (Tr P, Tr PH) partials; fixed thread-to-partial map and a fixed tree, so
+// the sum is deterministic
+__global__ void __launch_bounds__(1024) k_trace_sum(int32_t nparts, const double* __restrict__ part,
+                                                    double* __restrict__ out) {
+  __shared__ double r1[32], r2[32];
+  double a = 0.0, z = 0.0;
+  for (int32_t i = threadIdx.x; i < nparts; i += blockDim.x) {
+    a += part[2 * i];
+    z += part[2 * i + 1];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    z += __shfl_xor_sync(0xffffffffu, z, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    r1[threadIdx.x >> 5] = a;
+    r2[threadIdx.x >> 5] = z;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tz = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      ta += r1[i];
+      tz += r2[i];
     }
-    out[0] = a;
-    out[1] = z;
+    out[0] = ta;
+    out[1] = tz;
   }
 }
 
@@ -743,7 +761,9 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   la.small = small;
   la.tau = f32 ? 1e-5 : 1e-10;
   la.shift_rel = f32 ? 1e-5 : 1e-12;
-  la.flags = flags;
+  // FP32 Krylov vectors lose local orthogonality at the FP32 level, which biases the trace of
+  // the reconstructed P; the local reorthogonalisation pass removes that bias
+  la.flags = f32 ? (flags | CSS_REORTH_LOCAL) : flags;
   la.Qs = Qs;
   la.X = X;
   la.Z = Z;
@@ -881,7 +901,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     double* out_p = (n_sys == 1) ? Pout : sys[s].P_val;
     k_extract<<<blocks, EX_T, 0, st>>>(k0, k1, b, k0, brow, col_idx, trans, pob, sign, X, Hval, sym, out_p, tpart);
     CSS_LAUNCHED(ctx);
-    k_trace_sum<<<1, 32, 0, st>>>((int32_t)blocks, tpart, tout + 2 * s);
+    k_trace_sum<<<1, 1024, 0, st>>>((int32_t)blocks, tpart, tout + 2 * s);
     CSS_LAUNCHED(ctx);
   }
   k_count_breakdown<<<(unsigned)css_ceil_div(n_col, T), T, 0, st>>>(n_col, m, nblk, cnt, misc + 16);
