@@ -195,8 +195,9 @@ def main():
         dist.barrier()
     dev = torch.device("cuda", local)
     prec = css.CSS_MIXED_FP32 if a.precision == "mixed" else css.CSS_FP64
+    from paper_2605_20918_gb300 import shard
     n_steps = a.warmup + a.steps
-    my = [rank + ws * i for i in range(n_steps)]
+    my = shard.rank_steps(rank, ws, n_steps)
     geoms = build_inputs(a, my)
     # inputs resident in HBM before the timed region
     dev_in = {}
@@ -211,7 +212,7 @@ def main():
     ne = synth.n_electrons(a.n_mol)
 
     def step(i):
-        t = my[i] % a.geometries
+        t = shard.geometry_of(my[i], a.geometries)
         xyz, Hd = dev_in[t]
         nc = ctx.color(xyz, geoms[t][0].box, a.r_col, 1004, colour)
         ctx.probes(colour, Hd.b, 1005, sign)
@@ -239,11 +240,9 @@ def main():
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = ctx.info()["kernel_launches"] - launches0
     if ws > 1:
-        tt = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+        elapsed = shard.max_over_ranks(elapsed, dev)
         dist.barrier()
-    value = elapsed / (a.steps * ws)
+    value = shard.seconds_per_build(elapsed, a.steps, ws)
     last_r, last_nc, last_inf = results[-1]
     spmm_avg = statistics.mean(spmm_ms)
     achieved = last_inf["spmm_flops"] / (spmm_avg * 1e-3) / 1e12
@@ -294,7 +293,7 @@ def main():
         # end to end through css_pbuild with host buffers: pinned host inputs in, P out per step
         pin = {}
         for i in range(a.warmup, n_steps):
-            t = my[i] % a.geometries
+            t = shard.geometry_of(my[i], a.geometries)
             g, H = geoms[t]
             hv = torch.empty(H.val.shape, dtype=torch.float64, pin_memory=True)
             hv.numpy()[...] = H.val
@@ -310,7 +309,7 @@ def main():
         t0 = time.perf_counter()
         h2d = d2h = 0
         for i in range(a.warmup, n_steps):
-            t = my[i] % a.geometries
+            t = shard.geometry_of(my[i], a.geometries)
             pos, Hh, Ph, _ = pin[t]
             ctx.pbuild(pos, geoms[t][0].box, Hh, Ph.numpy(), r_col=a.r_col, kT=0.05, n_elec=ne, m=a.m,
                        precision=prec, flags=flags)
@@ -318,10 +317,8 @@ def main():
             d2h += Ph.numel() * 8
         e2e_t = time.perf_counter() - t0
         if ws > 1:
-            tt = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_t = float(tt.item())
-        line["e2e"] = {"value": e2e_t / (a.steps * ws), "unit": "s/P-build", "h2d_bytes_per_step": h2d // a.steps,
+            e2e_t = shard.max_over_ranks(e2e_t, dev)
+        line["e2e"] = {"value": shard.seconds_per_build(e2e_t, a.steps, ws), "unit": "s/P-build", "h2d_bytes_per_step": h2d // a.steps,
                        "d2h_bytes_per_step": d2h // a.steps, "api": "css_pbuild(CSS_HOST_IO)"}
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         g, H = geoms[my[0] % a.geometries]
