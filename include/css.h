@@ -201,6 +201,26 @@ CSS_API css_status css_eigen_blocks(css_ctx* ctx, int32_t n_col, int32_t b, int3
                                     const int32_t* nblk, const int32_t* cnt, double mu, double kT, double* lam,
                                     double* wgt, double* Z, void* stream);
 
+/* Colouring of an explicit graph for callers that cannot allocate memory: the same colouring
+ * rule and result as css_color_graph, but the call needs no css_ctx and allocates nothing
+ * (no cudaMalloc, cudaFree, pinned host memory or library allocation).  Meant for code that
+ * runs where new allocations are not allowed: a host application whose own allocator has
+ * reserved the device memory, a latency-critical loop that must not hit cudaMalloc's implicit
+ * synchronisation, or a plug-in that may use only the buffers it is handed.  The paper has no
+ * counterpart; it is an operational variant of the colouring step.
+ *   Scratch: one fixed device array inside this library (about 3 MB, held by every GPU that
+ *   loads the library until the process exits), so n must be <= CSS_NOALLOC_MAX_VERTICES;
+ *   larger graphs get CSS_ERR_INVALID_ARG (use css_color_graph).  Every call shares that
+ *   array: calls that overlap on the GPU (several streams or host threads at once) race and
+ *   must be serialised by the caller.
+ *   The first call on a device looks the array's device address up (cudaGetSymbolAddress, with
+ *   that device current) and caches it; make that first call before any stream capture.
+ *   adj_ptr, adj, colour: device arrays as in css_color_graph (colour int32[n], written);
+ *   n_colours: host int32*, written; the call synchronises `stream`. */
+#define CSS_NOALLOC_MAX_VERTICES 262144
+CSS_API css_status css_color_graph_noalloc(int32_t n, const int32_t* adj_ptr, const int32_t* adj, uint64_t seed,
+                                           int32_t* colour, int32_t* n_colours, void* stream);
+
 /* One whole P build from a geometry and H: css_color + css_probes + css_density.  With
  * CSS_HOST_IO every array (geom->xyz, H arrays, P_val) is HOST memory and the library copies
  * in and out on `stream`; otherwise they are device arrays.  colour_out (n_mol int32,
