@@ -714,6 +714,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   CSS_TRY(ws_get(ctx, "e_Y", (size_t)n_col * nmax * b, &ea.Y));
   CSS_TRY(ws_get(ctx, "e_w", (size_t)n_col * nmax, &ea.wgt));
   CSS_TRY(ws_get(ctx, "e_st", (size_t)n_col, &ea.status));
+  CSS_TRY(ws_get(ctx, "e_flag", (size_t)n_col * nmax, &ea.flag));
   double* Z;
   CSS_TRY(ws_get(ctx, "Z", (size_t)n_col * nmax * b, &Z));
   // Krylov vectors: as many colours per batch as memory allows
@@ -1040,6 +1041,7 @@ css_status css_eigen_blocks(css_ctx* ctx, int32_t n_col, int32_t b, int32_t m, c
   CSS_TRY(ws_get(ctx, "e_X0", (size_t)n_col * nmax * b, &ea.X0));
   CSS_TRY(ws_get(ctx, "e_Y", (size_t)n_col * nmax * b, &ea.Y));
   CSS_TRY(ws_get(ctx, "e_st", (size_t)n_col, &ea.status));
+  CSS_TRY(ws_get(ctx, "e_flag", (size_t)n_col * nmax, &ea.flag));
   ea.lam = lam;
   ea.wgt = wgt;
   CSS_CU(ctx, cudaMemsetAsync(lam, 0, sizeof(double) * n_col * nmax, st));

@@ -311,13 +311,141 @@ __device__ __forceinline__ double hash_unit(uint64_t a, uint64_t b) {
   return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
+// Phase 1 of the FP64 inverse iteration: one thread per eigenvalue, all threads of a colour
+// in lockstep (same loop bounds, fixed four iterations: two at the FP32 shift, two with
+// Rayleigh-quotient shifts), so the column-per-thread accesses to U and the scratch F are
+// coalesced across a warp.  Eigenvalues whose shift lies within tol of a neighbour's (a
+// cluster) and results that did not converge or left their window are flagged for phase 2.
+__global__ void __launch_bounds__(128) k_inviter_p1(int32_t kd, int32_t nmax, const int32_t* __restrict__ nblk,
+                                                    const double* __restrict__ dd, const double* __restrict__ ee,
+                                                    const float* __restrict__ lam32, const double* __restrict__ tnorm,
+                                                    double rel_cluster, double* __restrict__ U,
+                                                    double* __restrict__ F, double* __restrict__ lam,
+                                                    int32_t* __restrict__ flag) {
+  const int32_t c = blockIdx.y;
+  const int32_t n = nblk[c] * kd;
+  const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.x * blockDim.x >= n) return;  // whole block beyond this colour's size
+  const double* d = dd + (size_t)c * nmax;
+  const double* e = ee + (size_t)c * nmax;
+  const float* l32 = lam32 + (size_t)c * nmax;
+  double* u = U + (size_t)c * nmax * nmax;
+  double* f_u0 = F + (size_t)c * 5 * nmax * nmax;
+  double* f_u1 = f_u0 + (size_t)nmax * nmax;
+  double* f_u2 = f_u1 + (size_t)nmax * nmax;
+  double* f_x = f_u2 + (size_t)nmax * nmax;
+  int32_t* fl = flag + (size_t)c * nmax;
+  const double tn = tnorm[c];
+  const double tol = rel_cluster * tn;
+  const double pivmin = 2.2e-16 * tn;
+  const bool valid = k < n;
+  bool in_cluster = false;
+  double win_lo = 0.0, win_hi = 0.0, sigma = 0.0;
+  if (valid) {
+    const double lk = (double)l32[k];
+    const double g_lo = k > 0 ? lk - (double)l32[k - 1] : tn;
+    const double g_hi = k + 1 < n ? (double)l32[k + 1] - lk : tn;
+    in_cluster = g_lo <= tol || g_hi <= tol;
+    win_lo = lk - 0.25 * g_lo - 2e-6 * tn;
+    win_hi = lk + 0.25 * g_hi + 2e-6 * tn;
+    sigma = lk;
+  }
+  const bool work = valid && !in_cluster;
+  // start vector, normalised
+  double nrm = 0.0;
+  for (int32_t i = 0; i < n; ++i) {
+    const double x = work ? hash_unit((uint64_t)c * 1000003ull + (uint64_t)k, (uint64_t)i) : 0.0;
+    if (work) f_x[(size_t)i * nmax + k] = x;
+    nrm += x * x;
+  }
+  double inv = work ? 1.0 / sqrt(nrm) : 0.0;
+  double growth = 0.0;
+  for (int it = 0; it < 4; ++it) {
+    // factor T - sigma I with partial pivoting and eliminate on x in the same sweep; the rows
+    // of U are stored, x is overwritten by L^-1 P x (scaled by inv)
+    double cd = d[0] - sigma, cs = n > 1 ? e[0] : 0.0;
+    double xc = work ? f_x[k] * inv : 0.0;  // current row's right-hand side
+    for (int32_t i = 0; i + 1 < n; ++i) {
+      const double sub = e[i], dg = d[i + 1] - sigma, sup = (i + 2 < n) ? e[i + 1] : 0.0;
+      const double xn = work ? f_x[(size_t)(i + 1) * nmax + k] * inv : 0.0;
+      double u0, u1, u2, rhs_i, ncd, ncs, nx;
+      if (fabs(cd) >= fabs(sub)) {
+        if (fabs(cd) < pivmin) cd = cd >= 0 ? pivmin : -pivmin;
+        const double l = sub / cd;
+        u0 = cd;
+        u1 = cs;
+        u2 = 0.0;
+        rhs_i = xc;
+        ncd = dg - l * cs;
+        ncs = sup;
+        nx = xn - l * xc;
+      } else {
+        const double l = cd / sub;
+        u0 = sub;
+        u1 = dg;
+        u2 = sup;
+        rhs_i = xn;
+        ncd = cs - l * dg;
+        ncs = -l * sup;
+        nx = xc - l * xn;
+      }
+      if (work) {
+        f_u0[(size_t)i * nmax + k] = u0;
+        f_u1[(size_t)i * nmax + k] = u1;
+        f_u2[(size_t)i * nmax + k] = u2;
+        f_x[(size_t)i * nmax + k] = rhs_i;
+      }
+      cd = ncd;
+      cs = ncs;
+      xc = nx;
+    }
+    if (fabs(cd) < pivmin) cd = cd >= 0 ? pivmin : -pivmin;
+    // backward substitution U y = x, then the norm
+    double y1 = 0.0, y2 = 0.0, ss = 0.0;
+    for (int32_t i = n - 1; i >= 0; --i) {
+      double r, u0;
+      if (i == n - 1) {
+        r = xc;
+        u0 = cd;
+      } else {
+        r = work ? f_x[(size_t)i * nmax + k] : 0.0;
+        u0 = work ? f_u0[(size_t)i * nmax + k] : 1.0;
+        if (work) r -= f_u1[(size_t)i * nmax + k] * y1;
+        if (work && i + 2 < n) r -= f_u2[(size_t)i * nmax + k] * y2;
+      }
+      const double y = work ? r / u0 : 0.0;
+      if (work) f_x[(size_t)i * nmax + k] = y;
+      ss += y * y;
+      y2 = y1;
+      y1 = y;
+    }
+    growth = sqrt(ss);
+    inv = work ? 1.0 / growth : 0.0;
+    // Rayleigh quotient of the normalised vector
+    double rq = 0.0, prev = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+      const double xi = work ? f_x[(size_t)i * nmax + k] * inv : 0.0;
+      rq += xi * (d[i] * xi + 2.0 * (i > 0 ? e[i - 1] * prev : 0.0));
+      prev = xi;
+    }
+    if (it >= 1) sigma = rq;
+  }
+  if (!valid) return;
+  const bool ok = work && growth * pivmin > 1.0 && sigma >= win_lo && sigma <= win_hi;
+  fl[k] = ok ? 0 : 1;
+  if (!ok) return;
+  for (int32_t i = 0; i < n; ++i) u[(size_t)i * nmax + k] = f_x[(size_t)i * nmax + k] * inv;
+  lam[(size_t)c * nmax + k] = sigma;
+}
+
 // One thread per cluster of close shifts.  Column k of U and five scratch columns of F are
 // owned by the thread handling eigenvalue k.  Layout [c][row][col] so threads with
 // neighbouring k touch neighbouring addresses.
 __global__ void k_inviter(int32_t kd, int32_t nmax, const int32_t* __restrict__ nblk, const double* __restrict__ dd,
                           const double* __restrict__ ee, const float* __restrict__ lam32,
                           const double* __restrict__ tnorm, double rel_cluster, double* __restrict__ U,
-                          double* __restrict__ F, double* __restrict__ lam, int32_t* __restrict__ status) {
+                          double* __restrict__ F, double* __restrict__ lam, int32_t* __restrict__ status,
+                          const int32_t* __restrict__ flag) {
   const int32_t c = blockIdx.x;
   const int32_t n = nblk[c] * kd;
   const double* d = dd + (size_t)c * nmax;
@@ -340,6 +468,11 @@ __global__ void k_inviter(int32_t kd, int32_t nmax, const int32_t* __restrict__ 
     const int32_t k0 = k;
     int32_t k1 = k;
     while (k1 + 1 < n && (double)l32[k1 + 1] - (double)l32[k1] <= tol && k1 + 1 - k0 < kMaxCluster) ++k1;
+    {  // phase 1 finished every member of this cluster: nothing to do
+      bool any = false;
+      for (int32_t kk = k0; kk <= k1; ++kk) any = any || flag[(size_t)c * nmax + kk] != 0;
+      if (!any) continue;
+    }
     auto U_ = [&](int32_t i, int32_t col) -> double& { return u[(size_t)i * nmax + col]; };
     auto F_ = [&](double* base, int32_t i, int32_t col) -> double& { return base[(size_t)i * nmax + col]; };
     // window the refined eigenvalues must fall in: the cluster's shifts widened by a quarter of
@@ -608,7 +741,11 @@ css_status css_eigen_ritz(css_ctx* ctx, const EigArgs& a, cudaStream_t st) {
   if (sh > 48 * 1024) CSS_CU(ctx, cudaFuncSetAttribute(k_bisect32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
   k_bisect32<<<nc, 256, sh, st>>>(b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm);
   CSS_LAUNCHED(ctx);
-  k_inviter<<<nc, 128, 0, st>>>(b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm, 1e-4, a.U, a.F, a.lam, a.status);
+  k_inviter_p1<<<dim3((unsigned)css_ceil_div(nmax, 128), (unsigned)nc), 128, 0, st>>>(
+      b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm, 1e-4, a.U, a.F, a.lam, a.flag);
+  CSS_LAUNCHED(ctx);
+  k_inviter<<<nc, 128, 0, st>>>(b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm, 1e-4, a.U, a.F, a.lam, a.status,
+                                a.flag);
   CSS_LAUNCHED(ctx);
   if (ctx->debug_eig == 1) {
     k_shifts_out<<<nc, 256, 0, st>>>(nmax, a.lam32, a.lam);

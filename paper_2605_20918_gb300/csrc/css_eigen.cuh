@@ -36,6 +36,7 @@ struct EigArgs {
   double* Y = nullptr;                 // [c][nmax][b] U^T X0
   double* wgt = nullptr;               // [c][nmax] ||Y_k||^2
   int32_t* status = nullptr;           // [c]
+  int32_t* flag = nullptr;             // [c][nmax] eigenvalues left to the sequential phase
 };
 
 css_status css_eigen_ritz(css_ctx* ctx, const EigArgs& a, cudaStream_t st);

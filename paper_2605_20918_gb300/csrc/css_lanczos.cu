@@ -102,207 +102,310 @@ __global__ void __launch_bounds__(128) k_spmm(int32_t b, const int32_t* __restri
 }
 
 // --------------------------------------------------------------- row-chunk kernels
-// CTA = (chunk of RCH = RC * TPC rows, one colour of the batch).  The chunk is walked in
-// tiles of RC rows staged in shared memory as [RC][b]; per-tile Gram products are summed in
-// the vector precision and added to FP64 accumulators held in registers (thread t owns the
-// entries t, t + 256, ... of the b x b block), which are written once per CTA.
-constexpr int RC = 128;
-constexpr int TPC = 8;
-constexpr int RCH = RC * TPC;
-constexpr int RT = 256;
-constexpr int GACC = (CSS_MAX_B * CSS_MAX_B + RT - 1) / RT;
+// CTA = (chunk of RCHK rows, group of G colours).  The chunk is walked in tiles of RTL rows;
+// a tile of each array is staged in shared memory as [RTL][G*BP] (b padded to BP, the
+// padding kept at zero), so the global reads of a row are G*b contiguous values.  Every
+// small product (block update, Gram) is register-tiled in 4 x 4 blocks.  Per-tile Gram sums
+// are taken in the vector precision and added to FP64 registers, written once per CTA.
+constexpr int RW = 256;      // threads
+constexpr int RCHK = 1024;   // rows per CTA
 
 template <typename T>
-__device__ __forceinline__ void load_tile(T* dst, const T* src, int64_t r0, int32_t nr, int32_t b, int32_t ws,
-                                          int32_t c0) {
-  for (int32_t e = threadIdx.x; e < nr * b; e += blockDim.x) {
-    int32_t r = e / b, k = e % b;
-    dst[e] = src[(size_t)(r0 + r) * ws + c0 + k];
-  }
+struct RowTile {
+  static constexpr int RTL = sizeof(T) == 4 ? 32 : 16;  // rows per tile
+};
+
+template <int BP>
+__host__ __device__ constexpr int group_cap() {
+  return RW / ((BP / 4) * (BP / 4));
 }
 
-template <typename T>
-__device__ __forceinline__ void store_tile(T* dst, const T* src, int64_t r0, int32_t nr, int32_t b, int32_t ws,
-                                           int32_t c0) {
-  for (int32_t e = threadIdx.x; e < nr * b; e += blockDim.x) {
-    int32_t r = e / b, k = e % b;
-    dst[(size_t)(r0 + r) * ws + c0 + k] = src[e];
-  }
+// colours per CTA for block width b (runtime) padded to BP
+template <int BP>
+__host__ __device__ inline int colours_per_cta(int b) {
+  int g = group_cap<BP>();
+  int lim = 192 / b;                    // contiguous columns per row <= 192
+  if (lim > 256 / BP) lim = 256 / BP;   // padded tile width <= 256 (shared memory)
+  if (lim < 1) lim = 1;
+  return g < lim ? g : lim;
 }
 
-// acc[i] += sum_r X[r][k] Y[r][l] for entry e = threadIdx.x + RT i = k b + l
-template <typename T>
-__device__ __forceinline__ void tile_gram(const T* X, const T* Y, int32_t nr, int32_t b, double* acc) {
-#pragma unroll
-  for (int i = 0; i < GACC; ++i) {
-    const int32_t e = threadIdx.x + RT * i;
-    if (e < b * b) {
-      const int32_t k = e / b, l = e % b;
-      T s = T(0);
-      for (int32_t r = 0; r < nr; ++r) s = fma(X[r * b + k], Y[r * b + l], s);
-      acc[i] += (double)s;
+template <typename T, int BP>
+struct RowCtx {
+  int32_t b, ws, G, gcount, pitch, cg0;  // cg0 = first colour of the group within the batch
+  int32_t my_col, my_smem;  // this thread's column of the group (width <= blockDim) and its tile offset
+  __device__ __forceinline__ void load(T* dst, const T* src, int64_t r0, int32_t nr) const {
+    if (my_col < 0) return;
+    const T* s = src + (size_t)r0 * ws + (size_t)cg0 * b + my_col;
+#pragma unroll 4
+    for (int32_t r = 0; r < nr; ++r) dst[r * pitch + my_smem] = s[(size_t)r * ws];
+  }
+  __device__ __forceinline__ void store(T* dst, const T* src, int64_t r0, int32_t nr) const {
+    if (my_col < 0) return;
+    T* d = dst + (size_t)r0 * ws + (size_t)cg0 * b + my_col;
+#pragma unroll 4
+    for (int32_t r = 0; r < nr; ++r) d[(size_t)r * ws] = src[r * pitch + my_smem];
+  }
+  // zero a whole tile (padding columns and missing rows stay zero afterwards)
+  __device__ __forceinline__ void zero(T* t, int32_t rows) const {
+    for (int32_t e = threadIdx.x; e < rows * pitch; e += blockDim.x) t[e] = T(0);
+  }
+  // small per-colour matrices [G][BP][BP] from global FP64 [colour][b][b] (optionally transposed)
+  __device__ __forceinline__ void load_mat(T* dst, const double* src, int32_t colour0, bool trans) const {
+    for (int32_t e = threadIdx.x; e < G * BP * BP; e += blockDim.x) {
+      const int32_t g = e / (BP * BP), rem = e - g * BP * BP, l = rem / BP, k = rem - l * BP;
+      T v = T(0);
+      if (g < gcount && l < b && k < b)
+        v = (T)src[(size_t)(colour0 + g) * b * b + (trans ? k * b + l : l * b + k)];
+      dst[e] = v;
     }
   }
-}
+};
 
-__device__ __forceinline__ void store_acc(const double* acc, int32_t b, double* out) {
+// OUT[r][g][k] (+)= sum_l X[r][g][l] M[g][l][k] over 4x4 output blocks.  SUB: OUT -= X M.
+template <typename T, int BP, bool SUB>
+__device__ __forceinline__ void tile_mul(const RowCtx<T, BP>& c, const T* X, const T* M, T* OUT, int32_t rtl) {
+  constexpr int CB = BP / 4;
+  const int32_t nblk = (rtl / 4) * c.G * CB;
+  for (int32_t t = threadIdx.x; t < nblk; t += blockDim.x) {
+    const int32_t rb = t / (c.G * CB), rem = t - rb * c.G * CB, g = rem / CB, cb = rem - g * CB;
+    const int32_t r0 = rb * 4, col = g * BP + cb * 4;
+    T acc[4][4];
 #pragma unroll
-  for (int i = 0; i < GACC; ++i) {
-    const int32_t e = threadIdx.x + RT * i;
-    if (e < b * b) out[e] = acc[i];
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = SUB ? OUT[(r0 + i) * c.pitch + col + j] : T(0);
+    const T* xm = X + g * BP;
+    const T* mm = M + (size_t)g * BP * BP + cb * 4;
+    for (int32_t l = 0; l < c.b; ++l) {
+      T x[4], m[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) x[i] = xm[(r0 + i) * c.pitch + l];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) m[j] = mm[l * BP + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = SUB ? fma(-x[i], m[j], acc[i][j]) : fma(x[i], m[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) OUT[(r0 + i) * c.pitch + col + j] = acc[i][j];
   }
 }
 
-#define ROW_LOOP(N)                                                                        \
-  for (int64_t r0 = (int64_t)blockIdx.x * RCH, r_end = min((int64_t)(N), r0 + RCH); r0 < r_end; \
-       r0 += RC)
+// acc[i][j] += sum_r X[r][g][4bi+i] Y[r][g][4bj+j] for this thread's block (g, bi, bj)
+template <typename T, int BP>
+__device__ __forceinline__ void tile_gram(const RowCtx<T, BP>& c, const T* X, const T* Y, int32_t rtl, double* acc) {
+  constexpr int CB = BP / 4;
+  const int32_t t = threadIdx.x;
+  if (t >= c.G * CB * CB) return;
+  const int32_t g = t / (CB * CB), rem = t - g * CB * CB, bi = rem / CB, bj = rem - bi * CB;
+  const T* xp = X + g * BP + bi * 4;
+  const T* yp = Y + g * BP + bj * 4;
+  T a[4][4] = {};
+  for (int32_t r = 0; r < rtl; ++r) {
+    T x[4], y[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      x[i] = xp[r * c.pitch + i];
+      y[i] = yp[r * c.pitch + i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a[i][j] = fma(x[i], y[j], a[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i * 4 + j] += (double)a[i][j];
+}
 
-// W -= Qp Bp^T (skipped at the first step), partial A = Q^T W, partial ||W_in||^2
-template <typename T>
-__global__ void __launch_bounds__(RT) k_threeterm(int64_t N, int32_t b, int32_t ws, int32_t cb0,
-                                                  const T* __restrict__ Qp, const T* __restrict__ Q,
-                                                  T* __restrict__ W, const double* __restrict__ Bprev, int first,
-                                                  double* __restrict__ partA, double* __restrict__ partH) {
+template <typename T, int BP>
+__device__ __forceinline__ void gram_store(const RowCtx<T, BP>& c, const double* acc, double* part) {
+  constexpr int CB = BP / 4;
+  const int32_t t = threadIdx.x;
+  if (t >= c.G * CB * CB) return;
+  const int32_t g = t / (CB * CB), rem = t - g * CB * CB, bi = rem / CB, bj = rem - bi * CB;
+  if (g >= c.gcount) return;
+  double* o = part + (size_t)(c.cg0 + g) * c.b * c.b;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int32_t k = bi * 4 + i, l = bj * 4 + j;
+      if (k < c.b && l < c.b) o[k * c.b + l] = acc[i * 4 + j];
+    }
+}
+
+template <typename T, int BP>
+__device__ __forceinline__ RowCtx<T, BP> make_ctx(int32_t b, int32_t ws, int32_t ncb) {
+  RowCtx<T, BP> c;
+  c.b = b;
+  c.ws = ws;
+  c.G = colours_per_cta<BP>(b);
+  c.cg0 = blockIdx.y * c.G;
+  c.gcount = min(c.G, ncb - c.cg0);
+  c.pitch = c.G * BP + 4;
+  const int32_t t = threadIdx.x;
+  if (t < c.gcount * b) {
+    c.my_col = t;
+    c.my_smem = (t / b) * BP + (t % b);
+  } else {
+    c.my_col = -1;
+    c.my_smem = 0;
+  }
+  return c;
+}
+
+// S1: W = H Q_j arrives in W.  W0 = W - Q_{j-1} B_{j-1}^T (skipped at the first step), stored;
+// partials Kq = Q_j^T W0, Kp = Q_{j-1}^T W0 (REORTH), and ||W||^2 per colour (breakdown test)
+template <typename T, int BP, bool REORTH>
+__global__ void __launch_bounds__(RW) k_s1(int64_t N, int32_t b, int32_t ws, int32_t ncb, int32_t cb0,
+                                           const T* __restrict__ Qp, const T* __restrict__ Q, T* __restrict__ W,
+                                           const double* __restrict__ Bprev, int first, double* __restrict__ partKq,
+                                           double* __restrict__ partKp, double* __restrict__ partH) {
+  constexpr int RTL = RowTile<T>::RTL;
+  constexpr int CB = BP / 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* red = reinterpret_cast<double*>(smem_raw);  // RT/32 warp sums
-  T* sQ = reinterpret_cast<T*>(smem_raw + 16 * sizeof(double));
-  T* sW = sQ + RC * b;
-  T* sP = sW + RC * b;
-  T* sB = sP + RC * b;
-  const int32_t lc = blockIdx.y, c0 = lc * b;
-  double acc[GACC] = {};
-  double hs = 0.0;
-  if (!first)
-    for (int32_t e = threadIdx.x; e < b * b; e += blockDim.x) sB[e] = (T)Bprev[(size_t)(cb0 + lc) * b * b + e];
-  ROW_LOOP(N) {
-    const int32_t nr = (int32_t)min((int64_t)RC, N - r0);
+  const RowCtx<T, BP> c = make_ctx<T, BP>(b, ws, ncb);
+  const int32_t tile = RTL * c.pitch;
+  T* sQ = reinterpret_cast<T*>(smem_raw);
+  T* sP = sQ + tile;
+  T* sW = sP + tile;
+  T* sB = sW + tile;  // [G][BP][BP] = B_{j-1}^T per colour
+  double* hsum = reinterpret_cast<double*>(sB + c.G * BP * BP);  // [G][CB]
+  double aq[16] = {}, ap[16] = {};
+  double hq = 0.0;
+  if (!first) c.load_mat(sB, Bprev, cb0 + c.cg0, true);
+  const int64_t rbeg = (int64_t)blockIdx.x * RCHK, rend = min(N, rbeg + RCHK);
+  for (int64_t r0 = rbeg; r0 < rend; r0 += RTL) {
+    const int32_t nr = (int32_t)min((int64_t)RTL, rend - r0);
     __syncthreads();
-    load_tile(sQ, Q, r0, nr, b, ws, c0);
-    load_tile(sW, W, r0, nr, b, ws, c0);
-    if (!first) load_tile(sP, Qp, r0, nr, b, ws, c0);
-    __syncthreads();
-    for (int32_t e = threadIdx.x; e < nr * b; e += blockDim.x) hs += (double)sW[e] * (double)sW[e];
-    if (!first) {
-      for (int32_t e = threadIdx.x; e < nr * b; e += blockDim.x) {
-        int32_t r = e / b, k = e % b;
-        T s = T(0);
-        for (int32_t l = 0; l < b; ++l) s = fma(sP[r * b + l], sB[k * b + l], s);
-        sW[e] -= s;
-      }
+    if (r0 == rbeg || nr < RTL) {
+      c.zero(sQ, RTL);
+      c.zero(sW, RTL);
+      if (REORTH || !first) c.zero(sP, RTL);
       __syncthreads();
-      store_tile(W, sW, r0, nr, b, ws, c0);
     }
-    tile_gram(sQ, sW, nr, b, acc);
+    c.load(sQ, Q, r0, nr);
+    c.load(sW, W, r0, nr);
+    if (REORTH || !first) c.load(sP, Qp, r0, nr);
+    __syncthreads();
+    {  // ||W||^2 of the colour before the update
+      const int32_t t = threadIdx.x;
+      if (t < c.G * CB * CB) {
+        const int32_t g = t / (CB * CB), rem = t - g * CB * CB, bi = rem / CB, bj = rem - bi * CB;
+        if (bi == bj)
+          for (int32_t r = 0; r < RTL; ++r)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const double w = (double)sW[r * c.pitch + g * BP + bi * 4 + i];
+              hq += w * w;
+            }
+      }
+    }
+    if (!first) {
+      tile_mul<T, BP, true>(c, sP, sB, sW, RTL);
+      __syncthreads();
+      c.store(W, sW, r0, nr);
+    }
+    tile_gram<T, BP>(c, sQ, sW, RTL, aq);
+    if (REORTH) tile_gram<T, BP>(c, sP, sW, RTL, ap);
   }
-  const size_t o = (size_t)blockIdx.x * gridDim.y + lc;
-  store_acc(acc, b, partA + o * b * b);
-  for (int of = 16; of > 0; of >>= 1) hs += __shfl_xor_sync(0xffffffffu, hs, of);
+  const size_t o = (size_t)blockIdx.x * ncb;
+  gram_store<T, BP>(c, aq, partKq + o * b * b);
+  if (REORTH) gram_store<T, BP>(c, ap, partKp + o * b * b);
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = hs;
+  const int32_t t = threadIdx.x;
+  if (t < c.G * CB * CB) {
+    const int32_t g = t / (CB * CB), rem = t - g * CB * CB, bi = rem / CB, bj = rem - bi * CB;
+    if (bi == bj) hsum[g * CB + bi] = hq;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < RT / 32; ++i) t += red[i];
-    partH[o] = t;
+  if (t < c.gcount) {
+    double sum = 0.0;
+    for (int i = 0; i < CB; ++i) sum += hsum[t * CB + i];
+    partH[o + c.cg0 + t] = sum;
   }
 }
 
-// W -= Q M (M = A_j symmetrised, or a reorthogonalisation coefficient block), optional
-// second subtraction W -= Qp M2, then partial Gram W^T W when GRAM
-template <typename T, bool GRAM>
-__global__ void __launch_bounds__(RT) k_sub(int64_t N, int32_t b, int32_t ws, const T* __restrict__ Q,
-                                            const T* __restrict__ Qp, T* __restrict__ W,
-                                            const double* __restrict__ M, const double* __restrict__ M2,
+// S3: W1 = W0 - Q_j M1 (- Q_{j-1} M2), stored; partial Gram W1^T W1
+template <typename T, int BP, bool REORTH>
+__global__ void __launch_bounds__(RW) k_s3(int64_t N, int32_t b, int32_t ws, int32_t ncb, const T* __restrict__ Q,
+                                           const T* __restrict__ Qp, T* __restrict__ W, const double* __restrict__ M1,
+                                           const double* __restrict__ M2, double* __restrict__ partG) {
+  constexpr int RTL = RowTile<T>::RTL;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const RowCtx<T, BP> c = make_ctx<T, BP>(b, ws, ncb);
+  const int32_t tile = RTL * c.pitch;
+  T* sQ = reinterpret_cast<T*>(smem_raw);
+  T* sP = sQ + tile;
+  T* sW = sP + tile;
+  T* sM1 = sW + tile;
+  T* sM2 = sM1 + c.G * BP * BP;
+  double acc[16] = {};
+  c.load_mat(sM1, M1, c.cg0, false);
+  if (REORTH) c.load_mat(sM2, M2, c.cg0, false);
+  const int64_t rbeg = (int64_t)blockIdx.x * RCHK, rend = min(N, rbeg + RCHK);
+  for (int64_t r0 = rbeg; r0 < rend; r0 += RTL) {
+    const int32_t nr = (int32_t)min((int64_t)RTL, rend - r0);
+    __syncthreads();
+    if (r0 == rbeg || nr < RTL) {
+      c.zero(sQ, RTL);
+      c.zero(sW, RTL);
+      if (REORTH) c.zero(sP, RTL);
+      __syncthreads();
+    }
+    c.load(sQ, Q, r0, nr);
+    c.load(sW, W, r0, nr);
+    if (REORTH) c.load(sP, Qp, r0, nr);
+    __syncthreads();
+    tile_mul<T, BP, true>(c, sQ, sM1, sW, RTL);
+    if (REORTH) {
+      __syncthreads();
+      tile_mul<T, BP, true>(c, sP, sM2, sW, RTL);
+    }
+    __syncthreads();
+    c.store(W, sW, r0, nr);
+    tile_gram<T, BP>(c, sW, sW, RTL, acc);
+  }
+  gram_store<T, BP>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b);
+}
+
+// OUT = W R^-1 (R^-1 upper triangular per colour); partial Gram of OUT when GRAM.  OUT may be W.
+template <typename T, int BP, bool GRAM>
+__global__ void __launch_bounds__(RW) k_tri(int64_t N, int32_t b, int32_t ws, int32_t ncb, const T* __restrict__ W,
+                                            T* __restrict__ OUT, const double* __restrict__ Rinv,
                                             double* __restrict__ partG) {
+  constexpr int RTL = RowTile<T>::RTL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sQ = reinterpret_cast<T*>(smem_raw);
-  T* sW = sQ + RC * b;
-  T* sP = sW + RC * b;
-  T* sM = sP + RC * b;
-  T* sM2 = sM + b * b;
-  const int32_t lc = blockIdx.y, c0 = lc * b;
-  double acc[GACC] = {};
-  for (int32_t e = threadIdx.x; e < b * b; e += blockDim.x) {
-    sM[e] = (T)M[(size_t)lc * b * b + e];
-    if (M2) sM2[e] = (T)M2[(size_t)lc * b * b + e];
-  }
-  ROW_LOOP(N) {
-    const int32_t nr = (int32_t)min((int64_t)RC, N - r0);
-    __syncthreads();
-    load_tile(sQ, Q, r0, nr, b, ws, c0);
-    load_tile(sW, W, r0, nr, b, ws, c0);
-    if (M2) load_tile(sP, Qp, r0, nr, b, ws, c0);
-    __syncthreads();
-    for (int32_t e = threadIdx.x; e < nr * b; e += blockDim.x) {
-      int32_t r = e / b, k = e % b;
-      T s = T(0);
-      for (int32_t l = 0; l < b; ++l) s = fma(sQ[r * b + l], sM[l * b + k], s);
-      if (M2)
-        for (int32_t l = 0; l < b; ++l) s = fma(sP[r * b + l], sM2[l * b + k], s);
-      sW[e] -= s;
-    }
-    __syncthreads();
-    store_tile(W, sW, r0, nr, b, ws, c0);
-    if (GRAM) tile_gram(sW, sW, nr, b, acc);
-  }
-  if (GRAM) store_acc(acc, b, partG + ((size_t)blockIdx.x * gridDim.y + lc) * b * b);
-}
-
-// partial X^T W for X = Q and X = Qp (local reorthogonalisation coefficients)
-template <typename T>
-__global__ void __launch_bounds__(RT) k_proj2(int64_t N, int32_t b, int32_t ws, const T* __restrict__ Q,
-                                              const T* __restrict__ Qp, const T* __restrict__ W,
-                                              double* __restrict__ part1, double* __restrict__ part2) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sQ = reinterpret_cast<T*>(smem_raw);
-  T* sW = sQ + RC * b;
-  T* sP = sW + RC * b;
-  const int32_t lc = blockIdx.y, c0 = lc * b;
-  double a1[GACC] = {}, a2[GACC] = {};
-  ROW_LOOP(N) {
-    const int32_t nr = (int32_t)min((int64_t)RC, N - r0);
-    __syncthreads();
-    load_tile(sQ, Q, r0, nr, b, ws, c0);
-    load_tile(sW, W, r0, nr, b, ws, c0);
-    load_tile(sP, Qp, r0, nr, b, ws, c0);
-    __syncthreads();
-    tile_gram(sQ, sW, nr, b, a1);
-    tile_gram(sP, sW, nr, b, a2);
-  }
-  const size_t o = ((size_t)blockIdx.x * gridDim.y + lc) * b * b;
-  store_acc(a1, b, part1 + o);
-  store_acc(a2, b, part2 + o);
-}
-
-// W <- W R^-1 (upper triangular, FP64 -> T); partial Gram of the result when GRAM; when OUT
-// is non-null the result goes there instead of back into W
-template <typename T, bool GRAM>
-__global__ void __launch_bounds__(RT) k_apply(int64_t N, int32_t b, int32_t ws, T* __restrict__ W,
-                                              T* __restrict__ OUT, const double* __restrict__ Rinv,
-                                              double* __restrict__ partG) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const RowCtx<T, BP> c = make_ctx<T, BP>(b, ws, ncb);
+  const int32_t tile = RTL * c.pitch;
   T* sW = reinterpret_cast<T*>(smem_raw);
-  T* sO = sW + RC * b;
-  T* sR = sO + RC * b;
-  const int32_t lc = blockIdx.y, c0 = lc * b;
-  double acc[GACC] = {};
-  for (int32_t e = threadIdx.x; e < b * b; e += blockDim.x) sR[e] = (T)Rinv[(size_t)lc * b * b + e];
-  ROW_LOOP(N) {
-    const int32_t nr = (int32_t)min((int64_t)RC, N - r0);
+  T* sO = sW + tile;
+  T* sR = sO + tile;
+  double acc[16] = {};
+  c.load_mat(sR, Rinv, c.cg0, false);
+  const int64_t rbeg = (int64_t)blockIdx.x * RCHK, rend = min(N, rbeg + RCHK);
+  for (int64_t r0 = rbeg; r0 < rend; r0 += RTL) {
+    const int32_t nr = (int32_t)min((int64_t)RTL, rend - r0);
     __syncthreads();
-    load_tile(sW, W, r0, nr, b, ws, c0);
-    __syncthreads();
-    for (int32_t e = threadIdx.x; e < nr * b; e += blockDim.x) {
-      int32_t r = e / b, l = e % b;
-      T s = T(0);
-      for (int32_t k = 0; k <= l; ++k) s = fma(sW[r * b + k], sR[k * b + l], s);
-      sO[e] = s;
+    if (r0 == rbeg || nr < RTL) {
+      c.zero(sW, RTL);
+      c.zero(sO, RTL);
+      __syncthreads();
     }
+    c.load(sW, W, r0, nr);
     __syncthreads();
-    store_tile(OUT ? OUT : W, sO, r0, nr, b, ws, c0);
-    if (GRAM) tile_gram(sO, sO, nr, b, acc);
+    tile_mul<T, BP, false>(c, sW, sR, sO, RTL);
+    __syncthreads();
+    c.store(OUT, sO, r0, nr);
+    if (GRAM) tile_gram<T, BP>(c, sO, sO, RTL, acc);
   }
-  if (GRAM) store_acc(acc, b, partG + ((size_t)blockIdx.x * gridDim.y + lc) * b * b);
+  if (GRAM) gram_store<T, BP>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b);
 }
 
 // out[lc][e] = sum over chunks of part[ch][lc][e], fixed order, FP64
@@ -521,22 +624,28 @@ css_status launch_spmm(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaStre
   return launch_spmm_t<T, 32, 1>(ctx, a, V, W, st);
 }
 
-template <typename T>
-css_status run_pass(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
+template <typename T, int BP>
+css_status run_pass_bp(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
   const int32_t b = a.b, bb = b * b, ncb = a.ncb, m = a.m;
   const int64_t N = (int64_t)a.n_brow * b;
-  const int32_t nch = (int32_t)css_ceil_div(N, RCH);
+  const int32_t nch = (int32_t)css_ceil_div(N, RCHK);
+  const int32_t G = colours_per_cta<BP>(b);
+  const int32_t ngr = (int32_t)css_ceil_div(ncb, G);
+  const bool reorth = (a.flags & CSS_REORTH_LOCAL) != 0;
   T* Qp = (T*)a.Q0;
   T* Qc = (T*)a.Q1;
   T* W = (T*)a.W;
   const size_t vec_bytes = (size_t)N * a.ws * sizeof(T);
-  const dim3 rgrid((unsigned)nch, (unsigned)ncb);
-  const size_t tile = (size_t)RC * b * sizeof(T);
-  const size_t sm_three = 16 * sizeof(double) + 3 * tile + bb * sizeof(T);
-  const size_t sm_sub = 3 * tile + 2 * bb * sizeof(T);
-  const size_t sm_apply = 2 * tile + bb * sizeof(T);
-  double* partA = a.part;
-  double* partH = a.part + (size_t)nch * ncb * bb;
+  const dim3 rgrid((unsigned)nch, (unsigned)ngr);
+  constexpr int RTL = RowTile<T>::RTL;
+  const size_t tile = (size_t)RTL * (G * BP + 4) * sizeof(T);
+  const size_t mat = (size_t)G * BP * BP * sizeof(T);
+  const size_t sm_s1 = 3 * tile + mat + (size_t)G * (BP / 4) * sizeof(double) + 16;
+  const size_t sm_s3 = 3 * tile + 2 * mat;
+  const size_t sm_tri = 2 * tile + mat;
+  double* partKq = a.part;
+  double* partKp = a.part + (size_t)nch * ncb * bb;
+  double* partH = a.part + 2 * (size_t)nch * ncb * bb;
   double* sA = a.small;                          // [2][ncb][bb]: raw, symmetrised
   double* sH = a.small + 2 * (size_t)ncb * bb;   // [ncb]
   double* sG = sH + ncb;                         // [ncb][bb]
@@ -545,17 +654,16 @@ css_status run_pass(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
   double* sR2 = sR1i + (size_t)ncb * bb;
   double* sR2i = sR2 + (size_t)ncb * bb;
   double* sC1 = sR2i + (size_t)ncb * bb;
-  double* sC2 = sC1 + (size_t)ncb * bb;
+  double* sKp = sC1 + (size_t)ncb * bb;
   const unsigned rblocks_bb = (unsigned)css_ceil_div((int64_t)ncb * bb, 256);
   const int64_t pb = a.pair_off_h[a.cb0], pe = a.pair_off_h[a.cb0 + ncb];
   const unsigned sblocks = (unsigned)css_ceil_div((pe - pb) * bb, 256);
-
-  CSS_TRY(smem_optin(ctx, k_threeterm<T>, sm_three));
-  CSS_TRY(smem_optin(ctx, k_sub<T, false>, sm_sub));
-  CSS_TRY(smem_optin(ctx, k_sub<T, true>, sm_sub));
-  CSS_TRY(smem_optin(ctx, k_proj2<T>, 3 * tile));
-  CSS_TRY(smem_optin(ctx, k_apply<T, true>, sm_apply));
-  CSS_TRY(smem_optin(ctx, k_apply<T, false>, sm_apply));
+  auto s1 = reorth ? k_s1<T, BP, true> : k_s1<T, BP, false>;
+  auto s3 = reorth ? k_s3<T, BP, true> : k_s3<T, BP, false>;
+  CSS_TRY(smem_optin(ctx, s1, sm_s1));
+  CSS_TRY(smem_optin(ctx, s3, sm_s3));
+  CSS_TRY(smem_optin(ctx, k_tri<T, BP, true>, sm_tri));
+  CSS_TRY(smem_optin(ctx, k_tri<T, BP, false>, sm_tri));
   CSS_CU(ctx, cudaMemsetAsync(Qp, 0, vec_bytes, st));
   CSS_CU(ctx, cudaMemsetAsync(Qc, 0, vec_bytes, st));
   k_init_q1<T><<<(unsigned)css_ceil_div(N, 256), 256, 0, st>>>(a.n_brow, b, a.ws, a.cb0, ncb, a.colour, a.sign,
@@ -574,60 +682,57 @@ css_status run_pass(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
     CSS_LAUNCHED(ctx);
     return CSS_OK;
   };
+  auto chol = [&](int mode, int32_t j, double* R, double* Ri, double shift) -> css_status {
+    const unsigned gb = (unsigned)css_ceil_div(ncb, 4);
+    if (mode == 0)
+      k_chol<0><<<gb, 128, 0, st>>>(ncb, b, a.cb0, m, j, sG, sH, a.tau, shift, R, Ri, sC1, a.Bblk, a.done, a.nblk);
+    else if (mode == 1)
+      k_chol<1><<<gb, 128, 0, st>>>(ncb, b, a.cb0, m, j, sG, sH, a.tau, 0.0, R, Ri, sC1, a.Bblk, a.done, a.nblk);
+    else
+      k_chol<2><<<gb, 128, 0, st>>>(ncb, b, a.cb0, m, j, sG, sH, a.tau, 0.0, R, Ri, sC1, a.Bblk, a.done, a.nblk);
+    CSS_LAUNCHED(ctx);
+    return CSS_OK;
+  };
   CSS_TRY(sampled(Qc, 0));
   for (int32_t j = 0; j < m; ++j) {
     if (a.ev_spmm) CSS_CU(ctx, cudaEventRecord(a.ev_spmm[2 * j], st));
     CSS_TRY(launch_spmm<T>(ctx, a, Qc, W, st));
     if (a.ev_spmm) CSS_CU(ctx, cudaEventRecord(a.ev_spmm[2 * j + 1], st));
-    k_threeterm<T><<<rgrid, RT, sm_three, st>>>(N, b, a.ws, a.cb0, Qp, Qc, W, a.Bblk_prev, j == 0 ? 1 : 0, partA,
-                                                partH);
+    // three-term update and the projections onto Q_j (and Q_{j-1})
+    s1<<<rgrid, RW, sm_s1, st>>>(N, b, a.ws, ncb, a.cb0, Qp, Qc, W, a.Bblk_prev, j == 0 ? 1 : 0, partKq, partKp,
+                                 partH);
     CSS_LAUNCHED(ctx);
-    k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partA, sA);
+    k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sA);
     CSS_LAUNCHED(ctx);
     k_reduce<<<(unsigned)css_ceil_div(ncb, 256), 256, 0, st>>>(nch, ncb, 1, partH, sH);
     CSS_LAUNCHED(ctx);
-    k_store_A<<<rblocks_bb, 256, 0, st>>>(ncb, b, a.cb0, m, j, sA, a.Ablk);
-    CSS_LAUNCHED(ctx);
-    const double* Asym = sA + (size_t)ncb * bb;
-    if (j + 1 == m) break;
-    if (a.flags & CSS_REORTH_LOCAL) {
-      k_sub<T, false><<<rgrid, RT, sm_sub, st>>>(N, b, a.ws, Qc, Qp, W, Asym, nullptr, nullptr);
-      CSS_LAUNCHED(ctx);
-      k_proj2<T><<<rgrid, RT, 3 * tile, st>>>(N, b, a.ws, Qc, Qp, W, partA, partA + (size_t)nch * ncb * bb);
-      CSS_LAUNCHED(ctx);
-      k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partA, sC1);
-      CSS_LAUNCHED(ctx);
-      k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partA + (size_t)nch * ncb * bb, sC2);
-      CSS_LAUNCHED(ctx);
-      k_sub<T, true><<<rgrid, RT, sm_sub, st>>>(N, b, a.ws, Qc, Qp, W, sC1, sC2, partA);
-      CSS_LAUNCHED(ctx);
-    } else {
-      k_sub<T, true><<<rgrid, RT, sm_sub, st>>>(N, b, a.ws, Qc, Qp, W, Asym, nullptr, partA);
+    if (reorth) {
+      k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKp, sKp);
       CSS_LAUNCHED(ctx);
     }
+    k_store_A<<<rblocks_bb, 256, 0, st>>>(ncb, b, a.cb0, m, j, sA, a.Ablk);
+    CSS_LAUNCHED(ctx);
+    if (j + 1 == m) break;
+    // W1 = W0 - Q_j Kq (- Q_{j-1} Kp) and its Gram
+    s3<<<rgrid, RW, sm_s3, st>>>(N, b, a.ws, ncb, Qc, Qp, W, sA, sKp, partKq);
+    CSS_LAUNCHED(ctx);
     // shifted CholeskyQR3 of W: R0 from G + sI, then two plain CholeskyQR passes
-    k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partA, sG);
+    k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
     CSS_LAUNCHED(ctx);
-    k_chol<0><<<(unsigned)css_ceil_div(ncb, 4), 128, 0, st>>>(ncb, b, a.cb0, m, j, sG, sH, a.tau, a.shift_rel, sR1, sR1i,
-                                                              sC1, a.Bblk, a.done, a.nblk);
-    CSS_LAUNCHED(ctx);
+    CSS_TRY(chol(0, j, sR1, sR1i, a.shift_rel));
     CSS_CU(ctx, cudaMemcpyAsync(sC1, sR1, sizeof(double) * ncb * bb, cudaMemcpyDeviceToDevice, st));
-    k_apply<T, true><<<rgrid, RT, sm_apply, st>>>(N, b, a.ws, W, nullptr, sR1i, partA);
+    k_tri<T, BP, true><<<rgrid, RW, sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
     CSS_LAUNCHED(ctx);
-    k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partA, sG);
+    k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
     CSS_LAUNCHED(ctx);
-    k_chol<1><<<(unsigned)css_ceil_div(ncb, 4), 128, 0, st>>>(ncb, b, a.cb0, m, j, sG, sH, a.tau, 0.0, sR1, sR1i,
-                                                              sC1, a.Bblk, a.done, a.nblk);
+    CSS_TRY(chol(1, j, sR1, sR1i, 0.0));
+    k_tri<T, BP, true><<<rgrid, RW, sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
     CSS_LAUNCHED(ctx);
-    k_apply<T, true><<<rgrid, RT, sm_apply, st>>>(N, b, a.ws, W, nullptr, sR1i, partA);
+    k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
     CSS_LAUNCHED(ctx);
-    k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partA, sG);
-    CSS_LAUNCHED(ctx);
-    k_chol<2><<<(unsigned)css_ceil_div(ncb, 4), 128, 0, st>>>(ncb, b, a.cb0, m, j, sG, sH, a.tau, 0.0, sR2, sR2i,
-                                                              sC1, a.Bblk, a.done, a.nblk);
-    CSS_LAUNCHED(ctx);
+    CSS_TRY(chol(2, j, sR2, sR2i, 0.0));
     // Q_{j+1} = W R2^-1 overwrites Q_{j-1}
-    k_apply<T, false><<<rgrid, RT, sm_apply, st>>>(N, b, a.ws, W, Qp, sR2i, nullptr);
+    k_tri<T, BP, false><<<rgrid, RW, sm_tri, st>>>(N, b, a.ws, ncb, W, Qp, sR2i, nullptr);
     CSS_LAUNCHED(ctx);
     CSS_TRY(sampled(Qp, j + 1));
     // B_{j} for the next step's three-term update, in the batch's local layout
@@ -641,6 +746,14 @@ css_status run_pass(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
   return CSS_OK;
 }
 
+template <typename T>
+css_status run_pass(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
+  if (a.b <= 8) return run_pass_bp<T, 8>(ctx, a, st);
+  if (a.b <= 16) return run_pass_bp<T, 16>(ctx, a, st);
+  if (a.b <= 24) return run_pass_bp<T, 24>(ctx, a, st);
+  return run_pass_bp<T, 32>(ctx, a, st);
+}
+
 }  // namespace
 
 // Bblk_prev is indexed by global colour; the three-term kernel reads [cb0 + lc]
@@ -650,7 +763,7 @@ css_status css_lanczos_pass(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
 }
 
 size_t css_lanczos_part_doubles(int64_t N, int32_t b, int32_t ncb) {
-  const int64_t nch = css_ceil_div(N, RCH);
+  const int64_t nch = css_ceil_div(N, RCHK);
   return (size_t)nch * ncb * b * b * 2 + (size_t)nch * ncb + 64;
 }
 
