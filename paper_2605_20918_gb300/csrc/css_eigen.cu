@@ -305,6 +305,11 @@ __global__ void k_bisect32(int32_t kd, int32_t nmax, const int32_t* __restrict__
 
 // ------------------------------------------------- FP64 inverse iteration
 constexpr int kMaxCluster = 16;
+// Convergence: the last solve (T - sigma I) y = x, ||x|| = 1, grew by ||y|| > 1 / (kResTol ||T||), so
+// the returned y / ||y|| has residual ||(T - sigma I) y/||y|| || below kResTol ||T|| (128 eps);
+// with the shift that close, the step damps every component outside the target eigenvector by
+// at least that residual over the gap to the other eigenvalues.
+constexpr double kResTol = 128.0 * 2.2e-16;
 
 __device__ __forceinline__ double hash_unit(uint64_t a, uint64_t b) {
   uint64_t z = css_splitmix64(a * 0x9E3779B97F4A7C15ull + 0x5851F42D4C957F2Dull, b);
@@ -338,6 +343,7 @@ __global__ void __launch_bounds__(128) k_inviter_p1(int32_t kd, int32_t nmax, co
   const double tn = tnorm[c];
   const double tol = rel_cluster * tn;
   const double pivmin = 2.2e-16 * tn;
+  const double res_tol = kResTol * tn;
   const bool valid = k < n;
   bool in_cluster = false;
   double win_lo = 0.0, win_hi = 0.0, sigma = 0.0;
@@ -431,212 +437,355 @@ __global__ void __launch_bounds__(128) k_inviter_p1(int32_t kd, int32_t nmax, co
     if (it >= 1) sigma = rq;
   }
   if (!valid) return;
-  const bool ok = work && growth * pivmin > 1.0 && sigma >= win_lo && sigma <= win_hi;
+  const bool ok = work && growth * res_tol > 1.0 && sigma >= win_lo && sigma <= win_hi;
   fl[k] = ok ? 0 : 1;
   if (!ok) return;
   for (int32_t i = 0; i < n; ++i) u[(size_t)i * nmax + k] = f_x[(size_t)i * nmax + k] * inv;
   lam[(size_t)c * nmax + k] = sigma;
 }
 
-// One thread per cluster of close shifts.  Column k of U and five scratch columns of F are
-// owned by the thread handling eigenvalue k.  Layout [c][row][col] so threads with
-// neighbouring k touch neighbouring addresses.
-__global__ void k_inviter(int32_t kd, int32_t nmax, const int32_t* __restrict__ nblk, const double* __restrict__ dd,
-                          const double* __restrict__ ee, const float* __restrict__ lam32,
-                          const double* __restrict__ tnorm, double rel_cluster, double* __restrict__ U,
-                          double* __restrict__ F, double* __restrict__ lam, int32_t* __restrict__ status,
-                          const int32_t* __restrict__ flag) {
+// Phase 2 of the FP64 inverse iteration: one warp per cluster of close shifts (or per single
+// eigenvalue that phase 1 flagged).  Lane j < kc owns member k0 + j; its iterate is column k0 + j
+// of the scratch X and its LU factors columns k0 + j of U0..U2, so the lanes of a warp touch
+// contiguous addresses of a row.  Every member solves with its own shift, then the members are
+// orthonormalised by modified Gram-Schmidt in member order (simultaneous inverse iteration);
+// Rayleigh-Ritz inside the cluster gives the final pairs.  Every sweep over the rows loads a
+// batch of rows before the batch's dependent arithmetic, so one warp keeps several loads in
+// flight.
+constexpr int kCB = 8;  // rows per batch
+
+struct ClusterCols {
+  const double* d;
+  const double* e;
+  double* u0;
+  double* u1;
+  double* u2;
+  double* x;
+  int32_t n, nmax;
+};
+
+// LU with partial pivoting of T - sigma I fused with the forward elimination of column col of
+// X (scaled by scl), then the back substitution U y = x; y overwrites the column.  Returns ||y||.
+// Lanes with st == false compute but store nothing.
+__device__ double cl_solve(const ClusterCols& m, int32_t col, double sigma, double scl, double pivmin, bool st) {
+  const int32_t n = m.n, nmax = m.nmax;
+  double cd = m.d[0] - sigma, cs = n > 1 ? m.e[0] : 0.0;
+  double xc = m.x[col] * scl;
+  for (int32_t i0 = 0; i0 + 1 < n; i0 += kCB) {
+    double sub[kCB], dg[kCB], sup[kCB], xn[kCB];
+#pragma unroll
+    for (int q = 0; q < kCB; ++q) {
+      const int32_t i = i0 + q;
+      const bool ok = i + 1 < n;
+      sub[q] = ok ? m.e[i] : 1.0;
+      dg[q] = ok ? m.d[i + 1] - sigma : 0.0;
+      sup[q] = (i + 2 < n) ? m.e[i + 1] : 0.0;
+      xn[q] = ok ? m.x[(size_t)(i + 1) * nmax + col] * scl : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < kCB; ++q) {
+      const int32_t i = i0 + q;
+      if (i + 1 >= n) break;
+      double u0, u1, u2, rhs, ncd, ncs, nx;
+      if (fabs(cd) >= fabs(sub[q])) {
+        if (fabs(cd) < pivmin) cd = cd >= 0 ? pivmin : -pivmin;
+        const double l = sub[q] / cd;
+        u0 = cd;
+        u1 = cs;
+        u2 = 0.0;
+        rhs = xc;
+        ncd = dg[q] - l * cs;
+        ncs = sup[q];
+        nx = xn[q] - l * xc;
+      } else {
+        const double l = cd / sub[q];
+        u0 = sub[q];
+        u1 = dg[q];
+        u2 = sup[q];
+        rhs = xn[q];
+        ncd = cs - l * dg[q];
+        ncs = -l * sup[q];
+        nx = xc - l * xn[q];
+      }
+      if (st) {
+        m.u0[(size_t)i * nmax + col] = u0;
+        m.u1[(size_t)i * nmax + col] = u1;
+        m.u2[(size_t)i * nmax + col] = u2;
+        m.x[(size_t)i * nmax + col] = rhs;
+      }
+      cd = ncd;
+      cs = ncs;
+      xc = nx;
+    }
+  }
+  if (fabs(cd) < pivmin) cd = cd >= 0 ? pivmin : -pivmin;
+  // back substitution, rows n-1 down to 0, in batches
+  double y1 = xc / cd, y2 = 0.0;
+  double ss = y1 * y1;
+  if (st) m.x[(size_t)(n - 1) * nmax + col] = y1;
+  for (int32_t i0 = n - 2; i0 >= 0; i0 -= kCB) {
+    double r[kCB], a0[kCB], a1[kCB], a2[kCB];
+#pragma unroll
+    for (int q = 0; q < kCB; ++q) {
+      const int32_t i = i0 - q;
+      const bool ok = i >= 0;
+      const size_t o = (size_t)(ok ? i : 0) * nmax + col;
+      r[q] = ok ? m.x[o] : 0.0;
+      a0[q] = ok ? m.u0[o] : 1.0;
+      a1[q] = ok ? m.u1[o] : 0.0;
+      a2[q] = ok ? m.u2[o] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < kCB; ++q) {
+      const int32_t i = i0 - q;
+      if (i < 0) break;
+      const double y = (r[q] - a1[q] * y1 - a2[q] * y2) / a0[q];
+      if (st) m.x[(size_t)i * nmax + col] = y;
+      ss += y * y;
+      y2 = y1;
+      y1 = y;
+    }
+  }
+  return sqrt(ss);
+}
+
+__global__ void __launch_bounds__(256) k_inviter_cl(int32_t kd, int32_t nmax, const int32_t* __restrict__ nblk,
+                                                    const double* __restrict__ dd, const double* __restrict__ ee,
+                                                    const float* __restrict__ lam32,
+                                                    const double* __restrict__ tnorm, double rel_cluster,
+                                                    double* __restrict__ U, double* __restrict__ F,
+                                                    double* __restrict__ lam, int32_t* __restrict__ status,
+                                                    const int32_t* __restrict__ flag) {
+  __shared__ double sC[8][kMaxCluster][kMaxCluster + 1];
+  __shared__ double sV[8][kMaxCluster][kMaxCluster + 1];
+  constexpr unsigned FULL = 0xffffffffu;
   const int32_t c = blockIdx.x;
   const int32_t n = nblk[c] * kd;
-  const double* d = dd + (size_t)c * nmax;
-  const double* e = ee + (size_t)c * nmax;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const float* l32 = lam32 + (size_t)c * nmax;
   double* u = U + (size_t)c * nmax * nmax;
-  double* f_l = F + (size_t)c * 5 * nmax * nmax;
-  double* f_u0 = f_l + (size_t)nmax * nmax;
-  double* f_u1 = f_u0 + (size_t)nmax * nmax;
-  double* f_u2 = f_u1 + (size_t)nmax * nmax;
-  double* f_x = f_u2 + (size_t)nmax * nmax;
+  ClusterCols m;
+  m.d = dd + (size_t)c * nmax;
+  m.e = ee + (size_t)c * nmax;
+  m.u0 = F + (size_t)c * 5 * nmax * nmax;
+  m.u1 = m.u0 + (size_t)nmax * nmax;
+  m.u2 = m.u1 + (size_t)nmax * nmax;
+  m.x = m.u2 + (size_t)nmax * nmax;
+  m.n = n;
+  m.nmax = nmax;
   const double tn = tnorm[c];
   const double tol = rel_cluster * tn;
   const double pivmin = 2.2e-16 * tn;
-  for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
-    // cluster starts where the gap to the previous shift exceeds tol (and every 16 members)
-    int32_t s = k;
-    while (s > 0 && (double)l32[s] - (double)l32[s - 1] <= tol) --s;
-    if ((k - s) % kMaxCluster != 0) continue;
-    const int32_t k0 = k;
-    int32_t k1 = k;
-    while (k1 + 1 < n && (double)l32[k1 + 1] - (double)l32[k1] <= tol && k1 + 1 - k0 < kMaxCluster) ++k1;
-    {  // phase 1 finished every member of this cluster: nothing to do
+  const double res_tol = kResTol * tn;
+  int32_t failed = 0;
+  // the colour's shifts are dealt out in runs of 32 to the warps of gridDim.y CTAs
+  for (int32_t base = (blockIdx.y * nwarp + warp) * 32; base < n; base += gridDim.y * nwarp * 32) {
+    // cluster starts among this warp's 32 shifts: the gap to the previous shift exceeds tol,
+    // or a cluster longer than kMaxCluster is cut every kMaxCluster members
+    bool start = false;
+    const int32_t k = base + lane;
+    if (k < n) {
+      int32_t s = k;
+      while (s > 0 && (double)l32[s] - (double)l32[s - 1] <= tol) --s;
+      start = (k - s) % kMaxCluster == 0;
+    }
+    unsigned starts = __ballot_sync(FULL, start);
+    while (starts) {
+      const int32_t k0 = base + __ffs(starts) - 1;
+      starts &= starts - 1;
+      int32_t k1 = k0;
+      while (k1 + 1 < n && (double)l32[k1 + 1] - (double)l32[k1] <= tol && k1 + 1 - k0 < kMaxCluster) ++k1;
+      const int32_t kc = k1 - k0 + 1;
       bool any = false;
       for (int32_t kk = k0; kk <= k1; ++kk) any = any || flag[(size_t)c * nmax + kk] != 0;
-      if (!any) continue;
-    }
-    auto U_ = [&](int32_t i, int32_t col) -> double& { return u[(size_t)i * nmax + col]; };
-    auto F_ = [&](double* base, int32_t i, int32_t col) -> double& { return base[(size_t)i * nmax + col]; };
-    // window the refined eigenvalues must fall in: the cluster's shifts widened by a quarter of
-    // the gaps to the neighbouring shifts outside the cluster
-    const double g_lo = k0 > 0 ? (double)l32[k0] - (double)l32[k0 - 1] : tn;
-    const double g_hi = k1 + 1 < n ? (double)l32[k1 + 1] - (double)l32[k1] : tn;
-    const double win_lo = (double)l32[k0] - 0.25 * g_lo - 2e-6 * tn;
-    const double win_hi = (double)l32[k1] + 0.25 * g_hi + 2e-6 * tn;
-    for (int32_t kk = k0; kk <= k1; ++kk) {
-      double sigma = (double)l32[kk];
-      for (int attempt = 0; attempt < 3; ++attempt) {
-        sigma = (double)l32[kk];
-        // start vector
+      if (!any) continue;  // phase 1 finished every member
+      const bool act = lane < kc;
+      const int32_t col = k0 + (act ? lane : 0);  // idle lanes shadow member 0 and store nothing
+      const double g_lo = k0 > 0 ? (double)l32[k0] - (double)l32[k0 - 1] : tn;
+      const double g_hi = k1 + 1 < n ? (double)l32[k1 + 1] - (double)l32[k1] : tn;
+      const double win_lo = (double)l32[k0] - 0.25 * g_lo - 2e-6 * tn;
+      const double win_hi = (double)l32[k1] + 0.25 * g_hi + 2e-6 * tn;
+      double lamj = 0.0;
+      bool ok_all = false;
+      for (int attempt = 0; attempt < 3 && !ok_all; ++attempt) {
+        // start vectors (norm folded into the first solve's right-hand side)
         double nrm = 0.0;
-        for (int32_t i = 0; i < n; ++i) {
-          double x = hash_unit((uint64_t)c * 1000003ull + (uint64_t)kk + 7919ull * attempt, (uint64_t)i);
-          F_(f_x, i, kk) = x;
-          nrm += x * x;
+        for (int32_t i0 = 0; i0 < n; i0 += kCB) {
+#pragma unroll
+          for (int q = 0; q < kCB; ++q) {
+            const int32_t i = i0 + q;
+            if (i < n) {
+              const double x = hash_unit((uint64_t)c * 1000003ull + (uint64_t)col + 7919ull * attempt, (uint64_t)i);
+              if (act) m.x[(size_t)i * nmax + col] = x;
+              nrm += x * x;
+            }
+          }
         }
-        nrm = 1.0 / sqrt(nrm);
-        for (int32_t i = 0; i < n; ++i) F_(f_x, i, kk) *= nrm;
-        // two inverse-iteration steps at the fixed FP32 shift make the target eigenvector
-        // dominate whatever the start vector; Rayleigh-quotient shifts from then on
+        double scl = 1.0 / sqrt(nrm);
+        double sigma = (double)l32[col];
         for (int it = 0; it < 8; ++it) {
-          // LU with partial pivoting of T - sigma I (rows: sub e_{i-1}, diag d_i - sigma, sup e_i)
-          double cd = d[0] - sigma, cs = n > 1 ? e[0] : 0.0;
-          for (int32_t i = 0; i + 1 < n; ++i) {
-            const double sub = e[i], dg = d[i + 1] - sigma, sup = (i + 2 < n) ? e[i + 1] : 0.0;
-            if (fabs(cd) >= fabs(sub)) {
-              if (fabs(cd) < pivmin) cd = cd >= 0 ? pivmin : -pivmin;
-              const double l = sub / cd;
-              F_(f_l, i, kk) = l;
-              F_(f_u0, i, kk) = cd;
-              F_(f_u1, i, kk) = cs;
-              F_(f_u2, i, kk) = 0.0;  // no interchange
-              cd = dg - l * cs;
-              cs = sup;
-            } else {
-              // rows i and i+1 interchanged; |l| <= 1, so l + 4 in [3, 5] marks the interchange
-              const double l = cd / sub;
-              F_(f_l, i, kk) = l + 4.0;
-              F_(f_u0, i, kk) = sub;
-              F_(f_u1, i, kk) = dg;
-              F_(f_u2, i, kk) = sup;
-              const double ncd = cs - l * dg;
-              cs = -l * sup;
-              cd = ncd;
+          const double growth = cl_solve(m, col, sigma, scl, pivmin, act);
+          // modified Gram-Schmidt in member order; pass s subtracts the projection on member s-1
+          // (coefficient from pass s-1) and takes the inner products with member s
+          double cprev = 0.0, nrm2 = 1.0;
+          for (int32_t s = 0; s < kc; ++s) {
+            double dj = 0.0;
+            for (int32_t i0 = 0; i0 < n; i0 += kCB) {
+              double v[kCB];
+#pragma unroll
+              for (int q = 0; q < kCB; ++q) v[q] = (i0 + q < n) ? m.x[(size_t)(i0 + q) * nmax + col] : 0.0;
+#pragma unroll
+              for (int q = 0; q < kCB; ++q) {
+                if (s > 0) {
+                  const double xp = __shfl_sync(FULL, v[q], s - 1);
+                  if (lane >= s) v[q] = fma(-cprev, xp, v[q]);
+                }
+                const double xs = __shfl_sync(FULL, v[q], s);
+                dj = fma(xs, v[q], dj);
+              }
+              if (s > 0 && act && lane >= s) {
+#pragma unroll
+                for (int q = 0; q < kCB; ++q)
+                  if (i0 + q < n) m.x[(size_t)(i0 + q) * nmax + col] = v[q];
+              }
             }
+            const double ds = __shfl_sync(FULL, dj, s);
+            if (lane == s) nrm2 = ds;
+            cprev = lane > s ? dj / ds : 0.0;
           }
-          if (fabs(cd) < pivmin) cd = cd >= 0 ? pivmin : -pivmin;
-          F_(f_u0, n - 1, kk) = cd;
-          // forward: P and L
-          for (int32_t i = 0; i + 1 < n; ++i) {
-            double l = F_(f_l, i, kk);
-            double xi = F_(f_x, i, kk), xn = F_(f_x, i + 1, kk);
-            if (l >= 3.0) {  // interchange
-              l -= 4.0;
-              F_(f_x, i, kk) = xn;
-              F_(f_x, i + 1, kk) = xi - l * xn;
-            } else {
-              F_(f_x, i + 1, kk) = xn - l * xi;
-            }
-          }
-          // backward: U y = x
-          double y2 = 0.0, y1 = 0.0;
-          for (int32_t i = n - 1; i >= 0; --i) {
-            double r = F_(f_x, i, kk);
-            if (i + 1 < n) r -= F_(f_u1, i, kk) * y1;
-            if (i + 2 < n) r -= F_(f_u2, i, kk) * y2;
-            double y = r / F_(f_u0, i, kk);
-            F_(f_x, i, kk) = y;
-            y2 = y1;
-            y1 = y;
-          }
-          // Gram-Schmidt against the cluster's finished vectors, twice
-          for (int rep = 0; rep < 2; ++rep)
-            for (int32_t pq = k0; pq < kk; ++pq) {
-              double dot = 0.0;
-              for (int32_t i = 0; i < n; ++i) dot += U_(i, pq) * F_(f_x, i, kk);
-              for (int32_t i = 0; i < n; ++i) F_(f_x, i, kk) -= dot * U_(i, pq);
-            }
-          nrm = 0.0;
-          for (int32_t i = 0; i < n; ++i) nrm += F_(f_x, i, kk) * F_(f_x, i, kk);
-          const double growth = sqrt(nrm);
-          nrm = 1.0 / growth;
-          // Rayleigh quotient x^T T x of the normalised vector
+          // normalise and take the Rayleigh quotient x^T T x
+          const double r = 1.0 / sqrt(nrm2);
           double rq = 0.0, prev = 0.0;
-          for (int32_t i = 0; i < n; ++i) {
-            double xi = F_(f_x, i, kk) * nrm;
-            F_(f_x, i, kk) = xi;
-            rq += xi * (d[i] * xi + 2.0 * (i > 0 ? e[i - 1] * prev : 0.0));
-            prev = xi;
+          for (int32_t i0 = 0; i0 < n; i0 += kCB) {
+            double v[kCB], dv[kCB], ev[kCB];
+#pragma unroll
+            for (int q = 0; q < kCB; ++q) {
+              const int32_t i = i0 + q;
+              v[q] = i < n ? m.x[(size_t)i * nmax + col] * r : 0.0;
+              dv[q] = i < n ? m.d[i] : 0.0;
+              ev[q] = (i > 0 && i < n) ? m.e[i - 1] : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < kCB; ++q) {
+              rq += v[q] * (dv[q] * v[q] + 2.0 * ev[q] * prev);
+              prev = v[q];
+              if (act && i0 + q < n) m.x[(size_t)(i0 + q) * nmax + col] = v[q];
+            }
           }
+          scl = 1.0;
           if (it >= 1) sigma = rq;
-          if (it >= 2 && growth * pivmin > 1.0) break;
+          const bool conv = it >= 2 && growth * res_tol > 1.0;
+          if (__all_sync(FULL, !act || conv)) break;
         }
-        if (sigma >= win_lo && sigma <= win_hi) break;  // converged to an eigenvalue of this cluster
-      }
-      for (int32_t i = 0; i < n; ++i) U_(i, kk) = F_(f_x, i, kk);
-      lam[(size_t)c * nmax + kk] = sigma;
-    }
-    if (k1 > k0) {
-      // Rayleigh-Ritz inside the cluster: C = U_c^T T U_c, cyclic Jacobi, U_c <- U_c V
-      const int32_t kc = k1 - k0 + 1;
-      double C[kMaxCluster][kMaxCluster], V[kMaxCluster][kMaxCluster];
-      for (int32_t a = 0; a < kc; ++a)
-        for (int32_t bq = 0; bq < kc; ++bq) {
-          double s2 = 0.0;
-          for (int32_t i = 0; i < n; ++i) {
-            double tu = d[i] * U_(i, k0 + bq);
-            if (i > 0) tu += e[i - 1] * U_(i - 1, k0 + bq);
-            if (i + 1 < n) tu += e[i] * U_(i + 1, k0 + bq);
-            s2 += U_(i, k0 + a) * tu;
-          }
-          C[a][bq] = s2;
-          V[a][bq] = (a == bq) ? 1.0 : 0.0;
-        }
-      for (int32_t a = 0; a < kc; ++a)
-        for (int32_t bq = a + 1; bq < kc; ++bq) {
-          double t = 0.5 * (C[a][bq] + C[bq][a]);
-          C[a][bq] = t;
-          C[bq][a] = t;
-        }
-      for (int sweep = 0; sweep < 30; ++sweep) {
-        double off = 0.0, on = 0.0;
-        for (int32_t a = 0; a < kc; ++a)
-          for (int32_t bq = 0; bq < kc; ++bq) (a == bq ? on : off) += C[a][bq] * C[a][bq];
-        if (off <= 1e-32 * on || off == 0.0) break;
-        for (int32_t a = 0; a < kc; ++a)
-          for (int32_t bq = a + 1; bq < kc; ++bq) {
-            if (C[a][bq] == 0.0) continue;
-            double theta = (C[bq][bq] - C[a][a]) / (2.0 * C[a][bq]);
-            double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
-            for (int32_t r = 0; r < kc; ++r) {
-              double ca = C[r][a], cb = C[r][bq];
-              C[r][a] = cs * ca - sn * cb;
-              C[r][bq] = sn * ca + cs * cb;
+        lamj = sigma;
+        if (kc > 1) {
+          // Rayleigh-Ritz inside the cluster: C = X^T T X, column j accumulated by lane j
+          double cc[kMaxCluster];
+#pragma unroll
+          for (int a = 0; a < kMaxCluster; ++a) cc[a] = 0.0;
+          double xprev = 0.0;
+          double xcur = m.x[col];
+          for (int32_t i0 = 0; i0 < n; i0 += kCB) {
+            double xnx[kCB], dv[kCB], elo[kCB], ehi[kCB];
+#pragma unroll
+            for (int q = 0; q < kCB; ++q) {
+              const int32_t i = i0 + q;
+              xnx[q] = (i + 1 < n) ? m.x[(size_t)(i + 1) * nmax + col] : 0.0;
+              dv[q] = i < n ? m.d[i] : 0.0;
+              elo[q] = (i > 0 && i < n) ? m.e[i - 1] : 0.0;
+              ehi[q] = (i + 1 < n) ? m.e[i] : 0.0;
             }
-            for (int32_t r = 0; r < kc; ++r) {
-              double ca = C[a][r], cb = C[bq][r];
-              C[a][r] = cs * ca - sn * cb;
-              C[bq][r] = sn * ca + cs * cb;
-            }
-            for (int32_t r = 0; r < kc; ++r) {
-              double va = V[r][a], vb = V[r][bq];
-              V[r][a] = cs * va - sn * vb;
-              V[r][bq] = sn * va + cs * vb;
+#pragma unroll
+            for (int q = 0; q < kCB; ++q) {
+              const double tx = dv[q] * xcur + elo[q] * xprev + ehi[q] * xnx[q];
+#pragma unroll
+              for (int a = 0; a < kMaxCluster; ++a) {
+                const double xa = __shfl_sync(FULL, xcur, a);
+                if (a < kc) cc[a] = fma(xa, tx, cc[a]);
+              }
+              xprev = xcur;
+              xcur = xnx[q];
             }
           }
-      }
-      double row[kMaxCluster];
-      for (int32_t i = 0; i < n; ++i) {
-        for (int32_t a = 0; a < kc; ++a) {
-          double s2 = 0.0;
-          for (int32_t bq = 0; bq < kc; ++bq) s2 += U_(i, k0 + bq) * V[bq][a];
-          row[a] = s2;
+          if (act)
+#pragma unroll
+            for (int a = 0; a < kMaxCluster; ++a)
+              if (a < kc) sC[warp][a][lane] = cc[a];
+          __syncwarp();
+          if (lane == 0) {
+            double (*C)[kMaxCluster + 1] = sC[warp];
+            double (*V)[kMaxCluster + 1] = sV[warp];
+            for (int32_t a = 0; a < kc; ++a)
+              for (int32_t q = 0; q < kc; ++q) V[a][q] = a == q ? 1.0 : 0.0;
+            for (int32_t a = 0; a < kc; ++a)
+              for (int32_t q = a + 1; q < kc; ++q) {
+                const double t = 0.5 * (C[a][q] + C[q][a]);
+                C[a][q] = t;
+                C[q][a] = t;
+              }
+            for (int sweep = 0; sweep < 30; ++sweep) {  // cyclic Jacobi
+              double off = 0.0, on = 0.0;
+              for (int32_t a = 0; a < kc; ++a)
+                for (int32_t q = 0; q < kc; ++q) (a == q ? on : off) += C[a][q] * C[a][q];
+              if (off <= 1e-32 * on || off == 0.0) break;
+              for (int32_t a = 0; a < kc; ++a)
+                for (int32_t q = a + 1; q < kc; ++q) {
+                  if (C[a][q] == 0.0) continue;
+                  const double theta = (C[q][q] - C[a][a]) / (2.0 * C[a][q]);
+                  const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                  const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+                  for (int32_t r2 = 0; r2 < kc; ++r2) {
+                    const double ca = C[r2][a], cb = C[r2][q];
+                    C[r2][a] = cs * ca - sn * cb;
+                    C[r2][q] = sn * ca + cs * cb;
+                  }
+                  for (int32_t r2 = 0; r2 < kc; ++r2) {
+                    const double ca = C[a][r2], cb = C[q][r2];
+                    C[a][r2] = cs * ca - sn * cb;
+                    C[q][r2] = sn * ca + cs * cb;
+                  }
+                  for (int32_t r2 = 0; r2 < kc; ++r2) {
+                    const double va = V[r2][a], vb = V[r2][q];
+                    V[r2][a] = cs * va - sn * vb;
+                    V[r2][q] = sn * va + cs * vb;
+                  }
+                }
+            }
+          }
+          __syncwarp();
+          lamj = act ? sC[warp][lane][lane] : 0.0;
         }
-        for (int32_t a = 0; a < kc; ++a) U_(i, k0 + a) = row[a];
+        ok_all = __all_sync(FULL, !act || (lamj >= win_lo && lamj <= win_hi));
+        if (!ok_all && attempt < 2) continue;
+        // write the eigenvectors: X (rotated by V inside a cluster) into U
+        double vcol[kMaxCluster];
+#pragma unroll
+        for (int a = 0; a < kMaxCluster; ++a) vcol[a] = (kc > 1 && act && a < kc) ? sV[warp][a][lane] : 0.0;
+        for (int32_t i0 = 0; i0 < n; i0 += kCB) {
+          double v[kCB];
+#pragma unroll
+          for (int q = 0; q < kCB; ++q) v[q] = (i0 + q < n) ? m.x[(size_t)(i0 + q) * nmax + col] : 0.0;
+#pragma unroll
+          for (int q = 0; q < kCB; ++q) {
+            double o = v[q];
+            if (kc > 1) {
+              o = 0.0;
+#pragma unroll
+              for (int a = 0; a < kMaxCluster; ++a) {
+                const double xa = __shfl_sync(FULL, v[q], a);
+                if (a < kc) o = fma(xa, vcol[a], o);
+              }
+            }
+            if (act && i0 + q < n) u[(size_t)(i0 + q) * nmax + col] = o;
+          }
+        }
+        if (act) lam[(size_t)c * nmax + col] = lamj;
+        if (!ok_all) failed = 1;
+        __syncwarp();
       }
-      for (int32_t a = 0; a < kc; ++a) lam[(size_t)c * nmax + k0 + a] = C[a][a];
     }
   }
-  (void)status;
+  if (failed) atomicOr(&status[c], 1);  // an eigenvalue outside its window after every attempt
 }
 
 // Y[k][col] = sum_i U[i][k] X[i][col], w[k] = ||Y[k]||^2 (one thread per k)
@@ -744,8 +893,9 @@ css_status css_eigen_ritz(css_ctx* ctx, const EigArgs& a, cudaStream_t st) {
   k_inviter_p1<<<dim3((unsigned)css_ceil_div(nmax, 128), (unsigned)nc), 128, 0, st>>>(
       b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm, 1e-4, a.U, a.F, a.lam, a.flag);
   CSS_LAUNCHED(ctx);
-  k_inviter<<<nc, 128, 0, st>>>(b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm, 1e-4, a.U, a.F, a.lam, a.status,
-                                a.flag);
+  CSS_CU(ctx, cudaMemsetAsync(a.status, 0, sizeof(int32_t) * nc, st));
+  k_inviter_cl<<<dim3((unsigned)nc, 4), 256, 0, st>>>(b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm, 1e-4, a.U, a.F, a.lam, a.status,
+                                   a.flag);
   CSS_LAUNCHED(ctx);
   if (ctx->debug_eig == 1) {
     k_shifts_out<<<nc, 256, 0, st>>>(nmax, a.lam32, a.lam);

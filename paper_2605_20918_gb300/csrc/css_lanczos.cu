@@ -106,7 +106,9 @@ __global__ void __launch_bounds__(128) k_spmm(int32_t b, const int32_t* __restri
 // a tile of each array is staged in shared memory as [RTL][G*BP] (b padded to BP, the
 // padding kept at zero), so the global reads of a row are G*b contiguous values.  Every
 // small product (block update, Gram) is register-tiled in 4 x 4 blocks.  Per-tile Gram sums
-// are taken in the vector precision and added to FP64 registers, written once per CTA.
+// are taken in the vector precision; FP32 tiles are added into an unevaluated hi + lo pair
+// of floats (error-free TwoSum, so the running sum carries about 44 bits), FP64 tiles into
+// doubles.  The pair is widened to FP64 once per CTA: no FP64 arithmetic in the row loop.
 constexpr int RW = 256;      // threads
 constexpr int RCHK = 1024;   // rows per CTA
 
@@ -134,11 +136,26 @@ template <typename T, int BP>
 struct RowCtx {
   int32_t b, ws, G, gcount, pitch, cg0;  // cg0 = first colour of the group within the batch
   int32_t my_col, my_smem;  // this thread's column of the group (width <= blockDim) and its tile offset
+  // issue the asynchronous copy of one tile of RTL rows (rows >= nr are zero-filled); the copies
+  // hold no registers, so every row of the tile is in flight at once.  Completed by load_wait().
+  template <int RTL>
   __device__ __forceinline__ void load(T* dst, const T* src, int64_t r0, int32_t nr) const {
     if (my_col < 0) return;
     const T* s = src + (size_t)r0 * ws + (size_t)cg0 * b + my_col;
-#pragma unroll 4
-    for (int32_t r = 0; r < nr; ++r) dst[r * pitch + my_smem] = s[(size_t)r * ws];
+#pragma unroll
+    for (int32_t r = 0; r < RTL; ++r) {
+      const unsigned d = (unsigned)__cvta_generic_to_shared(dst + r * pitch + my_smem);
+      const T* g = s + (size_t)(r < nr ? r : 0) * ws;
+      const int n = r < nr ? (int)sizeof(T) : 0;
+      if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(g), "r"(n) : "memory");
+      else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(g), "r"(n) : "memory");
+    }
+  }
+  // wait for this thread's outstanding tile copies (a __syncthreads must follow)
+  __device__ __forceinline__ static void load_wait() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
   }
   __device__ __forceinline__ void store(T* dst, const T* src, int64_t r0, int32_t nr) const {
     if (my_col < 0) return;
@@ -195,11 +212,40 @@ __device__ __forceinline__ void tile_mul(const RowCtx<T, BP>& c, const T* X, con
   }
 }
 
+// running sum of 16 Gram entries: doubles for FP64 vectors, hi + lo float pairs for FP32
+template <typename T>
+struct GramAcc {
+  double s[16];
+  __device__ __forceinline__ GramAcc() {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) s[i] = 0.0;
+  }
+  __device__ __forceinline__ void add(int i, double x) { s[i] += x; }
+  __device__ __forceinline__ double get(int i) const { return s[i]; }
+};
+template <>
+struct GramAcc<float> {
+  float hi[16], lo[16];
+  __device__ __forceinline__ GramAcc() {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) hi[i] = lo[i] = 0.0f;
+  }
+  // Knuth's TwoSum: hi + x = t + err exactly; err is collected in lo
+  __device__ __forceinline__ void add(int i, float x) {
+    const float t = __fadd_rn(hi[i], x);
+    const float z = __fsub_rn(t, hi[i]);
+    const float err = __fadd_rn(__fsub_rn(hi[i], __fsub_rn(t, z)), __fsub_rn(x, z));
+    lo[i] = __fadd_rn(lo[i], err);
+    hi[i] = t;
+  }
+  __device__ __forceinline__ double get(int i) const { return (double)hi[i] + (double)lo[i]; }
+};
+
 // acc[i][j] += sum_r X[r][g][4bi+i] Y[r][g][4bj+j] for this thread's block (g, bi, bj)
 template <typename T, int BP>
-__device__ __forceinline__ void tile_gram(const RowCtx<T, BP>& c, const T* X, const T* Y, int32_t rtl, double* acc) {
+__device__ __forceinline__ void tile_gram(const RowCtx<T, BP>& c, const T* X, const T* Y, int32_t rtl,
+                                          GramAcc<T>& acc, int32_t t) {
   constexpr int CB = BP / 4;
-  const int32_t t = threadIdx.x;
   if (t >= c.G * CB * CB) return;
   const int32_t g = t / (CB * CB), rem = t - g * CB * CB, bi = rem / CB, bj = rem - bi * CB;
   const T* xp = X + g * BP + bi * 4;
@@ -220,13 +266,13 @@ __device__ __forceinline__ void tile_gram(const RowCtx<T, BP>& c, const T* X, co
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i * 4 + j] += (double)a[i][j];
+    for (int j = 0; j < 4; ++j) acc.add(i * 4 + j, a[i][j]);
 }
 
 template <typename T, int BP>
-__device__ __forceinline__ void gram_store(const RowCtx<T, BP>& c, const double* acc, double* part) {
+__device__ __forceinline__ void gram_store(const RowCtx<T, BP>& c, const GramAcc<T>& acc, double* part,
+                                           int32_t t) {
   constexpr int CB = BP / 4;
-  const int32_t t = threadIdx.x;
   if (t >= c.G * CB * CB) return;
   const int32_t g = t / (CB * CB), rem = t - g * CB * CB, bi = rem / CB, bj = rem - bi * CB;
   if (g >= c.gcount) return;
@@ -236,7 +282,7 @@ __device__ __forceinline__ void gram_store(const RowCtx<T, BP>& c, const double*
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int32_t k = bi * 4 + i, l = bj * 4 + j;
-      if (k < c.b && l < c.b) o[k * c.b + l] = acc[i * 4 + j];
+      if (k < c.b && l < c.b) o[k * c.b + l] = acc.get(i * 4 + j);
     }
 }
 
@@ -261,9 +307,10 @@ __device__ __forceinline__ RowCtx<T, BP> make_ctx(int32_t b, int32_t ws, int32_t
 }
 
 // S1: W = H Q_j arrives in W.  W0 = W - Q_{j-1} B_{j-1}^T (skipped at the first step), stored;
-// partials Kq = Q_j^T W0, Kp = Q_{j-1}^T W0 (REORTH), and ||W||^2 per colour (breakdown test)
+// partials Kq = Q_j^T W0, Kp = Q_{j-1}^T W0 (REORTH), and ||W||^2 per colour (breakdown test).
+// With REORTH the CTA has 2*RW threads: the first RW accumulate Kq, the second RW Kp.
 template <typename T, int BP, bool REORTH>
-__global__ void __launch_bounds__(RW) k_s1(int64_t N, int32_t b, int32_t ws, int32_t ncb, int32_t cb0,
+__global__ void __launch_bounds__(REORTH ? 2 * RW : RW, REORTH ? 1 : 2) k_s1(int64_t N, int32_t b, int32_t ws, int32_t ncb, int32_t cb0,
                                            const T* __restrict__ Qp, const T* __restrict__ Q, T* __restrict__ W,
                                            const double* __restrict__ Bprev, int first, double* __restrict__ partKq,
                                            double* __restrict__ partKp, double* __restrict__ partH) {
@@ -277,8 +324,10 @@ __global__ void __launch_bounds__(RW) k_s1(int64_t N, int32_t b, int32_t ws, int
   T* sW = sP + tile;
   T* sB = sW + tile;  // [G][BP][BP] = B_{j-1}^T per colour
   double* hsum = reinterpret_cast<double*>(sB + c.G * BP * BP);  // [G][CB]
-  double aq[16] = {}, ap[16] = {};
-  double hq = 0.0;
+  GramAcc<T> acc;                                   // Kq (first RW threads) or Kp (second RW)
+  const bool second = REORTH && threadIdx.x >= RW;
+  const int32_t tg = threadIdx.x - (second ? RW : 0);  // index of the thread's Gram block
+  T hq = T(0);  // ||W||^2 only feeds the breakdown threshold: the vector precision is enough
   if (!first) c.load_mat(sB, Bprev, cb0 + c.cg0, true);
   const int64_t rbeg = (int64_t)blockIdx.x * RCHK, rend = min(N, rbeg + RCHK);
   for (int64_t r0 = rbeg; r0 < rend; r0 += RTL) {
@@ -290,20 +339,21 @@ __global__ void __launch_bounds__(RW) k_s1(int64_t N, int32_t b, int32_t ws, int
       if (REORTH || !first) c.zero(sP, RTL);
       __syncthreads();
     }
-    c.load(sQ, Q, r0, nr);
-    c.load(sW, W, r0, nr);
-    if (REORTH || !first) c.load(sP, Qp, r0, nr);
+    c.template load<RTL>(sQ, Q, r0, nr);
+    c.template load<RTL>(sW, W, r0, nr);
+    if (REORTH || !first) c.template load<RTL>(sP, Qp, r0, nr);
+    c.load_wait();
     __syncthreads();
     {  // ||W||^2 of the colour before the update
       const int32_t t = threadIdx.x;
-      if (t < c.G * CB * CB) {
+      if (t < c.G * CB * CB) {  // first half only (G * CB * CB <= RW)
         const int32_t g = t / (CB * CB), rem = t - g * CB * CB, bi = rem / CB, bj = rem - bi * CB;
         if (bi == bj)
           for (int32_t r = 0; r < RTL; ++r)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-              const double w = (double)sW[r * c.pitch + g * BP + bi * 4 + i];
-              hq += w * w;
+              const T w = sW[r * c.pitch + g * BP + bi * 4 + i];
+              hq = fma(w, w, hq);
             }
       }
     }
@@ -312,17 +362,15 @@ __global__ void __launch_bounds__(RW) k_s1(int64_t N, int32_t b, int32_t ws, int
       __syncthreads();
       c.store(W, sW, r0, nr);
     }
-    tile_gram<T, BP>(c, sQ, sW, RTL, aq);
-    if (REORTH) tile_gram<T, BP>(c, sP, sW, RTL, ap);
+    tile_gram<T, BP>(c, second ? sP : sQ, sW, RTL, acc, tg);
   }
   const size_t o = (size_t)blockIdx.x * ncb;
-  gram_store<T, BP>(c, aq, partKq + o * b * b);
-  if (REORTH) gram_store<T, BP>(c, ap, partKp + o * b * b);
+  gram_store<T, BP>(c, acc, (second ? partKp : partKq) + o * b * b, tg);
   __syncthreads();
   const int32_t t = threadIdx.x;
   if (t < c.G * CB * CB) {
     const int32_t g = t / (CB * CB), rem = t - g * CB * CB, bi = rem / CB, bj = rem - bi * CB;
-    if (bi == bj) hsum[g * CB + bi] = hq;
+    if (bi == bj) hsum[g * CB + bi] = (double)hq;
   }
   __syncthreads();
   if (t < c.gcount) {
@@ -334,7 +382,7 @@ __global__ void __launch_bounds__(RW) k_s1(int64_t N, int32_t b, int32_t ws, int
 
 // S3: W1 = W0 - Q_j M1 (- Q_{j-1} M2), stored; partial Gram W1^T W1
 template <typename T, int BP, bool REORTH>
-__global__ void __launch_bounds__(RW) k_s3(int64_t N, int32_t b, int32_t ws, int32_t ncb, const T* __restrict__ Q,
+__global__ void __launch_bounds__(RW, 2) k_s3(int64_t N, int32_t b, int32_t ws, int32_t ncb, const T* __restrict__ Q,
                                            const T* __restrict__ Qp, T* __restrict__ W, const double* __restrict__ M1,
                                            const double* __restrict__ M2, double* __restrict__ partG) {
   constexpr int RTL = RowTile<T>::RTL;
@@ -346,7 +394,7 @@ __global__ void __launch_bounds__(RW) k_s3(int64_t N, int32_t b, int32_t ws, int
   T* sW = sP + tile;
   T* sM1 = sW + tile;
   T* sM2 = sM1 + c.G * BP * BP;
-  double acc[16] = {};
+  GramAcc<T> acc;
   c.load_mat(sM1, M1, c.cg0, false);
   if (REORTH) c.load_mat(sM2, M2, c.cg0, false);
   const int64_t rbeg = (int64_t)blockIdx.x * RCHK, rend = min(N, rbeg + RCHK);
@@ -359,9 +407,10 @@ __global__ void __launch_bounds__(RW) k_s3(int64_t N, int32_t b, int32_t ws, int
       if (REORTH) c.zero(sP, RTL);
       __syncthreads();
     }
-    c.load(sQ, Q, r0, nr);
-    c.load(sW, W, r0, nr);
-    if (REORTH) c.load(sP, Qp, r0, nr);
+    c.template load<RTL>(sQ, Q, r0, nr);
+    c.template load<RTL>(sW, W, r0, nr);
+    if (REORTH) c.template load<RTL>(sP, Qp, r0, nr);
+    c.load_wait();
     __syncthreads();
     tile_mul<T, BP, true>(c, sQ, sM1, sW, RTL);
     if (REORTH) {
@@ -370,14 +419,14 @@ __global__ void __launch_bounds__(RW) k_s3(int64_t N, int32_t b, int32_t ws, int
     }
     __syncthreads();
     c.store(W, sW, r0, nr);
-    tile_gram<T, BP>(c, sW, sW, RTL, acc);
+    tile_gram<T, BP>(c, sW, sW, RTL, acc, threadIdx.x);
   }
-  gram_store<T, BP>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b);
+  gram_store<T, BP>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b, threadIdx.x);
 }
 
 // OUT = W R^-1 (R^-1 upper triangular per colour); partial Gram of OUT when GRAM.  OUT may be W.
 template <typename T, int BP, bool GRAM>
-__global__ void __launch_bounds__(RW) k_tri(int64_t N, int32_t b, int32_t ws, int32_t ncb, const T* __restrict__ W,
+__global__ void __launch_bounds__(RW, 2) k_tri(int64_t N, int32_t b, int32_t ws, int32_t ncb, const T* __restrict__ W,
                                             T* __restrict__ OUT, const double* __restrict__ Rinv,
                                             double* __restrict__ partG) {
   constexpr int RTL = RowTile<T>::RTL;
@@ -387,7 +436,7 @@ __global__ void __launch_bounds__(RW) k_tri(int64_t N, int32_t b, int32_t ws, in
   T* sW = reinterpret_cast<T*>(smem_raw);
   T* sO = sW + tile;
   T* sR = sO + tile;
-  double acc[16] = {};
+  GramAcc<T> acc;
   c.load_mat(sR, Rinv, c.cg0, false);
   const int64_t rbeg = (int64_t)blockIdx.x * RCHK, rend = min(N, rbeg + RCHK);
   for (int64_t r0 = rbeg; r0 < rend; r0 += RTL) {
@@ -398,14 +447,15 @@ __global__ void __launch_bounds__(RW) k_tri(int64_t N, int32_t b, int32_t ws, in
       c.zero(sO, RTL);
       __syncthreads();
     }
-    c.load(sW, W, r0, nr);
+    c.template load<RTL>(sW, W, r0, nr);
+    c.load_wait();
     __syncthreads();
     tile_mul<T, BP, false>(c, sW, sR, sO, RTL);
     __syncthreads();
     c.store(OUT, sO, r0, nr);
-    if (GRAM) tile_gram<T, BP>(c, sO, sO, RTL, acc);
+    if (GRAM) tile_gram<T, BP>(c, sO, sO, RTL, acc, threadIdx.x);
   }
-  if (GRAM) gram_store<T, BP>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b);
+  if (GRAM) gram_store<T, BP>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b, threadIdx.x);
 }
 
 // out[lc][e] = sum over chunks of part[ch][lc][e], fixed order, FP64
@@ -699,7 +749,7 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
     CSS_TRY(launch_spmm<T>(ctx, a, Qc, W, st));
     if (a.ev_spmm) CSS_CU(ctx, cudaEventRecord(a.ev_spmm[2 * j + 1], st));
     // three-term update and the projections onto Q_j (and Q_{j-1})
-    s1<<<rgrid, RW, sm_s1, st>>>(N, b, a.ws, ncb, a.cb0, Qp, Qc, W, a.Bblk_prev, j == 0 ? 1 : 0, partKq, partKp,
+    s1<<<rgrid, reorth ? 2 * RW : RW, sm_s1, st>>>(N, b, a.ws, ncb, a.cb0, Qp, Qc, W, a.Bblk_prev, j == 0 ? 1 : 0, partKq, partKp,
                                  partH);
     CSS_LAUNCHED(ctx);
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sA);
