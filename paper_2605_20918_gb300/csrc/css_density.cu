@@ -147,23 +147,6 @@ __global__ void k_pob(int32_t nnzb, const int32_t* __restrict__ bpr, const int32
   if (k < nnzb) pob[k] = perm[bpr[k]];
 }
 
-__global__ void k_to_f32(int64_t n, const double* __restrict__ src, float* __restrict__ dst) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = (float)src[i];
-}
-
-// FP32 remainder of every diagonal block: lo = fl32(H_II - fl32(H_II))
-__global__ void k_diag_lo(int32_t n_brow, int32_t bb, const int32_t* __restrict__ row_ptr,
-                          const int32_t* __restrict__ col_idx, const double* __restrict__ src, float* __restrict__ lo) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)n_brow * bb) return;
-  const int32_t I = (int32_t)(t / bb), e = (int32_t)(t % bb);
-  int32_t k = row_ptr[I];
-  while (k < row_ptr[I + 1] && col_idx[k] != I) ++k;
-  const double h = src[(size_t)k * bb + e];
-  lo[t] = (float)(h - (double)(float)h);
-}
-
 // ----------------------------------------------------------- chemical potential
 // Bounded grid barrier (generation counter): every wait gives up after ~2^24 polls, sets
 // *err and returns false, so the kernel always terminates.
@@ -663,20 +646,9 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     CSS_CU(ctx, cudaStreamSynchronize(st));
     for (int32_t c = 0; c <= n_col; ++c) pair_off_h[c] = hb[c];
   }
-  const void* Hv = Hval;
+  const void* Hv = nullptr;
   const void* Hlo = nullptr;
-  if (f32) {
-    float* hf;
-    CSS_TRY(ws_get(ctx, "h_f32", (size_t)nnzb * bb, &hf));
-    k_to_f32<<<(unsigned)css_ceil_div((int64_t)nnzb * bb, T), T, 0, st>>>((int64_t)nnzb * bb, Hval, hf);
-    CSS_LAUNCHED(ctx);
-    Hv = hf;
-    float* hlo;
-    CSS_TRY(ws_get(ctx, "h_lo", (size_t)n_brow * bb, &hlo));
-    k_diag_lo<<<(unsigned)css_ceil_div((int64_t)n_brow * bb, T), T, 0, st>>>(n_brow, bb, row_ptr, col_idx, Hval, hlo);
-    CSS_LAUNCHED(ctx);
-    Hlo = hlo;
-  }
+  CSS_TRY(css_spmm_prepare(ctx, f32, b, n_brow, nnzb, row_ptr, col_idx, Hval, &Hv, &Hlo, st));
   tm.mark();  // 1
 
   // ----------------------------------------------------------- memory plan

@@ -4,9 +4,11 @@
 // Krylov blocks of a batch of colours live side by side as the columns of one N x w matrix
 // (row-major, row stride ws, w = b * colours): colour c of the batch owns columns
 // [c b, c b + b).  One step j is
-//     W = H Q_j                        (k_spmm: every H block multiplies all w columns)
-//     W -= Q_{j-1} B_{j-1}^T ; A_j = sym(Q_j^T W) ; W -= Q_j A_j      (k_threeterm, k_sub)
-//     W = Q_{j+1} B_j by CholQR2: R1 = chol(W^T W), W R1^-1, R2 = chol(.), B_j = R2 R1
+//     W = H Q_j                                       (k_spmm: every H block times all w columns)
+//     W0 = W - Q_{j-1} B_{j-1}^T;  A_j = sym(Q_j^T W0)                     (k_s1)
+//     W1 = W0 - Q_j (Q_j^T W0) - Q_{j-1} (Q_{j-1}^T W0)  (local reorthogonalisation; k_s3)
+//     W1 = Q_{j+1} B_j by shifted CholeskyQR3: R = chol(W^T W [+ shift]), W R^-1, three times
+//                                                      (k_chol, k_tri)
 // Small per-colour matrices (A_j, B_j, Grams, Cholesky factors) are FP64; the per-row-chunk
 // partial products are combined in FP64 in a fixed order, so every run is bitwise
 // reproducible (a second pass regenerates the same basis).
@@ -15,90 +17,158 @@
 namespace {
 
 // ------------------------------------------------------------------------ H * V
+// H is kept as transposed, zero-padded BM x BM blocks: Ht[p][k][a] = H_p[a][k] (a, k < b), 0
+// elsewhere (k_hpad, once per build), so a block is one contiguous run of 16-byte chunks and a
+// column k of H_p is BM contiguous values.
+//
 // One CTA per (block row I, tile of 128*TC columns); blockIdx.x runs over I so the CTAs in
-// flight share one column tile and the V rows they gather stay in L2.  The row's H blocks are
-// staged in shared memory (zero-padded to BM x BM), every thread keeps the b x TC outputs of
-// its columns in registers and streams the b rows of V of each neighbour J.
+// flight share one column tile and the V rows they gather stay in L2.  Thread t owns TC
+// contiguous columns (one 16-, 8- or 4-byte chunk per row) and all BM rows of W_I for them.
+// The neighbours J of row I are walked through a two-stage shared-memory ring filled by
+// cp.async: while step q is multiplied, the copies of step q+1 (the H block, and each
+// thread's own chunk of the b rows of V_J, rows >= b and columns >= w zero-filled) are in
+// flight.  In FP32 mode a last virtual step adds the low FP32 parts of the diagonal block
+// times V_I.
+template <typename T, int BM, int TC>
+struct SpmmCfg {
+  static constexpr int NT = 128;                 // threads
+  static constexpr int CT = NT * TC;             // columns per tile
+  static constexpr int CH = TC * sizeof(T);      // bytes of a thread's chunk of a row
+  static constexpr int HB = BM * BM * (int)sizeof(T);  // bytes of one padded block
+  static constexpr size_t stage = (size_t)BM * CT * sizeof(T) + HB;
+  static constexpr size_t smem = 2 * stage;
+};
+
+template <int CH>
+__device__ __forceinline__ void cp_async_chunk(void* dst, const void* src, int bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (CH == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+  else if constexpr (CH == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 template <typename T, int BM, int TC>
 __global__ void __launch_bounds__(128) k_spmm(int32_t b, const int32_t* __restrict__ row_ptr,
-                                              const int32_t* __restrict__ col_idx, const T* __restrict__ Hv,
+                                              const int32_t* __restrict__ col_idx, const T* __restrict__ Ht,
                                               const T* __restrict__ V, T* __restrict__ W, int32_t ws, int32_t w,
-                                              int32_t chunk, const T* __restrict__ Hlo) {
+                                              const T* __restrict__ Hlo_t) {
+  using C = SpmmCfg<T, BM, TC>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Hs = reinterpret_cast<T*>(smem_raw);
   const int32_t I = blockIdx.x;
-  const int32_t col0 = blockIdx.y * (128 * TC) + threadIdx.x;
+  const int32_t t = threadIdx.x;
+  const int32_t col = blockIdx.y * C::CT + TC * t;  // first of this thread's columns
   const int32_t p0 = row_ptr[I], p1 = row_ptr[I + 1];
-  const int32_t bb = b * b;
+  const int32_t nsteps = (p1 - p0) + (Hlo_t ? 1 : 0);
+  // bytes of this thread's chunk that lie inside the matrix (0 beyond the last column)
+  const int cbytes = col >= w ? 0 : (w - col >= TC ? C::CH : (w - col) * (int)sizeof(T));
+  const bool warp_live = blockIdx.y * C::CT + TC * 32 * (t >> 5) < w;  // some column of the warp
+  auto stage_v = [&](int s) { return reinterpret_cast<T*>(smem_raw + s * C::stage); };
+  auto stage_h = [&](int s) { return reinterpret_cast<T*>(smem_raw + s * C::stage + (size_t)BM * C::CT * sizeof(T)); };
+  auto issue = [&](int32_t q, int32_t J, int s) {
+    const bool lo = q == p1 - p0;  // the diagonal low-part step
+    const unsigned char* hsrc =
+        reinterpret_cast<const unsigned char*>(lo ? Hlo_t + (size_t)I * BM * BM : Ht + (size_t)(p0 + q) * BM * BM);
+    unsigned char* hdst = reinterpret_cast<unsigned char*>(stage_h(s));
+    for (int32_t o = t * 16; o < C::HB; o += C::NT * 16) cp_async_chunk<16>(hdst + o, hsrc + o, 16);
+    T* vd = stage_v(s) + TC * t;
+    const T* vsrc = V + (size_t)J * b * ws + (col < w ? col : 0);
+#pragma unroll
+    for (int k = 0; k < BM; ++k)
+      cp_async_chunk<C::CH>(vd + (size_t)k * C::CT, vsrc + (size_t)(k < b ? k : 0) * ws, k < b ? cbytes : 0);
+    cp_async_commit();
+  };
   T acc[BM][TC];
 #pragma unroll
   for (int a = 0; a < BM; ++a)
 #pragma unroll
     for (int u = 0; u < TC; ++u) acc[a][u] = T(0);
-  for (int32_t pc = p0; pc < p1; pc += chunk) {
-    const int32_t pe = min(p1, pc + chunk);
-    __syncthreads();
-    for (int32_t e = threadIdx.x; e < (pe - pc) * BM * BM; e += blockDim.x) {
-      int32_t blk = e / (BM * BM), r = e % (BM * BM), a = r / BM, k = r % BM;
-      Hs[e] = (a < b && k < b) ? Hv[(size_t)(pc + blk) * bb + a * b + k] : T(0);
-    }
-    __syncthreads();
-    for (int32_t p = pc; p < pe; ++p) {
-      const int32_t J = col_idx[p];
-      const T* Hb = Hs + (size_t)(p - pc) * BM * BM;
-      const T* Vr = V + (size_t)J * b * ws;
-      T v[BM][TC];
-#pragma unroll
-      for (int k = 0; k < BM; ++k)
-#pragma unroll
-        for (int u = 0; u < TC; ++u) {
-          const int32_t col = col0 + 128 * u;
-          v[k][u] = (k < b && col < w) ? __ldg(Vr + (size_t)k * ws + col) : T(0);
-        }
-#pragma unroll
-      for (int a = 0; a < BM; ++a)
-#pragma unroll
+  if (nsteps > 0) {
+    int32_t Jn = p0 < p1 ? col_idx[p0] : I;
+    issue(0, Jn, 0);
+    Jn = (1 < p1 - p0) ? col_idx[p0 + 1] : I;
+    for (int32_t q = 0; q < nsteps; ++q) {
+      const int s = q & 1;
+      if (q + 1 < nsteps) {
+        issue(q + 1, Jn, s ^ 1);
+        Jn = (q + 2 < p1 - p0) ? col_idx[p0 + q + 2] : I;  // its latency overlaps the multiply
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();  // the H block of step q (copied by every thread) is visible
+      if (warp_live) {
+        const T* hs = stage_h(s);
+        const T* vs = stage_v(s) + TC * t;
+#pragma unroll 4
         for (int k = 0; k < BM; ++k) {
-          const T h = Hb[a * BM + k];
+          T v[TC];
 #pragma unroll
-          for (int u = 0; u < TC; ++u) acc[a][u] = fma(h, v[k][u], acc[a][u]);
+          for (int u = 0; u < TC; ++u) v[u] = vs[(size_t)k * C::CT + u];
+#pragma unroll
+          for (int a = 0; a < BM; ++a) {
+            const T h = hs[k * BM + a];
+#pragma unroll
+            for (int u = 0; u < TC; ++u) acc[a][u] = fma(h, v[u], acc[a][u]);
+          }
         }
+      }
+      __syncthreads();  // stage s is free for step q + 2
     }
   }
-  if (Hlo) {
-    // low part of the diagonal block (FP32 mode: H_II = hi + lo, both FP32), W_I += lo V_I
-    __syncthreads();
-    for (int32_t e = threadIdx.x; e < BM * BM; e += blockDim.x) {
-      int32_t a = e / BM, k = e % BM;
-      Hs[e] = (a < b && k < b) ? Hlo[(size_t)I * bb + a * b + k] : T(0);
+  if (col >= w) return;
+  T* Wr = W + (size_t)I * b * ws + col;
+#pragma unroll
+  for (int a = 0; a < BM; ++a) {
+    if (a >= b) break;
+    if (cbytes == C::CH) {
+      if constexpr (C::CH == 16 && sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(Wr + (size_t)a * ws) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+      } else if constexpr (C::CH == 16) {
+        *reinterpret_cast<double2*>(Wr + (size_t)a * ws) = make_double2(acc[a][0], acc[a][1]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < TC; ++u) Wr[(size_t)a * ws + u] = acc[a][u];
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < TC; ++u)
+        if (col + u < w) Wr[(size_t)a * ws + u] = acc[a][u];
     }
-    __syncthreads();
-    const T* Vr = V + (size_t)I * b * ws;
-    T v[BM][TC];
-#pragma unroll
-    for (int k = 0; k < BM; ++k)
-#pragma unroll
-      for (int u = 0; u < TC; ++u) {
-        const int32_t col = col0 + 128 * u;
-        v[k][u] = (k < b && col < w) ? __ldg(Vr + (size_t)k * ws + col) : T(0);
-      }
-#pragma unroll
-    for (int a = 0; a < BM; ++a)
-#pragma unroll
-      for (int k = 0; k < BM; ++k) {
-        const T h = Hs[a * BM + k];
-#pragma unroll
-        for (int u = 0; u < TC; ++u) acc[a][u] = fma(h, v[k][u], acc[a][u]);
-      }
   }
-  T* Wr = W + (size_t)I * b * ws;
-#pragma unroll
-  for (int a = 0; a < BM; ++a)
-#pragma unroll
-    for (int u = 0; u < TC; ++u) {
-      const int32_t col = col0 + 128 * u;
-      if (a < b && col < w) Wr[(size_t)a * ws + col] = acc[a][u];
+}
+
+// Ht[p][k][a] = H_p[a][k] for a, k < b, zero padding to BM x BM; the source is FP64 [p][b][b].
+// LO: only the blocks p = diag[I] (the diagonal block of row I), and the FP32 remainder
+// fl32(h - fl32(h)) of each entry.
+template <typename T, bool LO>
+__global__ void k_hpad(int64_t nblocks, int32_t b, int32_t BM, const double* __restrict__ H,
+                       const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                       T* __restrict__ Ht) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t bb = (int64_t)BM * BM;
+  if (e >= nblocks * bb) return;
+  const int64_t p = e / bb;
+  const int32_t r = (int32_t)(e - p * bb), k = r / BM, a = r - k * BM;
+  T v = T(0);
+  if (a < b && k < b) {
+    int64_t src = p;
+    if (LO) {  // the row's diagonal block; a row without one has no low part
+      int32_t q = row_ptr[p];
+      while (q < row_ptr[p + 1] && col_idx[q] != (int32_t)p) ++q;
+      src = q < row_ptr[p + 1] ? q : -1;
     }
+    if (src >= 0) {
+      const double h = H[(size_t)src * b * b + (size_t)a * b + k];
+      v = LO ? (T)(h - (double)(float)h) : (T)h;
+    }
+  }
+  Ht[e] = v;
 }
 
 // --------------------------------------------------------------- row-chunk kernels
@@ -650,16 +720,12 @@ css_status smem_optin(css_ctx* ctx, K kern, size_t bytes) {
 
 template <typename T, int BM, int TC>
 css_status launch_spmm_t(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaStream_t st) {
-  const int64_t smem_cap = 160 * 1024;
-  int64_t cap_blocks = smem_cap / ((int64_t)BM * BM * sizeof(T));
-  int32_t chunk = (int32_t)(a.max_row_blocks < cap_blocks ? a.max_row_blocks : cap_blocks);
-  if (chunk < 1) chunk = 1;
-  const size_t smem = (size_t)chunk * BM * BM * sizeof(T);
+  using C = SpmmCfg<T, BM, TC>;
   auto kern = k_spmm<T, BM, TC>;
-  CSS_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((unsigned)a.n_brow, (unsigned)css_ceil_div(a.w, 128 * TC));
-  kern<<<grid, 128, smem, st>>>(a.b, a.row_ptr, a.col_idx, (const T*)a.Hval, V, W, a.ws, a.w, chunk,
-                                (const T*)a.Hlo_diag);
+  CSS_TRY(smem_optin(ctx, kern, C::smem));
+  dim3 grid((unsigned)a.n_brow, (unsigned)css_ceil_div(a.w, C::CT));
+  kern<<<grid, C::NT, C::smem, st>>>(a.b, a.row_ptr, a.col_idx, (const T*)a.Hval, V, W, a.ws, a.w,
+                                     (const T*)a.Hlo_diag);
   CSS_LAUNCHED(ctx);
   return CSS_OK;
 }
@@ -667,11 +733,13 @@ css_status launch_spmm_t(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaSt
 template <typename T>
 css_status launch_spmm(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaStream_t st) {
   constexpr bool F32 = sizeof(T) == 4;
-  if (a.b <= 6) return launch_spmm_t<T, 6, F32 ? 4 : 2>(ctx, a, V, W, st);
-  if (a.b <= 8) return launch_spmm_t<T, 8, F32 ? 4 : 2>(ctx, a, V, W, st);
-  if (a.b <= 16) return launch_spmm_t<T, 16, F32 ? 2 : 1>(ctx, a, V, W, st);
-  if (a.b <= 24) return launch_spmm_t<T, 24, F32 ? 2 : 1>(ctx, a, V, W, st);
-  return launch_spmm_t<T, 32, 1>(ctx, a, V, W, st);
+  switch (css_spmm_bm(a.b)) {
+    case 8: return launch_spmm_t<T, 8, F32 ? 4 : 2>(ctx, a, V, W, st);
+    case 12: return launch_spmm_t<T, 12, F32 ? 4 : 2>(ctx, a, V, W, st);
+    case 16: return launch_spmm_t<T, 16, F32 ? 4 : 2>(ctx, a, V, W, st);
+    case 24: return launch_spmm_t<T, 24, F32 ? 4 : 2>(ctx, a, V, W, st);
+    default: return launch_spmm_t<T, 32, F32 ? 2 : 1>(ctx, a, V, W, st);
+  }
 }
 
 template <typename T, int BP>
@@ -818,3 +886,35 @@ size_t css_lanczos_part_doubles(int64_t N, int32_t b, int32_t ncb) {
 }
 
 size_t css_lanczos_small_doubles(int32_t b, int32_t ncb) { return (size_t)ncb * b * b * 10 + ncb + 64; }
+
+int32_t css_spmm_bm(int32_t b) { return b <= 8 ? 8 : b <= 12 ? 12 : b <= 16 ? 16 : b <= 24 ? 24 : 32; }
+
+css_status css_spmm_prepare(css_ctx* ctx, bool fp32, int32_t b, int32_t n_brow, int32_t nnzb,
+                            const int32_t* row_ptr, const int32_t* col_idx, const double* H, const void** Hpad,
+                            const void** Hlo_pad, cudaStream_t st) {
+  const int32_t BM = css_spmm_bm(b);
+  const int64_t bb = (int64_t)BM * BM;
+  constexpr int T = 256;
+  if (fp32) {
+    float *hp, *lp;
+    CSS_TRY(css_ws(ctx, "h_pad32", (size_t)nnzb * bb * sizeof(float), (void**)&hp));
+    CSS_TRY(css_ws(ctx, "h_lopad32", (size_t)n_brow * bb * sizeof(float), (void**)&lp));
+    k_hpad<float, false><<<(unsigned)css_ceil_div((int64_t)nnzb * bb, T), T, 0, st>>>(nnzb, b, BM, H, row_ptr,
+                                                                                       col_idx, hp);
+    CSS_LAUNCHED(ctx);
+    k_hpad<float, true><<<(unsigned)css_ceil_div((int64_t)n_brow * bb, T), T, 0, st>>>(n_brow, b, BM, H, row_ptr,
+                                                                                       col_idx, lp);
+    CSS_LAUNCHED(ctx);
+    *Hpad = hp;
+    *Hlo_pad = lp;
+  } else {
+    double* hp;
+    CSS_TRY(css_ws(ctx, "h_pad64", (size_t)nnzb * bb * sizeof(double), (void**)&hp));
+    k_hpad<double, false><<<(unsigned)css_ceil_div((int64_t)nnzb * bb, T), T, 0, st>>>(nnzb, b, BM, H, row_ptr,
+                                                                                        col_idx, hp);
+    CSS_LAUNCHED(ctx);
+    *Hpad = hp;
+    *Hlo_pad = nullptr;
+  }
+  return CSS_OK;
+}

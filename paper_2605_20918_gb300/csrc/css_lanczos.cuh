@@ -8,8 +8,8 @@ struct LzArgs {
   int32_t w = 0, ws = 0;             // columns of the batch (b * ncb) and row stride
   const int32_t* row_ptr = nullptr;
   const int32_t* col_idx = nullptr;
-  const void* Hval = nullptr;        // [nnzb][b][b] in the vector precision
-  const void* Hlo_diag = nullptr;    // FP32 mode: [n_brow][b][b] low parts of the diagonal blocks
+  const void* Hval = nullptr;        // [nnzb][BM][BM] transposed, zero-padded (css_spmm_prepare)
+  const void* Hlo_diag = nullptr;    // FP32 mode: [n_brow][BM][BM] low parts of the diagonal blocks
   int32_t max_row_blocks = 0;        // largest block count of a row
   const int32_t* colour = nullptr;   // global colour of each molecule
   const int8_t* sign = nullptr;      // probe signs [n_brow * b]
@@ -40,3 +40,10 @@ struct LzArgs {
 css_status css_lanczos_pass(css_ctx* ctx, const LzArgs& a, cudaStream_t st);
 size_t css_lanczos_part_doubles(int64_t N, int32_t b, int32_t ncb);
 size_t css_lanczos_small_doubles(int32_t b, int32_t ncb);
+// padded block size of the H * V kernel for block width b
+int32_t css_spmm_bm(int32_t b);
+// H (FP64 [nnzb][b][b]) in the layout of the H * V kernel, in the vector precision; FP32 mode
+// also the low FP32 parts of the diagonal blocks.  Both live in the context's workspace.
+css_status css_spmm_prepare(css_ctx* ctx, bool fp32, int32_t b, int32_t n_brow, int32_t nnzb,
+                            const int32_t* row_ptr, const int32_t* col_idx, const double* H, const void** Hpad,
+                            const void** Hlo_pad, cudaStream_t st);
