@@ -373,6 +373,107 @@ __global__ void k_xcompute(int64_t n_pairs, int32_t b, int32_t m, int32_t nmax, 
   X[(size_t)p * bb + e] = acc;
 }
 
+// X_p = Qs_p Z_c for the FP32 Krylov rows: for every pair p of colour c a (b x m b) x (m b x b)
+// product.  A CTA takes up to XP pairs of one colour and walks the blocks j of Z_c: the
+// blocks Qs_p[j] (transposed) and the FP32 hi/lo halves of Z_c[j] are staged in shared memory
+// (zero padded to BP x BP), and each thread owns a 4 x 4 tile of one pair's X.  The hi product
+// of a block is summed in FP32 and added into an FP32 hi + lo pair by TwoSum; the lo product
+// (2^-24 of the hi one) is summed in FP32 over all blocks.  The sum is widened to FP64 once.
+template <int BP>
+__global__ void __launch_bounds__(256) k_xtile(int32_t n_col, int32_t b, int32_t m, int32_t nmax,
+                                               const int32_t* __restrict__ coff, const int32_t* __restrict__ cta_off,
+                                               const int32_t* __restrict__ nblk, const float* __restrict__ Qs,
+                                               const float* __restrict__ zh, const float* __restrict__ zl,
+                                               double* __restrict__ X) {
+  constexpr int CB = BP / 4, TPP = CB * CB, XP = 256 / TPP;
+  __shared__ __align__(16) float sQ[XP][BP][BP];  // [pair][l][a]
+  __shared__ __align__(16) float sZh[BP][BP];     // [l][k]
+  __shared__ __align__(16) float sZl[BP][BP];
+  const int32_t bid = blockIdx.x;
+  if (bid >= cta_off[n_col]) return;
+  int32_t lo = 0, hi = n_col - 1;  // colour c: cta_off[c] <= bid < cta_off[c + 1]
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (cta_off[mid] <= bid) lo = mid;
+    else hi = mid - 1;
+  }
+  const int32_t c = lo;
+  const int32_t p0 = coff[c] + (bid - cta_off[c]) * XP;
+  const int32_t np = min(XP, coff[c + 1] - p0);
+  const int32_t nb = nblk[c], bb = b * b;
+  const int t = threadIdx.x;
+  const int pp = t / TPP, rem = t - pp * TPP, ai = rem / CB, ki = rem - ai * CB;
+  for (int e = t; e < XP * BP * BP; e += 256) (&sQ[0][0][0])[e] = 0.0f;
+  for (int e = t; e < BP * BP; e += 256) {
+    (&sZh[0][0])[e] = 0.0f;
+    (&sZl[0][0])[e] = 0.0f;
+  }
+  float ahi[16], alo[16], asm_[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) ahi[i] = alo[i] = asm_[i] = 0.0f;
+  for (int32_t j = 0; j < nb; ++j) {
+    __syncthreads();  // the previous block's readers are done (and the zeroing is visible)
+    for (int32_t e = t; e < np * bb; e += 256) {
+      const int32_t q = e / bb, r = e - q * bb, a = r / b, l = r - a * b;
+      sQ[q][l][a] = Qs[((size_t)(p0 + q) * m + j) * bb + r];
+    }
+    for (int32_t e = t; e < bb; e += 256) {
+      const int32_t l = e / b, k = e - l * b;
+      const size_t o = ((size_t)c * nmax + (size_t)j * b + l) * b + k;
+      sZh[l][k] = zh[o];
+      sZl[l][k] = zl[o];
+    }
+    __syncthreads();
+    if (pp < np) {
+      float ph[4][4] = {};
+      for (int32_t l = 0; l < b; ++l) {
+        const float4 x = *reinterpret_cast<const float4*>(&sQ[pp][l][ai * 4]);
+        const float4 zH = *reinterpret_cast<const float4*>(&sZh[l][ki * 4]);
+        const float4 zL = *reinterpret_cast<const float4*>(&sZl[l][ki * 4]);
+        const float xv[4] = {x.x, x.y, x.z, x.w}, hv[4] = {zH.x, zH.y, zH.z, zH.w}, lv[4] = {zL.x, zL.y, zL.z, zL.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            ph[i][k] = fmaf(xv[i], hv[k], ph[i][k]);
+            asm_[i * 4 + k] = fmaf(xv[i], lv[k], asm_[i * 4 + k]);
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {  // TwoSum of the running hi sum and this block's product
+          const int u = i * 4 + k;
+          const float s = __fadd_rn(ahi[u], ph[i][k]);
+          const float z = __fsub_rn(s, ahi[u]);
+          alo[u] = __fadd_rn(alo[u], __fadd_rn(__fsub_rn(ahi[u], __fsub_rn(s, z)), __fsub_rn(ph[i][k], z)));
+          ahi[u] = s;
+        }
+    }
+  }
+  if (pp >= np) return;
+  double* xo = X + (size_t)(p0 + pp) * bb;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int32_t a = ai * 4 + i, kk = ki * 4 + k;
+      const int u = i * 4 + k;
+      if (a < b && kk < b) xo[a * b + kk] = (double)ahi[u] + (double)alo[u] + (double)asm_[u];
+    }
+}
+
+// CTAs of k_xtile per colour (ceil(pairs / xp)), prefix-summed; one thread, in colour order
+__global__ void k_xtile_plan(int32_t n_col, int32_t xp, const int32_t* __restrict__ coff, int32_t* __restrict__ cta_off) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int32_t s = 0;
+  for (int32_t c = 0; c < n_col; ++c) {
+    cta_off[c] = s;
+    s += (coff[c + 1] - coff[c] + xp - 1) / xp;
+  }
+  cta_off[n_col] = s;
+}
+
 // P_val and trace partials of one system's blocks [k0, k1)
 constexpr int EX_T = 256;
 __global__ void __launch_bounds__(EX_T) k_extract(int32_t k0, int32_t k1, int32_t b, int32_t blk_off,
@@ -850,8 +951,19 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
       k_zsplit<<<(unsigned)css_ceil_div((int64_t)n_col * nmax * b, T), T, 0, st>>>((int64_t)n_col * nmax * b, Z, zh,
                                                                                    zl);
       CSS_LAUNCHED(ctx);
-      k_xcompute<float><<<(unsigned)css_ceil_div(n_pairs * bb, T), T, 0, st>>>(n_pairs, b, m, nmax, pair_c, nblk,
-                                                                                (const float*)Qs, Z, zh, zl, X);
+      const int32_t BPx = b <= 8 ? 8 : b <= 16 ? 16 : b <= 24 ? 24 : 32;
+      const int32_t xp = 256 / ((BPx / 4) * (BPx / 4));
+      int32_t* cta_off;
+      CSS_TRY(ws_get(ctx, "x_cta", (size_t)n_col + 1, &cta_off));
+      k_xtile_plan<<<1, 32, 0, st>>>(n_col, xp, coff, cta_off);
+      CSS_LAUNCHED(ctx);
+      const unsigned nct = (unsigned)(n_pairs / xp + n_col + 1);  // >= sum over colours of ceil(pairs / xp)
+      auto launch_x = [&](auto kern) { kern<<<nct, 256, 0, st>>>(n_col, b, m, nmax, coff, cta_off, nblk,
+                                                                 (const float*)Qs, zh, zl, X); };
+      if (BPx == 8) launch_x(k_xtile<8>);
+      else if (BPx == 16) launch_x(k_xtile<16>);
+      else if (BPx == 24) launch_x(k_xtile<24>);
+      else launch_x(k_xtile<32>);
     } else {
       k_xcompute<double><<<(unsigned)css_ceil_div(n_pairs * bb, T), T, 0, st>>>(n_pairs, b, m, nmax, pair_c, nblk,
                                                                                  (const double*)Qs, Z, nullptr,

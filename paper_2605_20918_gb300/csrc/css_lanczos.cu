@@ -197,7 +197,8 @@ template <int BP>
 __host__ __device__ inline int colours_per_cta(int b) {
   int g = group_cap<BP>();
   int lim = 192 / b;                    // contiguous columns per row <= 192
-  if (lim > 256 / BP) lim = 256 / BP;   // padded tile width <= 256 (shared memory)
+  if (lim > 192 / BP) lim = 192 / BP;   // padded tile width <= 192: two stages of three tiles
+                                        // and two matrices stay below 180 KB of shared memory
   if (lim < 1) lim = 1;
   return g < lim ? g : lim;
 }
@@ -207,25 +208,16 @@ struct RowCtx {
   int32_t b, ws, G, gcount, pitch, cg0;  // cg0 = first colour of the group within the batch
   int32_t my_col, my_smem;  // this thread's column of the group (width <= blockDim) and its tile offset
   // issue the asynchronous copy of one tile of RTL rows (rows >= nr are zero-filled); the copies
-  // hold no registers, so every row of the tile is in flight at once.  Completed by load_wait().
+  // hold no registers, so every row of the tile is in flight at once.  The caller commits the
+  // group and waits for it (cp_async_commit / cp_async_wait).
   template <int RTL>
   __device__ __forceinline__ void load(T* dst, const T* src, int64_t r0, int32_t nr) const {
     if (my_col < 0) return;
     const T* s = src + (size_t)r0 * ws + (size_t)cg0 * b + my_col;
-#pragma unroll
-    for (int32_t r = 0; r < RTL; ++r) {
-      const unsigned d = (unsigned)__cvta_generic_to_shared(dst + r * pitch + my_smem);
-      const T* g = s + (size_t)(r < nr ? r : 0) * ws;
-      const int n = r < nr ? (int)sizeof(T) : 0;
-      if constexpr (sizeof(T) == 4)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(g), "r"(n) : "memory");
-      else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(g), "r"(n) : "memory");
-    }
-  }
-  // wait for this thread's outstanding tile copies (a __syncthreads must follow)
-  __device__ __forceinline__ static void load_wait() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+#pragma unroll 4
+    for (int32_t r = 0; r < RTL; ++r)
+      cp_async_chunk<sizeof(T)>(dst + r * pitch + my_smem, s + (size_t)(r < nr ? r : 0) * ws,
+                                r < nr ? (int)sizeof(T) : 0);
   }
   __device__ __forceinline__ void store(T* dst, const T* src, int64_t r0, int32_t nr) const {
     if (my_col < 0) return;
@@ -250,8 +242,10 @@ struct RowCtx {
 };
 
 // OUT[r][g][k] (+)= sum_l X[r][g][l] M[g][l][k] over 4x4 output blocks.  SUB: OUT -= X M.
-template <typename T, int BP, bool SUB>
-__device__ __forceinline__ void tile_mul(const RowCtx<T, BP>& c, const T* X, const T* M, T* OUT, int32_t rtl) {
+// TWO: a second product X2 M2 in the same pass (OUT -= X M + X2 M2)
+template <typename T, int BP, bool SUB, bool TWO>
+__device__ __forceinline__ void tile_mul(const RowCtx<T, BP>& c, const T* X, const T* M, T* OUT, int32_t rtl,
+                                         const T* X2, const T* M2) {
   constexpr int CB = BP / 4;
   const int32_t nblk = (rtl / 4) * c.G * CB;
   for (int32_t t = threadIdx.x; t < nblk; t += blockDim.x) {
@@ -274,6 +268,21 @@ __device__ __forceinline__ void tile_mul(const RowCtx<T, BP>& c, const T* X, con
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = SUB ? fma(-x[i], m[j], acc[i][j]) : fma(x[i], m[j], acc[i][j]);
+    }
+    if (TWO) {
+      const T* xm2 = X2 + g * BP;
+      const T* mm2 = M2 + (size_t)g * BP * BP + cb * 4;
+      for (int32_t l = 0; l < c.b; ++l) {
+        T x[4], m[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = xm2[(r0 + i) * c.pitch + l];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m[j] = mm2[l * BP + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = SUB ? fma(-x[i], m[j], acc[i][j]) : fma(x[i], m[j], acc[i][j]);
+      }
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -376,64 +385,96 @@ __device__ __forceinline__ RowCtx<T, BP> make_ctx(int32_t b, int32_t ws, int32_t
   return c;
 }
 
+// The row kernels below walk their chunk of RCHK rows in tiles of RTL rows through a
+// two-stage shared-memory ring: the cp.async copies of tile i+1 are in flight while tile i is
+// processed.  Padding columns of a stage are zeroed once and never written by a copy; rows past
+// the end of the matrix are zero-filled by the copies themselves.
+template <typename T, int BP>
+struct RowRing {
+  T* base;
+  int32_t tile, na;  // elements per tile, arrays per stage
+  __device__ __forceinline__ T* at(int s, int a) const { return base + ((size_t)s * na + a) * tile; }
+};
+
+// tiles of this CTA's row chunk: fn_issue(stage, r0, nr) issues and commits the copies of one
+// tile, fn_tile(stage, r0, nr) consumes it (with its own barriers where it needs them)
+template <typename Issue, typename Body>
+__device__ __forceinline__ void row_pipeline(int64_t N, int32_t rtl, Issue fn_issue, Body fn_tile) {
+  const int64_t rbeg = (int64_t)blockIdx.x * RCHK, rend = min(N, rbeg + RCHK);
+  if (rbeg >= rend) return;
+  const int32_t ntile = (int32_t)((rend - rbeg + rtl - 1) / rtl);
+  fn_issue(0, rbeg, (int32_t)min((int64_t)rtl, rend - rbeg));
+  for (int32_t it = 0; it < ntile; ++it) {
+    const int s = it & 1;
+    const int64_t r0 = rbeg + (int64_t)it * rtl;
+    const int32_t nr = (int32_t)min((int64_t)rtl, rend - r0);
+    if (it + 1 < ntile) {
+      const int64_t r1 = r0 + rtl;
+      fn_issue(s ^ 1, r1, (int32_t)min((int64_t)rtl, rend - r1));
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();  // tile it is in shared memory for every thread
+    fn_tile(s, r0, nr);
+    __syncthreads();  // stage s is free for tile it + 2
+  }
+}
+
 // S1: W = H Q_j arrives in W.  W0 = W - Q_{j-1} B_{j-1}^T (skipped at the first step), stored;
 // partials Kq = Q_j^T W0, Kp = Q_{j-1}^T W0 (REORTH), and ||W||^2 per colour (breakdown test).
 // With REORTH the CTA has 2*RW threads: the first RW accumulate Kq, the second RW Kp.
 template <typename T, int BP, bool REORTH>
-__global__ void __launch_bounds__(REORTH ? 2 * RW : RW, REORTH ? 1 : 2) k_s1(int64_t N, int32_t b, int32_t ws, int32_t ncb, int32_t cb0,
-                                           const T* __restrict__ Qp, const T* __restrict__ Q, T* __restrict__ W,
-                                           const double* __restrict__ Bprev, int first, double* __restrict__ partKq,
-                                           double* __restrict__ partKp, double* __restrict__ partH) {
+__global__ void __launch_bounds__(REORTH ? 2 * RW : RW, 1)
+    k_s1(int64_t N, int32_t b, int32_t ws, int32_t ncb, int32_t cb0, const T* __restrict__ Qp,
+         const T* __restrict__ Q, T* __restrict__ W, const double* __restrict__ Bprev, int first,
+         double* __restrict__ partKq, double* __restrict__ partKp, double* __restrict__ partH) {
   constexpr int RTL = RowTile<T>::RTL;
   constexpr int CB = BP / 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const RowCtx<T, BP> c = make_ctx<T, BP>(b, ws, ncb);
-  const int32_t tile = RTL * c.pitch;
-  T* sQ = reinterpret_cast<T*>(smem_raw);
-  T* sP = sQ + tile;
-  T* sW = sP + tile;
-  T* sB = sW + tile;  // [G][BP][BP] = B_{j-1}^T per colour
-  double* hsum = reinterpret_cast<double*>(sB + c.G * BP * BP);  // [G][CB]
+  const bool usep = REORTH || !first;
+  RowRing<T, BP> ring{reinterpret_cast<T*>(smem_raw), RTL * c.pitch, 3};  // Q, Q_{j-1}, W
+  T* sB = ring.at(2, 0);                                                    // [G][BP][BP] B_{j-1}^T
+  double* hsum = reinterpret_cast<double*>(sB + c.G * BP * BP);             // [G][CB]
   GramAcc<T> acc;                                   // Kq (first RW threads) or Kp (second RW)
   const bool second = REORTH && threadIdx.x >= RW;
   const int32_t tg = threadIdx.x - (second ? RW : 0);  // index of the thread's Gram block
   T hq = T(0);  // ||W||^2 only feeds the breakdown threshold: the vector precision is enough
   if (!first) c.load_mat(sB, Bprev, cb0 + c.cg0, true);
-  const int64_t rbeg = (int64_t)blockIdx.x * RCHK, rend = min(N, rbeg + RCHK);
-  for (int64_t r0 = rbeg; r0 < rend; r0 += RTL) {
-    const int32_t nr = (int32_t)min((int64_t)RTL, rend - r0);
-    __syncthreads();
-    if (r0 == rbeg || nr < RTL) {
-      c.zero(sQ, RTL);
-      c.zero(sW, RTL);
-      if (REORTH || !first) c.zero(sP, RTL);
-      __syncthreads();
-    }
-    c.template load<RTL>(sQ, Q, r0, nr);
-    c.template load<RTL>(sW, W, r0, nr);
-    if (REORTH || !first) c.template load<RTL>(sP, Qp, r0, nr);
-    c.load_wait();
-    __syncthreads();
-    {  // ||W||^2 of the colour before the update
-      const int32_t t = threadIdx.x;
-      if (t < c.G * CB * CB) {  // first half only (G * CB * CB <= RW)
-        const int32_t g = t / (CB * CB), rem = t - g * CB * CB, bi = rem / CB, bj = rem - bi * CB;
-        if (bi == bj)
-          for (int32_t r = 0; r < RTL; ++r)
+  c.zero(ring.at(0, 0), 6 * RTL);
+  __syncthreads();
+  row_pipeline(
+      N, RTL,
+      [&](int s, int64_t r0, int32_t nr) {
+        c.template load<RTL>(ring.at(s, 0), Q, r0, nr);
+        c.template load<RTL>(ring.at(s, 2), W, r0, nr);
+        if (usep) c.template load<RTL>(ring.at(s, 1), Qp, r0, nr);
+        cp_async_commit();
+      },
+      [&](int s, int64_t r0, int32_t nr) {
+        T* sQ = ring.at(s, 0);
+        T* sP = ring.at(s, 1);
+        T* sW = ring.at(s, 2);
+        const int32_t t = threadIdx.x;
+        if (t < c.G * CB * CB) {  // ||W||^2 of the colour before the update (first half only)
+          const int32_t g = t / (CB * CB), rem = t - g * CB * CB, bi = rem / CB, bj = rem - bi * CB;
+          if (bi == bj)
+            for (int32_t r = 0; r < RTL; ++r)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const T w = sW[r * c.pitch + g * BP + bi * 4 + i];
-              hq = fma(w, w, hq);
-            }
-      }
-    }
-    if (!first) {
-      tile_mul<T, BP, true>(c, sP, sB, sW, RTL);
-      __syncthreads();
-      c.store(W, sW, r0, nr);
-    }
-    tile_gram<T, BP>(c, second ? sP : sQ, sW, RTL, acc, tg);
-  }
+              for (int i = 0; i < 4; ++i) {
+                const T w = sW[r * c.pitch + g * BP + bi * 4 + i];
+                hq = fma(w, w, hq);
+              }
+        }
+        if (!first) {
+          __syncthreads();  // the norm has read W before the update
+          tile_mul<T, BP, true, false>(c, sP, sB, sW, RTL, nullptr, nullptr);
+          __syncthreads();
+          c.store(W, sW, r0, nr);
+        }
+        tile_gram<T, BP>(c, second ? sP : sQ, sW, RTL, acc, tg);
+      });
   const size_t o = (size_t)blockIdx.x * ncb;
   gram_store<T, BP>(c, acc, (second ? partKp : partKq) + o * b * b, tg);
   __syncthreads();
@@ -452,79 +493,66 @@ __global__ void __launch_bounds__(REORTH ? 2 * RW : RW, REORTH ? 1 : 2) k_s1(int
 
 // S3: W1 = W0 - Q_j M1 (- Q_{j-1} M2), stored; partial Gram W1^T W1
 template <typename T, int BP, bool REORTH>
-__global__ void __launch_bounds__(RW, 2) k_s3(int64_t N, int32_t b, int32_t ws, int32_t ncb, const T* __restrict__ Q,
-                                           const T* __restrict__ Qp, T* __restrict__ W, const double* __restrict__ M1,
-                                           const double* __restrict__ M2, double* __restrict__ partG) {
+__global__ void __launch_bounds__(2 * RW, 1)
+    k_s3(int64_t N, int32_t b, int32_t ws, int32_t ncb, const T* __restrict__ Q, const T* __restrict__ Qp,
+         T* __restrict__ W, const double* __restrict__ M1, const double* __restrict__ M2,
+         double* __restrict__ partG) {
   constexpr int RTL = RowTile<T>::RTL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const RowCtx<T, BP> c = make_ctx<T, BP>(b, ws, ncb);
-  const int32_t tile = RTL * c.pitch;
-  T* sQ = reinterpret_cast<T*>(smem_raw);
-  T* sP = sQ + tile;
-  T* sW = sP + tile;
-  T* sM1 = sW + tile;
+  RowRing<T, BP> ring{reinterpret_cast<T*>(smem_raw), RTL * c.pitch, 3};  // Q, Q_{j-1}, W
+  T* sM1 = ring.at(2, 0);
   T* sM2 = sM1 + c.G * BP * BP;
   GramAcc<T> acc;
   c.load_mat(sM1, M1, c.cg0, false);
   if (REORTH) c.load_mat(sM2, M2, c.cg0, false);
-  const int64_t rbeg = (int64_t)blockIdx.x * RCHK, rend = min(N, rbeg + RCHK);
-  for (int64_t r0 = rbeg; r0 < rend; r0 += RTL) {
-    const int32_t nr = (int32_t)min((int64_t)RTL, rend - r0);
-    __syncthreads();
-    if (r0 == rbeg || nr < RTL) {
-      c.zero(sQ, RTL);
-      c.zero(sW, RTL);
-      if (REORTH) c.zero(sP, RTL);
-      __syncthreads();
-    }
-    c.template load<RTL>(sQ, Q, r0, nr);
-    c.template load<RTL>(sW, W, r0, nr);
-    if (REORTH) c.template load<RTL>(sP, Qp, r0, nr);
-    c.load_wait();
-    __syncthreads();
-    tile_mul<T, BP, true>(c, sQ, sM1, sW, RTL);
-    if (REORTH) {
-      __syncthreads();
-      tile_mul<T, BP, true>(c, sP, sM2, sW, RTL);
-    }
-    __syncthreads();
-    c.store(W, sW, r0, nr);
-    tile_gram<T, BP>(c, sW, sW, RTL, acc, threadIdx.x);
-  }
+  c.zero(ring.at(0, 0), 6 * RTL);
+  __syncthreads();
+  row_pipeline(
+      N, RTL,
+      [&](int s, int64_t r0, int32_t nr) {
+        c.template load<RTL>(ring.at(s, 0), Q, r0, nr);
+        c.template load<RTL>(ring.at(s, 2), W, r0, nr);
+        if (REORTH) c.template load<RTL>(ring.at(s, 1), Qp, r0, nr);
+        cp_async_commit();
+      },
+      [&](int s, int64_t r0, int32_t nr) {
+        T* sW = ring.at(s, 2);
+        tile_mul<T, BP, true, REORTH>(c, ring.at(s, 0), sM1, sW, RTL, ring.at(s, 1), sM2);
+        __syncthreads();
+        c.store(W, sW, r0, nr);
+        tile_gram<T, BP>(c, sW, sW, RTL, acc, threadIdx.x);
+      });
   gram_store<T, BP>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b, threadIdx.x);
 }
 
 // OUT = W R^-1 (R^-1 upper triangular per colour); partial Gram of OUT when GRAM.  OUT may be W.
 template <typename T, int BP, bool GRAM>
-__global__ void __launch_bounds__(RW, 2) k_tri(int64_t N, int32_t b, int32_t ws, int32_t ncb, const T* __restrict__ W,
-                                            T* __restrict__ OUT, const double* __restrict__ Rinv,
-                                            double* __restrict__ partG) {
+__global__ void __launch_bounds__(RW, 2)
+    k_tri(int64_t N, int32_t b, int32_t ws, int32_t ncb, const T* __restrict__ W, T* __restrict__ OUT,
+          const double* __restrict__ Rinv, double* __restrict__ partG) {
   constexpr int RTL = RowTile<T>::RTL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const RowCtx<T, BP> c = make_ctx<T, BP>(b, ws, ncb);
-  const int32_t tile = RTL * c.pitch;
-  T* sW = reinterpret_cast<T*>(smem_raw);
-  T* sO = sW + tile;
-  T* sR = sO + tile;
+  RowRing<T, BP> ring{reinterpret_cast<T*>(smem_raw), RTL * c.pitch, 1};  // W
+  T* sO = ring.at(2, 0);
+  T* sR = sO + RTL * c.pitch;
   GramAcc<T> acc;
   c.load_mat(sR, Rinv, c.cg0, false);
-  const int64_t rbeg = (int64_t)blockIdx.x * RCHK, rend = min(N, rbeg + RCHK);
-  for (int64_t r0 = rbeg; r0 < rend; r0 += RTL) {
-    const int32_t nr = (int32_t)min((int64_t)RTL, rend - r0);
-    __syncthreads();
-    if (r0 == rbeg || nr < RTL) {
-      c.zero(sW, RTL);
-      c.zero(sO, RTL);
-      __syncthreads();
-    }
-    c.template load<RTL>(sW, W, r0, nr);
-    c.load_wait();
-    __syncthreads();
-    tile_mul<T, BP, false>(c, sW, sR, sO, RTL);
-    __syncthreads();
-    c.store(OUT, sO, r0, nr);
-    if (GRAM) tile_gram<T, BP>(c, sO, sO, RTL, acc, threadIdx.x);
-  }
+  c.zero(ring.at(0, 0), 3 * RTL);
+  __syncthreads();
+  row_pipeline(
+      N, RTL,
+      [&](int s, int64_t r0, int32_t nr) {
+        c.template load<RTL>(ring.at(s, 0), W, r0, nr);
+        cp_async_commit();
+      },
+      [&](int s, int64_t r0, int32_t nr) {
+        tile_mul<T, BP, false, false>(c, ring.at(s, 0), sR, sO, RTL, nullptr, nullptr);
+        __syncthreads();
+        c.store(OUT, sO, r0, nr);
+        if (GRAM) tile_gram<T, BP>(c, sO, sO, RTL, acc, threadIdx.x);
+      });
   if (GRAM) gram_store<T, BP>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b, threadIdx.x);
 }
 
@@ -758,9 +786,9 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
   constexpr int RTL = RowTile<T>::RTL;
   const size_t tile = (size_t)RTL * (G * BP + 4) * sizeof(T);
   const size_t mat = (size_t)G * BP * BP * sizeof(T);
-  const size_t sm_s1 = 3 * tile + mat + (size_t)G * (BP / 4) * sizeof(double) + 16;
-  const size_t sm_s3 = 3 * tile + 2 * mat;
-  const size_t sm_tri = 2 * tile + mat;
+  const size_t sm_s1 = 6 * tile + mat + (size_t)G * (BP / 4) * sizeof(double) + 16;
+  const size_t sm_s3 = 6 * tile + 2 * mat;
+  const size_t sm_tri = 3 * tile + mat;
   double* partKq = a.part;
   double* partKp = a.part + (size_t)nch * ncb * bb;
   double* partH = a.part + 2 * (size_t)nch * ncb * bb;
@@ -832,7 +860,7 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
     CSS_LAUNCHED(ctx);
     if (j + 1 == m) break;
     // W1 = W0 - Q_j Kq (- Q_{j-1} Kp) and its Gram
-    s3<<<rgrid, RW, sm_s3, st>>>(N, b, a.ws, ncb, Qc, Qp, W, sA, sKp, partKq);
+    s3<<<rgrid, 2 * RW, sm_s3, st>>>(N, b, a.ws, ncb, Qc, Qp, W, sA, sKp, partKq);
     CSS_LAUNCHED(ctx);
     // shifted CholeskyQR3 of W: R0 from G + sI, then two plain CholeskyQR passes
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
