@@ -58,6 +58,8 @@ struct css_ctx {
   // pinned host staging for scalars read back at the end of a call
   void* host_pinned = nullptr;
   size_t host_pinned_bytes = 0;
+  // H * V autotuner: launch variant chosen per (precision, block width, column count, rows)
+  std::vector<std::pair<uint64_t, int>> spmm_tune;
 };
 
 css_status css_set_cuda_error(css_ctx* ctx, cudaError_t e, const char* what, const char* file, int line);

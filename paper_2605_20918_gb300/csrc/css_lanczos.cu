@@ -29,9 +29,9 @@ namespace {
 // thread's own chunk of the b rows of V_J, rows >= b and columns >= w zero-filled) are in
 // flight.  In FP32 mode a last virtual step adds the low FP32 parts of the diagonal block
 // times V_I.
-template <typename T, int BM, int TC>
+template <typename T, int BM, int TC, int NT_>
 struct SpmmCfg {
-  static constexpr int NT = 128;                 // threads
+  static constexpr int NT = NT_;                 // threads
   static constexpr int CT = NT * TC;             // columns per tile
   static constexpr int CH = TC * sizeof(T);      // bytes of a thread's chunk of a row
   static constexpr int HB = BM * BM * (int)sizeof(T);  // bytes of one padded block
@@ -53,12 +53,12 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-template <typename T, int BM, int TC>
-__global__ void __launch_bounds__(128) k_spmm(int32_t b, const int32_t* __restrict__ row_ptr,
+template <typename T, int BM, int TC, int NT>
+__global__ void __launch_bounds__(NT) k_spmm(int32_t b, const int32_t* __restrict__ row_ptr,
                                               const int32_t* __restrict__ col_idx, const T* __restrict__ Ht,
                                               const T* __restrict__ V, T* __restrict__ W, int32_t ws, int32_t w,
                                               const T* __restrict__ Hlo_t) {
-  using C = SpmmCfg<T, BM, TC>;
+  using C = SpmmCfg<T, BM, TC, NT>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int32_t I = blockIdx.x;
   const int32_t t = threadIdx.x;
@@ -746,10 +746,10 @@ css_status smem_optin(css_ctx* ctx, K kern, size_t bytes) {
   return CSS_OK;
 }
 
-template <typename T, int BM, int TC>
+template <typename T, int BM, int TC, int NT>
 css_status launch_spmm_t(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaStream_t st) {
-  using C = SpmmCfg<T, BM, TC>;
-  auto kern = k_spmm<T, BM, TC>;
+  using C = SpmmCfg<T, BM, TC, NT>;
+  auto kern = k_spmm<T, BM, TC, NT>;
   CSS_TRY(smem_optin(ctx, kern, C::smem));
   dim3 grid((unsigned)a.n_brow, (unsigned)css_ceil_div(a.w, C::CT));
   kern<<<grid, C::NT, C::smem, st>>>(a.b, a.row_ptr, a.col_idx, (const T*)a.Hval, V, W, a.ws, a.w,
@@ -758,16 +758,61 @@ css_status launch_spmm_t(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaSt
   return CSS_OK;
 }
 
+// launch variants (columns per thread, threads per CTA); every variant sums each output in the
+// same order, so the choice changes the speed only, never the result
+constexpr int kSpmmVariants = 3;
+
+template <typename T, int BM>
+css_status launch_spmm_bm(css_ctx* ctx, const LzArgs& a, const T* V, T* W, int v, cudaStream_t st) {
+  constexpr int TCW = (sizeof(T) == 4 && BM < 32) ? 4 : (sizeof(T) == 4 || BM < 32) ? 2 : 1;  // widest
+  constexpr int TCN = TCW > 1 ? TCW / 2 : 1;
+  if (v == 0) return launch_spmm_t<T, BM, TCW, 128>(ctx, a, V, W, st);
+  if (v == 1) return launch_spmm_t<T, BM, TCN, 256>(ctx, a, V, W, st);
+  return launch_spmm_t<T, BM, TCN, 128>(ctx, a, V, W, st);
+}
+
+template <typename T>
+css_status launch_spmm_v(css_ctx* ctx, const LzArgs& a, const T* V, T* W, int v, cudaStream_t st) {
+  switch (css_spmm_bm(a.b)) {
+    case 8: return launch_spmm_bm<T, 8>(ctx, a, V, W, v, st);
+    case 12: return launch_spmm_bm<T, 12>(ctx, a, V, W, v, st);
+    case 16: return launch_spmm_bm<T, 16>(ctx, a, V, W, v, st);
+    case 24: return launch_spmm_bm<T, 24>(ctx, a, V, W, v, st);
+    default: return launch_spmm_bm<T, 32>(ctx, a, V, W, v, st);
+  }
+}
+
+// W = H V with the variant tuned for this shape: the first time a shape is seen, every variant
+// is timed once on the call's own data (each writes the same W) and the fastest is kept
 template <typename T>
 css_status launch_spmm(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaStream_t st) {
-  constexpr bool F32 = sizeof(T) == 4;
-  switch (css_spmm_bm(a.b)) {
-    case 8: return launch_spmm_t<T, 8, F32 ? 4 : 2>(ctx, a, V, W, st);
-    case 12: return launch_spmm_t<T, 12, F32 ? 4 : 2>(ctx, a, V, W, st);
-    case 16: return launch_spmm_t<T, 16, F32 ? 4 : 2>(ctx, a, V, W, st);
-    case 24: return launch_spmm_t<T, 24, F32 ? 4 : 2>(ctx, a, V, W, st);
-    default: return launch_spmm_t<T, 32, F32 ? 2 : 1>(ctx, a, V, W, st);
+  const uint64_t key = ((uint64_t)sizeof(T) << 60) ^ ((uint64_t)a.b << 48) ^ ((uint64_t)a.w << 24) ^
+                       (uint64_t)(a.n_brow >= (1 << 24) ? (1 << 24) - 1 : a.n_brow);
+  for (const auto& kv : ctx->spmm_tune)
+    if (kv.first == key) return launch_spmm_v<T>(ctx, a, V, W, kv.second, st);
+  cudaEvent_t ev[kSpmmVariants + 1];
+  for (auto& e : ev) CSS_CU(ctx, cudaEventCreate(&e));
+  css_status rc = CSS_OK;
+  CSS_CU(ctx, cudaEventRecord(ev[0], st));
+  for (int v = 0; v < kSpmmVariants && rc == CSS_OK; ++v) {
+    rc = launch_spmm_v<T>(ctx, a, V, W, v, st);
+    if (rc == CSS_OK) rc = cudaEventRecord(ev[v + 1], st) == cudaSuccess ? CSS_OK : CSS_ERR_CUDA;
   }
+  int best = 0;
+  if (rc == CSS_OK && cudaEventSynchronize(ev[kSpmmVariants]) == cudaSuccess) {
+    float tbest = 0.0f;
+    for (int v = 0; v < kSpmmVariants; ++v) {
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, ev[v], ev[v + 1]);
+      if (v == 0 || ms < tbest) {
+        tbest = ms;
+        best = v;
+      }
+    }
+    ctx->spmm_tune.emplace_back(key, best);
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return rc;
 }
 
 template <typename T, int BP>
