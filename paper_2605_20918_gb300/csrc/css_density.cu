@@ -555,6 +555,12 @@ __global__ void k_count_breakdown(int32_t n_col, int32_t m, const int32_t* __res
   if (c < n_col && cnt[c] > 0 && nblk[c] < m) atomicAdd(out, 1);
 }
 
+// OR of the eigen stage's per-colour status words (bit 2: a band-reduction wait gave up)
+__global__ void k_status_or(int32_t n_col, const int32_t* __restrict__ status, int32_t* __restrict__ out) {
+  int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n_col && (status[c] & 2)) atomicOr(out, 2);
+}
+
 template <typename Tp>
 css_status ws_get(css_ctx* ctx, const char* name, size_t count, Tp** p) {
   return css_ws(ctx, name, count * sizeof(Tp), (void**)p);
@@ -991,6 +997,8 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   }
   k_count_breakdown<<<(unsigned)css_ceil_div(n_col, T), T, 0, st>>>(n_col, m, nblk, cnt, misc + 16);
   CSS_LAUNCHED(ctx);
+  k_status_or<<<(unsigned)css_ceil_div(n_col, T), T, 0, st>>>(n_col, ea.status, misc + 17);
+  CSS_LAUNCHED(ctx);
   tm.mark();  // 6
   // ------------------------------------------------------------ read back
   double* hres;
@@ -1039,6 +1047,10 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   }
   if (mu_err) {
     ctx->last_error = "css_density: grid barrier of the mu bisection timed out";
+    return CSS_ERR_TIMEOUT;
+  }
+  if (hmisc[9] & 2) {
+    ctx->last_error = "css_density: a wait between pipelined band-reduction sweeps timed out";
     return CSS_ERR_TIMEOUT;
   }
   if (!finite) {

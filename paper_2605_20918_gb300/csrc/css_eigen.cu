@@ -4,14 +4,16 @@
 //
 // GB300 runs FP64 at about 1/64 of the FP32 rate and a dependent FP64 sqrt + divide costs
 // ~0.6 us, so no stage here is a long sequential FP64 chain:
-//   1. band -> tridiagonal by Householder bulge chasing (reflectors of length <= b; a sweep's
-//      reflectors touch disjoint rows, so their action on b-column blocks is applied sweep by
-//      sweep with all of a sweep's reflectors in parallel);
+//   1. band -> tridiagonal by Householder bulge chasing, up to 32 sweeps in flight (one warp
+//      each, a sweep waits only for the one before it to move past its window); reflectors
+//      of length <= b, and a sweep's reflectors touch disjoint rows, so their action on
+//      b-column blocks is applied sweep by sweep with all of a sweep's reflectors in parallel;
 //   2. eigenvalues of the tridiagonal by Sturm-count bisection in FP32 (one thread per
 //      eigenvalue), used only as shifts;
-//   3. FP64 Rayleigh-quotient inverse iteration per eigenvalue (one thread per cluster of
-//      close shifts, Gram-Schmidt inside the cluster and a Rayleigh-Ritz step on it), which
-//      gives eigenvalues and eigenvectors to FP64 accuracy;
+//   3. FP64 Rayleigh-quotient inverse iteration: one thread per eigenvalue in lockstep, then
+//      one warp per cluster of close shifts (simultaneous iteration with Gram-Schmidt and a
+//      Rayleigh-Ritz step inside the cluster), which gives eigenvalues and eigenvectors to
+//      FP64 accuracy;
 //   4. Y = U^T (Q_band^T E_1 B_0), weights w = ||Y_k||^2, and after mu is known
 //      Z = Q_band U f(Lambda) Y.
 #include "css_eigen.cuh"
@@ -74,38 +76,62 @@ __device__ void warp_house(double x, int32_t L, double* sv, double* stau, double
   }
 }
 
-// D <- H D H on the symmetric L x L diagonal block starting at r0 (H = I - tau v v^T).
-// 1024 threads: warp p owns row p, lane q owns column q.
-__device__ void two_sided(const Band& A, int32_t r0, int32_t L, const double* v, double tau, double* sp,
-                          double* salpha) {
-  const int32_t p = threadIdx.x >> 5, q = threadIdx.x & 31;
+// D <- H D H on the symmetric L x L diagonal block starting at r0 (H = I - tau v v^T), by one
+// warp: lane i owns row i.  pw is the warp's scratch of 32 doubles.
+__device__ void two_sided_w(const Band& A, int32_t r0, int32_t L, const double* v, double tau, double* pw) {
+  const int lane = threadIdx.x & 31;
   if (tau == 0.0) return;
-  double prod = 0.0;
-  if (p < L && q < L) prod = (p >= q ? A.at(r0 + p, r0 + q) : A.at(r0 + q, r0 + p)) * v[q];
-  prod = warp_sum(prod);
-  if (q == 0 && p < 32) sp[p] = (p < L) ? tau * prod : 0.0;
-  __syncthreads();
-  if (p == 0) {
-    double t = warp_sum(q < L ? sp[q] * v[q] : 0.0);
-    if (q == 0) *salpha = -0.5 * tau * t;
-  }
-  __syncthreads();
-  const double alpha = *salpha;
-  if (p < L && q <= p) {
-    double wp = sp[p] + alpha * v[p], wq = sp[q] + alpha * v[q];
-    A.at(r0 + p, r0 + q) -= v[p] * wq + wp * v[q];
-  }
-  __syncthreads();
+  double acc = 0.0;
+  if (lane < L)
+    for (int32_t j = 0; j < L; ++j)
+      acc += (lane >= j ? A.at(r0 + lane, r0 + j) : A.at(r0 + j, r0 + lane)) * v[j];
+  const double vi = lane < L ? v[lane] : 0.0;
+  const double pi = lane < L ? tau * acc : 0.0;
+  const double alpha = -0.5 * tau * warp_sum(pi * vi);
+  const double wi = pi + alpha * vi;
+  pw[lane] = wi;
+  __syncwarp();
+  if (lane < L)
+    for (int32_t j = 0; j <= lane; ++j) A.at(r0 + lane, r0 + j) -= vi * pw[j] + wi * v[j];
+  __syncwarp();
 }
 
-// Band -> tridiagonal (one CTA of 1024 threads per colour), reflectors recorded in order
+// reflectors recorded by sweep i (the type-1 reflector and one per chase step whose block has
+// at least two rows), the same count the sequential order produces
+__device__ int32_t sweep_refl_count(int32_t i, int32_t n, int32_t kd) {
+  int32_t cnt = 1, p0 = i + 1, Lp = min(kd, n - 1 - i);
+  for (;;) {
+    const int32_t q0 = p0 + Lp;
+    if (q0 > n - 1) break;
+    const int32_t Lq = min(kd, n - q0);
+    if (Lq < 2) break;
+    ++cnt;
+    p0 = q0;
+    Lp = Lq;
+  }
+  return cnt;
+}
+
+// Band -> tridiagonal (one CTA of 32 warps per colour) with the sweeps pipelined: warp w runs
+// sweeps w, w + 32, ...  Every step of a sweep touches the rows and columns of one window
+// [lo, hi) of the matrix, and the windows of a sweep move down the band.  Sweep s runs a step
+// only once sweep s - 1 has finished or its next step's window starts at or after the step's
+// hi: then no later step of s - 1 touches what the step reads or writes, and (by induction)
+// neither does any earlier sweep, so the result is the sequential order's.  Each warp
+// publishes (sweep, start of its next window) in one 64-bit shared word.  Reflector k of
+// sweep i is stored at sweep_off[i] + k, as in the sequential order.  A wait gives up after
+// 2^24 polls: the colour's status gets bit 2 and the CTA stops.
 __global__ void __launch_bounds__(1024) k_band_to_tri(int32_t kd, int32_t nmax, int32_t ldb, int32_t rcap,
                                                       const int32_t* __restrict__ nblk, double* __restrict__ AB,
                                                       double* __restrict__ RV, double* __restrict__ RT,
                                                       int32_t* __restrict__ RR0, int32_t* __restrict__ sweep_off,
-                                                      double* __restrict__ dd, double* __restrict__ ee) {
-  __shared__ double sv[32], sv2[32], sy[32], sp[32];
-  __shared__ double stau, stau2, sbeta, salpha;
+                                                      double* __restrict__ dd, double* __restrict__ ee,
+                                                      int32_t* __restrict__ status) {
+  constexpr int NW = 32;
+  __shared__ double sv[NW][32], svn[NW][32], spw[NW][32];
+  __shared__ double stau[NW], sbeta[NW];
+  __shared__ unsigned long long slot[NW];  // ((sweep + 1) << 32) | start of the next window
+  __shared__ int abort_flag;
   const int32_t c = blockIdx.x;
   const int32_t n = nblk[c] * kd;
   Band A{AB + (size_t)c * nmax * ldb, ldb};
@@ -113,79 +139,140 @@ __global__ void __launch_bounds__(1024) k_band_to_tri(int32_t kd, int32_t nmax, 
   double* rt = RT + (size_t)c * rcap;
   int32_t* rr = RR0 + (size_t)c * rcap;
   int32_t* so = sweep_off + (size_t)c * (nmax + 1);
-  const int32_t p = threadIdx.x >> 5, q = threadIdx.x & 31;
-  int32_t cnt = 0;
-  auto record = [&](int32_t r0, const double* v, double tau) {
-    if (threadIdx.x < kd) rv[(size_t)cnt * kd + threadIdx.x] = v[threadIdx.x];
-    if (threadIdx.x == 0) {
-      rt[cnt] = tau;
-      rr[cnt] = r0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int32_t nsweep = n > 2 ? n - 2 : 0;
+  // reflector offsets of the sweeps
+  for (int32_t i = threadIdx.x; i < nsweep; i += blockDim.x) so[i + 1] = sweep_refl_count(i, n, kd);
+  if (threadIdx.x < NW) slot[threadIdx.x] = 0ull;
+  if (threadIdx.x == 0) abort_flag = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    so[0] = 0;
+    for (int32_t i = 0; i < nsweep; ++i) so[i + 1] += so[i];
+    for (int32_t i = nsweep + 1; i <= n; ++i) so[i] = so[nsweep];
+  }
+  __syncthreads();
+  double* v = sv[w];
+  double* vn = svn[w];
+  double* pw = spw[w];
+  auto publish = [&](int32_t s, int32_t front) {
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      *(volatile unsigned long long*)&slot[w] =
+          ((unsigned long long)(uint32_t)(s + 1) << 32) | (unsigned long long)(uint32_t)front;
     }
-    ++cnt;
   };
-  for (int32_t i = 0; i + 2 < n; ++i) {
-    if (threadIdx.x == 0) so[i] = cnt;
+  // wait until sweep s - 1 cannot touch [.., hi) any more; false on timeout or abort
+  auto wait_prev = [&](int32_t s, int32_t hi) -> bool {
+    bool ok = true;
+    if (s > 0 && lane == 0) {
+      const int pw_ = (s - 1) % NW;
+      for (uint32_t it = 0;; ++it) {
+        const unsigned long long x = *(volatile unsigned long long*)&slot[pw_];
+        const int32_t id = (int32_t)(x >> 32) - 1;
+        const int32_t front = (int32_t)(uint32_t)(x & 0xffffffffull);
+        if (id > s - 1 || (id == s - 1 && front >= hi)) break;
+        if (*(volatile int*)&abort_flag) {
+          ok = false;
+          break;
+        }
+        if (it >= (1u << 24)) {
+          atomicOr(&status[c], 2);
+          *(volatile int*)&abort_flag = 1;
+          ok = false;
+          break;
+        }
+        __nanosleep(32);
+      }
+      __threadfence_block();
+    }
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    __syncwarp();
+    return ok;
+  };
+  auto record = [&](int32_t k, int32_t r0, const double* vv, double tau) {
+    if (lane < kd) rv[(size_t)k * kd + lane] = vv[lane];
+    if (lane == 0) {
+      rt[k] = tau;
+      rr[k] = r0;
+    }
+  };
+  constexpr int32_t kDone = 0x7fffffff;
+  bool dead = false;  // a wait gave up: leave the loops, still reach the final barrier
+  for (int32_t i = w; i < nsweep && !dead; i += NW) {
     const int32_t r0 = i + 1;
     const int32_t L = min(kd, n - 1 - i);
-    // type 1: annihilate column i below the sub-diagonal
-    if (p == 0) {
-      double x = (q < L) ? A.at(r0 + q, i) : 0.0;
-      warp_house(x, L, sv, &stau, &sbeta);
+    int32_t k = so[i];
+    publish(i, i);  // first window starts at column i
+    // type 1: annihilate column i below the sub-diagonal; window [i, r0 + L)
+    if (!wait_prev(i, r0 + L)) {
+      dead = true;
+      break;
     }
-    __syncthreads();
-    if (threadIdx.x < L) A.at(r0 + threadIdx.x, i) = (threadIdx.x == 0) ? sbeta : 0.0;
-    __syncthreads();
-    two_sided(A, r0, L, sv, stau, sp, &salpha);
-    record(r0, sv, stau);
+    {
+      const double x = (lane < L) ? A.at(r0 + lane, i) : 0.0;
+      warp_house(x, L, v, &stau[w], &sbeta[w]);
+      __syncwarp();
+      if (lane < L) A.at(r0 + lane, i) = (lane == 0) ? sbeta[w] : 0.0;
+      __syncwarp();
+      two_sided_w(A, r0, L, v, stau[w], pw);
+      record(k++, r0, v, stau[w]);
+    }
     int32_t p0 = r0, Lp = L;
-    double* v = sv;
-    double* vn = sv2;
-    double tau = stau;
+    double* cv = v;
+    double* nv = vn;
+    double tau = stau[w];
     for (;;) {
       const int32_t q0 = p0 + Lp;
       if (q0 > n - 1) break;
       const int32_t Lq = min(kd, n - q0);
-      // type 2a: B = A[q0.., p0..] <- B (I - tau v v^T)
-      if (tau != 0.0) {
-        double prod = (p < Lq && q < Lp) ? A.at(q0 + p, p0 + q) * v[q] : 0.0;
-        prod = warp_sum(prod);
-        if (q == 0) sy[p] = prod;
-        __syncthreads();
-        if (p < Lq && q < Lp) A.at(q0 + p, p0 + q) -= tau * sy[p] * v[q];
-        __syncthreads();
+      publish(i, p0);  // this chase step's window is [p0, q0 + Lq)
+      if (!wait_prev(i, q0 + Lq)) {
+        dead = true;
+        break;
       }
+      // type 2a: B = A[q0.., p0..] <- B (I - tau v v^T), lane = row of B
+      if (tau != 0.0 && lane < Lq) {
+        double y = 0.0;
+        for (int32_t j = 0; j < Lp; ++j) y += A.at(q0 + lane, p0 + j) * cv[j];
+        for (int32_t j = 0; j < Lp; ++j) A.at(q0 + lane, p0 + j) -= tau * y * cv[j];
+      }
+      __syncwarp();
       if (Lq < 2) break;
       // type 2b: new reflector from the bulge's first column, applied from the left
-      if (p == 0) {
-        double x = (q < Lq) ? A.at(q0 + q, p0) : 0.0;
-        warp_house(x, Lq, vn, &stau2, &sbeta);
+      {
+        const double x = (lane < Lq) ? A.at(q0 + lane, p0) : 0.0;
+        warp_house(x, Lq, nv, &stau[w], &sbeta[w]);
       }
-      __syncthreads();
-      const double tau2 = stau2;
+      __syncwarp();
+      const double tau2 = stau[w];
       if (tau2 != 0.0) {
-        // z[col] = v^T B[:, col] for col >= 1: warp col, lane row
-        double prod = (p >= 1 && p < Lp && q < Lq) ? vn[q] * A.at(q0 + q, p0 + p) : 0.0;
-        prod = warp_sum(prod);
-        if (q == 0) sy[p] = prod;
-        __syncthreads();
-        if (q >= 1 && q < Lp && p < Lq) A.at(q0 + p, p0 + q) -= tau2 * vn[p] * sy[q];
+        double z = 0.0;  // z[col] = nv^T B[:, col], lane = col >= 1
+        if (lane >= 1 && lane < Lp)
+          for (int32_t r = 0; r < Lq; ++r) z += nv[r] * A.at(q0 + r, p0 + lane);
+        pw[lane] = z;
+        __syncwarp();
+        if (lane < Lq)
+          for (int32_t j = 1; j < Lp; ++j) A.at(q0 + lane, p0 + j) -= tau2 * nv[lane] * pw[j];
+        __syncwarp();
       }
-      if (threadIdx.x < Lq) A.at(q0 + threadIdx.x, p0) = (threadIdx.x == 0) ? sbeta : 0.0;
-      __syncthreads();
+      if (lane < Lq) A.at(q0 + lane, p0) = (lane == 0) ? sbeta[w] : 0.0;
+      __syncwarp();
       // type 3: two-sided on the next diagonal block
-      two_sided(A, q0, Lq, vn, tau2, sp, &salpha);
-      record(q0, vn, tau2);
-      double* t = v;
-      v = vn;
-      vn = t;
+      two_sided_w(A, q0, Lq, nv, tau2, pw);
+      record(k++, q0, nv, tau2);
+      double* t = cv;
+      cv = nv;
+      nv = t;
       tau = tau2;
       p0 = q0;
       Lp = Lq;
     }
-    __syncthreads();
+    if (!dead) publish(i, kDone);
   }
-  for (int32_t i = max(0, n - 2); i <= n; ++i)
-    if (threadIdx.x == 0) so[i] = cnt;
+  __syncthreads();
+  if (abort_flag) return;
   for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
     dd[(size_t)c * nmax + i] = A.at(i, i);
     ee[(size_t)c * nmax + i] = (i + 1 < n) ? A.at(i + 1, i) : 0.0;
@@ -880,7 +967,9 @@ css_status css_eigen_ritz(css_ctx* ctx, const EigArgs& a, cudaStream_t st) {
   const int32_t nc = a.n_col, b = a.b, nmax = a.m * b, ldb = 2 * b + 1;
   k_band_build<<<nc, 256, 0, st>>>(b, a.m, nmax, ldb, a.Ablk, a.Bblk, a.nblk, a.AB);
   CSS_LAUNCHED(ctx);
-  k_band_to_tri<<<nc, 1024, 0, st>>>(b, nmax, ldb, a.rcap, a.nblk, a.AB, a.RV, a.RT, a.RR0, a.sweep_off, a.d, a.e);
+  CSS_CU(ctx, cudaMemsetAsync(a.status, 0, sizeof(int32_t) * nc, st));
+  k_band_to_tri<<<nc, 1024, 0, st>>>(b, nmax, ldb, a.rcap, a.nblk, a.AB, a.RV, a.RT, a.RR0, a.sweep_off, a.d, a.e,
+                                     a.status);
   CSS_LAUNCHED(ctx);
   k_x0<<<nc, 256, 0, st>>>(b, nmax, a.cnt, a.X0);
   CSS_LAUNCHED(ctx);
@@ -893,7 +982,6 @@ css_status css_eigen_ritz(css_ctx* ctx, const EigArgs& a, cudaStream_t st) {
   k_inviter_p1<<<dim3((unsigned)css_ceil_div(nmax, 128), (unsigned)nc), 128, 0, st>>>(
       b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm, 1e-4, a.U, a.F, a.lam, a.flag);
   CSS_LAUNCHED(ctx);
-  CSS_CU(ctx, cudaMemsetAsync(a.status, 0, sizeof(int32_t) * nc, st));
   k_inviter_cl<<<dim3((unsigned)nc, 4), 256, 0, st>>>(b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm, 1e-4, a.U, a.F, a.lam, a.status,
                                    a.flag);
   CSS_LAUNCHED(ctx);
