@@ -307,8 +307,15 @@ def main():
         torch.cuda.synchronize()
         t64 = time.perf_counter() - t0
         dP = float((P64 - P[t]).abs().max().item())
+        # FP64 at the mixed run's mu: the error of the mixed arithmetic alone, without the
+        # change of mu (any mu in the gap satisfies the electron count)
+        r64f = ctx.density(Hd, colour, sign, nc, P64, kT=0.05, n_elec=ne, m=a.m, precision=css.CSS_FP64,
+                           mu=last_r["mu"], solve_mu=False)
+        dPf = float((P64 - P[t]).abs().max().item())
         line["fp64_compare"] = {"fp64_s_per_pbuild": t64, "mixed_s_per_pbuild": value,
                                 "speedup_mixed_vs_fp64": t64 / value, "max_abs_dP": dP,
+                                "max_abs_dP_same_mu": dPf,
+                                "dE_band_eV_per_molecule_same_mu": abs(2 * (last_r["trPH"] - r64f["trPH"])) / a.n_mol,
                                 "dE_band_eV_per_molecule": abs(2 * (last_r["trPH"] - r64["trPH"])) / a.n_mol,
                                 "dTrP": last_r["trP"] - r64["trP"], "mu_fp64": r64["mu"],
                                 "note": "mixed P of the last timed geometry against the FP64 path on the same geometry"}

@@ -179,8 +179,18 @@ __global__ void k_hpad(int64_t nblocks, int32_t b, int32_t BM, const double* __r
 // are taken in the vector precision; FP32 tiles are added into an unevaluated hi + lo pair
 // of floats (error-free TwoSum, so the running sum carries about 44 bits), FP64 tiles into
 // doubles.  The pair is widened to FP64 once per CTA: no FP64 arithmetic in the row loop.
-constexpr int RW = 256;      // threads
+constexpr int RW = 256;      // threads of a Gram half (see the launch sizes below)
 constexpr int RCHK = 1024;   // rows per CTA
+
+// colours of a staged tile sit CS = BP + 4 values apart: for BP = 24 the seven colours of a
+// group start in seven different shared-memory banks
+template <int BP>
+struct ColStride {
+  static constexpr int CS = BP + 4;
+  // per-colour small matrices [G][BP][BP] sit MS = BP*BP + BP values apart: MS = BP (mod 32), so
+  // the 16-byte loads of a quarter warp that spans two colours fall in distinct banks
+  static constexpr int MS = BP * BP + BP;
+};
 
 template <typename T>
 struct RowTile {
@@ -192,15 +202,26 @@ __host__ __device__ constexpr int group_cap() {
   return RW / ((BP / 4) * (BP / 4));
 }
 
-// colours per CTA for block width b (runtime) padded to BP
+// colours per CTA for block width b (runtime) padded to BP: at most group_cap (one Gram thread
+// per 4 x 4 block), at most 192 contiguous columns per row, and small enough that two stages of
+// three tiles plus two matrices fit in 216 KB of shared memory (rows x value size is 128 bytes
+// for both precisions; matrices counted at 8 bytes a value)
 template <int BP>
 __host__ __device__ inline int colours_per_cta(int b) {
   int g = group_cap<BP>();
-  int lim = 192 / b;                    // contiguous columns per row <= 192
-  if (lim > 192 / BP) lim = 192 / BP;   // padded tile width <= 192: two stages of three tiles
-                                        // and two matrices stay below 180 KB of shared memory
-  if (lim < 1) lim = 1;
-  return g < lim ? g : lim;
+  if (g > 192 / b) g = 192 / b;
+  while (g > 1 && 6 * 128 * (g * (BP + 4) + 4) + 2 * g * (BP * BP + BP) * 8 > 216 * 1024) --g;
+  return g < 1 ? 1 : g;
+}
+
+// threads of a row-kernel launch: one per 4 x 4 output block of a tile (every block in one
+// round), at least one per Gram block, rounded up to whole warps
+template <typename T, int BP>
+__host__ __device__ inline int row_threads(int b) {
+  const int G = colours_per_cta<BP>(b);
+  const int items = (RowTile<T>::RTL / 4) * G * (BP / 4), gram = G * (BP / 4) * (BP / 4);
+  const int t = items > gram ? items : gram;
+  return (t + 31) / 32 * 32;
 }
 
 template <typename T, int BP>
@@ -231,8 +252,9 @@ struct RowCtx {
   }
   // small per-colour matrices [G][BP][BP] from global FP64 [colour][b][b] (optionally transposed)
   __device__ __forceinline__ void load_mat(T* dst, const double* src, int32_t colour0, bool trans) const {
-    for (int32_t e = threadIdx.x; e < G * BP * BP; e += blockDim.x) {
-      const int32_t g = e / (BP * BP), rem = e - g * BP * BP, l = rem / BP, k = rem - l * BP;
+    constexpr int MS = ColStride<BP>::MS;
+    for (int32_t e = threadIdx.x; e < G * MS; e += blockDim.x) {
+      const int32_t g = e / MS, rem = e - g * MS, l = rem / BP, k = rem - l * BP;
       T v = T(0);
       if (g < gcount && l < b && k < b)
         v = (T)src[(size_t)(colour0 + g) * b * b + (trans ? k * b + l : l * b + k)];
@@ -246,18 +268,19 @@ struct RowCtx {
 template <typename T, int BP, bool SUB, bool TWO>
 __device__ __forceinline__ void tile_mul(const RowCtx<T, BP>& c, const T* X, const T* M, T* OUT, int32_t rtl,
                                          const T* X2, const T* M2) {
+  constexpr int CS = ColStride<BP>::CS;
   constexpr int CB = BP / 4;
   const int32_t nblk = (rtl / 4) * c.G * CB;
   for (int32_t t = threadIdx.x; t < nblk; t += blockDim.x) {
     const int32_t rb = t / (c.G * CB), rem = t - rb * c.G * CB, g = rem / CB, cb = rem - g * CB;
-    const int32_t r0 = rb * 4, col = g * BP + cb * 4;
+    const int32_t r0 = rb * 4, col = g * CS + cb * 4;
     T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = SUB ? OUT[(r0 + i) * c.pitch + col + j] : T(0);
-    const T* xm = X + g * BP;
-    const T* mm = M + (size_t)g * BP * BP + cb * 4;
+    const T* xm = X + g * CS;
+    const T* mm = M + (size_t)g * ColStride<BP>::MS + cb * 4;
     for (int32_t l = 0; l < c.b; ++l) {
       T x[4], m[4];
 #pragma unroll
@@ -270,8 +293,8 @@ __device__ __forceinline__ void tile_mul(const RowCtx<T, BP>& c, const T* X, con
         for (int j = 0; j < 4; ++j) acc[i][j] = SUB ? fma(-x[i], m[j], acc[i][j]) : fma(x[i], m[j], acc[i][j]);
     }
     if (TWO) {
-      const T* xm2 = X2 + g * BP;
-      const T* mm2 = M2 + (size_t)g * BP * BP + cb * 4;
+      const T* xm2 = X2 + g * CS;
+      const T* mm2 = M2 + (size_t)g * ColStride<BP>::MS + cb * 4;
       for (int32_t l = 0; l < c.b; ++l) {
         T x[4], m[4];
 #pragma unroll
@@ -324,11 +347,12 @@ struct GramAcc<float> {
 template <typename T, int BP>
 __device__ __forceinline__ void tile_gram(const RowCtx<T, BP>& c, const T* X, const T* Y, int32_t rtl,
                                           GramAcc<T>& acc, int32_t t) {
+  constexpr int CS = ColStride<BP>::CS;
   constexpr int CB = BP / 4;
   if (t >= c.G * CB * CB) return;
   const int32_t g = t / (CB * CB), rem = t - g * CB * CB, bi = rem / CB, bj = rem - bi * CB;
-  const T* xp = X + g * BP + bi * 4;
-  const T* yp = Y + g * BP + bj * 4;
+  const T* xp = X + g * CS + bi * 4;
+  const T* yp = Y + g * CS + bj * 4;
   T a[4][4] = {};
   for (int32_t r = 0; r < rtl; ++r) {
     T x[4], y[4];
@@ -367,17 +391,18 @@ __device__ __forceinline__ void gram_store(const RowCtx<T, BP>& c, const GramAcc
 
 template <typename T, int BP>
 __device__ __forceinline__ RowCtx<T, BP> make_ctx(int32_t b, int32_t ws, int32_t ncb) {
+  constexpr int CS = ColStride<BP>::CS;
   RowCtx<T, BP> c;
   c.b = b;
   c.ws = ws;
   c.G = colours_per_cta<BP>(b);
   c.cg0 = blockIdx.y * c.G;
   c.gcount = min(c.G, ncb - c.cg0);
-  c.pitch = c.G * BP + 4;
+  c.pitch = c.G * CS + 4;
   const int32_t t = threadIdx.x;
   if (t < c.gcount * b) {
     c.my_col = t;
-    c.my_smem = (t / b) * BP + (t % b);
+    c.my_smem = (t / b) * CS + (t % b);
   } else {
     c.my_col = -1;
     c.my_smem = 0;
@@ -422,25 +447,22 @@ __device__ __forceinline__ void row_pipeline(int64_t N, int32_t rtl, Issue fn_is
 }
 
 // S1: W = H Q_j arrives in W.  W0 = W - Q_{j-1} B_{j-1}^T (skipped at the first step), stored;
-// partials Kq = Q_j^T W0, Kp = Q_{j-1}^T W0 (REORTH), and ||W||^2 per colour (breakdown test).
+// partials Kq = Q_j^T W0 and Kp = Q_{j-1}^T W0 (REORTH).
 // With REORTH the CTA has 2*RW threads: the first RW accumulate Kq, the second RW Kp.
 template <typename T, int BP, bool REORTH>
 __global__ void __launch_bounds__(REORTH ? 2 * RW : RW, 1)
     k_s1(int64_t N, int32_t b, int32_t ws, int32_t ncb, int32_t cb0, const T* __restrict__ Qp,
          const T* __restrict__ Q, T* __restrict__ W, const double* __restrict__ Bprev, int first,
-         double* __restrict__ partKq, double* __restrict__ partKp, double* __restrict__ partH) {
+         double* __restrict__ partKq, double* __restrict__ partKp) {
   constexpr int RTL = RowTile<T>::RTL;
-  constexpr int CB = BP / 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const RowCtx<T, BP> c = make_ctx<T, BP>(b, ws, ncb);
   const bool usep = REORTH || !first;
   RowRing<T, BP> ring{reinterpret_cast<T*>(smem_raw), RTL * c.pitch, 3};  // Q, Q_{j-1}, W
   T* sB = ring.at(2, 0);                                                    // [G][BP][BP] B_{j-1}^T
-  double* hsum = reinterpret_cast<double*>(sB + c.G * BP * BP);             // [G][CB]
   GramAcc<T> acc;                                   // Kq (first RW threads) or Kp (second RW)
   const bool second = REORTH && threadIdx.x >= RW;
   const int32_t tg = threadIdx.x - (second ? RW : 0);  // index of the thread's Gram block
-  T hq = T(0);  // ||W||^2 only feeds the breakdown threshold: the vector precision is enough
   if (!first) c.load_mat(sB, Bprev, cb0 + c.cg0, true);
   c.zero(ring.at(0, 0), 6 * RTL);
   __syncthreads();
@@ -456,19 +478,7 @@ __global__ void __launch_bounds__(REORTH ? 2 * RW : RW, 1)
         T* sQ = ring.at(s, 0);
         T* sP = ring.at(s, 1);
         T* sW = ring.at(s, 2);
-        const int32_t t = threadIdx.x;
-        if (t < c.G * CB * CB) {  // ||W||^2 of the colour before the update (first half only)
-          const int32_t g = t / (CB * CB), rem = t - g * CB * CB, bi = rem / CB, bj = rem - bi * CB;
-          if (bi == bj)
-            for (int32_t r = 0; r < RTL; ++r)
-#pragma unroll
-              for (int i = 0; i < 4; ++i) {
-                const T w = sW[r * c.pitch + g * BP + bi * 4 + i];
-                hq = fma(w, w, hq);
-              }
-        }
         if (!first) {
-          __syncthreads();  // the norm has read W before the update
           tile_mul<T, BP, true, false>(c, sP, sB, sW, RTL, nullptr, nullptr);
           __syncthreads();
           c.store(W, sW, r0, nr);
@@ -477,18 +487,6 @@ __global__ void __launch_bounds__(REORTH ? 2 * RW : RW, 1)
       });
   const size_t o = (size_t)blockIdx.x * ncb;
   gram_store<T, BP>(c, acc, (second ? partKp : partKq) + o * b * b, tg);
-  __syncthreads();
-  const int32_t t = threadIdx.x;
-  if (t < c.G * CB * CB) {
-    const int32_t g = t / (CB * CB), rem = t - g * CB * CB, bi = rem / CB, bj = rem - bi * CB;
-    if (bi == bj) hsum[g * CB + bi] = (double)hq;
-  }
-  __syncthreads();
-  if (t < c.gcount) {
-    double sum = 0.0;
-    for (int i = 0; i < CB; ++i) sum += hsum[t * CB + i];
-    partH[o + c.cg0 + t] = sum;
-  }
 }
 
 // S3: W1 = W0 - Q_j M1 (- Q_{j-1} M2), stored; partial Gram W1^T W1
@@ -502,7 +500,7 @@ __global__ void __launch_bounds__(2 * RW, 1)
   const RowCtx<T, BP> c = make_ctx<T, BP>(b, ws, ncb);
   RowRing<T, BP> ring{reinterpret_cast<T*>(smem_raw), RTL * c.pitch, 3};  // Q, Q_{j-1}, W
   T* sM1 = ring.at(2, 0);
-  T* sM2 = sM1 + c.G * BP * BP;
+  T* sM2 = sM1 + c.G * ColStride<BP>::MS;
   GramAcc<T> acc;
   c.load_mat(sM1, M1, c.cg0, false);
   if (REORTH) c.load_mat(sM2, M2, c.cg0, false);
@@ -528,7 +526,7 @@ __global__ void __launch_bounds__(2 * RW, 1)
 
 // OUT = W R^-1 (R^-1 upper triangular per colour); partial Gram of OUT when GRAM.  OUT may be W.
 template <typename T, int BP, bool GRAM>
-__global__ void __launch_bounds__(RW, 2)
+__global__ void __launch_bounds__(384, 2)
     k_tri(int64_t N, int32_t b, int32_t ws, int32_t ncb, const T* __restrict__ W, T* __restrict__ OUT,
           const double* __restrict__ Rinv, double* __restrict__ partG) {
   constexpr int RTL = RowTile<T>::RTL;
@@ -589,6 +587,27 @@ __global__ void k_store_A(int32_t ncb, int32_t b, int32_t cb0, int32_t m, int32_
 //           min_k B_kk <= tau ||H Q_j||_F (same rule as a Householder QR's R_kk)
 // A colour already finished, or a failed factorisation, gives R = I and R^-1 = 0, so the
 // colour's next block is zero.
+// ||H Q_j||_F^2 per colour for the breakdown test.  H Q_j = Q_{j-1} B_{j-1}^T + Q_j A_j + W1
+// with orthonormal blocks orthogonal to W1 (the residual after the projections), so its
+// square norm is ||B_{j-1}||^2 + ||A_j||^2 + trace(W1^T W1) (no B term at the first step).
+__global__ void k_hnorm(int32_t ncb, int32_t b, int32_t cb0, int32_t j, const double* __restrict__ Araw,
+                        const double* __restrict__ Bprev, const double* __restrict__ G, double* __restrict__ hq2) {
+  const int32_t lc = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (lc >= ncb) return;
+  const int32_t bb = b * b;
+  const double* a = Araw + (size_t)lc * bb;
+  const double* bp = Bprev + (size_t)(cb0 + lc) * bb;
+  const double* g = G + (size_t)lc * bb;
+  double s = 0.0;
+  for (int32_t e = lane; e < bb; e += 32) {
+    s += a[e] * a[e];
+    if (j > 0) s += bp[e] * bp[e];
+  }
+  if (lane < b) s += g[lane * b + lane];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) hq2[lc] = s;
+}
+
 template <int MODE>
 __global__ void k_chol(int32_t ncb, int32_t b, int32_t cb0, int32_t m, int32_t j, const double* __restrict__ G,
                        const double* __restrict__ hq2, double tau, double shift_rel, double* __restrict__ R,
@@ -789,6 +808,7 @@ template <typename T>
 css_status launch_spmm(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaStream_t st) {
   const uint64_t key = ((uint64_t)sizeof(T) << 60) ^ ((uint64_t)a.b << 48) ^ ((uint64_t)(a.w / 256) << 24) ^
                        (uint64_t)(a.n_brow >= (1 << 24) ? (1 << 24) - 1 : a.n_brow);
+  if (ctx->spmm_variant >= 0) return launch_spmm_v<T>(ctx, a, V, W, ctx->spmm_variant, st);
   for (const auto& kv : ctx->spmm_tune)
     if (kv.first == key) return launch_spmm_v<T>(ctx, a, V, W, kv.second, st);
   cudaEvent_t ev[kSpmmVariants + 1];
@@ -831,14 +851,13 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
   const size_t vec_bytes = (size_t)N * a.ws * sizeof(T);
   const dim3 rgrid((unsigned)nch, (unsigned)ngr);
   constexpr int RTL = RowTile<T>::RTL;
-  const size_t tile = (size_t)RTL * (G * BP + 4) * sizeof(T);
-  const size_t mat = (size_t)G * BP * BP * sizeof(T);
-  const size_t sm_s1 = 6 * tile + mat + (size_t)G * (BP / 4) * sizeof(double) + 16;
+  const size_t tile = (size_t)RTL * (G * (BP + 4) + 4) * sizeof(T);
+  const size_t mat = (size_t)G * ColStride<BP>::MS * sizeof(T);
+  const size_t sm_s1 = 6 * tile + mat;
   const size_t sm_s3 = 6 * tile + 2 * mat;
   const size_t sm_tri = 3 * tile + mat;
   double* partKq = a.part;
   double* partKp = a.part + (size_t)nch * ncb * bb;
-  double* partH = a.part + 2 * (size_t)nch * ncb * bb;
   double* sA = a.small;                          // [2][ncb][bb]: raw, symmetrised
   double* sH = a.small + 2 * (size_t)ncb * bb;   // [ncb]
   double* sG = sH + ncb;                         // [ncb][bb]
@@ -892,12 +911,10 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
     CSS_TRY(launch_spmm<T>(ctx, a, Qc, W, st));
     if (a.ev_spmm) CSS_CU(ctx, cudaEventRecord(a.ev_spmm[2 * j + 1], st));
     // three-term update and the projections onto Q_j (and Q_{j-1})
-    s1<<<rgrid, reorth ? 2 * RW : RW, sm_s1, st>>>(N, b, a.ws, ncb, a.cb0, Qp, Qc, W, a.Bblk_prev, j == 0 ? 1 : 0, partKq, partKp,
-                                 partH);
+    s1<<<rgrid, reorth ? 2 * RW : RW, sm_s1, st>>>(N, b, a.ws, ncb, a.cb0, Qp, Qc, W, a.Bblk_prev, j == 0 ? 1 : 0,
+                                                   partKq, partKp);
     CSS_LAUNCHED(ctx);
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sA);
-    CSS_LAUNCHED(ctx);
-    k_reduce<<<(unsigned)css_ceil_div(ncb, 256), 256, 0, st>>>(nch, ncb, 1, partH, sH);
     CSS_LAUNCHED(ctx);
     if (reorth) {
       k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKp, sKp);
@@ -907,25 +924,27 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
     CSS_LAUNCHED(ctx);
     if (j + 1 == m) break;
     // W1 = W0 - Q_j Kq (- Q_{j-1} Kp) and its Gram
-    s3<<<rgrid, 2 * RW, sm_s3, st>>>(N, b, a.ws, ncb, Qc, Qp, W, sA, sKp, partKq);
+    s3<<<rgrid, row_threads<T, BP>(b), sm_s3, st>>>(N, b, a.ws, ncb, Qc, Qp, W, sA, sKp, partKq);
     CSS_LAUNCHED(ctx);
     // shifted CholeskyQR3 of W: R0 from G + sI, then two plain CholeskyQR passes
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
     CSS_LAUNCHED(ctx);
+    k_hnorm<<<(unsigned)css_ceil_div(ncb, 8), 256, 0, st>>>(ncb, b, a.cb0, j, sA, a.Bblk_prev, sG, sH);
+    CSS_LAUNCHED(ctx);
     CSS_TRY(chol(0, j, sR1, sR1i, a.shift_rel));
     CSS_CU(ctx, cudaMemcpyAsync(sC1, sR1, sizeof(double) * ncb * bb, cudaMemcpyDeviceToDevice, st));
-    k_tri<T, BP, true><<<rgrid, RW, sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
+    k_tri<T, BP, true><<<rgrid, row_threads<T, BP>(b), sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
     CSS_LAUNCHED(ctx);
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
     CSS_LAUNCHED(ctx);
     CSS_TRY(chol(1, j, sR1, sR1i, 0.0));
-    k_tri<T, BP, true><<<rgrid, RW, sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
+    k_tri<T, BP, true><<<rgrid, row_threads<T, BP>(b), sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
     CSS_LAUNCHED(ctx);
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
     CSS_LAUNCHED(ctx);
     CSS_TRY(chol(2, j, sR2, sR2i, 0.0));
     // Q_{j+1} = W R2^-1 overwrites Q_{j-1}
-    k_tri<T, BP, false><<<rgrid, RW, sm_tri, st>>>(N, b, a.ws, ncb, W, Qp, sR2i, nullptr);
+    k_tri<T, BP, false><<<rgrid, row_threads<T, BP>(b), sm_tri, st>>>(N, b, a.ws, ncb, W, Qp, sR2i, nullptr);
     CSS_LAUNCHED(ctx);
     CSS_TRY(sampled(Qp, j + 1));
     // B_{j} for the next step's three-term update, in the batch's local layout
