@@ -186,44 +186,48 @@ __global__ void k_jp_init(int32_t n, const int32_t* __restrict__ adj_ptr, uint64
   colour[i] = -1;
 }
 
+// One Jones-Plassmann round, one warp per uncoloured vertex v (lanes walk v's neighbours): v is
+// ready when every higher-priority neighbour is coloured (a colour, once set, never changes);
+// then it takes the smallest colour none of them uses, searched 256 colours at a time with the
+// lanes' bit masks OR-reduced over the warp.  Vertices not ready count into *remaining.
 __global__ void k_jp_round(int32_t n, const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
                            const int32_t* __restrict__ deg, const uint64_t* __restrict__ key, int32_t* colour,
                            int32_t* __restrict__ remaining) {
-  int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int32_t v = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (v >= n) return;
-  if (__ldcg(&colour[v]) >= 0) return;
+  if (__ldcg(&colour[v]) >= 0) return;  // whole warp
   const int32_t dv = deg[v];
   const uint64_t kv = key[v];
   const int32_t s = adj_ptr[v], e = adj_ptr[v + 1];
-  // ready when every higher-priority neighbour is coloured (a colour, once set, never changes)
-  for (int32_t k = s; k < e; ++k) {
-    int32_t u = adj[k];
-    if (higher(deg[u], key[u], u, dv, kv, v) && __ldcg(&colour[u]) < 0) {
-      atomicAdd(remaining, 1);
-      return;
-    }
+  bool blocked = false;
+  for (int32_t k = s + lane; k < e; k += 32) {
+    const int32_t u = adj[k];
+    if (higher(deg[u], key[u], u, dv, kv, v) && __ldcg(&colour[u]) < 0) blocked = true;
   }
-  // smallest colour not used by a higher-priority neighbour, searched 256 colours at a time
+  if (__any_sync(0xffffffffu, blocked)) {
+    if (lane == 0) atomicAdd(remaining, 1);
+    return;
+  }
   for (int32_t base = 0;; base += 256) {
-    uint64_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
-    for (int32_t k = s; k < e; ++k) {
-      int32_t u = adj[k];
+    uint64_t w[4] = {0, 0, 0, 0};
+    for (int32_t k = s + lane; k < e; k += 32) {
+      const int32_t u = adj[k];
       if (!higher(deg[u], key[u], u, dv, kv, v)) continue;
-      int32_t c = __ldcg(&colour[u]) - base;
+      const int32_t c = __ldcg(&colour[u]) - base;
       if (c < 0 || c >= 256) continue;
-      uint64_t bit = 1ull << (c & 63);
-      if (c < 64) w0 |= bit;
-      else if (c < 128) w1 |= bit;
-      else if (c < 192) w2 |= bit;
-      else w3 |= bit;
+      w[c >> 6] |= 1ull << (c & 63);
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      for (int o = 16; o > 0; o >>= 1) w[q] |= __shfl_xor_sync(0xffffffffu, w[q], o);
     int32_t off = -1;
-    if (~w0) off = __ffsll((long long)~w0) - 1;
-    else if (~w1) off = 64 + __ffsll((long long)~w1) - 1;
-    else if (~w2) off = 128 + __ffsll((long long)~w2) - 1;
-    else if (~w3) off = 192 + __ffsll((long long)~w3) - 1;
+    if (~w[0]) off = __ffsll((long long)~w[0]) - 1;
+    else if (~w[1]) off = 64 + __ffsll((long long)~w[1]) - 1;
+    else if (~w[2]) off = 128 + __ffsll((long long)~w[2]) - 1;
+    else if (~w[3]) off = 192 + __ffsll((long long)~w[3]) - 1;
     if (off >= 0) {
-      colour[v] = base + off;
+      if (lane == 0) colour[v] = base + off;
       return;
     }
   }
@@ -314,7 +318,8 @@ css_status css_color_impl(css_ctx* ctx, int32_t n, const double* xyz, double box
   for (;;) {
     CSS_CU(ctx, cudaMemsetAsync(counters, 0, sizeof(int32_t) * group, st));
     for (int r = 0; r < group; ++r) {
-      k_jp_round<<<nbk, T, 0, st>>>(n, adj_ptr, adj, deg, key, colour, counters + r);
+      k_jp_round<<<(unsigned)css_ceil_div((int64_t)n * 32, T), T, 0, st>>>(n, adj_ptr, adj, deg, key, colour,
+                                                                           counters + r);
       CSS_LAUNCHED(ctx);
     }
     rounds += group;

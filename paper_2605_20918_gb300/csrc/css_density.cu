@@ -373,10 +373,16 @@ __global__ void k_xcompute(int64_t n_pairs, int32_t b, int32_t m, int32_t nmax, 
   X[(size_t)p * bb + e] = acc;
 }
 
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
 // X_p = Qs_p Z_c for the FP32 Krylov rows: for every pair p of colour c a (b x m b) x (m b x b)
 // product.  A CTA takes up to XP pairs of one colour and walks the blocks j of Z_c: the
 // blocks Qs_p[j] (transposed) and the FP32 hi/lo halves of Z_c[j] are staged in shared memory
-// (zero padded to BP x BP), and each thread owns a 4 x 4 tile of one pair's X.  The hi product
+// (zero padded to BP x BP; two stages filled by cp.async, the next block's copies in flight
+// during the current block's multiply), and each thread owns a 4 x 4 tile of one pair's X.  The hi product
 // of a block is summed in FP32 and added into an FP32 hi + lo pair by TwoSum; the lo product
 // (2^-24 of the hi one) is summed in FP32 over all blocks.  The sum is widened to FP64 once.
 template <int BP>
@@ -386,9 +392,9 @@ __global__ void __launch_bounds__(256) k_xtile(int32_t n_col, int32_t b, int32_t
                                                const float* __restrict__ zh, const float* __restrict__ zl,
                                                double* __restrict__ X) {
   constexpr int CB = BP / 4, TPP = CB * CB, XP = 256 / TPP;
-  __shared__ __align__(16) float sQ[XP][BP][BP];  // [pair][l][a]
-  __shared__ __align__(16) float sZh[BP][BP];     // [l][k]
-  __shared__ __align__(16) float sZl[BP][BP];
+  __shared__ __align__(16) float sQ[2][XP][BP][BP];  // [stage][pair][l][a]
+  __shared__ __align__(16) float sZh[2][BP][BP];     // [stage][l][k]
+  __shared__ __align__(16) float sZl[2][BP][BP];
   const int32_t bid = blockIdx.x;
   if (bid >= cta_off[n_col]) return;
   int32_t lo = 0, hi = n_col - 1;  // colour c: cta_off[c] <= bid < cta_off[c + 1]
@@ -403,33 +409,46 @@ __global__ void __launch_bounds__(256) k_xtile(int32_t n_col, int32_t b, int32_t
   const int32_t nb = nblk[c], bb = b * b;
   const int t = threadIdx.x;
   const int pp = t / TPP, rem = t - pp * TPP, ai = rem / CB, ki = rem - ai * CB;
-  for (int e = t; e < XP * BP * BP; e += 256) (&sQ[0][0][0])[e] = 0.0f;
-  for (int e = t; e < BP * BP; e += 256) {
-    (&sZh[0][0])[e] = 0.0f;
-    (&sZl[0][0])[e] = 0.0f;
+  // zero both stages once: the copies write only the b x b part of each block
+  for (int e = t; e < 2 * XP * BP * BP; e += 256) (&sQ[0][0][0][0])[e] = 0.0f;
+  for (int e = t; e < 2 * BP * BP; e += 256) {
+    (&sZh[0][0][0])[e] = 0.0f;
+    (&sZl[0][0][0])[e] = 0.0f;
   }
-  float ahi[16], alo[16], asm_[16];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) ahi[i] = alo[i] = asm_[i] = 0.0f;
-  for (int32_t j = 0; j < nb; ++j) {
-    __syncthreads();  // the previous block's readers are done (and the zeroing is visible)
+  __syncthreads();
+  // asynchronous copies of block j into stage s (Qs blocks transposed on the way)
+  auto issue = [&](int32_t j, int s) {
     for (int32_t e = t; e < np * bb; e += 256) {
       const int32_t q = e / bb, r = e - q * bb, a = r / b, l = r - a * b;
-      sQ[q][l][a] = Qs[((size_t)(p0 + q) * m + j) * bb + r];
+      cp_async4(&sQ[s][q][l][a], Qs + ((size_t)(p0 + q) * m + j) * bb + r);
     }
     for (int32_t e = t; e < bb; e += 256) {
       const int32_t l = e / b, k = e - l * b;
       const size_t o = ((size_t)c * nmax + (size_t)j * b + l) * b + k;
-      sZh[l][k] = zh[o];
-      sZl[l][k] = zl[o];
+      cp_async4(&sZh[s][l][k], zh + o);
+      cp_async4(&sZl[s][l][k], zl + o);
     }
-    __syncthreads();
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  float ahi[16], alo[16], asm_[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) ahi[i] = alo[i] = asm_[i] = 0.0f;
+  if (nb > 0) issue(0, 0);
+  for (int32_t j = 0; j < nb; ++j) {
+    const int s = j & 1;
+    if (j + 1 < nb) {
+      issue(j + 1, s ^ 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();  // block j is in stage s for every thread
     if (pp < np) {
       float ph[4][4] = {};
       for (int32_t l = 0; l < b; ++l) {
-        const float4 x = *reinterpret_cast<const float4*>(&sQ[pp][l][ai * 4]);
-        const float4 zH = *reinterpret_cast<const float4*>(&sZh[l][ki * 4]);
-        const float4 zL = *reinterpret_cast<const float4*>(&sZl[l][ki * 4]);
+        const float4 x = *reinterpret_cast<const float4*>(&sQ[s][pp][l][ai * 4]);
+        const float4 zH = *reinterpret_cast<const float4*>(&sZh[s][l][ki * 4]);
+        const float4 zL = *reinterpret_cast<const float4*>(&sZl[s][l][ki * 4]);
         const float xv[4] = {x.x, x.y, x.z, x.w}, hv[4] = {zH.x, zH.y, zH.z, zH.w}, lv[4] = {zL.x, zL.y, zL.z, zL.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -444,12 +463,13 @@ __global__ void __launch_bounds__(256) k_xtile(int32_t n_col, int32_t b, int32_t
 #pragma unroll
         for (int k = 0; k < 4; ++k) {  // TwoSum of the running hi sum and this block's product
           const int u = i * 4 + k;
-          const float s = __fadd_rn(ahi[u], ph[i][k]);
-          const float z = __fsub_rn(s, ahi[u]);
-          alo[u] = __fadd_rn(alo[u], __fadd_rn(__fsub_rn(ahi[u], __fsub_rn(s, z)), __fsub_rn(ph[i][k], z)));
-          ahi[u] = s;
+          const float sm = __fadd_rn(ahi[u], ph[i][k]);
+          const float z = __fsub_rn(sm, ahi[u]);
+          alo[u] = __fadd_rn(alo[u], __fadd_rn(__fsub_rn(ahi[u], __fsub_rn(sm, z)), __fsub_rn(ph[i][k], z)));
+          ahi[u] = sm;
         }
     }
+    __syncthreads();  // stage s is free for block j + 2
   }
   if (pp >= np) return;
   double* xo = X + (size_t)(p0 + pp) * bb;

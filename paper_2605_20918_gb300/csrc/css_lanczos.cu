@@ -724,18 +724,23 @@ __global__ void k_init_q1(int32_t n_brow, int32_t b, int32_t ws, int32_t cb0, in
   Q[(size_t)t * ws + (size_t)c * b + k] = (T)(sign[t] * inv_sqrt_cnt[cb0 + c]);
 }
 
-// Sampled rows of Q_j: Qs[p][j][a][k] = Q_j[(I_p, a), c_p block, k] for the batch's pairs
+// Sampled rows of Q_j: Qs[p][j][a][k] = Q_j[(I_p, a), c_p block, k] for the batch's pairs, one
+// warp per pair (its b x b block is one contiguous run of Qs)
 template <typename T>
 __global__ void k_scatter(int64_t p_begin, int64_t p_end, int32_t b, int32_t ws, int32_t cb0, int32_t m, int32_t j,
                           const int32_t* __restrict__ pair_I, const int32_t* __restrict__ pair_c,
                           const T* __restrict__ Q, T* __restrict__ Qs) {
-  const int32_t bb = b * b;
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t p = p_begin + t / bb;
+  const int64_t p = p_begin + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (p >= p_end) return;
-  int32_t e = (int32_t)(t % bb), a = e / b, k = e % b;
-  int32_t I = pair_I[p], c = pair_c[p] - cb0;
-  Qs[((size_t)p * m + j) * bb + e] = Q[((size_t)I * b + a) * ws + (size_t)c * b + k];
+  const int32_t bb = b * b;
+  const int32_t I = pair_I[p], c = pair_c[p] - cb0;
+  const T* q = Q + (size_t)I * b * ws + (size_t)c * b;
+  T* o = Qs + ((size_t)p * m + j) * bb;
+  for (int32_t e = lane; e < bb; e += 32) {
+    const int32_t a = e / b, k = e - a * b;
+    o[e] = q[(size_t)a * ws + k];
+  }
 }
 
 // Second pass: X[p][a][kk] += sum_l Q_j[(I_p, a), c_p block, l] Z_c[j b + l][kk] (FP64)
@@ -884,7 +889,8 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
   auto sampled = [&](const T* Qj, int32_t j) -> css_status {
     if (pe <= pb) return CSS_OK;
     if (a.mode == 1) {
-      k_scatter<T><<<sblocks, 256, 0, st>>>(pb, pe, b, a.ws, a.cb0, m, j, a.pair_I, a.pair_c, Qj, (T*)a.Qs);
+      k_scatter<T><<<(unsigned)css_ceil_div((pe - pb) * 32, 256), 256, 0, st>>>(pb, pe, b, a.ws, a.cb0, m, j,
+                                                                                a.pair_I, a.pair_c, Qj, (T*)a.Qs);
     } else if (a.mode == 2) {
       k_accum_x<T><<<sblocks, 256, 0, st>>>(pb, pe, b, a.ws, a.cb0, a.ldz, j, a.pair_I, a.pair_c, a.nblk, Qj, a.Z,
                                             a.X);
