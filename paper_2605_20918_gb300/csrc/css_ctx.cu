@@ -82,7 +82,7 @@ css_status css_create(css_ctx** out, int device) {
   const char* t = getenv("CSS_TIMING");
   ctx->timing = t && t[0] == '1';
   const char* sv = getenv("CSS_SPMM_VARIANT");
-  if (sv && sv[0] >= '0' && sv[0] <= '2' && sv[1] == 0) ctx->spmm_variant = sv[0] - '0';
+  if (sv && sv[0] >= '0' && sv[0] <= '4' && sv[1] == 0) ctx->spmm_variant = sv[0] - '0';
   const char* de = getenv("CSS_DEBUG_EIG");
   ctx->debug_eig = de ? atoi(de) : 0;
   *out = ctx;

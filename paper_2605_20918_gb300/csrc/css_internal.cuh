@@ -60,7 +60,7 @@ struct css_ctx {
   size_t host_pinned_bytes = 0;
   // H * V autotuner: launch variant chosen per (precision, block width, column count, rows)
   std::vector<std::pair<uint64_t, int>> spmm_tune;
-  int spmm_variant = -1;  // env CSS_SPMM_VARIANT = 0..2 fixes the variant (no tuning)
+  int spmm_variant = -1;  // env CSS_SPMM_VARIANT = 0..4 fixes the variant (no tuning)
 };
 
 css_status css_set_cuda_error(css_ctx* ctx, cudaError_t e, const char* what, const char* file, int line);

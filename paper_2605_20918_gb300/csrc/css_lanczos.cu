@@ -784,7 +784,7 @@ css_status launch_spmm_t(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaSt
 
 // launch variants (columns per thread, threads per CTA); every variant sums each output in the
 // same order, so the choice changes the speed only, never the result
-constexpr int kSpmmVariants = 3;
+constexpr int kSpmmVariants = 5;
 
 template <typename T, int BM>
 css_status launch_spmm_bm(css_ctx* ctx, const LzArgs& a, const T* V, T* W, int v, cudaStream_t st) {
@@ -792,7 +792,9 @@ css_status launch_spmm_bm(css_ctx* ctx, const LzArgs& a, const T* V, T* W, int v
   constexpr int TCN = TCW > 1 ? TCW / 2 : 1;
   if (v == 0) return launch_spmm_t<T, BM, TCW, 128>(ctx, a, V, W, st);
   if (v == 1) return launch_spmm_t<T, BM, TCN, 256>(ctx, a, V, W, st);
-  return launch_spmm_t<T, BM, TCN, 128>(ctx, a, V, W, st);
+  if (v == 2) return launch_spmm_t<T, BM, TCN, 128>(ctx, a, V, W, st);
+  if (v == 3) return launch_spmm_t<T, BM, TCW, 64>(ctx, a, V, W, st);  // more, smaller CTAs per SM
+  return launch_spmm_t<T, BM, TCW, 96>(ctx, a, V, W, st);
 }
 
 template <typename T>
