@@ -19,6 +19,7 @@ _LIB = _HERE / "libcss_oracle.so"
 
 SYMMETRIZE = 1
 REORTH_LOCAL = 4
+ENERGY_WEIGHTED = 16  # write the energy-weighted density matrix (Z built with lambda f(lambda))
 SIGNS_ONES = 1
 
 _lib = None

@@ -32,7 +32,11 @@
  *   - breakdown: stop the colour's recurrence at step j when min_k R_kk of the QR of the
  *     new block is <= 1e-10 ||H Q_j||_F; its projected matrix then has j blocks;
  *   - no reorthogonalisation unless CSS_REF_REORTH_LOCAL (one more pass against Q_j, Q_j-1);
- *   - symmetrisation P = (P~ + P~^T) / 2 when CSS_REF_SYMMETRIZE is set.
+ *   - symmetrisation P = (P~ + P~^T) / 2 when CSS_REF_SYMMETRIZE is set;
+ *   - CSS_REF_ENERGY_WEIGHTED: the energy-weighted density matrix (the paper's force section:
+ *     rho_E = sum_i f(e_i) e_i |psi_i><psi_i|, obtained in CSS as H rho~ for an orthogonal
+ *     basis), taken in each colour's Krylov subspace as Q_c T_c Z_c = Q_c U Lambda f(Lambda)
+ *     U^T E_1 B_0 (H Q_c = Q_c T_c up to the Lanczos residual); mu is still fixed by f.
  * Pins: the test-suite checks every function here against closed forms, dense
  * diagonalisation with LAPACK (numpy), brute force on tiny inputs and invariants; the
  * paper prints no worked numeric example, so agreement with the paper's own numbers is
@@ -49,6 +53,7 @@
 /* flag values of the oracle's own interface */
 #define CSS_REF_SYMMETRIZE 1
 #define CSS_REF_REORTH_LOCAL 4
+#define CSS_REF_ENERGY_WEIGHTED 16
 #define CSS_REF_SIGNS_ONES 1
 
 #define REF_OK 0
@@ -650,8 +655,11 @@ int css_ref_density(int32_t n_brow, int32_t b, int32_t nnzb, const int32_t* row_
     int32_t n = 0, bk = 0;
     ref_colour_eigen(&H, colour, sign, c, m, flags, &n, lam2, wg2, U, &bk, cnt[c]);
     double sq = sqrt((double)cnt[c]);
-    for (int32_t j = 0; j < n; ++j)  /* f(Lambda) Y, Y[j][k] = sqrt|c| U[k][j] */
-      for (int32_t k = 0; k < b; ++k) fy[(size_t)j * b + k] = ref_fermi(lam2[j], mu, kT) * sq * U[(size_t)k * n + j];
+    for (int32_t j = 0; j < n; ++j) {  /* f(Lambda) Y (Lambda f(Lambda) Y), Y[j][k] = sqrt|c| U[k][j] */
+      double fj = ref_fermi(lam2[j], mu, kT);
+      if (flags & CSS_REF_ENERGY_WEIGHTED) fj *= lam2[j];
+      for (int32_t k = 0; k < b; ++k) fy[(size_t)j * b + k] = fj * sq * U[(size_t)k * n + j];
+    }
     for (int32_t i = 0; i < nmax; ++i)
       for (int32_t k = 0; k < b; ++k) {
         double s = 0.0;

@@ -36,6 +36,10 @@ class Dense:
     def f(self, mu, kT):
         return (self.V * fermi(self.w, mu, kT)) @ self.V.T
 
+    def fe(self, mu, kT):
+        """Energy-weighted density matrix sum_i f(e_i) e_i |psi_i><psi_i| = f(H) H."""
+        return (self.V * (self.w * fermi(self.w, mu, kT))) @ self.V.T
+
     @staticmethod
     def _mid_of_tolerance_set(g, lo, hi, ne_tol):
         """Midpoint of {mu : |g(mu)| <= ne_tol} for increasing g (both ends by brentq)."""
@@ -68,12 +72,13 @@ class Dense:
             out[k] = M[I * b:(I + 1) * b, J * b:(J + 1) * b]
         return out
 
-    def css_extract(self, mu, kT, colour, sign, n_colours):
-        """P~_IJ = (f(H) R)[I, colour(J) block] diag(s_J) on the pattern (Eq. 2)."""
+    def css_extract(self, mu, kT, colour, sign, n_colours, energy=False):
+        """P~_IJ = (f(H) R)[I, colour(J) block] diag(s_J) on the pattern (Eq. 2); with energy,
+        the same extraction of f(H) H R."""
         H = self.H
         b = H.b
         R = probe_matrix(colour, sign, b, n_colours)
-        X = self.f(mu, kT) @ R
+        X = (self.fe(mu, kT) if energy else self.f(mu, kT)) @ R
         rows = H.rows()
         out = np.empty((H.nnzb, b, b))
         for k in range(H.nnzb):

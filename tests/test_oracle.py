@@ -415,3 +415,72 @@ def test_colour_subset_equals_full_columns(O):
     sel = np.isin(col[H.col_idx], sub)
     assert np.array_equal(part["P"][sel], full["P"][sel])
     assert np.all(np.isnan(part["P"][~sel]))
+
+
+# -------------------------------------------- energy-weighted density matrix (paper, forces)
+def test_energy_weighted_degenerate_colouring_is_f_of_H_times_H(O):
+    """Every molecule its own colour and a full Krylov space: rho_E = f(H) H on the pattern,
+    with mu fixed by f exactly as for P."""
+    g = synth.water_box(8)
+    H = synth.hamiltonian(g)
+    col, nc = O.color(g.pos, g.box, 100.0, 1004)
+    s = O.probes(col, H.b, 1005)
+    ne = synth.n_electrons(8)
+    r = O.density(H, col, s, nc, kT=0.05, n_elec=ne, m=8)
+    re = O.density(H, col, s, nc, kT=0.05, n_elec=ne, m=8, flags=O.SYMMETRIZE | O.ENERGY_WEIGHTED)
+    dn = Dense(H)
+    mu = dn.mu_exact(ne, 0.05)
+    assert re["mu"] == r["mu"]
+    ref = dn.on_pattern(dn.fe(mu, 0.05))
+    assert _pattern_err(re["P"], ref) < 1e-9
+    # Tr rho_E = sum_i f(e_i) e_i
+    assert abs(re["trP"] - float((dn.w * fermi(dn.w, mu, 0.05)).sum())) < 1e-8
+
+
+def test_energy_weighted_contaminated_full_krylov(O):
+    """Shared colours, full Krylov space: rho~_E = extract(f(H) H R) (Eq. 2 with f(x) x)."""
+    g = synth.water_box(12, box=9.0)
+    H = synth.hamiltonian(g, r_cut=5.0)
+    col, nc = O.color(g.pos, g.box, 4.0, 1004)
+    s = O.probes(col, H.b, 1005)
+    ne = synth.n_electrons(12)
+    dn = Dense(H)
+    R = probe_matrix(col, s, H.b, nc)
+    mu = dn.mu_projected(R, ne, 0.05, nc, H.b)
+    re = O.density(H, col, s, nc, kT=0.05, n_elec=ne, m=12, flags=O.ENERGY_WEIGHTED)
+    assert _pattern_err(re["P"], dn.css_extract(mu, 0.05, col, s, nc, energy=True)) < 1e-9
+    rs = O.density(H, col, s, nc, kT=0.05, n_elec=ne, m=12, flags=O.ENERGY_WEIGHTED | O.SYMMETRIZE)
+    assert _pattern_err(rs["P"], symmetrize(H, dn.css_extract(mu, 0.05, col, s, nc, energy=True))) < 1e-9
+
+
+def test_energy_weighted_trace_identity_truncated(O):
+    """With a truncated Krylov space the unsymmetrised trace is still the Ritz quadrature
+    sum_j lambda_j f(lambda_j) w_j (Eq. 6-7)."""
+    g = synth.water_box(64)
+    H = synth.hamiltonian(g)
+    col, nc = O.color(g.pos, g.box, 8.0, 1004)
+    s = O.probes(col, H.b, 1005)
+    ne = synth.n_electrons(64)
+    re = O.density(H, col, s, nc, kT=0.05, n_elec=ne, m=6, flags=O.ENERGY_WEIGHTED)
+    rz = O.ritz(H, col, s, nc, m=6)
+    quad = sum(float((l * fermi(l, re["mu"], 0.05) * w).sum()) for l, w in rz)
+    assert abs(re["trP"] - quad) < 1e-8 * max(1.0, abs(quad))
+
+
+def test_energy_weighted_zero_coupling_blocks(O):
+    """Block-diagonal H: (rho_E)_II = H_II f(H_II) and nothing off the diagonal."""
+    g = synth.water_box(27)
+    H = synth.hamiltonian(g, coupling=0.0)
+    col, nc = O.color(g.pos, g.box, 6.0, 1004)
+    s = O.probes(col, H.b, 1005)
+    ne = synth.n_electrons(27)
+    re = O.density(H, col, s, nc, kT=0.05, n_elec=ne, m=10, flags=O.SYMMETRIZE | O.ENERGY_WEIGHTED)
+    rows = H.rows()
+    for k in range(H.nnzb):
+        I, J = rows[k], H.col_idx[k]
+        if I == J:
+            w, V = np.linalg.eigh(H.val[k])
+            ref = (V * (w * fermi(w, re["mu"], 0.05))) @ V.T
+            assert np.abs(re["P"][k] - ref).max() < 1e-10
+        else:
+            assert np.abs(re["P"][k]).max() < 1e-11
