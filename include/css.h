@@ -58,6 +58,12 @@ typedef enum {
 #define CSS_TWO_PASS 2u     /* regenerate the Krylov basis instead of storing its sampled rows  */
 #define CSS_REORTH_LOCAL 4u /* one more orthogonalisation pass of each new block against Q_j, Q_j-1 */
 #define CSS_HOST_IO 8u      /* css_pbuild only: every array argument is HOST memory            */
+/* Energy-weighted density matrix instead of P (paper: the matrix rho_E = sum_i f(e_i) e_i
+ * |psi_i><psi_i| that DFTB forces need, obtained in CSS as H rho~ for an orthogonal basis),
+ * taken in each colour's Krylov subspace: Z_c = U Lambda f(Lambda) U^T E_1 B_0 = T_c Z_c(P).
+ * mu is still fixed by f (Tr P = n_elec/2); trP and trPH then return Tr rho_E and
+ * Tr(rho_E H). */
+#define CSS_ENERGY_WEIGHTED 16u
 /* css_probes flags */
 #define CSS_SIGNS_ONES 1u   /* all probe entries +1 instead of seeded random signs             */
 

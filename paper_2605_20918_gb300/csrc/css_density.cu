@@ -616,7 +616,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   // ------------------------------------------------------------ validation
   if (n_sys < 1 || n_sys > MU_MAXSYS) return css_set_arg_error(ctx, "css_density: n_sys out of range");
   if (prec != CSS_FP64 && prec != CSS_MIXED_FP32) return css_set_arg_error(ctx, "css_density: unknown precision");
-  if (flags & ~(CSS_SYMMETRIZE | CSS_TWO_PASS | CSS_REORTH_LOCAL))
+  if (flags & ~(CSS_SYMMETRIZE | CSS_TWO_PASS | CSS_REORTH_LOCAL | CSS_ENERGY_WEIGHTED))
     return css_set_arg_error(ctx, "css_density: unknown flag");
   const int32_t b = sys[0].H.b;
   if (b < 1) return css_set_arg_error(ctx, "css_density: b < 1");
@@ -960,7 +960,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     ++ctx->kernel_launches;
   }
   tm.mark();  // 4
-  CSS_TRY(css_eigen_z(ctx, ea, sys_of_colour, dmu, dkT, Z, st));
+  CSS_TRY(css_eigen_z(ctx, ea, sys_of_colour, dmu, dkT, Z, st, (flags & CSS_ENERGY_WEIGHTED) != 0));
 
   // --------------------------------------------------------- reconstruction
   if (two_pass) {

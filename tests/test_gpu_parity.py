@@ -206,6 +206,36 @@ def test_density_mixed_within_tolerance(torch, css, ctx, n, kind, r_col, m, solv
     assert abs(got["trP"] - ref["trP"]) < 1e-4
 
 
+# ------------------------------------------- energy-weighted density matrix (forces)
+@pytest.mark.parametrize("n,kind,r_col,m,flags", [(64, "minimal", 8.0, 10, 1), (125, "minimal", 8.0, 12, 0),
+                                                  (27, "dzp", 6.0, 6, 1), (64, "minimal", 8.0, 10, 1 | 2)])
+def test_energy_weighted_fp64_matches_oracle(torch, css, ctx, n, kind, r_col, m, flags):
+    """rho_E (Z built with lambda f(lambda), mu from f) against the oracle: FP64 to 1e-10 of
+    its scale (entries carry energies of tens of eV); the two-pass path too."""
+    g, H, col, s, nc = _system(n, kind, r_col)
+    ne = synth.n_electrons(n)
+    ew = css.CSS_ENERGY_WEIGHTED
+    ref = oracle.density(H, col, s, nc, kT=0.05, n_elec=ne, m=m, flags=(flags & ~2) | oracle.ENERGY_WEIGHTED)
+    got = gpu_density(torch, css, ctx, H, col, s, nc, kT=0.05, n_elec=ne, m=m, flags=flags | ew,
+                      precision=css.CSS_FP64)
+    scale = max(1.0, float(np.abs(ref["P"]).max()))
+    assert float(np.abs(got["P"] - ref["P"]).max()) < FP64_TOL * scale
+    assert abs(got["trP"] - ref["trP"]) < 1e-8 * max(1.0, abs(ref["trP"]))
+    assert got["mu"] == pytest.approx(ref["mu"], abs=1e-9)
+
+
+def test_energy_weighted_mixed_within_tolerance(torch, css, ctx):
+    g, H, col, s, nc = _system(125, "dzp", 10.0)
+    ne = synth.n_electrons(125)
+    ew = css.CSS_ENERGY_WEIGHTED
+    ref = oracle.density(H, col, s, nc, kT=0.05, n_elec=ne, m=20, mu=-4.0, solve_mu=False,
+                         flags=1 | oracle.ENERGY_WEIGHTED)
+    got = gpu_density(torch, css, ctx, H, col, s, nc, kT=0.05, n_elec=ne, m=20, mu=-4.0, solve_mu=False,
+                      flags=1 | ew, precision=css.CSS_MIXED_FP32)
+    scale = max(1.0, float(np.abs(ref["P"]).max()))
+    assert float(np.abs(got["P"] - ref["P"]).max()) < MIXED_P_TOL * scale
+
+
 # ------------------------------------------------------------------ batch / pbuild
 def test_batch_equals_single(torch, css, ctx):
     systems = [_system(n, "minimal", 10.0) for n in (27, 64, 100)]
