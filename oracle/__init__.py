@@ -20,6 +20,7 @@ _LIB = _HERE / "libcss_oracle.so"
 SYMMETRIZE = 1
 REORTH_LOCAL = 4
 ENERGY_WEIGHTED = 16  # write the energy-weighted density matrix (Z built with lambda f(lambda))
+INV_SQRT = 32  # the matrix is an overlap S: write S^(-1/2) (function x^(-1/2), no mu)
 SIGNS_ONES = 1
 
 _lib = None

@@ -36,7 +36,11 @@
  *   - CSS_REF_ENERGY_WEIGHTED: the energy-weighted density matrix (the paper's force section:
  *     rho_E = sum_i f(e_i) e_i |psi_i><psi_i|, obtained in CSS as H rho~ for an orthogonal
  *     basis), taken in each colour's Krylov subspace as Q_c T_c Z_c = Q_c U Lambda f(Lambda)
- *     U^T E_1 B_0 (H Q_c = Q_c T_c up to the Lanczos residual); mu is still fixed by f.
+ *     U^T E_1 B_0 (H Q_c = Q_c T_c up to the Lanczos residual); mu is still fixed by f;
+ *   - CSS_REF_INV_SQRT: the matrix is an overlap S (symmetric positive definite) and the
+ *     function is x^(-1/2) instead of f (the paper's S^(-1/2) step, Eq. 8-10: the same
+ *     block-Lanczos projection onto coloured probes, exact diagonalisation of the projected
+ *     S^K and its inverse square root); no mu, Tr returns Tr S~^(-1/2) and Tr(S~^(-1/2) S).
  * Pins: the test-suite checks every function here against closed forms, dense
  * diagonalisation with LAPACK (numpy), brute force on tiny inputs and invariants; the
  * paper prints no worked numeric example, so agreement with the paper's own numbers is
@@ -54,6 +58,7 @@
 #define CSS_REF_SYMMETRIZE 1
 #define CSS_REF_REORTH_LOCAL 4
 #define CSS_REF_ENERGY_WEIGHTED 16
+#define CSS_REF_INV_SQRT 32
 #define CSS_REF_SIGNS_ONES 1
 
 #define REF_OK 0
@@ -600,7 +605,7 @@ int css_ref_density(int32_t n_brow, int32_t b, int32_t nnzb, const int32_t* row_
    * bisections (lower end: smallest mu with N - N_e/2 >= -ne_tol; upper end: largest mu with
    * N - N_e/2 <= +ne_tol).  For a metal both ends meet at the root; for an insulator the
    * interval is the gap and mu lands mid-gap instead of at a band edge. */
-  if (solve_mu) {
+  if (solve_mu && !(flags & CSS_REF_INV_SQRT)) {
     double lo0 = INFINITY, hi0 = -INFINITY;
     for (int32_t t = 0; t < nwork; ++t)
       for (int32_t j = 0; j < nj[t]; ++j) {
@@ -656,7 +661,11 @@ int css_ref_density(int32_t n_brow, int32_t b, int32_t nnzb, const int32_t* row_
     ref_colour_eigen(&H, colour, sign, c, m, flags, &n, lam2, wg2, U, &bk, cnt[c]);
     double sq = sqrt((double)cnt[c]);
     for (int32_t j = 0; j < n; ++j) {  /* f(Lambda) Y (Lambda f(Lambda) Y), Y[j][k] = sqrt|c| U[k][j] */
-      double fj = ref_fermi(lam2[j], mu, kT);
+      double fj;
+      if (flags & CSS_REF_INV_SQRT)  /* S^K is positive definite: its Ritz values are > 0 */
+        fj = lam2[j] > 0.0 ? 1.0 / sqrt(lam2[j]) : NAN;
+      else
+        fj = ref_fermi(lam2[j], mu, kT);
       if (flags & CSS_REF_ENERGY_WEIGHTED) fj *= lam2[j];
       for (int32_t k = 0; k < b; ++k) fy[(size_t)j * b + k] = fj * sq * U[(size_t)k * n + j];
     }

@@ -265,6 +265,20 @@ def _coupling_G(pi, pj, n, b, coupling_seed, pair_chunk):
     return out
 
 
+def overlap(geom: Geometry, kind: str = "minimal", *, r_cut: float = 4.5, coupling: float = 0.05,
+            overlap_seed: int = 1007, cache: dict | None = None) -> BSR:
+    """Synthetic overlap S of a non-orthogonal basis (symmetric positive definite, BSR): unit
+    on-site blocks and couplings coupling * exp(-(r - 2.8)/0.5) * G for O-O distance r <= r_cut,
+    G drawn per unordered pair (seed `overlap_seed`) with N(0,1)/sqrt(b) entries.  With the
+    defaults the off-diagonal row sums stay well below 1 at water density, so S is positive
+    definite with a condition number of about 2."""
+    b = 6 if kind == "minimal" else 23 if kind == "dzp" else None
+    if b is None:
+        raise ValueError(f"unknown level kind {kind!r}")
+    return hamiltonian(geom, kind, r_cut=r_cut, coupling=coupling, levels=np.ones((geom.n_mol, b)),
+                       coupling_seed=overlap_seed, cache=cache)
+
+
 def hamiltonian(geom: Geometry, kind: str = "minimal", *, r_cut: float = 6.0, coupling: float = 0.5,
                 levels: np.ndarray | None = None, onsite_seed: int = 1002, coupling_seed: int = 1003,
                 pair_chunk: int = 200_000, cache: dict | None = None) -> BSR:

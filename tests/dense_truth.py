@@ -36,6 +36,25 @@ class Dense:
     def f(self, mu, kT):
         return (self.V * fermi(self.w, mu, kT)) @ self.V.T
 
+    def inv_sqrt(self):
+        """S^(-1/2) of a symmetric positive definite matrix."""
+        assert self.w.min() > 0
+        return (self.V / np.sqrt(self.w)) @ self.V.T
+
+    def extract(self, M, colour, sign, n_colours):
+        """(M R)[I, colour(J) block] diag(s_J) on the pattern for a dense matrix function M."""
+        H = self.H
+        b = H.b
+        R = probe_matrix(colour, sign, b, n_colours)
+        X = M @ R
+        rows = H.rows()
+        out = np.empty((H.nnzb, b, b))
+        for k in range(H.nnzb):
+            I, J = rows[k], H.col_idx[k]
+            c = colour[J]
+            out[k] = X[I * b:(I + 1) * b, c * b:(c + 1) * b] * sign[J * b:(J + 1) * b][None, :]
+        return out
+
     def fe(self, mu, kT):
         """Energy-weighted density matrix sum_i f(e_i) e_i |psi_i><psi_i| = f(H) H."""
         return (self.V * (self.w * fermi(self.w, mu, kT))) @ self.V.T

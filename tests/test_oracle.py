@@ -484,3 +484,53 @@ def test_energy_weighted_zero_coupling_blocks(O):
             assert np.abs(re["P"][k] - ref).max() < 1e-10
         else:
             assert np.abs(re["P"][k]).max() < 1e-11
+
+
+# ------------------------------------------- S^(-1/2) of an overlap matrix (paper, Eq. 8-10)
+def test_inv_sqrt_degenerate_colouring_is_exact(O):
+    """Every molecule its own colour and a full Krylov space: S~^(-1/2) = S^(-1/2) on the pattern."""
+    g = synth.water_box(8)
+    S = synth.overlap(g)
+    col, nc = O.color(g.pos, g.box, 100.0, 1004)
+    s = O.probes(col, S.b, 1005)
+    r = O.density(S, col, s, nc, m=8, flags=O.SYMMETRIZE | O.INV_SQRT)
+    dn = Dense(S)
+    assert _pattern_err(r["P"], dn.on_pattern(dn.inv_sqrt())) < 1e-11
+    assert abs(r["trP"] - float((1.0 / np.sqrt(dn.w)).sum())) < 1e-10
+
+
+def test_inv_sqrt_contaminated_full_krylov(O):
+    """Shared colours, full Krylov space: S~^(-1/2) = extract(S^(-1/2) o) (Eq. 8-9 taken literally)."""
+    g = synth.water_box(12, box=9.0)
+    S = synth.overlap(g)
+    col, nc = O.color(g.pos, g.box, 4.0, 1004)
+    assert nc < 12
+    s = O.probes(col, S.b, 1005)
+    dn = Dense(S)
+    ref = dn.extract(dn.inv_sqrt(), col, s, nc)
+    r = O.density(S, col, s, nc, m=12, flags=O.INV_SQRT)
+    assert _pattern_err(r["P"], ref) < 1e-11
+    r2 = O.density(S, col, s, nc, m=12, flags=O.INV_SQRT | O.SYMMETRIZE)
+    assert _pattern_err(r2["P"], symmetrize(S, ref)) < 1e-11
+
+
+def test_inv_sqrt_trace_identity_and_convergence(O):
+    """Truncated Krylov space: Tr of the extraction is the Ritz quadrature sum_j lambda_j^(-1/2)
+    w_j, and with a colouring radius beyond the overlap range the error against the dense
+    S^(-1/2) falls with the Krylov depth (the paper uses 10)."""
+    g = synth.water_box(64)
+    S = synth.overlap(g)
+    col, nc = O.color(g.pos, g.box, 9.0, 1004)
+    s = O.probes(col, S.b, 1005)
+    rz = O.ritz(S, col, s, nc, m=4)
+    r = O.density(S, col, s, nc, m=4, flags=O.INV_SQRT)
+    quad = sum(float((w / np.sqrt(l)).sum()) for l, w in rz)
+    assert abs(r["trP"] - quad) < 1e-9
+    dn = Dense(S)
+    contaminated = symmetrize(S, dn.extract(dn.inv_sqrt(), col, s, nc))
+    got = {m: O.density(S, col, s, nc, m=m, flags=O.INV_SQRT | O.SYMMETRIZE)["P"] for m in (2, 4, 8)}
+    errs = [_pattern_err(got[m], contaminated) for m in (2, 4, 8)]   # Krylov truncation only
+    assert errs[0] > errs[1] > errs[2], errs
+    assert errs[2] < 1e-8, errs
+    # what is left against the true S^(-1/2) is the same-colour contamination (Eq. 2)
+    assert _pattern_err(got[8], dn.on_pattern(dn.inv_sqrt())) < 1e-3
