@@ -64,6 +64,13 @@ typedef enum {
  * mu is still fixed by f (Tr P = n_elec/2); trP and trPH then return Tr rho_E and
  * Tr(rho_E H). */
 #define CSS_ENERGY_WEIGHTED 16u
+/* H is an overlap matrix S (symmetric positive definite) and the matrix function is x^(-1/2)
+ * instead of the Fermi function (paper, Eq. 8-10: S^(-1/2) by the same block-Lanczos
+ * projection onto coloured probes, the exact diagonalisation of the projected S^K and its
+ * inverse square root); fermi is ignored and mu_out returns fermi->mu; P_val receives
+ * S~^(-1/2) on S's pattern, trP Tr S~^(-1/2), trPH Tr(S~^(-1/2) S).  A non-positive Ritz
+ * value (S not positive definite) gives CSS_ERR_NUMERIC. */
+#define CSS_INV_SQRT 32u
 /* css_probes flags */
 #define CSS_SIGNS_ONES 1u   /* all probe entries +1 instead of seeded random signs             */
 

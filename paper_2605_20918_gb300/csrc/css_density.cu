@@ -616,7 +616,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   // ------------------------------------------------------------ validation
   if (n_sys < 1 || n_sys > MU_MAXSYS) return css_set_arg_error(ctx, "css_density: n_sys out of range");
   if (prec != CSS_FP64 && prec != CSS_MIXED_FP32) return css_set_arg_error(ctx, "css_density: unknown precision");
-  if (flags & ~(CSS_SYMMETRIZE | CSS_TWO_PASS | CSS_REORTH_LOCAL | CSS_ENERGY_WEIGHTED))
+  if (flags & ~(CSS_SYMMETRIZE | CSS_TWO_PASS | CSS_REORTH_LOCAL | CSS_ENERGY_WEIGHTED | CSS_INV_SQRT))
     return css_set_arg_error(ctx, "css_density: unknown flag");
   const int32_t b = sys[0].H.b;
   if (b < 1) return css_set_arg_error(ctx, "css_density: b < 1");
@@ -922,7 +922,8 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
       hp[s] = sys[s].fermi.kT;
       hp[n_sys + s] = 0.5 * sys[s].fermi.n_elec;
       hp[2 * n_sys + s] = sys[s].fermi.mu;
-      ((int32_t*)(hp + 3 * n_sys))[s] = sys[s].fermi.solve_mu ? 1 : 0;
+      // no chemical potential for the inverse square root of an overlap matrix
+      ((int32_t*)(hp + 3 * n_sys))[s] = (sys[s].fermi.solve_mu && !(flags & CSS_INV_SQRT)) ? 1 : 0;
       const double tl = sys[s].fermi.ne_tol;
       hp[4 * n_sys + s] = tl > 0.0 ? tl : 1e-6 * std::max(1.0, 0.5 * sys[s].fermi.n_elec);
     }
@@ -960,7 +961,8 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     ++ctx->kernel_launches;
   }
   tm.mark();  // 4
-  CSS_TRY(css_eigen_z(ctx, ea, sys_of_colour, dmu, dkT, Z, st, (flags & CSS_ENERGY_WEIGHTED) != 0));
+  CSS_TRY(css_eigen_z(ctx, ea, sys_of_colour, dmu, dkT, Z, st, ((flags & CSS_ENERGY_WEIGHTED) ? 1 : 0) |
+                                                                     ((flags & CSS_INV_SQRT) ? 2 : 0)));
 
   // --------------------------------------------------------- reconstruction
   if (two_pass) {

@@ -916,12 +916,13 @@ __global__ void k_ritz_y(int32_t kd, int32_t b, int32_t nmax, const int32_t* __r
   }
 }
 
-// Zt[i][col] = sum_k U[i][k] f(lam_k) Y[k][col] (one thread per row i); with energy the weight is
-// lam_k f(lam_k): the energy-weighted density matrix, T_c Z_c in the Krylov subspace
+// Zt[i][col] = sum_k U[i][k] g(lam_k) Y[k][col] (one thread per row i).  fn bit 1: g = x^(-1/2)
+// (inverse square root of an overlap, positive Ritz values; NaN otherwise) instead of the Fermi
+// function; bit 0: g multiplied by x (the energy-weighted density matrix, T_c Z_c).
 __global__ void k_zt(int32_t kd, int32_t b, int32_t nmax, const int32_t* __restrict__ nblk,
                      const int32_t* __restrict__ sys_of_colour, const double* __restrict__ mu,
                      const double* __restrict__ kT, const double* __restrict__ U, const double* __restrict__ lam,
-                     const double* __restrict__ Y, double* __restrict__ Z, int energy) {
+                     const double* __restrict__ Y, double* __restrict__ Z, int fn) {
   extern __shared__ double shy[];
   const int32_t c = blockIdx.y;
   const int32_t n = nblk[c] * kd;
@@ -939,7 +940,9 @@ __global__ void k_zt(int32_t kd, int32_t b, int32_t nmax, const int32_t* __restr
     for (int32_t t = threadIdx.x; t < (ke - k0) * b; t += blockDim.x) {
       const int32_t kk = k0 + t / b;
       const double l = lam[(size_t)c * nmax + kk];
-      const double fw = energy ? l * css_fermi_dirac(l, m_, t_) : css_fermi_dirac(l, m_, t_);
+      double fw = (fn & 2) ? (l > 0.0 ? 1.0 / sqrt(l) : __longlong_as_double(0x7ff8000000000000ll))
+                           : css_fermi_dirac(l, m_, t_);
+      if (fn & 1) fw *= l;
       shy[t] = fw * Y[((size_t)c * nmax) * b + (size_t)k0 * b + t];
     }
     __syncthreads();
@@ -999,11 +1002,11 @@ css_status css_eigen_ritz(css_ctx* ctx, const EigArgs& a, cudaStream_t st) {
 }
 
 css_status css_eigen_z(css_ctx* ctx, const EigArgs& a, const int32_t* sys_of_colour, const double* mu,
-                       const double* kT, double* Z, cudaStream_t st, bool energy) {
+                       const double* kT, double* Z, cudaStream_t st, int fn) {
   const int32_t nc = a.n_col, b = a.b, nmax = a.m * b;
   dim3 g((unsigned)css_ceil_div(nmax, 128), (unsigned)nc);
   k_zt<<<g, 128, 64 * b * sizeof(double), st>>>(b, b, nmax, a.nblk, sys_of_colour, mu, kT, a.U, a.lam, a.Y, Z,
-                                                 energy ? 1 : 0);
+                                                 fn);
   CSS_LAUNCHED(ctx);
   k_apply_refl<false><<<nc, 1024, 0, st>>>(b, b, nmax, a.rcap, a.nblk, a.RV, a.RT, a.RR0, a.sweep_off, Z);
   CSS_LAUNCHED(ctx);

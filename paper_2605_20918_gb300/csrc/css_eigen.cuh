@@ -41,4 +41,4 @@ struct EigArgs {
 
 css_status css_eigen_ritz(css_ctx* ctx, const EigArgs& a, cudaStream_t st);
 css_status css_eigen_z(css_ctx* ctx, const EigArgs& a, const int32_t* sys_of_colour, const double* mu,
-                       const double* kT, double* Z, cudaStream_t st, bool energy = false);
+                       const double* kT, double* Z, cudaStream_t st, int fn = 0);

@@ -236,6 +236,32 @@ def test_energy_weighted_mixed_within_tolerance(torch, css, ctx):
     assert float(np.abs(got["P"] - ref["P"]).max()) < MIXED_P_TOL * scale
 
 
+# ------------------------------------------------ S^(-1/2) of an overlap (Eq. 8-10)
+@pytest.mark.parametrize("n,kind,r_col,m,flags", [(64, "minimal", 6.0, 10, 1), (125, "minimal", 9.0, 10, 0),
+                                                  (27, "dzp", 6.0, 6, 1), (64, "minimal", 6.0, 10, 1 | 2)])
+def test_inv_sqrt_fp64_matches_oracle(torch, css, ctx, n, kind, r_col, m, flags):
+    g = synth.water_box(n)
+    S = synth.overlap(g, kind)
+    col, nc = oracle.color(g.pos, g.box, r_col, 1004)
+    s = oracle.probes(col, S.b, 1005)
+    ref = oracle.density(S, col, s, nc, m=m, flags=(flags & ~2) | oracle.INV_SQRT)
+    got = gpu_density(torch, css, ctx, S, col, s, nc, m=m, flags=flags | css.CSS_INV_SQRT,
+                      precision=css.CSS_FP64)
+    assert float(np.abs(got["P"] - ref["P"]).max()) < FP64_TOL
+    assert abs(got["trP"] - ref["trP"]) < 1e-9 * max(1.0, abs(ref["trP"]))
+
+
+def test_inv_sqrt_mixed_within_tolerance(torch, css, ctx):
+    g = synth.water_box(343)
+    S = synth.overlap(g, "dzp")
+    col, nc = oracle.color(g.pos, g.box, 9.0, 1004)
+    s = oracle.probes(col, S.b, 1005)
+    ref = oracle.density(S, col, s, nc, m=10, flags=1 | oracle.INV_SQRT)
+    got = gpu_density(torch, css, ctx, S, col, s, nc, m=10, flags=1 | css.CSS_INV_SQRT,
+                      precision=css.CSS_MIXED_FP32)
+    assert float(np.abs(got["P"] - ref["P"]).max()) < MIXED_P_TOL
+
+
 # ------------------------------------------------------------------ batch / pbuild
 def test_batch_equals_single(torch, css, ctx):
     systems = [_system(n, "minimal", 10.0) for n in (27, 64, 100)]
