@@ -58,6 +58,7 @@ def _load():
         lib.css_ref_density.argtypes = [i32, i32, i32, p, p, p, p, p, i32, f64, f64, f64, f64, C.c_int, i32,
                                         C.c_int, p, i32, p, p, p, p, p]
         lib.css_ref_ritz.argtypes = [i32, i32, p, p, p, p, p, i32, i32, C.c_int, p, p, p]
+        lib.css_ref_hprime.argtypes = [i32, i32, i32, p, p, p, i32, p, p, p, p, p, i32, i32, C.c_int, p, p, p]
         lib.css_ref_num_threads.restype = C.c_int
         _lib = lib
     return _lib
@@ -192,6 +193,23 @@ def density(H, colour, sign, n_colours: int, *, mu: float = 0.0, kT: float = 0.0
     _chk(st, "density")
     return {"P": P, "trP": float(out[0]), "trPH": float(out[1]), "mu": float(out[2]),
             "n_breakdown": int(nb[0])}
+
+
+def hprime(S, H, colour, sign, n_colours: int, *, m: int = 10, flags: int = SYMMETRIZE):
+    """H' of a non-orthogonal basis: S~^(-1/2) by CSS on S (probes from colour/sign), then
+    H' extracted from S~^(-1/2) H Y <o|.  Returns dict(Sinv=(nnzb_S, b, b), Hp=(nnzb_H, b, b), trHp)."""
+    colour = np.ascontiguousarray(colour, dtype=np.int32)
+    sign = np.ascontiguousarray(sign, dtype=np.int8)
+    Si = np.zeros((S.nnzb, S.b, S.b)); Hp = np.zeros((H.nnzb, H.b, H.b)); tr = np.zeros(1)
+    arrs = []
+    for M in (S, H):
+        arrs.append((np.ascontiguousarray(M.row_ptr, dtype=np.int32), np.ascontiguousarray(M.col_idx, dtype=np.int32),
+                     np.ascontiguousarray(M.val, dtype=np.float64)))
+    (sr, sc, sv), (hr, hc, hv) = arrs
+    st = _load().css_ref_hprime(S.n_brow, S.b, S.nnzb, _ptr(sr), _ptr(sc), _ptr(sv), H.nnzb, _ptr(hr), _ptr(hc),
+                                _ptr(hv), _ptr(colour), _ptr(sign), n_colours, m, flags, _ptr(Si), _ptr(Hp), _ptr(tr))
+    _chk(st, "hprime")
+    return {"Sinv": Si, "Hp": Hp, "trHp": float(tr[0])}
 
 
 def num_threads() -> int:

@@ -724,6 +724,99 @@ int css_ref_density(int32_t n_brow, int32_t b, int32_t nnzb, const int32_t* row_
   return REF_OK;
 }
 
+/* H' of a non-orthogonal basis (paper, Eq. 8-10 and the paragraph after them): with
+ * Y = S^(-1/2) |o> from the CSS projection of the overlap S onto the probes o (block-Lanczos
+ * on S, x^(-1/2) in the Krylov subspace), S~^(-1/2) = Y <o| on S's pattern, and the sparse H'
+ * extracted from S~^(-1/2) H Y <o| on H's pattern:
+ *   H'~_IJ = [S~^(-1/2) (H Y_c)]_I diag(o_J),  c = colour(J),
+ * where the left factor is the sparse S~^(-1/2) just obtained (symmetrised when
+ * CSS_REF_SYMMETRIZE is set, as is H'~).  S and H share n_brow and b; their patterns may
+ * differ.  Outputs: Sinv_val (S's pattern), Hp_val (H's pattern), *trHp = Tr H'. */
+int css_ref_hprime(int32_t n_brow, int32_t b, int32_t nnzb_s, const int32_t* s_row_ptr, const int32_t* s_col_idx,
+                   const double* s_val, int32_t nnzb_h, const int32_t* h_row_ptr, const int32_t* h_col_idx,
+                   const double* h_val, const int32_t* colour, const int8_t* sign, int32_t n_colours, int32_t m,
+                   int flags, double* Sinv_val, double* Hp_val, double* trHp) {
+  if (n_brow < 1 || b < 1 || m < 1 || n_colours < 1 || !Sinv_val || !Hp_val) return REF_ERR_ARG;
+  const int sym = flags & CSS_REF_SYMMETRIZE;
+  double t1, t2, mu0;
+  int32_t nbrk;
+  int st = css_ref_density(n_brow, b, nnzb_s, s_row_ptr, s_col_idx, s_val, colour, sign, n_colours, 0.0, 0.0,
+                           0.0, 0.0, 0, m, (flags & (CSS_REF_SYMMETRIZE | CSS_REF_REORTH_LOCAL)) | CSS_REF_INV_SQRT,
+                           NULL, 0, Sinv_val, &t1, &t2, &mu0, &nbrk);
+  if (st != REF_OK) return st;
+  ref_h S = {n_brow, b, s_row_ptr, s_col_idx, s_val};
+  const int64_t N = (int64_t)n_brow * b;
+  const int32_t nmax = m * b;
+  int64_t* cnt = (int64_t*)calloc((size_t)n_colours, sizeof(int64_t));
+  int32_t* brow = (int32_t*)malloc(sizeof(int32_t) * (size_t)nnzb_h);
+  double* Ht = (double*)calloc((size_t)nnzb_h * b * b, sizeof(double));
+  if (!cnt || !brow || !Ht) return REF_ERR_NOMEM;
+  for (int32_t J = 0; J < n_brow; ++J) cnt[colour[J]]++;
+  for (int32_t I = 0; I < n_brow; ++I)
+    for (int32_t p = h_row_ptr[I]; p < h_row_ptr[I + 1]; ++p) brow[p] = I;
+  int status = REF_OK;
+#pragma omp parallel for schedule(dynamic, 1) if (n_colours > 1)
+  for (int32_t c = 0; c < n_colours; ++c) {
+    if (cnt[c] == 0) continue;
+    double* U = (double*)malloc(sizeof(double) * (size_t)nmax * nmax);
+    double* lam = (double*)malloc(sizeof(double) * nmax);
+    double* wg = (double*)malloc(sizeof(double) * nmax);
+    double* Z = (double*)malloc(sizeof(double) * (size_t)nmax * b);
+    double* fy = (double*)malloc(sizeof(double) * (size_t)nmax * b);
+    double* Y = (double*)malloc(sizeof(double) * (size_t)N * b);
+    double* W1 = (double*)malloc(sizeof(double) * (size_t)N * b);
+    double* W2 = (double*)malloc(sizeof(double) * (size_t)N * b);
+    int32_t n = 0, bk = 0;
+    int sc = ref_colour_eigen(&S, colour, sign, c, m, flags & CSS_REF_REORTH_LOCAL, &n, lam, wg, U, &bk, cnt[c]);
+    double sq = sqrt((double)cnt[c]);
+    for (int32_t j = 0; j < n; ++j) {  /* Lambda^(-1/2) U^T E_1 B_0 */
+      double g = lam[j] > 0.0 ? 1.0 / sqrt(lam[j]) : NAN;
+      for (int32_t k = 0; k < b; ++k) fy[(size_t)j * b + k] = g * sq * U[(size_t)k * n + j];
+    }
+    for (int32_t i = 0; i < nmax; ++i)
+      for (int32_t k = 0; k < b; ++k) {
+        double sum = 0.0;
+        if (i < n)
+          for (int32_t j = 0; j < n; ++j) sum += U[(size_t)i * n + j] * fy[(size_t)j * b + k];
+        Z[(size_t)i * b + k] = sum;
+      }
+    ref_lanczos_colour(&S, colour, sign, c, n / b, flags & CSS_REF_REORTH_LOCAL, NULL, Z, Y, NULL);  /* Y_c */
+    ref_bsr_mul(n_brow, b, h_row_ptr, h_col_idx, h_val, Y, W1, b);          /* H Y_c */
+    ref_bsr_mul(n_brow, b, s_row_ptr, s_col_idx, Sinv_val, W1, W2, b);      /* S~^(-1/2) H Y_c */
+    for (int32_t p = 0; p < nnzb_h; ++p) {
+      int32_t J = h_col_idx[p];
+      if (colour[J] != c) continue;
+      int32_t I = brow[p];
+      for (int32_t a = 0; a < b; ++a)
+        for (int32_t k = 0; k < b; ++k)
+          Ht[(size_t)p * b * b + a * b + k] = W2[((size_t)I * b + a) * b + k] * sign[(size_t)J * b + k];
+    }
+    if (sc != REF_OK) {
+#pragma omp critical
+      status = sc;
+    }
+    free(U); free(lam); free(wg); free(Z); free(fy); free(Y); free(W1); free(W2);
+  }
+  double tr = 0.0;
+  for (int32_t p = 0; p < nnzb_h; ++p) {
+    int32_t I = brow[p], J = h_col_idx[p];
+    int32_t q = -1;
+    for (int32_t r = h_row_ptr[J]; r < h_row_ptr[J + 1]; ++r)
+      if (h_col_idx[r] == I) { q = r; break; }
+    for (int32_t a = 0; a < b; ++a)
+      for (int32_t k = 0; k < b; ++k) {
+        double x = Ht[(size_t)p * b * b + a * b + k];
+        if (sym && q >= 0) x = 0.5 * (x + Ht[(size_t)q * b * b + k * b + a]);
+        Hp_val[(size_t)p * b * b + a * b + k] = x;
+        if (I == J && a == k) tr += x;
+      }
+  }
+  if (trHp) *trHp = tr;
+  free(cnt); free(brow); free(Ht);
+  if (status != REF_OK) return status;
+  return isfinite(tr) ? REF_OK : REF_ERR_NUMERIC;
+}
+
 /* Ritz data of all colours (test hook): lam/wgt are n_colours x (m b), n_per receives the
  * size of each colour's projected matrix. */
 int css_ref_ritz(int32_t n_brow, int32_t b, const int32_t* row_ptr, const int32_t* col_idx, const double* val,

@@ -534,3 +534,81 @@ def test_inv_sqrt_trace_identity_and_convergence(O):
     assert errs[2] < 1e-8, errs
     # what is left against the true S^(-1/2) is the same-colour contamination (Eq. 2)
     assert _pattern_err(got[8], dn.on_pattern(dn.inv_sqrt())) < 1e-3
+
+
+# ------------------------------------- H' of a non-orthogonal basis (paper, after Eq. 10)
+def _block_mask(M):
+    """Dense 0/1 mask of a BSR pattern."""
+    b = M.b
+    mask = np.zeros((M.n_brow * b, M.n_brow * b))
+    rows = M.rows()
+    for k in range(M.nnzb):
+        I, J = rows[k], M.col_idx[k]
+        mask[I * b:(I + 1) * b, J * b:(J + 1) * b] = 1.0
+    return mask
+
+
+def test_hprime_full_pattern_is_the_orthogonalised_H(O):
+    """An overlap whose pattern covers every pair and molecules in their own colours: H' is
+    S^(-1/2) H S^(-1/2) exactly, and its spectrum is the generalised spectrum of (H, S)."""
+    g = synth.water_box(6, box=6.0)
+    S = synth.overlap(g, r_cut=20.0)
+    H = synth.hamiltonian(g, r_cut=20.0)
+    col, nc = O.color(g.pos, g.box, 100.0, 1004)
+    s = O.probes(col, S.b, 1005)
+    r = O.hprime(S, H, col, s, nc, m=6)
+    ds = Dense(S)
+    Si = ds.inv_sqrt()
+    ref = Si @ H.dense() @ Si
+    assert _pattern_err(r["Sinv"], ds.on_pattern(Si)) < 1e-11
+    assert _pattern_err(r["Hp"], Dense(H).on_pattern(ref)) < 1e-9
+    import scipy.linalg as sl
+    w = sl.eigh(H.dense(), S.dense(), eigvals_only=True)
+    assert np.abs(np.linalg.eigvalsh(ref) - w).max() < 1e-9
+    assert abs(r["trHp"] - np.trace(ref)) < 1e-9
+
+
+def test_hprime_truncated_and_contaminated(O):
+    """Shared colours, a truncated overlap pattern and a full Krylov space: H'~ is the literal
+    extraction of trunc(S^(-1/2)) H (S^(-1/2) R) (the left factor is the sparse S~^(-1/2))."""
+    g = synth.water_box(12, box=9.0)
+    S = synth.overlap(g)
+    H = synth.hamiltonian(g, r_cut=5.0)
+    col, nc = O.color(g.pos, g.box, 4.0, 1004)
+    assert nc < 12
+    s = O.probes(col, S.b, 1005)
+    r = O.hprime(S, H, col, s, nc, m=12, flags=0)
+    ds, dh = Dense(S), Dense(H)
+    R = probe_matrix(col, s, S.b, nc)
+    Si = ds.inv_sqrt()
+    Y = Si @ R
+    Sinv_t = ds.extract(Si, col, s, nc)             # S~^(-1/2) on S's pattern (unsymmetrised)
+    assert _pattern_err(r["Sinv"], Sinv_t) < 1e-11
+    # dense S~^(-1/2) from its pattern blocks
+    St = np.zeros_like(Si)
+    rows = S.rows()
+    b = S.b
+    for k in range(S.nnzb):
+        I, J = rows[k], S.col_idx[k]
+        St[I * b:(I + 1) * b, J * b:(J + 1) * b] = Sinv_t[k]
+    hrows = H.rows()
+
+    def extract_h(Left):
+        X = Left @ H.dense() @ Y
+        out = np.empty((H.nnzb, b, b))
+        for k in range(H.nnzb):
+            I, J = hrows[k], H.col_idx[k]
+            c = col[J]
+            out[k] = X[I * b:(I + 1) * b, c * b:(c + 1) * b] * s[J * b:(J + 1) * b][None, :]
+        return out
+
+    assert _pattern_err(r["Hp"], extract_h(St)) < 1e-10
+    # symmetrised: both S~^(-1/2) and H'~ are symmetrised on their patterns
+    rs = O.hprime(S, H, col, s, nc, m=12)
+    Sinv_s = symmetrize(S, Sinv_t)
+    Ss = np.zeros_like(Si)
+    for k in range(S.nnzb):
+        I, J = rows[k], S.col_idx[k]
+        Ss[I * b:(I + 1) * b, J * b:(J + 1) * b] = Sinv_s[k]
+    assert _pattern_err(rs["Sinv"], Sinv_s) < 1e-11
+    assert _pattern_err(rs["Hp"], symmetrize(H, extract_h(Ss))) < 1e-10
