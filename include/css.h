@@ -177,6 +177,24 @@ CSS_API css_status css_density(css_ctx* ctx, const css_bsr* H, const int32_t* co
                        const css_fermi* fermi, int32_t m, css_precision prec, uint32_t flags, double* P_val,
                        double* trP, double* trPH, double* mu_out, void* stream);
 
+/* H' of a non-orthogonal basis (paper, Eq. 8-10 and the paragraph after them).  With the probes
+ * o of (colour, sign) -- a colouring of S's pattern at the caller's cut-off d_cut^S --
+ *   Y = S^(-1/2) |o>  by block-Lanczos on S (depth m) and x^(-1/2) in the Krylov subspace,
+ *   S~^(-1/2) = Y <o| extracted on S's pattern                       -> Sinv_val,
+ *   H'~ extracted from S~^(-1/2) H Y <o| on H's pattern               -> Hp_val,
+ * i.e. H'~_IJ = [S~^(-1/2) (H Y_c)]_I diag(o_J), c = colour(J): two SpMMs on the full
+ * N x (n_colours b) block Y.  With CSS_SYMMETRIZE both outputs are symmetrised on their
+ * (structurally symmetric) patterns.
+ *   S, H      host structs of device arrays; same n_brow and b, patterns may differ
+ *   Sinv_val  device double[S->nnzb*b*b], Hp_val device double[H->nnzb*b*b], written
+ *   trHp      host double, written: Tr H'
+ *   flags     CSS_SYMMETRIZE, CSS_REORTH_LOCAL
+ * Workspace: three N x (n_colours b) blocks in the vector precision beyond css_density's.
+ * Returns CSS_WARN_BREAKDOWN when a colour's recurrence on S stopped early.  Synchronises. */
+CSS_API css_status css_hprime(css_ctx* ctx, const css_bsr* S, const css_bsr* H, const int32_t* colour,
+                              const int8_t* sign, int32_t n_colours, int32_t m, css_precision prec, uint32_t flags,
+                              double* Sinv_val, double* Hp_val, double* trHp, void* stream);
+
 /* Many independent systems in one call (MD snapshots of uneven size).  Arrays of n_sys
  * host structs / host arrays of device pointers; mu is solved per system (fermi[s]).
  * Outputs per system: P_val[s] (device), trP[s], trPH[s], mu_out[s] (host arrays). */

@@ -105,6 +105,9 @@ def load_library(path: str | Path | None = None):
     lib.css_projected.restype = st
     lib.css_eigen_blocks.argtypes = [v, i32, i32, i32, v, v, v, v, f64, f64, v, v, v, v]
     lib.css_eigen_blocks.restype = st
+    lib.css_hprime.argtypes = [v, C.POINTER(_BSR), C.POINTER(_BSR), v, v, i32, i32, st, u32, v, v,
+                               C.POINTER(C.c_double), v]
+    lib.css_hprime.restype = st
     lib.css_ritz.restype = st
     _lib = lib
     return lib
@@ -237,6 +240,20 @@ def css_density(ctx, H: DeviceBSR, colour, sign, n_colours: int, P, *, mu=0.0, k
                                           int(precision), int(flags), _dev(P, torch.float64, "P"), C.byref(tp),
                                           C.byref(tph), C.byref(mo), _stream(stream)), "css_density")
     return {"trP": tp.value, "trPH": tph.value, "mu": mo.value, "status": st}
+
+
+def css_hprime(ctx, S: DeviceBSR, H: DeviceBSR, colour, sign, n_colours: int, Sinv, Hp, *, m=10,
+               precision=CSS_FP64, flags=CSS_SYMMETRIZE, stream=None) -> dict:
+    """S~^(-1/2) (into Sinv, S's pattern) and H' (into Hp, H's pattern) of a non-orthogonal basis."""
+    torch = _torch()
+    lib = load_library()
+    sb, hb = S._c(), H._c()
+    tr = C.c_double()
+    st = _check(lib, ctx, lib.css_hprime(ctx, C.byref(sb), C.byref(hb), _dev(colour, torch.int32, "colour"),
+                                         _dev(sign, torch.int8, "sign"), int(n_colours), int(m), int(precision),
+                                         int(flags), _dev(Sinv, torch.float64, "Sinv"), _dev(Hp, torch.float64, "Hp"),
+                                         C.byref(tr), _stream(stream)), "css_hprime")
+    return {"trHp": tr.value, "status": st}
 
 
 def css_density_batch(ctx, Hs, colours, signs, n_colours, Ps, fermis, *, m=30, precision=CSS_FP64,
@@ -378,6 +395,9 @@ class Context:
 
     def density(self, *a, **k):
         return css_density(self.handle, *a, **k)
+
+    def hprime(self, *a, **k):
+        return css_hprime(self.handle, *a, **k)
 
     def density_batch(self, *a, **k):
         return css_density_batch(self.handle, *a, **k)

@@ -612,7 +612,8 @@ struct Timer {
 }  // namespace
 
 css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys, int32_t m, css_precision prec,
-                            uint32_t flags, double* trP, double* trPH, double* mu_out, cudaStream_t st) {
+                            uint32_t flags, double* trP, double* trPH, double* mu_out, cudaStream_t st,
+                            void* yfull, int32_t ldy) {
   // ------------------------------------------------------------ validation
   if (n_sys < 1 || n_sys > MU_MAXSYS) return css_set_arg_error(ctx, "css_density: n_sys out of range");
   if (prec != CSS_FP64 && prec != CSS_MIXED_FP32) return css_set_arg_error(ctx, "css_density: unknown precision");
@@ -645,7 +646,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   const int64_t N = (int64_t)n_brow * b;
   const int32_t bb = b * b, nmax = m * b;
   const bool f32 = prec == CSS_MIXED_FP32;
-  const bool two_pass = (flags & CSS_TWO_PASS) != 0;
+  const bool two_pass = (flags & CSS_TWO_PASS) != 0 || yfull != nullptr;
   const int T = 256;
   Timer tm(ctx, st);
   tm.mark();  // 0
@@ -866,6 +867,8 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   la.flags = f32 ? (flags | CSS_REORTH_LOCAL) : flags;
   la.Qs = Qs;
   la.X = X;
+  la.Yfull = yfull;
+  la.ldy = ldy;
   la.Z = Z;
   la.ldz = nmax;
   la.pair_I = pair_I;
@@ -1082,6 +1085,52 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   return n_break > 0 ? CSS_WARN_BREAKDOWN : CSS_OK;
 }
 
+
+namespace {
+
+__global__ void k_block_rows(int32_t n_brow, const int32_t* __restrict__ row_ptr, int32_t* __restrict__ brow) {
+  const int32_t I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n_brow) return;
+  for (int32_t p = row_ptr[I]; p < row_ptr[I + 1]; ++p) brow[p] = I;
+}
+
+// H'~_IJ = W[I rows][c(J) block] diag(o_J) on H's pattern, symmetrised with the transpose
+// element W[J rows][c(I) block] diag(o_I) when sym; per-CTA partial sums of the trace
+template <typename T>
+__global__ void __launch_bounds__(EX_T) k_hp_extract(int32_t nnzb, int32_t b, const int32_t* __restrict__ brow,
+                                                     const int32_t* __restrict__ col_idx,
+                                                     const int32_t* __restrict__ colour, const int8_t* __restrict__ sign,
+                                                     const T* __restrict__ Wm, int32_t ldy, int sym,
+                                                     double* __restrict__ out, double* __restrict__ part) {
+  __shared__ double r1[EX_T / 32];
+  const int32_t bb = b * b;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double tp = 0.0;
+  if (t < (int64_t)nnzb * bb) {
+    const int32_t k = (int32_t)(t / bb), e = (int32_t)(t % bb), a = e / b, kk = e % b;
+    const int32_t I = brow[k], J = col_idx[k];
+    double v = (double)Wm[((size_t)I * b + a) * ldy + (size_t)colour[J] * b + kk] * (double)sign[(size_t)J * b + kk];
+    if (sym) {
+      const double w = (double)Wm[((size_t)J * b + kk) * ldy + (size_t)colour[I] * b + a] *
+                       (double)sign[(size_t)I * b + a];
+      v = 0.5 * (v + w);
+    }
+    out[t] = v;
+    if (I == J && a == kk) tp = v;
+  }
+  for (int o = 16; o > 0; o >>= 1) tp += __shfl_xor_sync(0xffffffffu, tp, o);
+  if ((threadIdx.x & 31) == 0) r1[threadIdx.x >> 5] = tp;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int i = 0; i < EX_T / 32; ++i) a += r1[i];
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = 0.0;
+  }
+}
+
+}  // namespace
+
 extern "C" {
 
 css_status css_ritz(css_ctx* ctx, double* lam, double* wgt, int32_t* n_per, int64_t capacity, int32_t* n_colours) {
@@ -1197,6 +1246,84 @@ css_status css_density_batch(css_ctx* ctx, int32_t n_sys, const css_bsr* H, cons
   std::vector<css_sys_desc> d(n_sys);
   for (int32_t s = 0; s < n_sys; ++s) d[s] = css_sys_desc{H[s], colour[s], sign[s], n_colours[s], fermi[s], P_val[s]};
   return css_density_impl(ctx, n_sys, d.data(), m, prec, flags, trP, trPH, mu_out, (cudaStream_t)stream);
+}
+
+
+css_status css_hprime(css_ctx* ctx, const css_bsr* S, const css_bsr* H, const int32_t* colour, const int8_t* sign,
+                      int32_t n_colours, int32_t m, css_precision prec, uint32_t flags, double* Sinv_val,
+                      double* Hp_val, double* trHp, void* stream) {
+  if (!ctx || !S || !H || !Sinv_val || !Hp_val) return css_set_arg_error(ctx, "css_hprime: null pointer");
+  if (S->n_brow != H->n_brow || S->b != H->b || H->nnzb < H->n_brow || !H->row_ptr || !H->col_idx || !H->val)
+    return css_set_arg_error(ctx, "css_hprime: S and H need the same n_brow and b, and a valid H");
+  if (flags & ~(CSS_SYMMETRIZE | CSS_REORTH_LOCAL)) return css_set_arg_error(ctx, "css_hprime: unknown flag");
+  if (n_colours < 1) return css_set_arg_error(ctx, "css_hprime: n_colours < 1");
+  CSS_CU(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool f32 = prec == CSS_MIXED_FP32;
+  const int32_t b = S->b, n_brow = S->n_brow;
+  const int64_t N = (int64_t)n_brow * b;
+  const int32_t w = n_colours * b;
+  const int32_t ldy = (int32_t)css_ceil_div(w, 8) * 8;
+  const size_t sv = f32 ? sizeof(float) : sizeof(double);
+  void *Y, *W1, *W2;
+  CSS_TRY(css_ws(ctx, "hp_Y", (size_t)N * ldy * sv, &Y));
+  CSS_TRY(css_ws(ctx, "hp_W1", (size_t)N * ldy * sv, &W1));
+  CSS_TRY(css_ws(ctx, "hp_W2", (size_t)N * ldy * sv, &W2));
+  CSS_CU(ctx, cudaMemsetAsync(Y, 0, (size_t)N * ldy * sv, st));
+  // 1. S~^(-1/2) on S's pattern and Y = S^(-1/2) |o> for every colour (paper, Eq. 8-10)
+  css_fermi fz{0.0, 0.0, 0.0, 0.0, 0};
+  css_sys_desc d{*S, colour, sign, n_colours, fz, Sinv_val};
+  double t1, t2, mu0;
+  const css_status s1 = css_density_impl(ctx, 1, &d, m, prec, (flags & (CSS_SYMMETRIZE | CSS_REORTH_LOCAL)) |
+                                                                    CSS_INV_SQRT, &t1, &t2, &mu0, st, Y, ldy);
+  if (s1 != CSS_OK && s1 != CSS_WARN_BREAKDOWN) return s1;
+  // 2. W1 = H Y, W2 = S~^(-1/2) W1 (the left factor is the sparse S~^(-1/2) just obtained)
+  LzArgs la;
+  la.fp32 = f32;
+  la.n_brow = n_brow;
+  la.b = b;
+  la.w = w;
+  la.ws = ldy;
+  la.row_ptr = H->row_ptr;
+  la.col_idx = H->col_idx;
+  CSS_TRY(css_spmm_prepare(ctx, f32, b, n_brow, H->nnzb, H->row_ptr, H->col_idx, H->val, &la.Hval, &la.Hlo_diag,
+                           st));
+  CSS_TRY(css_spmm(ctx, la, Y, W1, st));
+  la.row_ptr = S->row_ptr;
+  la.col_idx = S->col_idx;
+  CSS_TRY(css_spmm_prepare(ctx, f32, b, n_brow, S->nnzb, S->row_ptr, S->col_idx, Sinv_val, &la.Hval,
+                           &la.Hlo_diag, st));
+  CSS_TRY(css_spmm(ctx, la, W1, W2, st));
+  // 3. H' on H's pattern and its trace
+  int32_t* brow;
+  double *part, *tout;
+  const int64_t nth = (int64_t)H->nnzb * b * b;
+  const unsigned blocks = (unsigned)css_ceil_div(nth, EX_T);
+  CSS_TRY(css_ws(ctx, "hp_brow", sizeof(int32_t) * (size_t)H->nnzb, (void**)&brow));
+  CSS_TRY(css_ws(ctx, "hp_part", sizeof(double) * 2 * (size_t)blocks, (void**)&part));
+  CSS_TRY(css_ws(ctx, "hp_tout", sizeof(double) * 2, (void**)&tout));
+  k_block_rows<<<(unsigned)css_ceil_div(n_brow, 256), 256, 0, st>>>(n_brow, H->row_ptr, brow);
+  CSS_LAUNCHED(ctx);
+  const int sym = (flags & CSS_SYMMETRIZE) ? 1 : 0;
+  if (f32)
+    k_hp_extract<float><<<blocks, EX_T, 0, st>>>(H->nnzb, b, brow, H->col_idx, colour, sign, (const float*)W2, ldy,
+                                                 sym, Hp_val, part);
+  else
+    k_hp_extract<double><<<blocks, EX_T, 0, st>>>(H->nnzb, b, brow, H->col_idx, colour, sign, (const double*)W2,
+                                                  ldy, sym, Hp_val, part);
+  CSS_LAUNCHED(ctx);
+  k_trace_sum<<<1, 1024, 0, st>>>((int32_t)blocks, part, tout);
+  CSS_LAUNCHED(ctx);
+  double* h;
+  CSS_TRY(css_pinned(ctx, sizeof(double) * 2, (void**)&h));
+  CSS_CU(ctx, cudaMemcpyAsync(h, tout, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CSS_CU(ctx, cudaStreamSynchronize(st));
+  if (trHp) *trHp = h[0];
+  if (!std::isfinite(h[0])) {
+    ctx->last_error = "css_hprime: non-finite trace of H'";
+    return CSS_ERR_NUMERIC;
+  }
+  return s1;
 }
 
 }  // extern "C"

@@ -93,5 +93,8 @@ struct css_sys_desc {
   css_fermi fermi;
   double* P_val;
 };
+// yfull (optional, device, [N][ldy] in the vector precision, zeroed by the caller): forces the
+// regenerating second pass and accumulates Y = Q_c Z_c of every colour over all rows into it
 css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys, int32_t m, css_precision prec,
-                            uint32_t flags, double* trP, double* trPH, double* mu_out, cudaStream_t st);
+                            uint32_t flags, double* trP, double* trPH, double* mu_out, cudaStream_t st,
+                            void* yfull = nullptr, int32_t ldy = 0);

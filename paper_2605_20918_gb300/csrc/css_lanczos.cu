@@ -743,6 +743,25 @@ __global__ void k_scatter(int64_t p_begin, int64_t p_end, int32_t b, int32_t ws,
   }
 }
 
+// Second pass, every row: Y[r][c b + k] += sum_l Q_j[r][lc b + l] Z_c[j b + l][k] for the
+// batch's colours (lc = c - cb0), one CTA per row r
+template <typename T>
+__global__ void k_accum_full(int32_t b, int32_t ws, int32_t ncb, int32_t cb0, int32_t ldz, int32_t j,
+                             const int32_t* __restrict__ nblk, const T* __restrict__ Q,
+                             const double* __restrict__ Z, T* __restrict__ Y, int32_t ldy) {
+  const int64_t r = blockIdx.x;
+  const T* q = Q + (size_t)r * ws;
+  for (int32_t col = threadIdx.x; col < ncb * b; col += blockDim.x) {
+    const int32_t lc = col / b, k = col - lc * b, cg = cb0 + lc;
+    if (j >= nblk[cg]) continue;
+    const double* z = Z + ((size_t)cg * ldz + (size_t)j * b) * b + k;
+    double s = 0.0;
+    for (int32_t l = 0; l < b; ++l) s = fma((double)q[(size_t)lc * b + l], z[(size_t)l * b], s);
+    T* y = Y + (size_t)r * ldy + (size_t)cg * b + k;
+    *y = (T)((double)*y + s);
+  }
+}
+
 // Second pass: X[p][a][kk] += sum_l Q_j[(I_p, a), c_p block, l] Z_c[j b + l][kk] (FP64)
 template <typename T>
 __global__ void k_accum_x(int64_t p_begin, int64_t p_end, int32_t b, int32_t ws, int32_t cb0, int32_t ldz,
@@ -889,6 +908,11 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
                                                                 a.inv_sqrt_cnt, Qc);
   CSS_LAUNCHED(ctx);
   auto sampled = [&](const T* Qj, int32_t j) -> css_status {
+    if (a.mode == 2 && a.Yfull) {
+      k_accum_full<T><<<(unsigned)((int64_t)a.n_brow * b), 128, 0, st>>>(b, a.ws, a.ncb, a.cb0, a.ldz, j, a.nblk,
+                                                                         Qj, a.Z, (T*)a.Yfull, a.ldy);
+      CSS_LAUNCHED(ctx);
+    }
     if (pe <= pb) return CSS_OK;
     if (a.mode == 1) {
       k_scatter<T><<<(unsigned)css_ceil_div((pe - pb) * 32, 256), 256, 0, st>>>(pb, pe, b, a.ws, a.cb0, m, j,
@@ -980,6 +1004,11 @@ css_status run_pass(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
 css_status css_lanczos_pass(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
   if (a.fp32) return run_pass<float>(ctx, a, st);
   return run_pass<double>(ctx, a, st);
+}
+
+css_status css_spmm(css_ctx* ctx, const LzArgs& a, const void* V, void* W, cudaStream_t st) {
+  if (a.fp32) return launch_spmm<float>(ctx, a, (const float*)V, (float*)W, st);
+  return launch_spmm<double>(ctx, a, (const double*)V, (double*)W, st);
 }
 
 size_t css_lanczos_part_doubles(int64_t N, int32_t b, int32_t ncb) {

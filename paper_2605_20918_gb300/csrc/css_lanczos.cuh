@@ -35,9 +35,14 @@ struct LzArgs {
   const int32_t* pair_c = nullptr;
   const int64_t* pair_off_h = nullptr;  // host: first pair of each colour (n_colours + 1)
   cudaEvent_t* ev_spmm = nullptr;    // when set: 2 events per step bracket each H*V launch
+  void* Yfull = nullptr;             // mode 2 only: also Y += Q_j Z_c[j] over ALL rows, [N][ldy] in the
+  int32_t ldy = 0;                   //   vector precision, colour c at columns [c b, c b + b)
 };
 
 css_status css_lanczos_pass(css_ctx* ctx, const LzArgs& a, cudaStream_t st);
+// W = M V for a BSR matrix prepared by css_spmm_prepare (a.Hval, a.Hlo_diag, a.row_ptr,
+// a.col_idx, a.n_brow, a.b) and N x a.w blocks V, W of row stride a.ws in the vector precision
+css_status css_spmm(css_ctx* ctx, const LzArgs& a, const void* V, void* W, cudaStream_t st);
 size_t css_lanczos_part_doubles(int64_t N, int32_t b, int32_t ncb);
 size_t css_lanczos_small_doubles(int32_t b, int32_t ncb);
 // padded block size of the H * V kernel for block width b

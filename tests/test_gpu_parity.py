@@ -262,6 +262,35 @@ def test_inv_sqrt_mixed_within_tolerance(torch, css, ctx):
     assert float(np.abs(got["P"] - ref["P"]).max()) < MIXED_P_TOL
 
 
+# ------------------------------------------- H' of a non-orthogonal basis (after Eq. 10)
+@pytest.mark.parametrize("n,kind,r_col,m,flags,prec", [(64, "minimal", 6.0, 10, 1, "fp64"),
+                                                        (125, "minimal", 9.0, 10, 0, "fp64"),
+                                                        (27, "dzp", 6.0, 6, 1, "fp64"),
+                                                        (125, "dzp", 9.0, 10, 1, "mixed")])
+def test_hprime_matches_oracle(torch, css, ctx, n, kind, r_col, m, flags, prec):
+    g = synth.water_box(n)
+    S = synth.overlap(g, kind)
+    H = synth.hamiltonian(g, kind)
+    col, nc = oracle.color(g.pos, g.box, r_col, 1004)
+    s = oracle.probes(col, S.b, 1005)
+    ref = oracle.hprime(S, H, col, s, nc, m=m, flags=flags)
+    Sd, Hd = css.DeviceBSR.from_host(S), css.DeviceBSR.from_host(H)
+    Si = torch.full((S.nnzb, S.b, S.b), float("nan"), dtype=torch.float64, device="cuda")
+    Hp = torch.full((H.nnzb, H.b, H.b), float("nan"), dtype=torch.float64, device="cuda")
+    p = css.CSS_FP64 if prec == "fp64" else css.CSS_MIXED_FP32
+    r = ctx.hprime(Sd, Hd, torch.as_tensor(col, device="cuda"), torch.as_tensor(s, device="cuda"), nc, Si, Hp,
+                   m=m, precision=p, flags=flags)
+    tol = FP64_TOL if prec == "fp64" else MIXED_P_TOL
+    scale = max(1.0, float(np.abs(ref["Hp"]).max()))
+    assert float(np.abs(Si.cpu().numpy() - ref["Sinv"]).max()) < tol
+    # mixed: Y is accumulated over m steps and H Y, S~^(-1/2) (H Y) are FP32 products; rounding
+    # of 2^-24 per operation grows as sqrt(m b (S and H neighbours)) ~ sqrt(10 * 23 * 50), i.e.
+    # about 6e-6 relative to the entries of H'
+    htol = FP64_TOL if prec == "fp64" else 5e-6
+    assert float(np.abs(Hp.cpu().numpy() - ref["Hp"]).max()) < htol * scale
+    assert abs(r["trHp"] - ref["trHp"]) < htol * scale * H.n_brow * H.b
+
+
 # ------------------------------------------------------------------ batch / pbuild
 def test_batch_equals_single(torch, css, ctx):
     systems = [_system(n, "minimal", 10.0) for n in (27, 64, 100)]
