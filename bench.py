@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-modes", action="store_true", help="skip the energy-weighted and S^-1/2 timings")
     return ap.parse_args()
 
 
@@ -319,6 +320,54 @@ def main():
                                 "dE_band_eV_per_molecule": abs(2 * (last_r["trPH"] - r64["trPH"])) / a.n_mol,
                                 "dTrP": last_r["trP"] - r64["trP"], "mu_fp64": r64["mu"],
                                 "note": "mixed P of the last timed geometry against the FP64 path on the same geometry"}
+    if rank == 0 and not a.no_modes:
+        # the other matrix functions of the library on the same workload, one build each
+        # (after a warm-up call): the energy-weighted density matrix and S^-1/2 of an overlap
+        t = my[n_steps - 1] % a.geometries
+        xyz, Hd = dev_in[t]
+        nc = ctx.color(xyz, geoms[t][0].box, a.r_col, 1004, colour)
+        ctx.probes(colour, Hd.b, 1005, sign)
+        PE = torch.empty_like(P[t])
+        ew = css.CSS_SYMMETRIZE | css.CSS_ENERGY_WEIGHTED
+        ctx.density(Hd, colour, sign, nc, PE, kT=0.05, n_elec=ne, m=a.m, precision=prec, flags=ew)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rE = ctx.density(Hd, colour, sign, nc, PE, kT=0.05, n_elec=ne, m=a.m, precision=prec, flags=ew)
+        torch.cuda.synchronize()
+        tE = time.perf_counter() - t0
+        del PE
+        S = synth.overlap(geoms[t][0], a.kind)
+        Sd = css.DeviceBSR.from_host(S, dev)
+        colS = torch.empty(a.n_mol, dtype=torch.int32, device=dev)
+        signS = torch.empty(a.n_mol * S.b, dtype=torch.int8, device=dev)
+        PS = torch.empty((S.nnzb, S.b, S.b), dtype=torch.float64, device=dev)
+        fl = css.CSS_SYMMETRIZE | css.CSS_INV_SQRT
+        ncS = ctx.color(xyz, geoms[t][0].box, 9.0, 1004, colS)
+        ctx.probes(colS, S.b, 1005, signS)
+        ctx.density(Sd, colS, signS, ncS, PS, m=10, precision=prec, flags=fl)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ncS = ctx.color(xyz, geoms[t][0].box, 9.0, 1004, colS)
+        ctx.probes(colS, S.b, 1005, signS)
+        rS = ctx.density(Sd, colS, signS, ncS, PS, m=10, precision=prec, flags=fl)
+        torch.cuda.synchronize()
+        tS = time.perf_counter() - t0
+        Hp = torch.empty_like(P[t])
+        ctx.hprime(Sd, Hd, colS, signS, ncS, PS, Hp, m=10, precision=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rH = ctx.hprime(Sd, Hd, colS, signS, ncS, PS, Hp, m=10, precision=prec)
+        torch.cuda.synchronize()
+        tH = time.perf_counter() - t0
+        line["modes"] = {
+            "energy_weighted": {"s_per_build": tE, "trace": rE["trP"],
+                                "note": "rho_E = f(H) H in each colour's Krylov subspace, same workload"},
+            "inv_sqrt_overlap": {"s_per_build": tS, "trace": rS["trP"], "n_colours": int(ncS),
+                                 "note": f"S^-1/2 of a synthetic {a.n_mol}-molecule overlap ({S.nnzb} blocks), "
+                                         "R_col^S = 9 A, Krylov depth 10, colour + probes + density"},
+            "hprime": {"s_per_call": tH, "trace": rH["trHp"],
+                       "note": "S~^-1/2 and H' (two-pass Lanczos on S keeping Y, H Y, S~^-1/2 H Y, extraction)"}}
+        del PS, Sd, Hp
     if not a.no_e2e:
         # end to end through css_pbuild with host buffers: pinned host inputs in, P out per step
         pin = {}
