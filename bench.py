@@ -368,6 +368,45 @@ def main():
             "hprime": {"s_per_call": tH, "trace": rH["trHp"],
                        "note": "S~^-1/2 and H' (two-pass Lanczos on S keeping Y, H Y, S~^-1/2 H Y, extraction)"}}
         del PS, Sd, Hp
+        # batched serving: 32 systems of uneven size (200-5000 molecules, log-uniform, minimal
+        # basis, R_col = 10 A, m = 30) in one css_density_batch call against one call each
+        sizes = synth.log_uniform_sizes(32)
+        sysd = []
+        for i, n_i in enumerate(sizes):
+            gi = synth.water_box(int(n_i), seed=1001 + i)
+            Hi = synth.hamiltonian(gi, "minimal")
+            sysd.append((gi, css.DeviceBSR.from_host(Hi, dev), torch.as_tensor(gi.pos, device=dev),
+                         torch.empty(int(n_i), dtype=torch.int32, device=dev),
+                         torch.empty(int(n_i) * Hi.b, dtype=torch.int8, device=dev),
+                         torch.empty((Hi.nnzb, Hi.b, Hi.b), dtype=torch.float64, device=dev)))
+
+        def batched():
+            ncs = [ctx.color(x, gi.box, 10.0, 1004, ci) for gi, Hd_i, x, ci, si, Pi in sysd]
+            for (gi, Hd_i, x, ci, si, Pi) in sysd:
+                ctx.probes(ci, Hd_i.b, 1005, si)
+            fs = [{"kT": 0.05, "n_elec": synth.n_electrons(gi.n_mol), "solve_mu": True} for gi, *_ in sysd]
+            ctx.density_batch([d[1] for d in sysd], [d[3] for d in sysd], [d[4] for d in sysd], ncs,
+                              [d[5] for d in sysd], fs, m=30, precision=prec)
+
+        def one_by_one():
+            for gi, Hd_i, x, ci, si, Pi in sysd:
+                nci = ctx.color(x, gi.box, 10.0, 1004, ci)
+                ctx.probes(ci, Hd_i.b, 1005, si)
+                ctx.density(Hd_i, ci, si, nci, Pi, kT=0.05, n_elec=synth.n_electrons(gi.n_mol), m=30, precision=prec)
+
+        times = {}
+        for name, fn in (("batched", batched), ("one_by_one", one_by_one)):
+            fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            times[name] = time.perf_counter() - t0
+        line["modes"]["batch_32_systems"] = {
+            "batched_s": times["batched"], "one_by_one_s": times["one_by_one"],
+            "molecules": int(sizes.sum()), "sizes_min_max": [int(sizes.min()), int(sizes.max())],
+            "note": "32 systems, 6 orbitals, R_col 10 A, m 30: css_density_batch vs css_density per system"}
+        del sysd
     if not a.no_e2e:
         # end to end through css_pbuild with host buffers: pinned host inputs in, P out per step
         pin = {}

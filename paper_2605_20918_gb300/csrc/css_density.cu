@@ -817,23 +817,32 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   CSS_TRY(ws_get(ctx, "e_flag", (size_t)n_col * nmax, &ea.flag));
   double* Z;
   CSS_TRY(ws_get(ctx, "Z", (size_t)n_col * nmax * b, &Z));
-  // Krylov vectors: as many colours per batch as memory allows
+  // Krylov vectors.  The combined matrix of a batch is block-diagonal by system, so each
+  // system's colours are run on that system's rows only (per-system passes); the blocks are
+  // sized for the largest system, with as many of its colours per pass as memory allows.
+  int64_t Nmax = 0;
+  int32_t ncmax = 0;
+  for (int32_t s = 0; s < n_sys; ++s) {
+    Nmax = std::max(Nmax, (int64_t)sys[s].H.n_brow * b);
+    ncmax = std::max(ncmax, sys[s].n_colours);
+  }
   size_t free_b = 0, total_b = 0;
   CSS_CU(ctx, cudaMemGetInfo(&free_b, &total_b));
-  int32_t ncb = n_col;
+  int32_t ncb = ncmax;
   auto vec_need = [&](int32_t k) -> size_t {
     const int32_t ws = (int32_t)css_ceil_div((int64_t)k * b, 8) * 8;
-    return 3 * (size_t)N * ws * s_vec + css_lanczos_part_doubles(N, b, k) * 8 * 2 + css_lanczos_small_doubles(b, k) * 8;
+    return 3 * (size_t)Nmax * ws * s_vec + css_lanczos_part_doubles(Nmax, b, k) * 8 * 2 +
+           css_lanczos_small_doubles(b, k) * 8;
   };
   const size_t reserve = (size_t)2 << 30;
   while (ncb > 1 && vec_need(ncb) + reserve > free_b) ncb = (ncb + 1) / 2;
   const int32_t ws = (int32_t)css_ceil_div((int64_t)ncb * b, 8) * 8;
   void *Q0, *Q1, *Wv;
   double *part, *small;
-  CSS_TRY(css_ws(ctx, "Q0", (size_t)N * ws * s_vec, &Q0));
-  CSS_TRY(css_ws(ctx, "Q1", (size_t)N * ws * s_vec, &Q1));
-  CSS_TRY(css_ws(ctx, "W", (size_t)N * ws * s_vec, &Wv));
-  CSS_TRY(ws_get(ctx, "lz_part", css_lanczos_part_doubles(N, b, ncb) * 2, &part));
+  CSS_TRY(css_ws(ctx, "Q0", (size_t)Nmax * ws * s_vec, &Q0));
+  CSS_TRY(css_ws(ctx, "Q1", (size_t)Nmax * ws * s_vec, &Q1));
+  CSS_TRY(css_ws(ctx, "W", (size_t)Nmax * ws * s_vec, &Wv));
+  CSS_TRY(ws_get(ctx, "lz_part", css_lanczos_part_doubles(Nmax, b, ncb) * 2, &part));
   CSS_TRY(ws_get(ctx, "lz_small", css_lanczos_small_doubles(b, ncb), &small));
 
   LzArgs la;
@@ -881,21 +890,30 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     for (auto& e : evs) cudaEventCreate(&e);
   }
   double spmm_ms = 0.0;
+  const int32_t BMh = css_spmm_bm(b);
   auto run_batches = [&](int mode) -> css_status {
     la.mode = mode;
-    for (int32_t cb0 = 0; cb0 < n_col; cb0 += ncb) {
-      la.cb0 = cb0;
-      la.ncb = min(ncb, n_col - cb0);
-      la.w = la.ncb * b;
-      la.ev_spmm = ctx->timing ? evs.data() : nullptr;
-      CSS_TRY(css_lanczos_pass(ctx, la, st));
-      if (ctx->timing) {
-        CSS_CU(ctx, cudaStreamSynchronize(st));
-        for (int32_t j = 0; j < m; ++j) {
-          float t = 0.f;
-          if (cudaEventElapsedTime(&t, evs[2 * j], evs[2 * j + 1]) == cudaSuccess) {
-            spmm_ms += t;
-            ++n_spmm;
+    for (int32_t s = 0; s < n_sys; ++s) {
+      la.row0 = row_off[s];
+      la.n_brow = sys[s].H.n_brow;
+      la.row_ptr = row_ptr + row_off[s];
+      la.colour = colour + row_off[s];
+      la.sign = sign + (size_t)row_off[s] * b;
+      la.Hlo_diag = Hlo ? (const void*)((const char*)Hlo + (size_t)row_off[s] * BMh * BMh * s_vec) : nullptr;
+      for (int32_t cb0 = col_off[s]; cb0 < col_off[s + 1]; cb0 += ncb) {
+        la.cb0 = cb0;
+        la.ncb = min(ncb, col_off[s + 1] - cb0);
+        la.w = la.ncb * b;
+        la.ev_spmm = ctx->timing ? evs.data() : nullptr;
+        CSS_TRY(css_lanczos_pass(ctx, la, st));
+        if (ctx->timing) {
+          CSS_CU(ctx, cudaStreamSynchronize(st));
+          for (int32_t j = 0; j < m; ++j) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, evs[2 * j], evs[2 * j + 1]) == cudaSuccess) {
+              spmm_ms += t;
+              ++n_spmm;
+            }
           }
         }
       }

@@ -57,7 +57,7 @@ template <typename T, int BM, int TC, int NT>
 __global__ void __launch_bounds__(NT) k_spmm(int32_t b, const int32_t* __restrict__ row_ptr,
                                               const int32_t* __restrict__ col_idx, const T* __restrict__ Ht,
                                               const T* __restrict__ V, T* __restrict__ W, int32_t ws, int32_t w,
-                                              const T* __restrict__ Hlo_t) {
+                                              const T* __restrict__ Hlo_t, int32_t jbase) {
   using C = SpmmCfg<T, BM, TC, NT>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int32_t I = blockIdx.x;
@@ -89,14 +89,14 @@ __global__ void __launch_bounds__(NT) k_spmm(int32_t b, const int32_t* __restric
 #pragma unroll
     for (int u = 0; u < TC; ++u) acc[a][u] = T(0);
   if (nsteps > 0) {
-    int32_t Jn = p0 < p1 ? col_idx[p0] : I;
+    int32_t Jn = p0 < p1 ? col_idx[p0] - jbase : I;
     issue(0, Jn, 0);
-    Jn = (1 < p1 - p0) ? col_idx[p0 + 1] : I;
+    Jn = (1 < p1 - p0) ? col_idx[p0 + 1] - jbase : I;
     for (int32_t q = 0; q < nsteps; ++q) {
       const int s = q & 1;
       if (q + 1 < nsteps) {
         issue(q + 1, Jn, s ^ 1);
-        Jn = (q + 2 < p1 - p0) ? col_idx[p0 + q + 2] : I;  // its latency overlaps the multiply
+        Jn = (q + 2 < p1 - p0) ? col_idx[p0 + q + 2] - jbase : I;  // its latency overlaps the multiply
         cp_async_wait<1>();
       } else {
         cp_async_wait<0>();
@@ -729,12 +729,12 @@ __global__ void k_init_q1(int32_t n_brow, int32_t b, int32_t ws, int32_t cb0, in
 template <typename T>
 __global__ void k_scatter(int64_t p_begin, int64_t p_end, int32_t b, int32_t ws, int32_t cb0, int32_t m, int32_t j,
                           const int32_t* __restrict__ pair_I, const int32_t* __restrict__ pair_c,
-                          const T* __restrict__ Q, T* __restrict__ Qs) {
+                          const T* __restrict__ Q, T* __restrict__ Qs, int32_t ibase) {
   const int64_t p = p_begin + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (p >= p_end) return;
   const int32_t bb = b * b;
-  const int32_t I = pair_I[p], c = pair_c[p] - cb0;
+  const int32_t I = pair_I[p] - ibase, c = pair_c[p] - cb0;
   const T* q = Q + (size_t)I * b * ws + (size_t)c * b;
   T* o = Qs + ((size_t)p * m + j) * bb;
   for (int32_t e = lane; e < bb; e += 32) {
@@ -767,13 +767,13 @@ template <typename T>
 __global__ void k_accum_x(int64_t p_begin, int64_t p_end, int32_t b, int32_t ws, int32_t cb0, int32_t ldz,
                           int32_t j, const int32_t* __restrict__ pair_I, const int32_t* __restrict__ pair_c,
                           const int32_t* __restrict__ nblk, const T* __restrict__ Q, const double* __restrict__ Z,
-                          double* __restrict__ X) {
+                          double* __restrict__ X, int32_t ibase) {
   const int32_t bb = b * b;
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t p = p_begin + t / bb;
   if (p >= p_end) return;
   int32_t e = (int32_t)(t % bb), a = e / b, kk = e % b;
-  int32_t I = pair_I[p], cg = pair_c[p], c = cg - cb0;
+  int32_t I = pair_I[p] - ibase, cg = pair_c[p], c = cg - cb0;
   if (j >= nblk[cg]) return;
   const T* q = Q + ((size_t)I * b + a) * ws + (size_t)c * b;
   const double* z = Z + ((size_t)cg * ldz + (size_t)j * b) * b + kk;
@@ -796,7 +796,7 @@ css_status launch_spmm_t(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaSt
   CSS_TRY(smem_optin(ctx, kern, C::smem));
   dim3 grid((unsigned)a.n_brow, (unsigned)css_ceil_div(a.w, C::CT));
   kern<<<grid, C::NT, C::smem, st>>>(a.b, a.row_ptr, a.col_idx, (const T*)a.Hval, V, W, a.ws, a.w,
-                                     (const T*)a.Hlo_diag);
+                                     (const T*)a.Hlo_diag, a.row0);
   CSS_LAUNCHED(ctx);
   return CSS_OK;
 }
@@ -916,10 +916,11 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
     if (pe <= pb) return CSS_OK;
     if (a.mode == 1) {
       k_scatter<T><<<(unsigned)css_ceil_div((pe - pb) * 32, 256), 256, 0, st>>>(pb, pe, b, a.ws, a.cb0, m, j,
-                                                                                a.pair_I, a.pair_c, Qj, (T*)a.Qs);
+                                                                                a.pair_I, a.pair_c, Qj, (T*)a.Qs,
+                                                                                a.row0);
     } else if (a.mode == 2) {
       k_accum_x<T><<<sblocks, 256, 0, st>>>(pb, pe, b, a.ws, a.cb0, a.ldz, j, a.pair_I, a.pair_c, a.nblk, Qj, a.Z,
-                                            a.X);
+                                            a.X, a.row0);
     } else {
       return CSS_OK;
     }

@@ -5,6 +5,9 @@
 struct LzArgs {
   bool fp32 = false;                 // Krylov vectors and H*V in FP32 (else FP64)
   int32_t n_brow = 0, b = 0, m = 0;  // molecules, block width, block steps
+  int32_t row0 = 0;                  // first block row of this pass in the combined numbering of a
+                                     // batch (row_ptr, colour, sign, Hlo_diag already offset by it;
+                                     // column indices and pair molecules are global: minus row0)
   int32_t w = 0, ws = 0;             // columns of the batch (b * ncb) and row stride
   const int32_t* row_ptr = nullptr;
   const int32_t* col_idx = nullptr;
