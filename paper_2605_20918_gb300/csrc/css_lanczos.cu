@@ -343,14 +343,36 @@ struct GramAcc<float> {
   __device__ __forceinline__ double get(int i) const { return (double)hi[i] + (double)lo[i]; }
 };
 
+// Gram block of thread t: (g, bi, bj) over all CB x CB blocks, or with SYM (X = Y, a symmetric
+// Gram) over the CB (CB + 1) / 2 blocks with bi <= bj only
+template <int CB, bool SYM>
+__device__ __forceinline__ bool gram_block(int32_t t, int32_t G, int32_t& g, int32_t& bi, int32_t& bj) {
+  constexpr int NB = SYM ? CB * (CB + 1) / 2 : CB * CB;
+  if (t >= G * NB) return false;
+  g = t / NB;
+  int32_t q = t - g * NB;
+  if (!SYM) {
+    bi = q / CB;
+    bj = q - bi * CB;
+    return true;
+  }
+  bi = 0;
+  while (q >= CB - bi) {  // row bi holds the blocks bj = bi .. CB-1
+    q -= CB - bi;
+    ++bi;
+  }
+  bj = bi + q;
+  return true;
+}
+
 // acc[i][j] += sum_r X[r][g][4bi+i] Y[r][g][4bj+j] for this thread's block (g, bi, bj)
-template <typename T, int BP>
+template <typename T, int BP, bool SYM = false>
 __device__ __forceinline__ void tile_gram(const RowCtx<T, BP>& c, const T* X, const T* Y, int32_t rtl,
                                           GramAcc<T>& acc, int32_t t) {
   constexpr int CS = ColStride<BP>::CS;
   constexpr int CB = BP / 4;
-  if (t >= c.G * CB * CB) return;
-  const int32_t g = t / (CB * CB), rem = t - g * CB * CB, bi = rem / CB, bj = rem - bi * CB;
+  int32_t g, bi, bj;
+  if (!gram_block<CB, SYM>(t, c.G, g, bi, bj)) return;
   const T* xp = X + g * CS + bi * 4;
   const T* yp = Y + g * CS + bj * 4;
   T a[4][4] = {};
@@ -372,12 +394,12 @@ __device__ __forceinline__ void tile_gram(const RowCtx<T, BP>& c, const T* X, co
     for (int j = 0; j < 4; ++j) acc.add(i * 4 + j, a[i][j]);
 }
 
-template <typename T, int BP>
+template <typename T, int BP, bool SYM = false>
 __device__ __forceinline__ void gram_store(const RowCtx<T, BP>& c, const GramAcc<T>& acc, double* part,
                                            int32_t t) {
   constexpr int CB = BP / 4;
-  if (t >= c.G * CB * CB) return;
-  const int32_t g = t / (CB * CB), rem = t - g * CB * CB, bi = rem / CB, bj = rem - bi * CB;
+  int32_t g, bi, bj;
+  if (!gram_block<CB, SYM>(t, c.G, g, bi, bj)) return;
   if (g >= c.gcount) return;
   double* o = part + (size_t)(c.cg0 + g) * c.b * c.b;
 #pragma unroll
@@ -385,7 +407,11 @@ __device__ __forceinline__ void gram_store(const RowCtx<T, BP>& c, const GramAcc
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int32_t k = bi * 4 + i, l = bj * 4 + j;
-      if (k < c.b && l < c.b) o[k * c.b + l] = acc.get(i * 4 + j);
+      if (k < c.b && l < c.b) {
+        const double v = acc.get(i * 4 + j);
+        o[k * c.b + l] = v;
+        if (SYM && bi != bj) o[l * c.b + k] = v;  // the mirrored block of a symmetric Gram
+      }
     }
 }
 
@@ -519,9 +545,9 @@ __global__ void __launch_bounds__(2 * RW, 1)
         tile_mul<T, BP, true, REORTH>(c, ring.at(s, 0), sM1, sW, RTL, ring.at(s, 1), sM2);
         __syncthreads();
         c.store(W, sW, r0, nr);
-        tile_gram<T, BP>(c, sW, sW, RTL, acc, threadIdx.x);
+        tile_gram<T, BP, true>(c, sW, sW, RTL, acc, threadIdx.x);
       });
-  gram_store<T, BP>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b, threadIdx.x);
+  gram_store<T, BP, true>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b, threadIdx.x);
 }
 
 // OUT = W R^-1 (R^-1 upper triangular per colour); partial Gram of OUT when GRAM.  OUT may be W.
@@ -549,9 +575,9 @@ __global__ void __launch_bounds__(384, 2)
         tile_mul<T, BP, false, false>(c, ring.at(s, 0), sR, sO, RTL, nullptr, nullptr);
         __syncthreads();
         c.store(OUT, sO, r0, nr);
-        if (GRAM) tile_gram<T, BP>(c, sO, sO, RTL, acc, threadIdx.x);
+        if (GRAM) tile_gram<T, BP, true>(c, sO, sO, RTL, acc, threadIdx.x);
       });
-  if (GRAM) gram_store<T, BP>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b, threadIdx.x);
+  if (GRAM) gram_store<T, BP, true>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b, threadIdx.x);
 }
 
 // out[lc][e] = sum over chunks of part[ch][lc][e], fixed order, FP64
