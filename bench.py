@@ -33,7 +33,7 @@ ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 METRIC = "P build s/step at 10k H2O"
-SPMM_KERNEL_VERSION = "k_spmm-cpasync-v3"  # profiles/spmm_traffic.json must name the kernel measured
+SPMM_KERNEL_VERSION = "k_spmm-f32x2-v4"  # profiles/spmm_traffic.json must name the kernel measured
 FP32_PEAK_NOTE = "FP32 FFMA peak derived from 152 SMs x 128 lanes x 2 flop x 2070 MHz max SM clock"
 FP64_PEAK_NOTE = "FP64 peak: 1.25 TFLOP/s nominal GB300 FP64 rate"
 FP32_PEAK = 152 * 128 * 2 * 2070e6 / 1e12       # TFLOP/s

@@ -83,9 +83,20 @@ __global__ void __launch_bounds__(NT) k_spmm(int32_t b, const int32_t* __restric
       cp_async_chunk<C::CH>(vd + (size_t)k * C::CT, vsrc + (size_t)(k < b ? k : 0) * ws, k < b ? cbytes : 0);
     cp_async_commit();
   };
-  T acc[BM][TC];
+  // FP32: accumulators packed in pairs of adjacent rows (a, a+1) and updated with the packed
+  // FMA fma.rn.f32x2 (two IEEE round-to-nearest FMAs per instruction, element by element the
+  // same arithmetic as two scalar FMAs): the H pair comes from one 8-byte shared load, the V
+  // value is packed into both halves once per k.  FP64: one scalar FMA per element.
+  constexpr bool PACK = sizeof(T) == 4;
+  constexpr int AP = PACK ? BM / 2 : 1;
+  unsigned long long acc2[AP][TC];
+  T acc[PACK ? 1 : BM][TC];
 #pragma unroll
-  for (int a = 0; a < BM; ++a)
+  for (int a = 0; a < AP; ++a)
+#pragma unroll
+    for (int u = 0; u < TC; ++u) acc2[a][u] = 0ull;
+#pragma unroll
+  for (int a = 0; a < (PACK ? 1 : BM); ++a)
 #pragma unroll
     for (int u = 0; u < TC; ++u) acc[a][u] = T(0);
   if (nsteps > 0) {
@@ -105,16 +116,35 @@ __global__ void __launch_bounds__(NT) k_spmm(int32_t b, const int32_t* __restric
       if (warp_live) {
         const T* hs = stage_h(s);
         const T* vs = stage_v(s) + TC * t;
+        if constexpr (PACK) {
 #pragma unroll 4
-        for (int k = 0; k < BM; ++k) {
-          T v[TC];
+          for (int k = 0; k < BM; ++k) {
+            unsigned long long vv[TC];
 #pragma unroll
-          for (int u = 0; u < TC; ++u) v[u] = vs[(size_t)k * C::CT + u];
+            for (int u = 0; u < TC; ++u) {
+              const float x = (float)vs[(size_t)k * C::CT + u];
+              asm("mov.b64 %0, {%1, %1};" : "=l"(vv[u]) : "f"(x));
+            }
+            const unsigned long long* hp = reinterpret_cast<const unsigned long long*>(hs + k * BM);
 #pragma unroll
-          for (int a = 0; a < BM; ++a) {
-            const T h = hs[k * BM + a];
+            for (int a = 0; a < AP; ++a) {
+              const unsigned long long h2 = hp[a];
 #pragma unroll
-            for (int u = 0; u < TC; ++u) acc[a][u] = fma(h, v[u], acc[a][u]);
+              for (int u = 0; u < TC; ++u) asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc2[a][u]) : "l"(h2), "l"(vv[u]));
+            }
+          }
+        } else {
+#pragma unroll 4
+          for (int k = 0; k < BM; ++k) {
+            T v[TC];
+#pragma unroll
+            for (int u = 0; u < TC; ++u) v[u] = vs[(size_t)k * C::CT + u];
+#pragma unroll
+            for (int a = 0; a < BM; ++a) {
+              const T h = hs[k * BM + a];
+#pragma unroll
+              for (int u = 0; u < TC; ++u) acc[a][u] = fma(h, v[u], acc[a][u]);
+            }
           }
         }
       }
@@ -123,22 +153,30 @@ __global__ void __launch_bounds__(NT) k_spmm(int32_t b, const int32_t* __restric
   }
   if (col >= w) return;
   T* Wr = W + (size_t)I * b * ws + col;
+  auto out = [&](int a, int u) -> T {
+    if constexpr (PACK) {
+      const unsigned long long x = acc2[a >> 1][u];
+      return (T)__uint_as_float((unsigned)((a & 1) ? (x >> 32) : (x & 0xffffffffull)));
+    } else {
+      return acc[a][u];
+    }
+  };
 #pragma unroll
   for (int a = 0; a < BM; ++a) {
     if (a >= b) break;
     if (cbytes == C::CH) {
       if constexpr (C::CH == 16 && sizeof(T) == 4) {
-        *reinterpret_cast<float4*>(Wr + (size_t)a * ws) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+        *reinterpret_cast<float4*>(Wr + (size_t)a * ws) = make_float4(out(a, 0), out(a, 1), out(a, 2), out(a, 3));
       } else if constexpr (C::CH == 16) {
-        *reinterpret_cast<double2*>(Wr + (size_t)a * ws) = make_double2(acc[a][0], acc[a][1]);
+        *reinterpret_cast<double2*>(Wr + (size_t)a * ws) = make_double2(out(a, 0), out(a, 1));
       } else {
 #pragma unroll
-        for (int u = 0; u < TC; ++u) Wr[(size_t)a * ws + u] = acc[a][u];
+        for (int u = 0; u < TC; ++u) Wr[(size_t)a * ws + u] = out(a, u);
       }
     } else {
 #pragma unroll
       for (int u = 0; u < TC; ++u)
-        if (col + u < w) Wr[(size_t)a * ws + u] = acc[a][u];
+        if (col + u < w) Wr[(size_t)a * ws + u] = out(a, u);
     }
   }
 }
