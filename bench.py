@@ -70,7 +70,8 @@ def workload_config(a):
 def l2_note(H):
     gb = H.nnzb * H.b * H.b * 8 / 1e9
     return (f"inputs larger than L2: H alone is {gb:.2f} GB in FP64 and every Krylov block "
-            f"{H.n_brow * H.b * 4 / 1e6:.0f} MB per colour in FP32, against a 129 MB L2")
+            f"{H.n_brow * H.b * H.b * 4 / 1e6:.0f} MB per colour in FP32 (the Lanczos step streams three "
+            f"such blocks for every colour of the system), against a 129 MB L2")
 
 
 class ClockSampler:
