@@ -52,6 +52,7 @@ def _load():
         lib.css_ref_free.argtypes = [p]
         lib.css_ref_color_graph.argtypes = [i32, p, p, u64, p, p]
         lib.css_ref_color.argtypes = [i32, p, f64, f64, u64, p, p]
+        lib.css_ref_color_conflicts.argtypes = [i32, p, f64, f64, p, p]
         lib.css_ref_probes.argtypes = [p, i32, i32, u64, C.c_int, p]
         lib.css_ref_eigh.argtypes = [i32, p, p]
         lib.css_ref_lanczos.argtypes = [i32, i32, p, p, p, p, p, i32, i32, C.c_int, p, p, p]
@@ -114,6 +115,30 @@ def color(xyz, box: float, r_col: float, seed: int):
     nc = np.zeros(1, dtype=np.int32)
     _chk(lib.css_ref_color(n, _ptr(xyz), box, r_col, seed, _ptr(col), _ptr(nc)), "color")
     return col, int(nc[0])
+
+
+def color_conflicts(xyz, box: float, r_col: float, colour) -> int:
+    """Same-coloured pairs closer than r_col (the colour-graph rule, brute force)."""
+    lib = _load()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    colour = np.ascontiguousarray(colour, dtype=np.int32)
+    if colour.shape[0] != xyz.shape[0]:
+        raise ValueError("one colour per molecule")
+    k = np.zeros(1, dtype=np.int64)
+    _chk(lib.css_ref_color_conflicts(xyz.shape[0], _ptr(xyz), box, r_col, _ptr(colour), _ptr(k)), "color_conflicts")
+    return int(k[0])
+
+
+def color_update(xyz, box: float, r_col: float, seed: int, colour, n_colours: int):
+    """Keep (colour, n_colours) when it has no conflict on this geometry, else recolour from
+    scratch: returns (colour, n_colours, recoloured)."""
+    colour = np.ascontiguousarray(colour, dtype=np.int32)
+    ok = (n_colours >= 1 and colour.size == len(xyz) and colour.min(initial=0) >= 0
+          and colour.max(initial=0) < n_colours and color_conflicts(xyz, box, r_col, colour) == 0)
+    if ok:
+        return colour.copy(), int(n_colours), False
+    col, nc = color(xyz, box, r_col, seed)
+    return col, nc, True
 
 
 def probes(colour, b: int, sign_seed: int, flags: int = 0):

@@ -9,6 +9,8 @@
  *
  *   colouring   greedy multicolouring: objects closer than the cut-off get different
  *               colours (paper, CSS construction paragraph after Eq. 2; Welsh-Powell order)
+ *   conflicts   same-coloured pairs closer than the cut-off on a new geometry (zero: the
+ *               colouring still satisfies that condition and can be kept across MD steps)
  *   probes      |r_i> = +-1 on the indices of colour i, 0 elsewhere (same paragraph, Fig. 1c)
  *   Lanczos     block-Lanczos (Golub-Underwood) basis of K^v(H, r) (paragraph after Eq. 4)
  *   rho^K       exact diagonalisation of the projected Hamiltonian, f(lambda) (Eq. 7)
@@ -187,6 +189,30 @@ int css_ref_color(int32_t n, const double* xyz, double box, double r_col, uint64
   free(adj);
   free(adj_ptr);
   return st;
+}
+
+/* Colouring conflicts on a (new) geometry: the number of unordered pairs {i, j} that share a
+ * colour although their minimum-image centre distance is < r_col, i.e. the edges of this
+ * geometry's colour graph that the colouring violates.  Zero means the colouring is still a
+ * valid distance-r_col colouring (the condition of the CSS construction paragraph after
+ * Eq. 2), so it may be kept from one MD step to the next.  Brute force over all pairs. */
+int css_ref_color_conflicts(int32_t n, const double* xyz, double box, double r_col, const int32_t* colour,
+                            int64_t* count) {
+  if (n < 0 || !(box > 0) || !(r_col >= 0) || !colour || !count) return REF_ERR_ARG;
+  int64_t Lq = ref_fixed(box), Rq = ref_fixed(r_col);
+  int64_t R2 = Rq * Rq;
+  int64_t k = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    for (int32_t j = i + 1; j < n; ++j) {
+      if (colour[i] != colour[j]) continue;
+      int64_t dx = ref_min_image(ref_fixed(xyz[3 * i]) - ref_fixed(xyz[3 * j]), Lq);
+      int64_t dy = ref_min_image(ref_fixed(xyz[3 * i + 1]) - ref_fixed(xyz[3 * j + 1]), Lq);
+      int64_t dz = ref_min_image(ref_fixed(xyz[3 * i + 2]) - ref_fixed(xyz[3 * j + 2]), Lq);
+      if (dx * dx + dy * dy + dz * dz < R2) ++k;
+    }
+  }
+  *count = k;
+  return REF_OK;
 }
 
 /* --------------------------------------------------------------- probes */

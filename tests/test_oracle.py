@@ -143,6 +143,83 @@ def test_lattice_colouring_valid_and_greedy(O):
     assert np.array_equal(col, col2)
 
 
+# --------------------------------------------------- colouring kept across MD steps
+def _pair_dists(x, L, pairs):
+    d = x[pairs[:, 0]] - x[pairs[:, 1]]
+    d -= L * np.round(d / L)
+    return np.sqrt((d * d).sum(1))
+
+
+def test_conflicts_match_periodic_kdtree(O):
+    """Same-coloured pairs closer than R_col on displaced geometries, counted independently
+    with scipy's periodic k-d tree on float distances (no pair lies within 1e-5 A of the
+    cut-off in these geometries, so float and fixed point agree on every pair)."""
+    spatial = pytest.importorskip("scipy.spatial")
+    R = 8.0
+    g0 = synth.water_box(400)
+    col, nc = O.color(g0.pos, g0.box, R, 1004)
+    counts = []
+    for sigma, seed in [(0.0, 0), (0.05, 3001), (0.3, 3002), (1.0, 3006)]:
+        g = synth.perturb(g0, seed, sigma=sigma) if sigma else g0
+        x = np.mod(g.pos, g.box)
+        pairs = spatial.cKDTree(x, boxsize=g.box).query_pairs(R + 1e-5, output_type="ndarray")
+        d = _pair_dists(x, g.box, pairs)
+        assert not np.any(np.abs(d - R) < 1e-5)
+        want = int(((col[pairs[:, 0]] == col[pairs[:, 1]]) & (d < R)).sum())
+        assert O.color_conflicts(g.pos, g.box, R, col) == want
+        counts.append(want)
+    # the colouring is valid on its own geometry and breaks as the displacements grow
+    assert counts[0] == 0 and counts[-1] > counts[1]
+
+
+def test_conflicts_brute_force_tiny(O):
+    rng = np.random.default_rng(11)
+    L, R, n = 15.0, 5.0, 40
+    x = rng.uniform(-2.0, L + 2.0, size=(n, 3))
+    d = np.array([[_min_image_dist(x[i], x[j], L) for j in range(n)] for i in range(n)])
+    iu = np.triu_indices(n, 1)
+    assert not np.any(np.abs(d[iu] - R) < 1e-5)
+    col = rng.integers(0, 4, size=n).astype(np.int32)
+    want = sum(1 for i in range(n) for j in range(i + 1, n) if col[i] == col[j] and d[i, j] < R)
+    assert O.color_conflicts(x, L, R, col) == want
+    # one colour: every edge of the colour graph is a conflict; all colours distinct: none
+    assert O.color_conflicts(x, L, R, np.zeros(n, np.int32)) == int((d[iu] < R).sum())
+    assert O.color_conflicts(x, L, R, np.arange(n, dtype=np.int32)) == 0
+    # R = 0: no pair is closer than 0
+    assert O.color_conflicts(x, L, 0.0, np.zeros(n, np.int32)) == 0
+
+
+def test_conflicts_strict_cutoff_and_minimum_image(O):
+    same = np.zeros(3, np.int32)
+    x = np.array([[1.0, 1.0, 1.0], [9.0, 1.0, 1.0], [1.0, 1.0, 8.999999]])
+    assert O.color_conflicts(x, 100.0, 8.0, same) == 1  # only (0, 2); (0, 1) is exactly R apart
+    y = np.array([[0.5, 0.5, 0.5], [9.5, 0.5, 0.5]])
+    assert O.color_conflicts(y, 10.0, 1.5, same[:2]) == 1  # 1 A apart across the boundary
+    assert O.color_conflicts(y, 10.0, 1.5, np.array([0, 1], np.int32)) == 0
+
+
+def test_color_update_keeps_valid_colourings(O):
+    R = 8.0
+    g0 = synth.water_box(216)
+    col, nc = O.color(g0.pos, g0.box, R, 1004)
+    # a small displacement that keeps the colouring valid: kept as it is
+    g1 = synth.perturb(g0, 3100, sigma=0.001)
+    assert O.color_conflicts(g1.pos, g1.box, R, col) == 0
+    c1, n1, re1 = O.color_update(g1.pos, g1.box, R, 1004, col, nc)
+    assert not re1 and n1 == nc and np.array_equal(c1, col)
+    # a large one breaks it: recoloured from scratch, exactly as a fresh colouring
+    g2 = synth.perturb(g0, 3101, sigma=1.0)
+    assert O.color_conflicts(g2.pos, g2.box, R, col) > 0
+    c2, n2, re2 = O.color_update(g2.pos, g2.box, R, 1004, col, nc)
+    fresh, nf = O.color(g2.pos, g2.box, R, 1004)
+    assert re2 and n2 == nf and np.array_equal(c2, fresh)
+    # no colouring yet (n_colours = 0) or colours out of range: recoloured
+    fresh1, nf1 = O.color(g1.pos, g1.box, R, 1004)
+    for bad_col, bad_nc in [(col, 0), (col, int(col.max())), (col - 1, nc)]:
+        c3, n3, re3 = O.color_update(g1.pos, g1.box, R, 1004, bad_col, bad_nc)
+        assert re3 and n3 == nf1 and np.array_equal(c3, fresh1)
+
+
 # ------------------------------------------------------------------- eigensolver
 @pytest.mark.parametrize("n", [1, 2, 3, 17, 120])
 def test_eigh_against_lapack(O, n):
