@@ -149,6 +149,34 @@ CSS_API css_status css_color(css_ctx* ctx, const css_geom* geom, double r_col, u
 CSS_API css_status css_color_graph(css_ctx* ctx, int32_t n, const int32_t* adj_ptr, const int32_t* adj, uint64_t seed,
                            int32_t* colour, int32_t* n_colours, void* stream);
 
+/* Conflicts of a colouring on a (new) geometry: the number of unordered molecule pairs
+ * {I, J} with colour[I] == colour[J] whose minimum-image centre distance is < r_col, in the
+ * same fixed-point arithmetic as css_color.  Zero means the colouring still meets the
+ * condition of the CSS construction (paragraph after Eq. 2) on this geometry, so it can be
+ * kept from one MD step to the next.
+ *   geom        as in css_color (xyz a DEVICE array)
+ *   colour      device int32[n_mol], read; values must lie in [0, n_colours)
+ *   n_conflicts host int64*, written (the call synchronises `stream`)
+ * Errors: INVALID_ARG for bad geometry or r_col (as css_color), n_colours < 1, or a colour
+ * outside [0, n_colours) (detected on the device). */
+CSS_API css_status css_color_check(css_ctx* ctx, const css_geom* geom, double r_col, const int32_t* colour,
+                           int32_t n_colours, int64_t* n_conflicts, void* stream);
+
+/* Colouring kept across MD steps: when *n_colours >= 1 and `colour` has no conflict at r_col
+ * on geom (css_color_check) and all its values lie in [0, *n_colours), nothing is written
+ * and *recoloured = 0; otherwise geom is coloured from scratch exactly as
+ * css_color(r_col + skin, seed) does, into colour and *n_colours, and *recoloured = 1.  A
+ * skin > 0 (like a neighbour-list skin) leaves same-coloured molecules room to move before
+ * the colouring has to change, at the price of more colours.  Pass *n_colours = 0 for the
+ * first step.
+ *   skin        Angstrom, >= 0
+ *   colour      device int32[n_mol], read and possibly written
+ *   n_colours   host int32*, read and possibly written
+ *   recoloured  host int32* or NULL
+ * Blocking like css_color.  No counterpart in the paper, which colours each geometry. */
+CSS_API css_status css_color_update(css_ctx* ctx, const css_geom* geom, double r_col, double skin, uint64_t seed,
+                            int32_t* colour, int32_t* n_colours, int32_t* recoloured, void* stream);
+
 /* ------------------------------------------------------------------- probes */
 /* CSS probe signs (paper: same paragraph, Fig. 1c): column k of colour c's probe block holds
  * sign[J*b+k] = +-1 on orbital k of every molecule J of colour c, 0 elsewhere.  sign is -1

@@ -129,15 +129,15 @@ def color_conflicts(xyz, box: float, r_col: float, colour) -> int:
     return int(k[0])
 
 
-def color_update(xyz, box: float, r_col: float, seed: int, colour, n_colours: int):
-    """Keep (colour, n_colours) when it has no conflict on this geometry, else recolour from
-    scratch: returns (colour, n_colours, recoloured)."""
+def color_update(xyz, box: float, r_col: float, seed: int, colour, n_colours: int, skin: float = 0.0):
+    """Keep (colour, n_colours) when it has no conflict at r_col on this geometry, else
+    recolour from scratch at r_col + skin: returns (colour, n_colours, recoloured)."""
     colour = np.ascontiguousarray(colour, dtype=np.int32)
     ok = (n_colours >= 1 and colour.size == len(xyz) and colour.min(initial=0) >= 0
           and colour.max(initial=0) < n_colours and color_conflicts(xyz, box, r_col, colour) == 0)
     if ok:
         return colour.copy(), int(n_colours), False
-    col, nc = color(xyz, box, r_col, seed)
+    col, nc = color(xyz, box, r_col + skin, seed)
     return col, nc, True
 
 

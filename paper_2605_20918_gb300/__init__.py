@@ -17,7 +17,7 @@ import numpy as np
 
 __all__ = [
     "CSSError", "Context", "DeviceBSR", "load_library", "library_path", "css_create", "css_destroy", "css_color",
-    "css_color_graph", "css_probes", "css_density", "css_density_batch", "css_pbuild", "css_get_info", "css_ritz", "css_projected", "css_eigen_blocks",
+    "css_color_graph", "css_color_check", "css_color_update", "css_probes", "css_density", "css_density_batch", "css_pbuild", "css_get_info", "css_ritz", "css_projected", "css_eigen_blocks",
     "CSS_OK", "CSS_WARN_BREAKDOWN", "CSS_FP64", "CSS_MIXED_FP32", "CSS_SYMMETRIZE", "CSS_TWO_PASS",
     "CSS_REORTH_LOCAL", "CSS_HOST_IO", "CSS_SIGNS_ONES", "CSS_ENERGY_WEIGHTED", "CSS_INV_SQRT",
 ]
@@ -87,6 +87,11 @@ def load_library(path: str | Path | None = None):
     lib.css_color.restype = st
     lib.css_color_graph.argtypes = [v, i32, v, v, u64, v, C.POINTER(C.c_int32), v]
     lib.css_color_graph.restype = st
+    lib.css_color_check.argtypes = [v, C.POINTER(_Geom), f64, v, i32, C.POINTER(C.c_int64), v]
+    lib.css_color_check.restype = st
+    lib.css_color_update.argtypes = [v, C.POINTER(_Geom), f64, f64, u64, v, C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_int32), v]
+    lib.css_color_update.restype = st
     lib.css_probes.argtypes = [v, v, i32, i32, u64, u32, v, v]
     lib.css_probes.restype = st
     lib.css_density.argtypes = [v, C.POINTER(_BSR), v, v, i32, C.POINTER(_Fermi), i32, st, u32, v,
@@ -213,6 +218,37 @@ def css_color_graph(ctx, adj_ptr, adj, seed: int, colour, stream=None) -> int:
                                          C.c_uint64(seed), _dev(colour, torch.int32, "colour"), C.byref(nc),
                                          _stream(stream)), "css_color_graph")
     return int(nc.value)
+
+
+def css_color_check(ctx, xyz, box: float, r_col: float, colour, n_colours: int, stream=None) -> int:
+    """Same-coloured molecule pairs closer than r_col on the geometry xyz (0: still valid)."""
+    torch = _torch()
+    lib = load_library()
+    g = _Geom(int(xyz.shape[0]), _dev(xyz, torch.float64, "xyz"), float(box))
+    if int(colour.numel()) != g.n_mol:
+        raise ValueError("css_color_check: one colour per molecule")
+    k = C.c_int64()
+    _check(lib, ctx, lib.css_color_check(ctx, C.byref(g), float(r_col), _dev(colour, torch.int32, "colour"),
+                                         int(n_colours), C.byref(k), _stream(stream)), "css_color_check")
+    return int(k.value)
+
+
+def css_color_update(ctx, xyz, box: float, r_col: float, seed: int, colour, n_colours: int, *, skin: float = 0.0,
+                     stream=None):
+    """Keep `colour` (device int32 [n]) when it has no conflict at r_col on xyz, else recolour
+    it in place at r_col + skin; n_colours = 0 means no colouring yet.  Returns
+    (n_colours, recoloured)."""
+    torch = _torch()
+    lib = load_library()
+    g = _Geom(int(xyz.shape[0]), _dev(xyz, torch.float64, "xyz"), float(box))
+    if int(colour.numel()) != g.n_mol:
+        raise ValueError("css_color_update: one colour per molecule")
+    nc = C.c_int32(int(n_colours))
+    re = C.c_int32(0)
+    _check(lib, ctx, lib.css_color_update(ctx, C.byref(g), float(r_col), float(skin), C.c_uint64(seed),
+                                          _dev(colour, torch.int32, "colour"), C.byref(nc), C.byref(re),
+                                          _stream(stream)), "css_color_update")
+    return int(nc.value), bool(re.value)
 
 
 def css_probes(ctx, colour, b: int, sign_seed: int, sign, flags: int = 0, stream=None) -> None:
@@ -389,6 +425,12 @@ class Context:
 
     def color_graph(self, *a, **k):
         return css_color_graph(self.handle, *a, **k)
+
+    def color_check(self, *a, **k):
+        return css_color_check(self.handle, *a, **k)
+
+    def color_update(self, *a, **k):
+        return css_color_update(self.handle, *a, **k)
 
     def probes(self, *a, **k):
         return css_probes(self.handle, *a, **k)

@@ -246,6 +246,119 @@ __global__ void k_probe_signs(int64_t count, uint64_t seed, int ones, int8_t* __
   sign[i] = ones ? (int8_t)1 : ((css_splitmix64(seed, (uint64_t)i) & 1ull) ? (int8_t)-1 : (int8_t)1);
 }
 
+// Molecule centres in fixed point, binned into a periodic grid of cells at least r_col wide
+// (about one molecule per cell; any coarser grid is also correct), members of each cell
+// sorted by id.  nc = 1 (one cell) when the box holds fewer than 3 cells per edge.
+struct CellList {
+  q4* q;
+  int32_t *cell, *cstart, *members;
+  int32_t nc;
+  int64_t Lq, R2;
+};
+
+css_status build_cells(css_ctx* ctx, int32_t n, const double* xyz, double box, double r_col, CellList* cl,
+                       cudaStream_t st) {
+  const int T = 256;
+  const unsigned nbk = (unsigned)css_ceil_div(n, T);
+  const int64_t Lq = llrint(box * (double)kFix);
+  const int64_t Rq = llrint(r_col * (double)kFix);
+  int64_t nc64 = Rq > 0 ? Lq / Rq : 1024;
+  int64_t nc_cap = (int64_t)cbrt((double)n) + 1;
+  if (nc64 > nc_cap) nc64 = nc_cap;
+  if (nc64 > 1024) nc64 = 1024;
+  const int32_t nc = nc64 < 3 ? 1 : (int32_t)nc64;
+  const int32_t ncells = nc >= 3 ? nc * nc * nc : 1;
+  int32_t *ccnt, *cfill;
+  CSS_TRY(css_ws(ctx, "col_q", sizeof(q4) * n, (void**)&cl->q));
+  CSS_TRY(css_ws(ctx, "col_cell", sizeof(int32_t) * n, (void**)&cl->cell));
+  CSS_TRY(css_ws(ctx, "col_ccnt", sizeof(int32_t) * (ncells + 1), (void**)&ccnt));
+  CSS_TRY(css_ws(ctx, "col_cstart", sizeof(int32_t) * (ncells + 1), (void**)&cl->cstart));
+  CSS_TRY(css_ws(ctx, "col_cfill", sizeof(int32_t) * (ncells + 1), (void**)&cfill));
+  CSS_TRY(css_ws(ctx, "col_members", sizeof(int32_t) * n, (void**)&cl->members));
+  k_quantise<<<nbk, T, 0, st>>>(n, xyz, Lq, nc, cl->q, cl->cell);
+  CSS_LAUNCHED(ctx);
+  CSS_CU(ctx, cudaMemsetAsync(ccnt, 0, sizeof(int32_t) * (ncells + 1), st));
+  CSS_CU(ctx, cudaMemsetAsync(cfill, 0, sizeof(int32_t) * (ncells + 1), st));
+  k_cell_count<<<nbk, T, 0, st>>>(n, cl->cell, ccnt);
+  CSS_LAUNCHED(ctx);
+  CSS_TRY(css_scan_i32(ctx, ccnt, cl->cstart, ncells, st));
+  k_cell_fill<<<nbk, T, 0, st>>>(n, cl->cell, cl->cstart, cfill, cl->members);
+  CSS_LAUNCHED(ctx);
+  k_cell_sort<<<(unsigned)css_ceil_div(ncells, T), T, 0, st>>>(ncells, cl->cstart, cl->members);
+  CSS_LAUNCHED(ctx);
+  cl->nc = nc;
+  cl->Lq = Lq;
+  cl->R2 = Rq * Rq;
+  return CSS_OK;
+}
+
+// Same-coloured pairs {i, j}, i < j, closer than r_col: thread i walks the 27 cells around
+// molecule i (or all molecules when there is one cell).  Colours outside [0, n_colours) set
+// *bad.  Per-warp sums are added into *count.
+__global__ void k_conflicts(int32_t n, const q4* __restrict__ q, const int32_t* __restrict__ cell, int32_t nc,
+                            const int32_t* __restrict__ cstart, const int32_t* __restrict__ members, int64_t Lq,
+                            int64_t R2, const int32_t* __restrict__ colour, int32_t n_colours,
+                            unsigned long long* __restrict__ count, int32_t* __restrict__ bad) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long k = 0;
+  if (i < n) {
+    const int32_t ci = colour[i];
+    if (ci < 0 || ci >= n_colours) atomicOr(bad, 1);
+    const q4 qi = q[i];
+    auto test = [&](int32_t j) {
+      if (j <= i || colour[j] != ci) return;
+      const q4 qj = q[j];
+      const int64_t dx = min_image(qi.x - qj.x, Lq), dy = min_image(qi.y - qj.y, Lq),
+                    dz = min_image(qi.z - qj.z, Lq);
+      if (dx * dx + dy * dy + dz * dz < R2) ++k;
+    };
+    if (nc < 3) {
+      for (int32_t j = i + 1; j < n; ++j) test(j);
+    } else {
+      const int32_t c = cell[i];
+      const int32_t cx = c / (nc * nc), cy = (c / nc) % nc, cz = c % nc;
+      for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dz = -1; dz <= 1; ++dz) {
+            const int32_t x = (cx + dx + nc) % nc, y = (cy + dy + nc) % nc, z = (cz + dz + nc) % nc;
+            const int32_t cc = (x * nc + y) * nc + z;
+            for (int32_t p = cstart[cc]; p < cstart[cc + 1]; ++p) test(members[p]);
+          }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+  if ((threadIdx.x & 31) == 0 && k) atomicAdd(count, k);
+}
+
+// conflicts of a colouring on a geometry (blocking); *bad = 1 when a colour is out of range
+css_status count_conflicts(css_ctx* ctx, const css_geom* geom, double r_col, const int32_t* colour,
+                           int32_t n_colours, int64_t* count, int32_t* bad, cudaStream_t st) {
+  const int32_t n = geom->n_mol;
+  CellList cl;
+  CSS_TRY(build_cells(ctx, n, geom->xyz, geom->box, r_col, &cl, st));
+  unsigned long long* dcount;
+  int32_t* dbad;
+  CSS_TRY(css_ws(ctx, "chk_count", 2 * sizeof(unsigned long long), (void**)&dcount));
+  dbad = (int32_t*)(dcount + 1);
+  CSS_CU(ctx, cudaMemsetAsync(dcount, 0, 2 * sizeof(unsigned long long), st));
+  k_conflicts<<<(unsigned)css_ceil_div(n, 256), 256, 0, st>>>(n, cl.q, cl.cell, cl.nc, cl.cstart, cl.members, cl.Lq,
+                                                               cl.R2, colour, n_colours, dcount, dbad);
+  CSS_LAUNCHED(ctx);
+  unsigned long long* h;
+  CSS_TRY(css_pinned(ctx, 64, (void**)&h));
+  CSS_CU(ctx, cudaMemcpyAsync(h, dcount, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CSS_CU(ctx, cudaStreamSynchronize(st));
+  *count = (int64_t)h[0];
+  *bad = *(const int32_t*)(h + 1) != 0 ? 1 : 0;
+  return CSS_OK;
+}
+
+css_status check_geom(css_ctx* ctx, const css_geom* geom, double r_col, const char* what) {
+  if (geom->n_mol < 1 || !(geom->box > 0.0) || geom->box > 1000.0 || !(r_col >= 0.0) || r_col > 1000.0)
+    return css_set_arg_error(ctx, what);
+  return CSS_OK;
+}
+
 }  // namespace
 
 // Colour either a geometry (xyz != nullptr) or an explicit CSR graph.
@@ -259,38 +372,13 @@ css_status css_color_impl(css_ctx* ctx, int32_t n, const double* xyz, double box
   int32_t* hbuf = nullptr;
   CSS_TRY(css_pinned(ctx, 64, (void**)&hbuf));
   if (xyz) {
-    const int64_t Lq = llrint(box * (double)kFix);
-    const int64_t Rq = llrint(r_col * (double)kFix);
-    const int64_t R2 = Rq * Rq;
-    // cells at least r_col wide (any coarser grid is also correct); about one molecule per cell
-    int64_t nc64 = Rq > 0 ? Lq / Rq : 1024;
-    int64_t nc_cap = (int64_t)cbrt((double)n) + 1;
-    if (nc64 > nc_cap) nc64 = nc_cap;
-    if (nc64 > 1024) nc64 = 1024;
-    int32_t nc = nc64 < 3 ? 1 : (int32_t)nc64;
-    const int32_t ncells = nc >= 3 ? nc * nc * nc : 1;
-    q4* q;
-    int32_t *cell, *ccnt, *cstart, *cfill, *members, *deg, *ptr;
-    CSS_TRY(css_ws(ctx, "col_q", sizeof(q4) * n, (void**)&q));
-    CSS_TRY(css_ws(ctx, "col_cell", sizeof(int32_t) * n, (void**)&cell));
-    CSS_TRY(css_ws(ctx, "col_ccnt", sizeof(int32_t) * (ncells + 1), (void**)&ccnt));
-    CSS_TRY(css_ws(ctx, "col_cstart", sizeof(int32_t) * (ncells + 1), (void**)&cstart));
-    CSS_TRY(css_ws(ctx, "col_cfill", sizeof(int32_t) * (ncells + 1), (void**)&cfill));
-    CSS_TRY(css_ws(ctx, "col_members", sizeof(int32_t) * n, (void**)&members));
+    CellList cl;
+    CSS_TRY(build_cells(ctx, n, xyz, box, r_col, &cl, st));
+    int32_t *deg, *ptr;
     CSS_TRY(css_ws(ctx, "col_deg", sizeof(int32_t) * (n + 1), (void**)&deg));
     CSS_TRY(css_ws(ctx, "col_adjptr", sizeof(int32_t) * (n + 1), (void**)&ptr));
-    k_quantise<<<nbk, T, 0, st>>>(n, xyz, Lq, nc, q, cell);
-    CSS_LAUNCHED(ctx);
-    CSS_CU(ctx, cudaMemsetAsync(ccnt, 0, sizeof(int32_t) * (ncells + 1), st));
-    CSS_CU(ctx, cudaMemsetAsync(cfill, 0, sizeof(int32_t) * (ncells + 1), st));
-    k_cell_count<<<nbk, T, 0, st>>>(n, cell, ccnt);
-    CSS_LAUNCHED(ctx);
-    CSS_TRY(css_scan_i32(ctx, ccnt, cstart, ncells, st));
-    k_cell_fill<<<nbk, T, 0, st>>>(n, cell, cstart, cfill, members);
-    CSS_LAUNCHED(ctx);
-    k_cell_sort<<<(unsigned)css_ceil_div(ncells, T), T, 0, st>>>(ncells, cstart, members);
-    CSS_LAUNCHED(ctx);
-    k_neighbours<0><<<nbk, T, 0, st>>>(n, q, cell, nc, cstart, members, Lq, R2, deg, nullptr, nullptr);
+    k_neighbours<0><<<nbk, T, 0, st>>>(n, cl.q, cl.cell, cl.nc, cl.cstart, cl.members, cl.Lq, cl.R2, deg, nullptr,
+                                       nullptr);
     CSS_LAUNCHED(ctx);
     CSS_TRY(css_scan_i32(ctx, deg, ptr, n, st));
     CSS_CU(ctx, cudaMemcpyAsync(hbuf, ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -298,7 +386,8 @@ css_status css_color_impl(css_ctx* ctx, int32_t n, const double* xyz, double box
     int64_t nadj = hbuf[0];
     int32_t* a;
     CSS_TRY(css_ws(ctx, "col_adj", sizeof(int32_t) * (nadj > 0 ? nadj : 1), (void**)&a));
-    k_neighbours<1><<<nbk, T, 0, st>>>(n, q, cell, nc, cstart, members, Lq, R2, nullptr, ptr, a);
+    k_neighbours<1><<<nbk, T, 0, st>>>(n, cl.q, cl.cell, cl.nc, cl.cstart, cl.members, cl.Lq, cl.R2, nullptr, ptr,
+                                       a);
     CSS_LAUNCHED(ctx);
     adj_ptr = ptr;
     adj = a;
@@ -354,6 +443,45 @@ css_status css_color_graph(css_ctx* ctx, int32_t n, const int32_t* adj_ptr, cons
   if (!ctx || !adj_ptr || !colour || !n_colours || n < 1) return css_set_arg_error(ctx, "css_color_graph: bad argument");
   CSS_CU(ctx, cudaSetDevice(ctx->device));
   return css_color_impl(ctx, n, nullptr, 0.0, 0.0, seed, adj_ptr, adj, colour, n_colours, (cudaStream_t)stream);
+}
+
+css_status css_color_check(css_ctx* ctx, const css_geom* geom, double r_col, const int32_t* colour,
+                           int32_t n_colours, int64_t* n_conflicts, void* stream) {
+  if (!ctx || !geom || !geom->xyz || !colour || !n_conflicts) return css_set_arg_error(ctx, "css_color_check: null pointer");
+  CSS_TRY(check_geom(ctx, geom, r_col, "css_color_check: n_mol < 1, box not in (0, 1000] or r_col not in [0, 1000]"));
+  if (n_colours < 1) return css_set_arg_error(ctx, "css_color_check: n_colours < 1");
+  CSS_CU(ctx, cudaSetDevice(ctx->device));
+  int64_t k = 0;
+  int32_t bad = 0;
+  CSS_TRY(count_conflicts(ctx, geom, r_col, colour, n_colours, &k, &bad, (cudaStream_t)stream));
+  if (bad) return css_set_arg_error(ctx, "css_color_check: colour outside [0, n_colours)");
+  *n_conflicts = k;
+  return CSS_OK;
+}
+
+css_status css_color_update(css_ctx* ctx, const css_geom* geom, double r_col, double skin, uint64_t seed,
+                            int32_t* colour, int32_t* n_colours, int32_t* recoloured, void* stream) {
+  if (!ctx || !geom || !geom->xyz || !colour || !n_colours) return css_set_arg_error(ctx, "css_color_update: null pointer");
+  if (!(skin >= 0.0)) return css_set_arg_error(ctx, "css_color_update: skin < 0");
+  CSS_TRY(check_geom(ctx, geom, r_col + skin,
+                     "css_color_update: n_mol < 1, box not in (0, 1000] or r_col + skin not in [0, 1000]"));
+  CSS_CU(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (*n_colours >= 1) {
+    int64_t k = 0;
+    int32_t bad = 0;
+    CSS_TRY(count_conflicts(ctx, geom, r_col, colour, *n_colours, &k, &bad, st));
+    if (k == 0 && !bad) {
+      if (recoloured) *recoloured = 0;
+      return CSS_OK;
+    }
+  }
+  int32_t nc = 0;
+  CSS_TRY(css_color_impl(ctx, geom->n_mol, geom->xyz, geom->box, r_col + skin, seed, nullptr, nullptr, colour, &nc,
+                         st));
+  *n_colours = nc;
+  if (recoloured) *recoloured = 1;
+  return CSS_OK;
 }
 
 css_status css_probes(css_ctx* ctx, const int32_t* colour, int32_t n_mol, int32_t b, uint64_t sign_seed,

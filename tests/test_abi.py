@@ -26,7 +26,8 @@ def declared_symbols():
 
 def test_header_declares_the_boundary():
     names = declared_symbols()
-    for want in ("css_create", "css_destroy", "css_color", "css_color_graph", "css_probes", "css_density",
+    for want in ("css_create", "css_destroy", "css_color", "css_color_graph", "css_color_check", "css_color_update",
+                 "css_probes", "css_density",
                  "css_density_batch", "css_pbuild", "css_get_info", "css_status_str", "css_last_error"):
         assert want in names
 

@@ -220,6 +220,25 @@ def test_color_update_keeps_valid_colourings(O):
         assert re3 and n3 == nf1 and np.array_equal(c3, fresh1)
 
 
+def test_color_update_with_a_skin(O):
+    """Recolouring at R_col + skin leaves room to move: on an MD-like walk of 0.02 A steps the
+    skinned colouring stays conflict-free at R_col for several steps, while a colouring at
+    R_col itself has conflicts after the first step (greedy colourings pack same-coloured
+    molecules just outside the cut-off)."""
+    R, skin = 8.0, 0.3
+    seq = list(synth.md_sequence(400, 6))
+    tight, _ = O.color(seq[0].pos, seq[0].box, R, 1004)
+    assert O.color_conflicts(seq[1].pos, seq[1].box, R, tight) > 0
+    col, nc, re = O.color_update(seq[0].pos, seq[0].box, R, 1004, np.zeros(400, np.int32), 0, skin=skin)
+    fresh, nf = O.color(seq[0].pos, seq[0].box, R + skin, 1004)
+    assert re and nc == nf and np.array_equal(col, fresh)
+    # a colouring at the larger radius is valid at the smaller one
+    assert O.color_conflicts(seq[0].pos, seq[0].box, R + skin, col) == 0
+    for g in seq[1:]:
+        c2, n2, re2 = O.color_update(g.pos, g.box, R, 1004, col, nc, skin=skin)
+        assert not re2 and n2 == nc and np.array_equal(c2, col)
+
+
 # ------------------------------------------------------------------- eigensolver
 @pytest.mark.parametrize("n", [1, 2, 3, 17, 120])
 def test_eigh_against_lapack(O, n):
