@@ -60,6 +60,8 @@ def _load():
                                         C.c_int, p, i32, p, p, p, p, p]
         lib.css_ref_ritz.argtypes = [i32, i32, p, p, p, p, p, i32, i32, C.c_int, p, p, p]
         lib.css_ref_hprime.argtypes = [i32, i32, i32, p, p, p, i32, p, p, p, p, p, i32, i32, C.c_int, p, p, p]
+        lib.css_ref_density_nonorth.argtypes = [i32, i32, i32, p, p, p, p, i32, p, p, p, p, p, p, i32, f64, f64,
+                                                f64, f64, C.c_int, i32, C.c_int, p, p, p, p, p]
         lib.css_ref_num_threads.restype = C.c_int
         _lib = lib
     return _lib
@@ -235,6 +237,31 @@ def hprime(S, H, colour, sign, n_colours: int, *, m: int = 10, flags: int = SYMM
                                 _ptr(hv), _ptr(colour), _ptr(sign), n_colours, m, flags, _ptr(Si), _ptr(Hp), _ptr(tr))
     _chk(st, "hprime")
     return {"Sinv": Si, "Hp": Hp, "trHp": float(tr[0])}
+
+
+def density_nonorth(S, Sinv, H, Hp, colour, sign, n_colours: int, *, mu: float = 0.0, kT: float = 0.05,
+                    n_elec: float = 0.0, solve_mu: bool = True, m: int = 30, flags: int = SYMMETRIZE,
+                    ne_tol: float = 0.0):
+    """Density matrix of a non-orthogonal basis from S~^(-1/2) (values Sinv on S's pattern) and
+    H' (values Hp on H's pattern), with Krylov spaces of H' started at S~^(-1/2) r_c; mu from the
+    electron count Tr(rho S).  Returns dict(P=(nnzb_H, b, b), trPS, trPH, mu, n_breakdown)."""
+    colour = np.ascontiguousarray(colour, dtype=np.int32)
+    sign = np.ascontiguousarray(sign, dtype=np.int8)
+    P = np.zeros((H.nnzb, H.b, H.b))
+    out = np.zeros(3)
+    nb = np.zeros(1, dtype=np.int32)
+    sr, sc, sv = (np.ascontiguousarray(S.row_ptr, dtype=np.int32), np.ascontiguousarray(S.col_idx, dtype=np.int32),
+                  np.ascontiguousarray(S.val, dtype=np.float64))
+    hr, hc, hv = (np.ascontiguousarray(H.row_ptr, dtype=np.int32), np.ascontiguousarray(H.col_idx, dtype=np.int32),
+                  np.ascontiguousarray(H.val, dtype=np.float64))
+    si = np.ascontiguousarray(Sinv, dtype=np.float64).reshape(S.nnzb, S.b, S.b)
+    hp = np.ascontiguousarray(Hp, dtype=np.float64).reshape(H.nnzb, H.b, H.b)
+    st = _load().css_ref_density_nonorth(
+        H.n_brow, H.b, S.nnzb, _ptr(sr), _ptr(sc), _ptr(sv), _ptr(si), H.nnzb, _ptr(hr), _ptr(hc), _ptr(hv),
+        _ptr(hp), _ptr(colour), _ptr(sign), n_colours, mu, kT, n_elec, ne_tol, int(bool(solve_mu)), m, flags,
+        _ptr(P), _ptr(out[0:1]), _ptr(out[1:2]), _ptr(out[2:3]), _ptr(nb))
+    _chk(st, "density_nonorth")
+    return {"P": P, "trPS": float(out[0]), "trPH": float(out[1]), "mu": float(out[2]), "n_breakdown": int(nb[0])}
 
 
 def num_threads() -> int:

@@ -16,6 +16,10 @@
  *   rho^K       exact diagonalisation of the projected Hamiltonian, f(lambda) (Eq. 7)
  *   extraction  rho~ = Phi rho^K <Phi|r><r| restricted to the sparse pattern (Eq. 2, Eq. 6)
  *   traces      Tr(P) and Tr(PH) = E_orbit (convergence study of Fig. 2 inset a)
+ *   S^(-1/2), H' the same projection applied to an overlap S with x^(-1/2) (Eq. 8-10), and H'
+ *               extracted from S~^(-1/2) H Y <o| (the paragraph after Eq. 10)
+ *   non-orthogonal density  rho~ = S~^(-1/2) Phi rho^K <Phi|r~><r| from Krylov spaces of H'
+ *               started at r~ = S~^(-1/2) r (Eq. 4-6 with S != I)
  *
  * Readings where the paper is silent (each one also listed in the design notes):
  *   - orthogonal basis, S = I, so H' = H and r~ = r (Eq. 4 with S = I);
@@ -43,6 +47,9 @@
  *     function is x^(-1/2) instead of f (the paper's S^(-1/2) step, Eq. 8-10: the same
  *     block-Lanczos projection onto coloured probes, exact diagonalisation of the projected
  *     S^K and its inverse square root); no mu, Tr returns Tr S~^(-1/2) and Tr(S~^(-1/2) S).
+ *   - non-orthogonal basis: the electron count is Tr(rho S) (Mulliken), evaluated as a
+ *     quadrature over the Ritz pairs of H' whose weights make it equal the extracted
+ *     Tr(rho~ S) exactly; mu is solved on it with the rule above.
  * Pins: the test-suite checks every function here against closed forms, dense
  * diagonalisation with LAPACK (numpy), brute force on tiny inputs and invariants; the
  * paper prints no worked numeric example, so agreement with the paper's own numbers is
@@ -426,7 +433,8 @@ typedef struct {
 } ref_h;
 
 /* Block-Lanczos for colour c (paper, paragraph after Eq. 4; Golub-Underwood):
- *   Q_1 = R_c / sqrt|c|, B_0 = sqrt|c| I, Q_0 = 0
+ *   Q_1 = R_c / sqrt|c|, B_0 = sqrt|c| I, Q_0 = 0  (or Q_1 = Q1start when it is given: the
+ *   orthonormal factor of a general start block, whose B_0 the caller keeps)
  *   W = H Q_j - Q_{j-1} B_{j-1}^T ;  A_j = sym(Q_j^T W) ;  W -= Q_j A_j
  *   W = Q_{j+1} B_j  (QR)
  * T (nmax x nmax, nmax = m b) receives the block-tridiagonal projected matrix
@@ -434,7 +442,7 @@ typedef struct {
  * If Zc != NULL (pass 2) X (N x b) accumulates sum_j Q_j Zc[j-th block rows]. */
 static int32_t ref_lanczos_colour(const ref_h* H, const int32_t* colour, const int8_t* sign, int32_t c,
                                   int32_t m, int flags, double* T, const double* Zc, double* X,
-                                  double* Qout) {
+                                  double* Qout, const double* Q1start) {
   const int32_t b = H->b;
   const int64_t N = (int64_t)H->n_brow * b;
   const int32_t nmax = m * b;
@@ -447,12 +455,16 @@ static int32_t ref_lanczos_colour(const ref_h* H, const int32_t* colour, const i
   double* R = (double*)malloc(sizeof(double) * b * b);
   double* C = (double*)malloc(sizeof(double) * b * b);
   double* v = (double*)malloc(sizeof(double) * (size_t)N);
-  int64_t cnt = 0;
-  for (int32_t J = 0; J < H->n_brow; ++J) cnt += (colour[J] == c);
-  double sq = sqrt((double)cnt);
-  for (int32_t J = 0; J < H->n_brow; ++J)
-    if (colour[J] == c)
-      for (int32_t k = 0; k < b; ++k) Qj[((size_t)J * b + k) * b + k] = sign[(size_t)J * b + k] / sq;
+  if (Q1start) {
+    memcpy(Qj, Q1start, sizeof(double) * (size_t)N * b);
+  } else {
+    int64_t cnt = 0;
+    for (int32_t J = 0; J < H->n_brow; ++J) cnt += (colour[J] == c);
+    double sq = sqrt((double)cnt);
+    for (int32_t J = 0; J < H->n_brow; ++J)
+      if (colour[J] == c)
+        for (int32_t k = 0; k < b; ++k) Qj[((size_t)J * b + k) * b + k] = sign[(size_t)J * b + k] / sq;
+  }
   if (T) memset(T, 0, sizeof(double) * (size_t)nmax * nmax);
   if (X) memset(X, 0, sizeof(double) * (size_t)N * b);
   int32_t used = 0;
@@ -543,7 +555,7 @@ int css_ref_lanczos(int32_t n_brow, int32_t b, const int32_t* row_ptr, const int
                     int flags, double* T, double* Q, int32_t* n_blocks) {
   if (n_brow < 1 || b < 1 || m < 1 || !T || !n_blocks) return REF_ERR_ARG;
   ref_h H = {n_brow, b, row_ptr, col_idx, val};
-  *n_blocks = ref_lanczos_colour(&H, colour, sign, c, m, flags, T, NULL, NULL, Q);
+  *n_blocks = ref_lanczos_colour(&H, colour, sign, c, m, flags, T, NULL, NULL, Q, NULL);
   return REF_OK;
 }
 
@@ -566,7 +578,7 @@ static int ref_colour_eigen(const ref_h* H, const int32_t* colour, const int8_t*
   const int32_t b = H->b, nmax = m * b;
   double* T = (double*)malloc(sizeof(double) * (size_t)nmax * nmax);
   if (!T) return REF_ERR_NOMEM;
-  int32_t blocks = ref_lanczos_colour(H, colour, sign, c, m, flags, T, NULL, NULL, NULL);
+  int32_t blocks = ref_lanczos_colour(H, colour, sign, c, m, flags, T, NULL, NULL, NULL, NULL);
   if (blocks < m) *breakdown = 1;
   int32_t n = blocks * b;
   for (int32_t i = 0; i < n; ++i)
@@ -580,6 +592,47 @@ static int ref_colour_eigen(const ref_h* H, const int32_t* colour, const int8_t*
   }
   *n_out = n;
   return st;
+}
+
+/* mu from a Ritz quadrature N(mu) = sum_t sum_j f(lam_tj; mu) wgt_tj (nj[t] pairs per colour,
+ * stride nmax): the midpoint of the interval where |N(mu) - N_e/2| <= ne_tol, each end found
+ * by bisection on [min lam - 1, max lam + 1] (lower end: smallest mu with N - N_e/2 >= -ne_tol;
+ * upper end: largest mu with N - N_e/2 <= +ne_tol) until hi - lo <= 1e-13 max(1, |mid|) or 200
+ * halvings.  For a metal both ends meet at the root; for an insulator the interval is the gap
+ * and mu lands mid-gap instead of at a band edge. */
+static double ref_solve_mu(int32_t nwork, const int32_t* nj, int32_t nmax, const double* lam, const double* wgt,
+                           double kT, double n_elec, double ne_tol) {
+  double lo0 = INFINITY, hi0 = -INFINITY;
+  for (int32_t t = 0; t < nwork; ++t)
+    for (int32_t j = 0; j < nj[t]; ++j) {
+      double x = lam[(size_t)t * nmax + j];
+      if (x < lo0) lo0 = x;
+      if (x > hi0) hi0 = x;
+    }
+  lo0 -= 1.0;
+  hi0 += 1.0;
+  double ends[2];
+  for (int side = 0; side < 2; ++side) {
+    double lo = lo0, hi = hi0;
+    for (int it = 0; it < 200; ++it) {
+      double mid = 0.5 * (lo + hi);
+      double g = 0.0;
+      for (int32_t t = 0; t < nwork; ++t)
+        for (int32_t j = 0; j < nj[t]; ++j)
+          g += ref_fermi(lam[(size_t)t * nmax + j], mid, kT) * wgt[(size_t)t * nmax + j];
+      g -= 0.5 * n_elec;
+      if (side == 0) {
+        if (g >= -ne_tol) hi = mid;
+        else lo = mid;
+      } else {
+        if (g <= ne_tol) lo = mid;
+        else hi = mid;
+      }
+      if (hi - lo <= 1e-13 * fmax(1.0, fabs(mid))) break;
+    }
+    ends[side] = 0.5 * (lo + hi);
+  }
+  return 0.5 * (ends[0] + ends[1]);
 }
 
 /* Full CSS density matrix on H's pattern.  colour_subset (n_subset entries) restricts the
@@ -626,44 +679,8 @@ int css_ref_density(int32_t n_brow, int32_t b, int32_t nnzb, const int32_t* row_
     free(U);
   }
   if (status != REF_OK) return status;
-  /* chemical potential from the Ritz quadrature N(mu) = sum_c sum_j f(lambda_cj; mu) w_cj:
-   * mu is the midpoint of the interval where |N(mu) - N_e/2| <= ne_tol, found by two
-   * bisections (lower end: smallest mu with N - N_e/2 >= -ne_tol; upper end: largest mu with
-   * N - N_e/2 <= +ne_tol).  For a metal both ends meet at the root; for an insulator the
-   * interval is the gap and mu lands mid-gap instead of at a band edge. */
-  if (solve_mu && !(flags & CSS_REF_INV_SQRT)) {
-    double lo0 = INFINITY, hi0 = -INFINITY;
-    for (int32_t t = 0; t < nwork; ++t)
-      for (int32_t j = 0; j < nj[t]; ++j) {
-        double x = lam[(size_t)t * nmax + j];
-        if (x < lo0) lo0 = x;
-        if (x > hi0) hi0 = x;
-      }
-    lo0 -= 1.0;
-    hi0 += 1.0;
-    double ends[2];
-    for (int side = 0; side < 2; ++side) {
-      double lo = lo0, hi = hi0;
-      for (int it = 0; it < 200; ++it) {
-        double mid = 0.5 * (lo + hi);
-        double g = 0.0;
-        for (int32_t t = 0; t < nwork; ++t)
-          for (int32_t j = 0; j < nj[t]; ++j)
-            g += ref_fermi(lam[(size_t)t * nmax + j], mid, kT) * wgt[(size_t)t * nmax + j];
-        g -= 0.5 * n_elec;
-        if (side == 0) {
-          if (g >= -ne_tol) hi = mid;
-          else lo = mid;
-        } else {
-          if (g <= ne_tol) lo = mid;
-          else hi = mid;
-        }
-        if (hi - lo <= 1e-13 * fmax(1.0, fabs(mid))) break;
-      }
-      ends[side] = 0.5 * (lo + hi);
-    }
-    mu = 0.5 * (ends[0] + ends[1]);
-  }
+  /* chemical potential from the Ritz quadrature N(mu) = sum_c sum_j f(lambda_cj; mu) w_cj */
+  if (solve_mu && !(flags & CSS_REF_INV_SQRT)) mu = ref_solve_mu(nwork, nj, nmax, lam, wgt, kT, n_elec, ne_tol);
   if (mu_out) *mu_out = mu;
   /* pass 2: rebuild each colour's basis, X_c = Q_c Z_c with Z_c = U f(Lambda) U^T E_1 B_0,
    * and extract P~_IJ = X_c[I] diag(s_J) on the pattern (Eq. 2, Eq. 6) */
@@ -702,7 +719,7 @@ int css_ref_density(int32_t n_brow, int32_t b, int32_t nnzb, const int32_t* row_
           for (int32_t j = 0; j < n; ++j) s += U[(size_t)i * n + j] * fy[(size_t)j * b + k];
         Z[(size_t)i * b + k] = s;
       }
-    ref_lanczos_colour(&H, colour, sign, c, n / b, flags, NULL, Z, X, NULL);
+    ref_lanczos_colour(&H, colour, sign, c, n / b, flags, NULL, Z, X, NULL, NULL);
     for (int32_t p = 0; p < nnzb; ++p) {
       int32_t J = col_idx[p];
       if (colour[J] != c) continue;
@@ -806,7 +823,7 @@ int css_ref_hprime(int32_t n_brow, int32_t b, int32_t nnzb_s, const int32_t* s_r
           for (int32_t j = 0; j < n; ++j) sum += U[(size_t)i * n + j] * fy[(size_t)j * b + k];
         Z[(size_t)i * b + k] = sum;
       }
-    ref_lanczos_colour(&S, colour, sign, c, n / b, flags & CSS_REF_REORTH_LOCAL, NULL, Z, Y, NULL);  /* Y_c */
+    ref_lanczos_colour(&S, colour, sign, c, n / b, flags & CSS_REF_REORTH_LOCAL, NULL, Z, Y, NULL, NULL);  /* Y_c */
     ref_bsr_mul(n_brow, b, h_row_ptr, h_col_idx, h_val, Y, W1, b);          /* H Y_c */
     ref_bsr_mul(n_brow, b, s_row_ptr, s_col_idx, Sinv_val, W1, W2, b);      /* S~^(-1/2) H Y_c */
     for (int32_t p = 0; p < nnzb_h; ++p) {
@@ -841,6 +858,205 @@ int css_ref_hprime(int32_t n_brow, int32_t b, int32_t nnzb_s, const int32_t* s_r
   free(cnt); free(brow); free(Ht);
   if (status != REF_OK) return status;
   return isfinite(tr) ? REF_OK : REF_ERR_NUMERIC;
+}
+
+/* y (N x w) = A^T x for a BSR matrix A (the transpose of ref_bsr_mul) */
+static void ref_bsr_mul_t(int32_t n_brow, int32_t b, const int32_t* row_ptr, const int32_t* col_idx,
+                          const double* val, const double* x, double* y, int32_t w) {
+  memset(y, 0, sizeof(double) * (size_t)n_brow * b * w);
+  for (int32_t I = 0; I < n_brow; ++I)
+    for (int32_t p = row_ptr[I]; p < row_ptr[I + 1]; ++p) {
+      int32_t J = col_idx[p];
+      const double* a = val + (size_t)p * b * b;
+      for (int32_t r = 0; r < b; ++r)
+        for (int32_t c = 0; c < b; ++c) {
+          double arc = a[r * b + c];  /* y[J, c] += A_IJ[r][c] x[I, r] */
+          for (int32_t k = 0; k < w; ++k) y[((size_t)J * b + c) * w + k] += arc * x[((size_t)I * b + r) * w + k];
+        }
+    }
+}
+
+/* Density matrix of a NON-ORTHOGONAL basis (paper, Eq. 4-6 with S != I): the Krylov space of
+ * H' is built from r~_c = S^(-1/2) r_c, and rho~ = S^(-1/2) Phi rho^K <Phi|r~><r| (the
+ * displayed form of rho~ after Eq. 5, with rho^K of Eq. 6).  Per colour c of the probes r:
+ *   r~_c = S~^(-1/2) R_c,  r~_c = Q_1 B_0 (QR),  block-Lanczos on H' from Q_1 -> T_c, Phi_c
+ *   T_c = U Lambda U^T,  Y = U^T E_1 B_0,  Z_c = U f(Lambda) Y
+ *   X_c = S~^(-1/2) Phi_c Z_c,  rho~_IJ = X_c[I] diag(s_J) for J of colour c (H's pattern)
+ * Inputs are the sparse S~^(-1/2) (sinv_val on S's pattern) and H' (hp_val on H's pattern)
+ * of css_ref_hprime, S itself and H (h_val, same pattern as H').  S's pattern must lie inside
+ * H's.  Electron count (reading where the paper is silent): in a non-orthogonal basis it is
+ * Tr(rho S); with u_c = S~^(-1/2)^T S R_c and V_c = Phi_c^T u_c, the weights
+ *   kappa_cj = (U^T V_c)_j . Y_j
+ * give sum_c sum_j f(lambda_cj) kappa_cj = sum_c Tr(R_c^T S X_c), which is exactly the
+ * extracted Tr(rho~ S); mu is solved on that quadrature with the rule of css_ref_density.
+ * Outputs: P_val (H's pattern, symmetrised with CSS_REF_SYMMETRIZE), Tr(rho~ S), Tr(rho~ H). */
+int css_ref_density_nonorth(int32_t n_brow, int32_t b, int32_t nnzb_s, const int32_t* s_row_ptr,
+                            const int32_t* s_col_idx, const double* s_val, const double* sinv_val, int32_t nnzb_h,
+                            const int32_t* h_row_ptr, const int32_t* h_col_idx, const double* h_val,
+                            const double* hp_val, const int32_t* colour, const int8_t* sign, int32_t n_colours,
+                            double mu, double kT, double n_elec, double ne_tol, int solve_mu, int32_t m, int flags,
+                            double* P_val, double* trPS, double* trPH, double* mu_out, int32_t* n_breakdown) {
+  if (n_brow < 1 || b < 1 || m < 1 || n_colours < 1 || nnzb_h < n_brow || !P_val || kT < 0.0) return REF_ERR_ARG;
+  if (!(ne_tol > 0.0)) ne_tol = 1e-6 * fmax(1.0, 0.5 * n_elec);
+  const int64_t N = (int64_t)n_brow * b;
+  const int32_t nmax = m * b, bb = b * b;
+  ref_h Hp = {n_brow, b, h_row_ptr, h_col_idx, hp_val};
+  /* position of each S block in H's pattern (S's pattern must be inside H's) */
+  int32_t* s_in_h = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnzb_s > 0 ? nnzb_s : 1));
+  int64_t* cnt = (int64_t*)calloc((size_t)n_colours, sizeof(int64_t));
+  double* lam = (double*)calloc((size_t)n_colours * nmax, sizeof(double));
+  double* kap = (double*)calloc((size_t)n_colours * nmax, sizeof(double));
+  double* Us = (double*)calloc((size_t)n_colours * nmax * nmax, sizeof(double));
+  double* Ys = (double*)calloc((size_t)n_colours * nmax * b, sizeof(double));
+  int32_t* nj = (int32_t*)calloc((size_t)n_colours, sizeof(int32_t));
+  int32_t* brk = (int32_t*)calloc((size_t)n_colours, sizeof(int32_t));
+  double** Phi = (double**)calloc((size_t)n_colours, sizeof(double*));
+  if (!s_in_h || !cnt || !lam || !kap || !Us || !Ys || !nj || !brk || !Phi) return REF_ERR_NOMEM;
+  int status = REF_OK;
+  for (int32_t I = 0; I < n_brow && status == REF_OK; ++I)
+    for (int32_t p = s_row_ptr[I]; p < s_row_ptr[I + 1]; ++p) {
+      s_in_h[p] = -1;
+      for (int32_t q = h_row_ptr[I]; q < h_row_ptr[I + 1]; ++q)
+        if (h_col_idx[q] == s_col_idx[p]) { s_in_h[p] = q; break; }
+      if (s_in_h[p] < 0) status = REF_ERR_ARG;
+    }
+  for (int32_t J = 0; J < n_brow && status == REF_OK; ++J) {
+    if (colour[J] < 0 || colour[J] >= n_colours) status = REF_ERR_ARG;
+    else cnt[colour[J]]++;
+  }
+  if (status != REF_OK) return status;
+  /* pass 1 per colour: start block, Lanczos on H' (basis kept), eigen-data and kappa */
+#pragma omp parallel for schedule(dynamic, 1) if (n_colours > 1)
+  for (int32_t c = 0; c < n_colours; ++c) {
+    if (cnt[c] == 0) continue;
+    double* R = (double*)calloc((size_t)N * b, sizeof(double));
+    double* rt = (double*)malloc(sizeof(double) * (size_t)N * b);
+    double* Q1 = (double*)malloc(sizeof(double) * (size_t)N * b);
+    double* SR = (double*)malloc(sizeof(double) * (size_t)N * b);
+    double* u = (double*)malloc(sizeof(double) * (size_t)N * b);
+    double* B0 = (double*)malloc(sizeof(double) * bb);
+    double* v = (double*)malloc(sizeof(double) * (size_t)N);
+    double* T = (double*)malloc(sizeof(double) * (size_t)nmax * nmax);
+    double* Q = (double*)malloc(sizeof(double) * (size_t)N * nmax);
+    double* V = (double*)malloc(sizeof(double) * (size_t)nmax * b);
+    double* UV = (double*)malloc(sizeof(double) * (size_t)nmax * b);
+    for (int32_t J = 0; J < n_brow; ++J)  /* R_c: column k = s_Jk on orbital k of each J in c */
+      if (colour[J] == c)
+        for (int32_t k = 0; k < b; ++k) R[((size_t)J * b + k) * b + k] = sign[(size_t)J * b + k];
+    ref_bsr_mul(n_brow, b, s_row_ptr, s_col_idx, sinv_val, R, rt, b);  /* r~_c = S~^(-1/2) R_c */
+    ref_bsr_mul(n_brow, b, s_row_ptr, s_col_idx, s_val, R, SR, b);     /* S R_c */
+    ref_bsr_mul_t(n_brow, b, s_row_ptr, s_col_idx, sinv_val, SR, u, b); /* u_c = S~^(-1/2)^T S R_c */
+    ref_qr(N, b, rt, Q1, B0, v);                                        /* r~_c = Q_1 B_0 */
+    int32_t blocks = ref_lanczos_colour(&Hp, colour, sign, c, m, flags & CSS_REF_REORTH_LOCAL, T, NULL, NULL, Q, Q1);
+    if (blocks < m) brk[c] = 1;
+    const int32_t n = blocks * b;
+    double* U = Us + (size_t)c * nmax * nmax;
+    double* Y = Ys + (size_t)c * nmax * b;
+    for (int32_t i = 0; i < n; ++i)
+      for (int32_t j = 0; j < n; ++j) U[(size_t)i * n + j] = T[(size_t)i * nmax + j];
+    int st = css_ref_eigh(n, U, lam + (size_t)c * nmax);
+    for (int32_t j = 0; j < n; ++j)  /* Y = U^T E_1 B_0 */
+      for (int32_t k = 0; k < b; ++k) {
+        double sum = 0.0;
+        for (int32_t l = 0; l <= k; ++l) sum += U[(size_t)l * n + j] * B0[l * b + k];
+        Y[(size_t)j * b + k] = sum;
+      }
+    for (int32_t i = 0; i < n; ++i)  /* V = Phi^T u */
+      for (int32_t k = 0; k < b; ++k) {
+        double sum = 0.0;
+        for (int64_t r = 0; r < N; ++r) sum += Q[(size_t)r * nmax + i] * u[(size_t)r * b + k];
+        V[(size_t)i * b + k] = sum;
+      }
+    for (int32_t j = 0; j < n; ++j) {  /* kappa_j = (U^T V)_j . Y_j */
+      double kj = 0.0;
+      for (int32_t k = 0; k < b; ++k) {
+        double sum = 0.0;
+        for (int32_t i = 0; i < n; ++i) sum += U[(size_t)i * n + j] * V[(size_t)i * b + k];
+        UV[(size_t)j * b + k] = sum;
+        kj += sum * Y[(size_t)j * b + k];
+      }
+      kap[(size_t)c * nmax + j] = kj;
+    }
+    nj[c] = n;
+    Phi[c] = Q;
+    if (st != REF_OK) {
+#pragma omp critical
+      status = st;
+    }
+    free(R); free(rt); free(Q1); free(SR); free(u); free(B0); free(v); free(T); free(V); free(UV);
+  }
+  if (status == REF_OK && solve_mu) mu = ref_solve_mu(n_colours, nj, nmax, lam, kap, kT, n_elec, ne_tol);
+  if (mu_out) *mu_out = mu;
+  /* pass 2 per colour: Z_c, X_c = S~^(-1/2) Phi_c Z_c, extraction on H's pattern */
+  int32_t* brow = (int32_t*)malloc(sizeof(int32_t) * (size_t)nnzb_h);
+  double* Pt = (double*)calloc((size_t)nnzb_h * bb, sizeof(double));
+  if (!brow || !Pt) return REF_ERR_NOMEM;
+  for (int32_t I = 0; I < n_brow; ++I)
+    for (int32_t p = h_row_ptr[I]; p < h_row_ptr[I + 1]; ++p) brow[p] = I;
+#pragma omp parallel for schedule(dynamic, 1) if (n_colours > 1)
+  for (int32_t c = 0; c < n_colours; ++c) {
+    if (cnt[c] == 0 || status != REF_OK) continue;
+    const int32_t n = nj[c];
+    const double* U = Us + (size_t)c * nmax * nmax;
+    const double* Y = Ys + (size_t)c * nmax * b;
+    double* fy = (double*)malloc(sizeof(double) * (size_t)nmax * b);
+    double* Z = (double*)malloc(sizeof(double) * (size_t)nmax * b);
+    double* Xt = (double*)malloc(sizeof(double) * (size_t)N * b);
+    double* X = (double*)malloc(sizeof(double) * (size_t)N * b);
+    for (int32_t j = 0; j < n; ++j) {
+      double fj = ref_fermi(lam[(size_t)c * nmax + j], mu, kT);
+      for (int32_t k = 0; k < b; ++k) fy[(size_t)j * b + k] = fj * Y[(size_t)j * b + k];
+    }
+    for (int32_t i = 0; i < n; ++i)  /* Z = U f(Lambda) Y */
+      for (int32_t k = 0; k < b; ++k) {
+        double sum = 0.0;
+        for (int32_t j = 0; j < n; ++j) sum += U[(size_t)i * n + j] * fy[(size_t)j * b + k];
+        Z[(size_t)i * b + k] = sum;
+      }
+    for (int64_t r = 0; r < N; ++r)  /* X~ = Phi Z */
+      for (int32_t k = 0; k < b; ++k) {
+        double sum = 0.0;
+        for (int32_t i = 0; i < n; ++i) sum += Phi[c][(size_t)r * nmax + i] * Z[(size_t)i * b + k];
+        Xt[(size_t)r * b + k] = sum;
+      }
+    ref_bsr_mul(n_brow, b, s_row_ptr, s_col_idx, sinv_val, Xt, X, b);  /* X = S~^(-1/2) X~ */
+    for (int32_t p = 0; p < nnzb_h; ++p) {
+      int32_t J = h_col_idx[p];
+      if (colour[J] != c) continue;
+      int32_t I = brow[p];
+      for (int32_t a = 0; a < b; ++a)
+        for (int32_t k = 0; k < b; ++k)
+          Pt[(size_t)p * bb + a * b + k] = X[((size_t)I * b + a) * b + k] * sign[(size_t)J * b + k];
+    }
+    free(fy); free(Z); free(Xt); free(X);
+  }
+  /* symmetrise on H's pattern and take Tr(rho~ H) and Tr(rho~ S) */
+  double tph = 0.0, tps = 0.0;
+  for (int32_t p = 0; p < nnzb_h; ++p) {
+    int32_t I = brow[p], J = h_col_idx[p];
+    int32_t q = -1;
+    for (int32_t r = h_row_ptr[J]; r < h_row_ptr[J + 1]; ++r)
+      if (h_col_idx[r] == I) { q = r; break; }
+    for (int32_t a = 0; a < b; ++a)
+      for (int32_t k = 0; k < b; ++k) {
+        double x = Pt[(size_t)p * bb + a * b + k];
+        if ((flags & CSS_REF_SYMMETRIZE) && q >= 0) x = 0.5 * (x + Pt[(size_t)q * bb + k * b + a]);
+        P_val[(size_t)p * bb + a * b + k] = x;
+        tph += x * h_val[(size_t)p * bb + a * b + k];
+      }
+  }
+  for (int32_t p = 0; p < nnzb_s; ++p)
+    for (int32_t e = 0; e < bb; ++e) tps += P_val[(size_t)s_in_h[p] * bb + e] * s_val[(size_t)p * bb + e];
+  if (trPS) *trPS = tps;
+  if (trPH) *trPH = tph;
+  int32_t nb = 0;
+  for (int32_t c = 0; c < n_colours; ++c) nb += brk[c];
+  if (n_breakdown) *n_breakdown = nb;
+  for (int32_t c = 0; c < n_colours; ++c) free(Phi[c]);
+  free(Phi); free(s_in_h); free(cnt); free(lam); free(kap); free(Us); free(Ys); free(nj); free(brk);
+  free(brow); free(Pt);
+  if (status != REF_OK) return status;
+  return (isfinite(tps) && isfinite(tph)) ? REF_OK : REF_ERR_NUMERIC;
 }
 
 /* Ritz data of all colours (test hook): lam/wgt are n_colours x (m b), n_per receives the

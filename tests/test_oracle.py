@@ -708,3 +708,133 @@ def test_hprime_truncated_and_contaminated(O):
         Ss[I * b:(I + 1) * b, J * b:(J + 1) * b] = Sinv_s[k]
     assert _pattern_err(rs["Sinv"], Sinv_s) < 1e-11
     assert _pattern_err(rs["Hp"], symmetrize(H, extract_h(Ss))) < 1e-10
+
+
+# ------------------------------------------ density matrix of a non-orthogonal basis
+def _dense_from_blocks(M, vals):
+    b = M.b
+    out = np.zeros((M.n, M.n))
+    rows = M.rows()
+    for k in range(M.nnzb):
+        I, J = rows[k], M.col_idx[k]
+        out[I * b:(I + 1) * b, J * b:(J + 1) * b] = vals[k]
+    return out
+
+
+def _mid_tolerance_set(g, lo, hi, tol):
+    import scipy.optimize as so
+    a = so.brentq(lambda m: g(m) + tol, lo, hi, xtol=1e-15, rtol=1e-15, maxiter=500)
+    z = so.brentq(lambda m: g(m) - tol, lo, hi, xtol=1e-15, rtol=1e-15, maxiter=500)
+    return 0.5 * (a + z)
+
+
+def test_nonorth_full_is_the_generalised_density(O):
+    """Full overlap and Hamiltonian patterns, every molecule its own colour and full Krylov
+    spaces: rho~ is the density matrix of the generalised problem H C = S C E, C^T S C = I,
+    i.e. C f(E) C^T from scipy's generalised eigensolver; mu makes Tr(rho S) = sum f(e) equal
+    N_e/2; Tr(rho H) = sum e f(e)."""
+    import scipy.linalg as sl
+    g = synth.water_box(6, box=6.0)
+    S = synth.overlap(g, r_cut=20.0)
+    H = synth.hamiltonian(g, r_cut=20.0)
+    col, nc = O.color(g.pos, g.box, 100.0, 1004)
+    s = O.probes(col, S.b, 1005)
+    hp = O.hprime(S, H, col, s, nc, m=6)
+    e, C = sl.eigh(H.dense(), S.dense())
+    dh = Dense(H)
+    kT, mu = 0.05, -5.0
+    r = O.density_nonorth(S, hp["Sinv"], H, hp["Hp"], col, s, nc, mu=mu, kT=kT, solve_mu=False, m=6)
+    rho = (C * fermi(e, mu, kT)) @ C.T
+    assert _pattern_err(r["P"], dh.on_pattern(rho)) < 1e-9
+    assert abs(r["trPS"] - fermi(e, mu, kT).sum()) < 1e-9
+    assert abs(r["trPH"] - (e * fermi(e, mu, kT)).sum()) < 1e-8
+    # mu solved on the electron count: the generalised spectrum's own mu (tolerance-set midpoint)
+    ne = synth.n_electrons(6)
+    tol = 1e-6 * 0.5 * ne
+    mu_ref = _mid_tolerance_set(lambda m: fermi(e, m, kT).sum() - 0.5 * ne, e.min() - 5, e.max() + 5, tol)
+    rs = O.density_nonorth(S, hp["Sinv"], H, hp["Hp"], col, s, nc, kT=kT, n_elec=ne, m=6)
+    assert abs(rs["mu"] - mu_ref) < 1e-7
+    assert _pattern_err(rs["P"], dh.on_pattern((C * fermi(e, rs["mu"], kT)) @ C.T)) < 1e-9
+    assert abs(rs["trPS"] - 0.5 * ne) <= tol
+
+
+def test_nonorth_contaminated_full_krylov(O):
+    """Shared colours for the density probes, truncated overlap and Hamiltonian patterns and a
+    full Krylov space of H': rho~ is the literal extraction of S~^(-1/2) f(H'~) S~^(-1/2) R, with
+    S~^(-1/2) and H'~ the sparse matrices given as inputs.  (The overlap probes are one molecule
+    per colour so that S~^(-1/2) stays well conditioned: with a heavily contaminated S~^(-1/2)
+    the plain block-Lanczos loses orthogonality before the Krylov space is full.)"""
+    g = synth.water_box(12, box=9.0)
+    S = synth.overlap(g)
+    H = synth.hamiltonian(g, r_cut=5.0)
+    colS, ncS = O.color(g.pos, g.box, 100.0, 1004)
+    sS = O.probes(colS, S.b, 1005)
+    hp = O.hprime(S, H, colS, sS, ncS, m=12)
+    col, nc = O.color(g.pos, g.box, 3.5, 2004)
+    assert nc < 12
+    s = O.probes(col, H.b, 2005)
+    kT, mu = 0.05, -5.0
+    r = O.density_nonorth(S, hp["Sinv"], H, hp["Hp"], col, s, nc, mu=mu, kT=kT, solve_mu=False, m=12, flags=0)
+    Si = _dense_from_blocks(S, hp["Sinv"])
+    Hp = _dense_from_blocks(H, hp["Hp"])
+    w, V = np.linalg.eigh(Hp)
+    R = probe_matrix(col, s, H.b, nc)
+    X = Si @ ((V * fermi(w, mu, kT)) @ V.T) @ (Si @ R)
+    b, rows = H.b, H.rows()
+    want = np.empty((H.nnzb, b, b))
+    for k in range(H.nnzb):
+        I, J = rows[k], H.col_idx[k]
+        c = col[J]
+        want[k] = X[I * b:(I + 1) * b, c * b:(c + 1) * b] * s[J * b:(J + 1) * b][None, :]
+    assert _pattern_err(r["P"], want) < 1e-10
+    rsym = O.density_nonorth(S, hp["Sinv"], H, hp["Hp"], col, s, nc, mu=mu, kT=kT, solve_mu=False, m=12)
+    assert _pattern_err(rsym["P"], symmetrize(H, want)) < 1e-10
+    assert abs(r["trPH"] - float((want * H.val).sum())) < 1e-9
+
+
+@pytest.mark.parametrize("m,hp_flags", [(2, 1), (4, 1), (3, 0)])
+def test_nonorth_electron_count_identity(O, m, hp_flags):
+    """Truncated Krylov spaces and shared colours: the kappa quadrature the chemical potential
+    is solved on equals the extracted Tr(rho~ S), so at the solved mu the density matrix
+    (symmetrised or not) holds N_e/2 electrons in the Mulliken count sum_IJ <rho_IJ, S_IJ>,
+    taken here from the returned blocks.  hp_flags = 0 gives an unsymmetrised S~^(-1/2), for
+    which the weights need its transpose."""
+    g = synth.water_box(27)
+    S = synth.overlap(g)
+    H = synth.hamiltonian(g)
+    colS, ncS = O.color(g.pos, g.box, 6.0, 1004)
+    sS = O.probes(colS, S.b, 1005)
+    hp = O.hprime(S, H, colS, sS, ncS, m=6, flags=hp_flags)
+    if hp_flags == 0:
+        Si = _dense_from_blocks(S, hp["Sinv"])
+        assert np.abs(Si - Si.T).max() > 1e-6
+    col, nc = O.color(g.pos, g.box, 5.0, 2004)
+    s = O.probes(col, H.b, 2005)
+    ne = synth.n_electrons(27)
+    hpos = {(int(I), int(J)): k for k, (I, J) in enumerate(zip(H.rows(), H.col_idx))}
+    for flags in (0, O.SYMMETRIZE):
+        r = O.density_nonorth(S, hp["Sinv"], H, hp["Hp"], col, s, nc, kT=0.05, n_elec=ne, m=m, flags=flags)
+        mulliken = sum(float((r["P"][hpos[(int(I), int(J))]] * S.val[k]).sum())
+                       for k, (I, J) in enumerate(zip(S.rows(), S.col_idx)))
+        assert abs(mulliken - 0.5 * ne) <= 1e-6 * 0.5 * ne + 1e-9, (flags, mulliken)
+        assert abs(r["trPS"] - mulliken) < 1e-9
+
+
+def test_nonorth_identity_overlap_is_the_orthogonal_density(O):
+    """S = I (so S~^(-1/2) = I and H' = H): the start blocks are the probe blocks themselves,
+    the electron-count weights are the Ritz weights, and the result is the orthogonal CSS
+    density matrix, mu included."""
+    g = synth.water_box(27)
+    H = synth.hamiltonian(g)
+    n, b = H.n_brow, H.b
+    eye = synth.BSR(n, b, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32),
+                    np.broadcast_to(np.eye(b), (n, b, b)).copy())
+    col, nc = O.color(g.pos, g.box, 5.0, 2004)
+    s = O.probes(col, b, 2005)
+    ne = synth.n_electrons(27)
+    for kw in ({"mu": -5.0, "solve_mu": False}, {"n_elec": ne}):
+        r = O.density_nonorth(eye, eye.val, H, H.val, col, s, nc, kT=0.05, m=5, **kw)
+        ref = O.density(H, col, s, nc, kT=0.05, m=5, **kw)
+        assert _pattern_err(r["P"], ref["P"]) < 1e-11
+        assert abs(r["mu"] - ref["mu"]) < 1e-9 and abs(r["trPH"] - ref["trPH"]) < 1e-9
+        assert abs(r["trPS"] - ref["trP"]) < 1e-9
