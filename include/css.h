@@ -17,7 +17,9 @@
  *     once a call has run with a given shape, repeating it allocates nothing.
  *   - No C++ exception crosses this interface.  Errors are returned as css_status; a
  *     CUDA error is reported as CSS_ERR_CUDA and the message is kept for css_last_error().
- *   - Orthogonal basis: S = I, so H' = H in the paper's Eq. 4.
+ *   - css_density works in an orthogonal basis (S = I, so H' = H in the paper's Eq. 4);
+ *     css_density with CSS_INV_SQRT and css_hprime give S~^(-1/2) and H' of a non-orthogonal
+ *     one (Eq. 8-10).
  */
 #ifndef CSS_H
 #define CSS_H
@@ -40,7 +42,7 @@ typedef enum {
   CSS_ERR_INVALID_ARG = 1, /* a size, pointer, flag or value is out of range          */
   CSS_ERR_NOMEM = 2,       /* device workspace could not be allocated                  */
   CSS_ERR_CUDA = 3,        /* a CUDA runtime call or kernel failed                      */
-  CSS_ERR_TIMEOUT = 4,     /* a bounded device wait ran out (grid barrier)              */
+  CSS_ERR_TIMEOUT = 4,     /* a bounded device wait ran out (mu grid barrier, band-reduction sweeps) */
   CSS_ERR_NUMERIC = 5,     /* NaN/Inf in the result or a non-convergent eigen-step      */
   CSS_WARN_BREAKDOWN = 6,  /* some colour's Krylov space became invariant early; result valid */
   CSS_ERR_UNSUPPORTED = 7  /* a shape the build does not support (b > 32)              */

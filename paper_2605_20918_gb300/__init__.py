@@ -147,6 +147,14 @@ def _dev(t, dtype, name):
     return C.c_void_p(t.data_ptr())
 
 
+def _need(t, n: int, name: str) -> None:
+    """Refuse a buffer of the wrong size before any pointer reaches the library (the C-ABI
+    takes raw pointers and cannot check lengths)."""
+    k = int(t.numel()) if hasattr(t, "numel") else int(np.asarray(t).size)
+    if k != int(n):
+        raise ValueError(f"{name} has {k} elements, expected {int(n)}")
+
+
 def _stream(stream):
     torch = _torch()
     s = torch.cuda.current_stream() if stream is None else stream
@@ -168,13 +176,23 @@ class DeviceBSR:
 
     @classmethod
     def from_host(cls, H, device="cuda"):
+        """Upload a host BSR (synth.BSR-like) after checking its pattern arrays."""
         torch = _torch()
+        rp = np.asarray(H.row_ptr)
+        ci = np.asarray(H.col_idx)
+        if rp.shape != (H.n_brow + 1,) or rp[0] != 0 or np.any(np.diff(rp) < 0) or rp[-1] != ci.size:
+            raise ValueError("row_ptr must have n_brow + 1 non-decreasing entries from 0 to nnzb")
+        if ci.size and (ci.min() < 0 or ci.max() >= H.n_brow):
+            raise ValueError("col_idx outside [0, n_brow)")
+        _need(H.val, ci.size * H.b * H.b, "val")
         return cls(H.n_brow, H.b, torch.as_tensor(np.ascontiguousarray(H.row_ptr, np.int32), device=device),
                    torch.as_tensor(np.ascontiguousarray(H.col_idx, np.int32), device=device),
                    torch.as_tensor(np.ascontiguousarray(H.val, np.float64), device=device))
 
     def _c(self) -> _BSR:
         torch = _torch()
+        _need(self.row_ptr, self.n_brow + 1, "row_ptr")
+        _need(self.val, self.nnzb * self.b * self.b, "val")
         return _BSR(self.n_brow, self.b, self.nnzb, _dev(self.row_ptr, torch.int32, "row_ptr"),
                     _dev(self.col_idx, torch.int32, "col_idx"), _dev(self.val, torch.float64, "val"))
 
@@ -201,7 +219,10 @@ def css_color(ctx, xyz, box: float, r_col: float, seed: int, colour, stream=None
     """Colour molecules (device xyz float64 [n,3] -> device colour int32 [n]); returns n_colours."""
     torch = _torch()
     lib = load_library()
-    g = _Geom(int(xyz.shape[0]), _dev(xyz, torch.float64, "xyz"), float(box))
+    n = int(xyz.shape[0])
+    _need(xyz, 3 * n, "xyz")
+    _need(colour, n, "colour")
+    g = _Geom(n, _dev(xyz, torch.float64, "xyz"), float(box))
     nc = C.c_int32()
     _check(lib, ctx, lib.css_color(ctx, C.byref(g), float(r_col), C.c_uint64(seed), _dev(colour, torch.int32, "colour"),
                                    C.byref(nc), _stream(stream)), "css_color")
@@ -213,6 +234,7 @@ def css_color_graph(ctx, adj_ptr, adj, seed: int, colour, stream=None) -> int:
     lib = load_library()
     nc = C.c_int32()
     n = int(adj_ptr.numel()) - 1
+    _need(colour, n, "colour")
     _check(lib, ctx, lib.css_color_graph(ctx, n, _dev(adj_ptr, torch.int32, "adj_ptr"),
                                          _dev(adj, torch.int32, "adj") if adj.numel() else C.c_void_p(0),
                                          C.c_uint64(seed), _dev(colour, torch.int32, "colour"), C.byref(nc),
@@ -224,9 +246,10 @@ def css_color_check(ctx, xyz, box: float, r_col: float, colour, n_colours: int, 
     """Same-coloured molecule pairs closer than r_col on the geometry xyz (0: still valid)."""
     torch = _torch()
     lib = load_library()
-    g = _Geom(int(xyz.shape[0]), _dev(xyz, torch.float64, "xyz"), float(box))
-    if int(colour.numel()) != g.n_mol:
-        raise ValueError("css_color_check: one colour per molecule")
+    n = int(xyz.shape[0])
+    _need(xyz, 3 * n, "xyz")
+    _need(colour, n, "colour")
+    g = _Geom(n, _dev(xyz, torch.float64, "xyz"), float(box))
     k = C.c_int64()
     _check(lib, ctx, lib.css_color_check(ctx, C.byref(g), float(r_col), _dev(colour, torch.int32, "colour"),
                                          int(n_colours), C.byref(k), _stream(stream)), "css_color_check")
@@ -240,9 +263,10 @@ def css_color_update(ctx, xyz, box: float, r_col: float, seed: int, colour, n_co
     (n_colours, recoloured)."""
     torch = _torch()
     lib = load_library()
-    g = _Geom(int(xyz.shape[0]), _dev(xyz, torch.float64, "xyz"), float(box))
-    if int(colour.numel()) != g.n_mol:
-        raise ValueError("css_color_update: one colour per molecule")
+    n = int(xyz.shape[0])
+    _need(xyz, 3 * n, "xyz")
+    _need(colour, n, "colour")
+    g = _Geom(n, _dev(xyz, torch.float64, "xyz"), float(box))
     nc = C.c_int32(int(n_colours))
     re = C.c_int32(0)
     _check(lib, ctx, lib.css_color_update(ctx, C.byref(g), float(r_col), float(skin), C.c_uint64(seed),
@@ -254,6 +278,7 @@ def css_color_update(ctx, xyz, box: float, r_col: float, seed: int, colour, n_co
 def css_probes(ctx, colour, b: int, sign_seed: int, sign, flags: int = 0, stream=None) -> None:
     torch = _torch()
     lib = load_library()
+    _need(sign, int(colour.numel()) * int(b), "sign")
     _check(lib, ctx, lib.css_probes(ctx, _dev(colour, torch.int32, "colour"), int(colour.numel()), int(b),
                                     C.c_uint64(sign_seed), flags, _dev(sign, torch.int8, "sign"), _stream(stream)),
            "css_probes")
@@ -268,6 +293,9 @@ def css_density(ctx, H: DeviceBSR, colour, sign, n_colours: int, P, *, mu=0.0, k
     """CSS density matrix on H's pattern into P (device float64 [nnzb, b, b])."""
     torch = _torch()
     lib = load_library()
+    _need(colour, H.n_brow, "colour")
+    _need(sign, H.n_brow * H.b, "sign")
+    _need(P, H.nnzb * H.b * H.b, "P")
     hb = H._c()
     f = _fermi(mu, kT, n_elec, solve_mu, ne_tol)
     tp, tph, mo = C.c_double(), C.c_double(), C.c_double()
@@ -283,6 +311,10 @@ def css_hprime(ctx, S: DeviceBSR, H: DeviceBSR, colour, sign, n_colours: int, Si
     """S~^(-1/2) (into Sinv, S's pattern) and H' (into Hp, H's pattern) of a non-orthogonal basis."""
     torch = _torch()
     lib = load_library()
+    _need(colour, S.n_brow, "colour")
+    _need(sign, S.n_brow * S.b, "sign")
+    _need(Sinv, S.nnzb * S.b * S.b, "Sinv")
+    _need(Hp, H.nnzb * H.b * H.b, "Hp")
     sb, hb = S._c(), H._c()
     tr = C.c_double()
     st = _check(lib, ctx, lib.css_hprime(ctx, C.byref(sb), C.byref(hb), _dev(colour, torch.int32, "colour"),
@@ -298,6 +330,12 @@ def css_density_batch(ctx, Hs, colours, signs, n_colours, Ps, fermis, *, m=30, p
     torch = _torch()
     lib = load_library()
     n = len(Hs)
+    if not (len(colours) == len(signs) == len(n_colours) == len(Ps) == len(fermis) == n):
+        raise ValueError("css_density_batch: one colour, sign, n_colours, P and fermi entry per system")
+    for h, c, s_, p in zip(Hs, colours, signs, Ps):
+        _need(c, h.n_brow, "colour")
+        _need(s_, h.n_brow * h.b, "sign")
+        _need(p, h.nnzb * h.b * h.b, "P")
     hb = (_BSR * n)(*[h._c() for h in Hs])
     cp = (C.c_void_p * n)(*[_dev(c, torch.int32, "colour") for c in colours])
     sp = (C.c_void_p * n)(*[_dev(s, torch.int8, "sign") for s in signs])
@@ -317,12 +355,21 @@ def css_pbuild(ctx, xyz, box, H, P, *, r_col, colour_seed=1004, sign_seed=1005, 
     numpy arrays and the copies happen inside the call; otherwise torch CUDA tensors."""
     lib = load_library()
     host = bool(flags & CSS_HOST_IO)
+    n_mol = int(xyz.shape[0])
+    _need(xyz, 3 * n_mol, "xyz")
+    _need(P, H.nnzb * H.b * H.b, "P")
+    if colour_out is not None:
+        _need(colour_out, n_mol, "colour_out")
     if host:
         xyz = np.ascontiguousarray(xyz, np.float64)
         rp = np.ascontiguousarray(H.row_ptr, np.int32)
         ci = np.ascontiguousarray(H.col_idx, np.int32)
         vv = np.ascontiguousarray(H.val, np.float64)
-        assert P.flags.c_contiguous and P.dtype == np.float64
+        if not (isinstance(P, np.ndarray) and P.flags.c_contiguous and P.dtype == np.float64):
+            raise TypeError("P must be a C-contiguous float64 numpy array with CSS_HOST_IO")
+        if colour_out is not None and not (isinstance(colour_out, np.ndarray) and colour_out.dtype == np.int32
+                                           and colour_out.flags.c_contiguous):
+            raise TypeError("colour_out must be a C-contiguous int32 numpy array with CSS_HOST_IO")
         g = _Geom(xyz.shape[0], xyz.ctypes.data_as(C.c_void_p), float(box))
         hb = _BSR(H.n_brow, H.b, int(ci.shape[0]), rp.ctypes.data_as(C.c_void_p), ci.ctypes.data_as(C.c_void_p),
                   vv.ctypes.data_as(C.c_void_p))
@@ -386,6 +433,10 @@ def css_eigen_blocks(ctx, A, B, nblk, cnt, *, mu=0.0, kT=0.05, want_z=True, stre
     torch = _torch()
     lib = load_library()
     n_col, m, b = int(A.shape[0]), int(A.shape[1]), int(A.shape[2])
+    _need(A, n_col * m * b * b, "A")
+    _need(B, n_col * m * b * b, "B")
+    _need(nblk, n_col, "nblk")
+    _need(cnt, n_col, "cnt")
     lam = torch.zeros((n_col, m * b), dtype=torch.float64, device=A.device)
     wgt = torch.zeros_like(lam)
     Z = torch.zeros((n_col, m * b, b), dtype=torch.float64, device=A.device) if want_z else None

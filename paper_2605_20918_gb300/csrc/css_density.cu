@@ -883,11 +883,10 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   la.pair_I = pair_I;
   la.pair_c = pair_c;
   la.pair_off_h = pair_off_h.data();
-  std::vector<cudaEvent_t> evs;
+  css_events evs;
   int64_t n_spmm = 0;
   if (ctx->timing) {
-    evs.resize(2 * (size_t)m);
-    for (auto& e : evs) cudaEventCreate(&e);
+    CSS_CU(ctx, evs.create(2 * (size_t)m));
   }
   double spmm_ms = 0.0;
   const int32_t BMh = css_spmm_bm(b);
@@ -1086,7 +1085,6 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     ctx->info.ms_mu = tm.ms(3, 4);
     ctx->info.ms_extract = tm.ms(4, 6);
     ctx->info.ms_total = tm.ms(0, 6);
-    for (auto& e : evs) cudaEventDestroy(e);
   }
   if (mu_err) {
     ctx->last_error = "css_density: grid barrier of the mu bisection timed out";

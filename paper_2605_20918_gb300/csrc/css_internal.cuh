@@ -63,6 +63,28 @@ struct css_ctx {
   int spmm_variant = -1;  // env CSS_SPMM_VARIANT = 0..4 fixes the variant (no tuning)
 };
 
+// CUDA events owned by the holder: destroyed when it goes out of scope, early returns included
+struct css_events {
+  std::vector<cudaEvent_t> ev;
+  css_events() = default;
+  css_events(const css_events&) = delete;
+  css_events& operator=(const css_events&) = delete;
+  ~css_events() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  cudaError_t create(size_t n) {  // n more events; stops at the first failure
+    for (size_t i = 0; i < n; ++i) {
+      cudaEvent_t e = nullptr;
+      const cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return r;
+      ev.push_back(e);
+    }
+    return cudaSuccess;
+  }
+  cudaEvent_t& operator[](size_t i) { return ev[i]; }
+  cudaEvent_t* data() { return ev.data(); }
+};
+
 css_status css_set_cuda_error(css_ctx* ctx, cudaError_t e, const char* what, const char* file, int line);
 css_status css_set_arg_error(css_ctx* ctx, const char* what);
 // Device buffer `name` with at least `bytes` bytes (grow-only; contents not preserved on growth).

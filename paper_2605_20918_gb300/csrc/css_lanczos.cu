@@ -901,8 +901,8 @@ css_status launch_spmm(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaStre
   if (ctx->spmm_variant >= 0) return launch_spmm_v<T>(ctx, a, V, W, ctx->spmm_variant, st);
   for (const auto& kv : ctx->spmm_tune)
     if (kv.first == key) return launch_spmm_v<T>(ctx, a, V, W, kv.second, st);
-  cudaEvent_t ev[kSpmmVariants + 1];
-  for (auto& e : ev) CSS_CU(ctx, cudaEventCreate(&e));
+  css_events ev;
+  CSS_CU(ctx, ev.create(kSpmmVariants + 1));
   css_status rc = CSS_OK;
   for (int v = 0; v < kSpmmVariants && rc == CSS_OK; ++v) rc = launch_spmm_v<T>(ctx, a, V, W, v, st);
   if (rc == CSS_OK) CSS_CU(ctx, cudaEventRecord(ev[0], st));
@@ -923,7 +923,6 @@ css_status launch_spmm(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaStre
     }
     ctx->spmm_tune.emplace_back(key, best);
   }
-  for (auto& e : ev) cudaEventDestroy(e);
   return rc;
 }
 
