@@ -58,10 +58,11 @@ def _load():
         lib.css_ref_lanczos.argtypes = [i32, i32, p, p, p, p, p, i32, i32, C.c_int, p, p, p]
         lib.css_ref_density.argtypes = [i32, i32, i32, p, p, p, p, p, i32, f64, f64, f64, f64, C.c_int, i32,
                                         C.c_int, p, i32, p, p, p, p, p]
-        lib.css_ref_ritz.argtypes = [i32, i32, p, p, p, p, p, i32, i32, C.c_int, p, p, p]
+        lib.css_ref_ritz.argtypes = [i32, i32, p, p, p, p, p, i32, i32, C.c_int, p, p, p, p]
         lib.css_ref_hprime.argtypes = [i32, i32, i32, p, p, p, i32, p, p, p, p, p, i32, i32, C.c_int, p, p, p]
         lib.css_ref_density_nonorth.argtypes = [i32, i32, i32, p, p, p, p, i32, p, p, p, p, p, p, i32, f64, f64,
                                                 f64, f64, C.c_int, i32, C.c_int, p, p, p, p, p]
+        lib.css_ref_solve_mu.argtypes = [i32, p, i32, p, p, f64, f64, f64, p]
         lib.css_ref_num_threads.restype = C.c_int
         _lib = lib
     return _lib
@@ -184,18 +185,40 @@ def lanczos(H, colour, sign, c: int, m: int, flags: int = 0, want_q: bool = Fals
     return (T, Q[:, :n].copy()) if want_q else T
 
 
-def ritz(H, colour, sign, n_colours: int, m: int, flags: int = 0):
-    """Per-colour Ritz values and weights: list of (lam, w) arrays."""
+def ritz(H, colour, sign, n_colours: int, m: int, flags: int = 0, colours=None):
+    """Per-colour Ritz values and weights: list of (lam, w) arrays (empty for colours not in
+    `colours` when that is given)."""
     colour = np.ascontiguousarray(colour, dtype=np.int32)
     sign = np.ascontiguousarray(sign, dtype=np.int8)
+    want = None
+    if colours is not None:
+        want = np.zeros(n_colours, dtype=np.int8)
+        want[np.asarray(colours, dtype=np.int64)] = 1
     nmax = m * H.b
     lam = np.zeros((n_colours, nmax)); wgt = np.zeros((n_colours, nmax))
     nper = np.zeros(n_colours, dtype=np.int32)
     rp = np.ascontiguousarray(H.row_ptr, dtype=np.int32); ci = np.ascontiguousarray(H.col_idx, dtype=np.int32)
     vv = np.ascontiguousarray(H.val, dtype=np.float64)
     _chk(_load().css_ref_ritz(H.n_brow, H.b, _ptr(rp), _ptr(ci), _ptr(vv), _ptr(colour), _ptr(sign),
-                              n_colours, m, flags, _ptr(lam), _ptr(wgt), _ptr(nper)), "ritz")
+                              n_colours, m, flags, _ptr(want), _ptr(lam), _ptr(wgt), _ptr(nper)), "ritz")
     return [(lam[c, :nper[c]].copy(), wgt[c, :nper[c]].copy()) for c in range(n_colours)]
+
+
+def solve_mu(ritz_lists, kT: float, n_elec: float, ne_tol: float = 0.0) -> float:
+    """mu from per-colour Ritz lists [(lam, w), ...] (the rule of `density`, lists summed in the
+    order given)."""
+    n = len(ritz_lists)
+    nmax = max(1, max(len(l) for l, _ in ritz_lists))
+    lam = np.zeros((n, nmax)); wgt = np.zeros((n, nmax))
+    nper = np.zeros(n, dtype=np.int32)
+    for t, (l, w) in enumerate(ritz_lists):
+        nper[t] = len(l)
+        lam[t, :len(l)] = l
+        wgt[t, :len(w)] = w
+    mu = np.zeros(1)
+    _chk(_load().css_ref_solve_mu(n, _ptr(nper), nmax, _ptr(lam), _ptr(wgt), kT, n_elec, ne_tol, _ptr(mu)),
+         "solve_mu")
+    return float(mu[0])
 
 
 def density(H, colour, sign, n_colours: int, *, mu: float = 0.0, kT: float = 0.05, n_elec: float = 0.0,

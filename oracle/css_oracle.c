@@ -635,6 +635,16 @@ static double ref_solve_mu(int32_t nwork, const int32_t* nj, int32_t nmax, const
   return 0.5 * (ends[0] + ends[1]);
 }
 
+/* mu from Ritz lists gathered elsewhere (n_lists lists of n_per[t] pairs, stride nmax), with
+ * the rule of css_ref_density; the lists enter the sums in the order given. */
+int css_ref_solve_mu(int32_t n_lists, const int32_t* n_per, int32_t nmax, const double* lam, const double* wgt,
+                     double kT, double n_elec, double ne_tol, double* mu) {
+  if (n_lists < 1 || nmax < 1 || !n_per || !lam || !wgt || !mu || kT < 0.0) return REF_ERR_ARG;
+  if (!(ne_tol > 0.0)) ne_tol = 1e-6 * fmax(1.0, 0.5 * n_elec);
+  *mu = ref_solve_mu(n_lists, n_per, nmax, lam, wgt, kT, n_elec, ne_tol);
+  return isfinite(*mu) ? REF_OK : REF_ERR_NUMERIC;
+}
+
 /* Full CSS density matrix on H's pattern.  colour_subset (n_subset entries) restricts the
  * work to those colours (then solve_mu must be 0 and only the blocks (I, J) with colour(J)
  * in the subset are written).  Returns REF_OK; *n_breakdown counts truncated colours. */
@@ -1059,11 +1069,12 @@ int css_ref_density_nonorth(int32_t n_brow, int32_t b, int32_t nnzb_s, const int
   return (isfinite(tps) && isfinite(tph)) ? REF_OK : REF_ERR_NUMERIC;
 }
 
-/* Ritz data of all colours (test hook): lam/wgt are n_colours x (m b), n_per receives the
- * size of each colour's projected matrix. */
+/* Ritz data of all colours, or of the colours with want[c] != 0 when want is given (test hook):
+ * lam/wgt are n_colours x (m b), n_per receives the size of each colour's projected matrix (0
+ * for colours left out). */
 int css_ref_ritz(int32_t n_brow, int32_t b, const int32_t* row_ptr, const int32_t* col_idx, const double* val,
                  const int32_t* colour, const int8_t* sign, int32_t n_colours, int32_t m, int flags,
-                 double* lam, double* wgt, int32_t* n_per) {
+                 const int8_t* want, double* lam, double* wgt, int32_t* n_per) {
   ref_h H = {n_brow, b, row_ptr, col_idx, val};
   const int32_t nmax = m * b;
   int64_t* cnt = (int64_t*)calloc((size_t)n_colours, sizeof(int64_t));
@@ -1071,7 +1082,7 @@ int css_ref_ritz(int32_t n_brow, int32_t b, const int32_t* row_ptr, const int32_
   int status = REF_OK;
   for (int32_t c = 0; c < n_colours; ++c) {
     n_per[c] = 0;
-    if (cnt[c] == 0) continue;
+    if (cnt[c] == 0 || (want && !want[c])) continue;
     double* U = (double*)malloc(sizeof(double) * (size_t)nmax * nmax);
     int32_t bk = 0;
     int st = ref_colour_eigen(&H, colour, sign, c, m, flags, &n_per[c], lam + (size_t)c * nmax,

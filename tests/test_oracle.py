@@ -838,3 +838,22 @@ def test_nonorth_identity_overlap_is_the_orthogonal_density(O):
         assert _pattern_err(r["P"], ref["P"]) < 1e-11
         assert abs(r["mu"] - ref["mu"]) < 1e-9 and abs(r["trPH"] - ref["trPH"]) < 1e-9
         assert abs(r["trPS"] - ref["trP"]) < 1e-9
+
+
+# ------------------------------------------------ mu from Ritz lists gathered across ranks
+def test_solve_mu_on_ritz_lists_is_the_density_rule(O):
+    g = synth.water_box(64)
+    H = synth.hamiltonian(g, "minimal")
+    col, nc = O.color(g.pos, g.box, 8.0, 1004)
+    s = O.probes(col, H.b, 1005)
+    ne = synth.n_electrons(64)
+    ref = O.density(H, col, s, nc, kT=0.05, n_elec=ne, m=10)
+    full = O.ritz(H, col, s, nc, 10)
+    assert O.solve_mu(full, 0.05, ne) == ref["mu"]
+    # the colour mask returns exactly the chosen colours' lists
+    sub = O.ritz(H, col, s, nc, 10, colours=[1, 3])
+    for c in range(nc):
+        if c in (1, 3):
+            assert np.array_equal(sub[c][0], full[c][0]) and np.array_equal(sub[c][1], full[c][1])
+        else:
+            assert sub[c][0].size == 0
