@@ -225,6 +225,27 @@ CSS_API css_status css_hprime(css_ctx* ctx, const css_bsr* S, const css_bsr* H, 
                               const int8_t* sign, int32_t n_colours, int32_t m, css_precision prec, uint32_t flags,
                               double* Sinv_val, double* Hp_val, double* trHp, void* stream);
 
+/* Density matrix of a NON-ORTHOGONAL basis (paper, Eq. 4-6 with S != I): the block-Krylov space
+ * of H' for colour c starts at r~_c = S~^(-1/2) r_c (r_c the probe block of the colouring
+ * `colour`/`sign`), r~_c = Q_1 B_0 by QR, and rho~ = S~^(-1/2) Phi_c f(T_c) E_1 B_0 <r_c|,
+ * extracted on H's pattern (rho~_IJ = X_c(J)[I] diag(s_J)) and symmetrised with CSS_SYMMETRIZE.
+ * The electron count of a non-orthogonal basis is Tr(rho S); mu is solved (fermi->solve_mu) on the
+ * Ritz quadrature whose weights kappa_cj = (U^T Phi_c^T S~^(-1/2)^T S R_c)_j . (U^T E_1 B_0)_j make
+ * it equal to the extracted Tr(rho~ S), with the rule of css_fermi.
+ *   S         overlap matrix (BSR, FP64, structurally symmetric); its pattern must lie inside H's
+ *   Sinv_val  S~^(-1/2) on S's pattern ([S->nnzb][b][b], e.g. from css_hprime)
+ *   Hp        H' (values on H's pattern, e.g. from css_hprime) with H's row_ptr / col_idx
+ *   H_val     the Hamiltonian H itself on the same pattern (for Tr(rho H))
+ *   P_val     [Hp->nnzb][b][b], written;  trPS, trPH, mu_out: host double*, written
+ * flags: CSS_SYMMETRIZE, CSS_REORTH_LOCAL.  Workspace: seven N x (n_colours b) blocks in the vector
+ * precision (all colours at once; CSS_ERR_NOMEM when they do not fit).  After the call css_ritz
+ * returns the Ritz values of H' and the weights kappa.  Synchronises. */
+CSS_API css_status css_density_nonorth(css_ctx* ctx, const css_bsr* S, const double* Sinv_val, const css_bsr* Hp,
+                                       const double* H_val, const int32_t* colour, const int8_t* sign,
+                                       int32_t n_colours, const css_fermi* fermi, int32_t m, css_precision prec,
+                                       uint32_t flags, double* P_val, double* trPS, double* trPH, double* mu_out,
+                                       void* stream);
+
 /* Many independent systems in one call (MD snapshots of uneven size).  Arrays of n_sys
  * host structs / host arrays of device pointers; mu is solved per system (fermi[s]).
  * Outputs per system: P_val[s] (device), trP[s], trPH[s], mu_out[s] (host arrays). */

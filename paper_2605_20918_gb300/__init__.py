@@ -17,7 +17,7 @@ import numpy as np
 
 __all__ = [
     "CSSError", "Context", "DeviceBSR", "load_library", "library_path", "css_create", "css_destroy", "css_color",
-    "css_color_graph", "css_color_check", "css_color_update", "css_probes", "css_density", "css_density_batch", "css_pbuild", "css_get_info", "css_ritz", "css_projected", "css_eigen_blocks",
+    "css_color_graph", "css_color_check", "css_color_update", "css_probes", "css_density", "css_density_nonorth", "css_density_batch", "css_pbuild", "css_get_info", "css_ritz", "css_projected", "css_eigen_blocks",
     "CSS_OK", "CSS_WARN_BREAKDOWN", "CSS_FP64", "CSS_MIXED_FP32", "CSS_SYMMETRIZE", "CSS_TWO_PASS",
     "CSS_REORTH_LOCAL", "CSS_HOST_IO", "CSS_SIGNS_ONES", "CSS_ENERGY_WEIGHTED", "CSS_INV_SQRT",
 ]
@@ -113,6 +113,9 @@ def load_library(path: str | Path | None = None):
     lib.css_hprime.argtypes = [v, C.POINTER(_BSR), C.POINTER(_BSR), v, v, i32, i32, st, u32, v, v,
                                C.POINTER(C.c_double), v]
     lib.css_hprime.restype = st
+    lib.css_density_nonorth.argtypes = [v, C.POINTER(_BSR), v, C.POINTER(_BSR), v, v, v, i32, C.POINTER(_Fermi), i32,
+                                        st, u32, v, C.POINTER(f64), C.POINTER(f64), C.POINTER(f64), v]
+    lib.css_density_nonorth.restype = st
     lib.css_ritz.restype = st
     _lib = lib
     return lib
@@ -324,6 +327,30 @@ def css_hprime(ctx, S: DeviceBSR, H: DeviceBSR, colour, sign, n_colours: int, Si
     return {"trHp": tr.value, "status": st}
 
 
+def css_density_nonorth(ctx, S: DeviceBSR, Sinv, Hp: DeviceBSR, H_val, colour, sign, n_colours: int, P, *, mu=0.0,
+                        kT=0.05, n_elec=0.0, solve_mu=True, ne_tol=0.0, m=30, precision=CSS_FP64,
+                        flags=CSS_SYMMETRIZE, stream=None) -> dict:
+    """Density matrix of a non-orthogonal basis into P (H's pattern) from S, S~^(-1/2) (Sinv, S's
+    pattern), H' (Hp: values of H' on H's pattern) and H's own values (H_val)."""
+    torch = _torch()
+    lib = load_library()
+    _need(Sinv, S.nnzb * S.b * S.b, "Sinv")
+    _need(H_val, Hp.nnzb * Hp.b * Hp.b, "H_val")
+    _need(colour, Hp.n_brow, "colour")
+    _need(sign, Hp.n_brow * Hp.b, "sign")
+    _need(P, Hp.nnzb * Hp.b * Hp.b, "P")
+    sb, hb = S._c(), Hp._c()
+    f = _fermi(mu, kT, n_elec, solve_mu, ne_tol)
+    tps, tph, mo = C.c_double(), C.c_double(), C.c_double()
+    st = _check(lib, ctx, lib.css_density_nonorth(ctx, C.byref(sb), _dev(Sinv, torch.float64, "Sinv"), C.byref(hb),
+                                                  _dev(H_val, torch.float64, "H_val"),
+                                                  _dev(colour, torch.int32, "colour"), _dev(sign, torch.int8, "sign"),
+                                                  int(n_colours), C.byref(f), int(m), int(precision), int(flags),
+                                                  _dev(P, torch.float64, "P"), C.byref(tps), C.byref(tph),
+                                                  C.byref(mo), _stream(stream)), "css_density_nonorth")
+    return {"trPS": tps.value, "trPH": tph.value, "mu": mo.value, "status": st}
+
+
 def css_density_batch(ctx, Hs, colours, signs, n_colours, Ps, fermis, *, m=30, precision=CSS_FP64,
                       flags=CSS_SYMMETRIZE, stream=None) -> dict:
     """Several systems in one call.  fermis: list of dicts(mu, kT, n_elec, solve_mu)."""
@@ -491,6 +518,9 @@ class Context:
 
     def hprime(self, *a, **k):
         return css_hprime(self.handle, *a, **k)
+
+    def density_nonorth(self, *a, **k):
+        return css_density_nonorth(self.handle, *a, **k)
 
     def density_batch(self, *a, **k):
         return css_density_batch(self.handle, *a, **k)

@@ -1145,6 +1145,83 @@ __global__ void __launch_bounds__(EX_T) k_hp_extract(int32_t nnzb, int32_t b, co
   }
 }
 
+// Mt[p] = M[trans[p]]^T: the transpose of a BSR matrix on a structurally symmetric pattern
+__global__ void k_block_transpose(int32_t nnzb, int32_t b, const int32_t* __restrict__ trans,
+                                  const double* __restrict__ M, double* __restrict__ Mt) {
+  const int32_t bb = b * b;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nnzb * bb) return;
+  const int32_t p = (int32_t)(t / bb), e = (int32_t)(t % bb), i = e / b, k = e % b;
+  Mt[t] = M[(size_t)trans[p] * bb + k * b + i];
+}
+
+__global__ void k_fill(int32_t n, double v, double* __restrict__ x) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = v;
+}
+
+// electron-count weights kappa[c][k] = YV[c][k] . Y[c][k] (0 past the colour's projected size)
+__global__ void k_kappa(int32_t n_col, int32_t b, int32_t nmax, const int32_t* __restrict__ nblk,
+                        const double* __restrict__ YV, const double* __restrict__ Y, double* __restrict__ kap) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n_col * nmax) return;
+  const int32_t c = (int32_t)(t / nmax), k = (int32_t)(t % nmax);
+  double s = 0.0;
+  if (k < nblk[c] * b)
+    for (int32_t a = 0; a < b; ++a) s = fma(YV[(size_t)t * b + a], Y[(size_t)t * b + a], s);
+  kap[t] = s;
+}
+
+// per-CTA partial sums of Tr(rho H) over H's blocks and of Tr(rho S) over S's blocks; each S
+// block is found in H's row by bisection (columns sorted), err = 1 when it is not there
+__global__ void __launch_bounds__(EX_T) k_trace_hs(int64_t nh, int64_t ns, int32_t b, const double* __restrict__ P,
+                                                   const double* __restrict__ Hval, const int32_t* __restrict__ h_row_ptr,
+                                                   const int32_t* __restrict__ h_col_idx,
+                                                   const int32_t* __restrict__ s_brow,
+                                                   const int32_t* __restrict__ s_col_idx,
+                                                   const double* __restrict__ Sval, double* __restrict__ part,
+                                                   int32_t* __restrict__ err) {
+  __shared__ double r1[EX_T / 32], r2[EX_T / 32];
+  const int32_t bb = b * b;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double th = 0.0, ts = 0.0;
+  if (t < nh) th = P[t] * Hval[t];
+  if (t < ns) {
+    const int32_t p = (int32_t)(t / bb), e = (int32_t)(t % bb);
+    const int32_t I = s_brow[p], J = s_col_idx[p];
+    int32_t lo = h_row_ptr[I], hi = h_row_ptr[I + 1] - 1, q = -1;
+    while (lo <= hi) {
+      const int32_t mid = (lo + hi) >> 1, v = h_col_idx[mid];
+      if (v == J) {
+        q = mid;
+        break;
+      }
+      if (v < J) lo = mid + 1;
+      else hi = mid - 1;
+    }
+    if (q >= 0) ts = P[(size_t)q * bb + e] * Sval[t];
+    else atomicOr(err, 1);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    th += __shfl_xor_sync(0xffffffffu, th, o);
+    ts += __shfl_xor_sync(0xffffffffu, ts, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    r1[threadIdx.x >> 5] = th;
+    r2[threadIdx.x >> 5] = ts;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0, y = 0.0;
+    for (int i = 0; i < EX_T / 32; ++i) {
+      x += r1[i];
+      y += r2[i];
+    }
+    part[2 * blockIdx.x] = x;
+    part[2 * blockIdx.x + 1] = y;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -1340,6 +1417,349 @@ css_status css_hprime(css_ctx* ctx, const css_bsr* S, const css_bsr* H, const in
     return CSS_ERR_NUMERIC;
   }
   return s1;
+}
+
+css_status css_density_nonorth(css_ctx* ctx, const css_bsr* S, const double* Sinv_val, const css_bsr* Hp,
+                               const double* H_val, const int32_t* colour, const int8_t* sign, int32_t n_colours,
+                               const css_fermi* fermi, int32_t m, css_precision prec, uint32_t flags, double* P_val,
+                               double* trPS, double* trPH, double* mu_out, void* stream) {
+  // ------------------------------------------------------------ validation
+  if (!ctx || !S || !Hp || !fermi || !Sinv_val || !H_val || !colour || !sign || !P_val)
+    return css_set_arg_error(ctx, "css_density_nonorth: null pointer");
+  if (!S->row_ptr || !S->col_idx || !S->val || !Hp->row_ptr || !Hp->col_idx || !Hp->val)
+    return css_set_arg_error(ctx, "css_density_nonorth: S or H' without pattern or values");
+  if (S->n_brow != Hp->n_brow || S->b != Hp->b || S->n_brow < 1 || S->nnzb < S->n_brow || Hp->nnzb < Hp->n_brow)
+    return css_set_arg_error(ctx, "css_density_nonorth: S and H' need the same n_brow and b and a diagonal");
+  if (prec != CSS_FP64 && prec != CSS_MIXED_FP32) return css_set_arg_error(ctx, "css_density_nonorth: unknown precision");
+  if (flags & ~(CSS_SYMMETRIZE | CSS_REORTH_LOCAL)) return css_set_arg_error(ctx, "css_density_nonorth: unknown flag");
+  const int32_t b = Hp->b;
+  if (b < 1) return css_set_arg_error(ctx, "css_density_nonorth: b < 1");
+  if (b > CSS_MAX_B) {
+    ctx->last_error = "css_density_nonorth: b > 32 is not supported";
+    return CSS_ERR_UNSUPPORTED;
+  }
+  if (m < 1 || (int64_t)m * b > 4096) return css_set_arg_error(ctx, "css_density_nonorth: need 1 <= m and m*b <= 4096");
+  if (n_colours < 1 || n_colours > (1 << 24)) return css_set_arg_error(ctx, "css_density_nonorth: n_colours out of range");
+  if (!(fermi->kT >= 0.0) || !std::isfinite(fermi->kT) || !std::isfinite(fermi->mu) || !std::isfinite(fermi->n_elec) ||
+      !std::isfinite(fermi->ne_tol))
+    return css_set_arg_error(ctx, "css_density_nonorth: kT must be finite and >= 0, mu and n_elec finite");
+  if ((int64_t)Hp->nnzb * b * b > (1ll << 40) || (int64_t)S->nnzb * b * b > (1ll << 40))
+    return css_set_arg_error(ctx, "css_density_nonorth: problem too large");
+  CSS_CU(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool f32 = prec == CSS_MIXED_FP32;
+  const int32_t n_brow = Hp->n_brow, nc = n_colours, bb = b * b, nmax = m * b;
+  const int64_t N = (int64_t)n_brow * b;
+  const size_t s_vec = f32 ? 4 : 8;
+  const int T = 256;
+  const unsigned gb = (unsigned)css_ceil_div(n_brow, T);
+
+  // ------------------------------------- patterns, colour counts, validation
+  int32_t *hbrow, *htrans, *sbrow, *strans, *cnt, *cnt2, *nblk, *done, *misc, *soc;
+  double* isq;
+  CSS_TRY(ws_get(ctx, "no_hbrow", Hp->nnzb, &hbrow));
+  CSS_TRY(ws_get(ctx, "no_htrans", Hp->nnzb, &htrans));
+  CSS_TRY(ws_get(ctx, "no_sbrow", S->nnzb, &sbrow));
+  CSS_TRY(ws_get(ctx, "no_strans", S->nnzb, &strans));
+  CSS_TRY(ws_get(ctx, "no_cnt", nc, &cnt));
+  CSS_TRY(ws_get(ctx, "no_cnt2", nc, &cnt2));
+  CSS_TRY(ws_get(ctx, "no_nblk", nc, &nblk));
+  CSS_TRY(ws_get(ctx, "no_done", nc, &done));
+  CSS_TRY(ws_get(ctx, "no_soc", nc, &soc));
+  CSS_TRY(ws_get(ctx, "no_isq", nc, &isq));
+  CSS_TRY(ws_get(ctx, "no_misc", 64, &misc));
+  CSS_CU(ctx, cudaMemsetAsync(misc, 0, 64 * sizeof(int32_t), st));
+  CSS_CU(ctx, cudaMemsetAsync(cnt, 0, nc * sizeof(int32_t), st));
+  CSS_CU(ctx, cudaMemsetAsync(cnt2, 0, nc * sizeof(int32_t), st));
+  CSS_CU(ctx, cudaMemsetAsync(soc, 0, nc * sizeof(int32_t), st));  // one system
+  k_rows<<<gb, T, 0, st>>>(n_brow, Hp->row_ptr, Hp->col_idx, colour, nc, hbrow, htrans, cnt, misc + 1, misc);
+  CSS_LAUNCHED(ctx);
+  k_rows<<<gb, T, 0, st>>>(n_brow, S->row_ptr, S->col_idx, colour, nc, sbrow, strans, cnt2, misc + 3, misc + 2);
+  CSS_LAUNCHED(ctx);
+  k_inv_sqrt<<<(unsigned)css_ceil_div(nc, T), T, 0, st>>>(nc, cnt, isq, nblk, done, m);
+  CSS_LAUNCHED(ctx);
+  int32_t* hb;
+  CSS_TRY(css_pinned(ctx, 256, (void**)&hb));
+  CSS_CU(ctx, cudaMemcpyAsync(hb, misc, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CSS_CU(ctx, cudaStreamSynchronize(st));
+  if ((hb[0] | hb[2]) & ERR_COLOUR) return css_set_arg_error(ctx, "css_density_nonorth: colour outside [0, n_colours)");
+  if ((hb[0] | hb[2]) & ERR_PATTERN)
+    return css_set_arg_error(ctx, "css_density_nonorth: a pattern is not symmetric, has a column out of range or "
+                                  "misses a diagonal block");
+  const int32_t max_row = hb[1];
+
+  // ------------------------- H', S~^(-1/2), S and S~^(-1/2)^T in the H*V layout
+  double* sinvT;
+  CSS_TRY(ws_get(ctx, "no_sinvT", (size_t)S->nnzb * bb, &sinvT));
+  k_block_transpose<<<(unsigned)css_ceil_div((int64_t)S->nnzb * bb, T), T, 0, st>>>(S->nnzb, b, strans, Sinv_val,
+                                                                                    sinvT);
+  CSS_LAUNCHED(ctx);
+  const void *hpv, *hplo, *siv, *silo, *sv, *slo, *sitv, *sitlo;
+  CSS_TRY(css_spmm_prepare_as(ctx, "no_hp", f32, b, n_brow, Hp->nnzb, Hp->row_ptr, Hp->col_idx, Hp->val, &hpv, &hplo,
+                              st));
+  CSS_TRY(css_spmm_prepare_as(ctx, "no_si", f32, b, n_brow, S->nnzb, S->row_ptr, S->col_idx, Sinv_val, &siv, &silo,
+                              st));
+  CSS_TRY(css_spmm_prepare_as(ctx, "no_s", f32, b, n_brow, S->nnzb, S->row_ptr, S->col_idx, S->val, &sv, &slo, st));
+  CSS_TRY(css_spmm_prepare_as(ctx, "no_sit", f32, b, n_brow, S->nnzb, S->row_ptr, S->col_idx, sinvT, &sitv, &sitlo,
+                              st));
+
+  // ------------------------------------------ vectors (all colours at once)
+  const int32_t ws = (int32_t)css_ceil_div((int64_t)nc * b, 8) * 8;
+  const size_t vbytes = (size_t)N * ws * s_vec;
+  size_t free_b = 0, total_b = 0;
+  CSS_CU(ctx, cudaMemGetInfo(&free_b, &total_b));
+  if (7 * vbytes + ((size_t)1 << 30) > free_b + ctx->ws_bytes) {
+    ctx->last_error = "css_density_nonorth: the Krylov blocks of all colours do not fit in device memory";
+    return CSS_ERR_NOMEM;
+  }
+  void *R, *R0, *SR, *U, *Q0, *Q1, *Wv;
+  CSS_TRY(css_ws(ctx, "no_R", vbytes, &R));
+  CSS_TRY(css_ws(ctx, "no_start", vbytes, &R0));
+  CSS_TRY(css_ws(ctx, "no_SR", vbytes, &SR));
+  CSS_TRY(css_ws(ctx, "no_u", vbytes, &U));
+  CSS_TRY(css_ws(ctx, "no_Q0", vbytes, &Q0));
+  CSS_TRY(css_ws(ctx, "no_Q1", vbytes, &Q1));
+  CSS_TRY(css_ws(ctx, "no_W", vbytes, &Wv));
+  LzArgs op;  // one H*V operand at a time: pattern and prepared values
+  op.fp32 = f32;
+  op.n_brow = n_brow;
+  op.b = b;
+  op.w = nc * b;
+  op.ws = ws;
+  auto spmm_with = [&](const css_bsr* M, const void* val, const void* lo, const void* V, void* W) -> css_status {
+    op.row_ptr = M->row_ptr;
+    op.col_idx = M->col_idx;
+    op.Hval = val;
+    op.Hlo_diag = lo;
+    return css_spmm(ctx, op, V, W, st);
+  };
+  // probe blocks R_c, start blocks r~_c = S~^(-1/2) R_c, and u_c = S~^(-1/2)^T S R_c
+  double* ones;
+  CSS_TRY(ws_get(ctx, "no_ones", nc, &ones));
+  k_fill<<<(unsigned)css_ceil_div(nc, T), T, 0, st>>>(nc, 1.0, ones);
+  CSS_LAUNCHED(ctx);
+  CSS_TRY(css_probe_block(ctx, f32, n_brow, b, ws, 0, nc, colour, sign, ones, R, st));
+  CSS_TRY(spmm_with(S, siv, silo, R, R0));
+  CSS_TRY(spmm_with(S, sv, slo, R, SR));
+  CSS_TRY(spmm_with(S, sitv, sitlo, SR, U));
+
+  // ---------------------------- block-Lanczos on H' (pass 1: T_c, B_0, V_c)
+  double *Ablk, *Bblk, *Bprev, *B0, *Vc, *part, *small, *Z;
+  CSS_TRY(ws_get(ctx, "no_A", (size_t)nc * m * bb, &Ablk));
+  CSS_TRY(ws_get(ctx, "no_B", (size_t)nc * m * bb, &Bblk));
+  CSS_TRY(ws_get(ctx, "no_Bprev", (size_t)nc * bb, &Bprev));
+  CSS_TRY(ws_get(ctx, "no_B0", (size_t)nc * bb, &B0));
+  CSS_TRY(ws_get(ctx, "no_Vc", (size_t)nc * nmax * b, &Vc));
+  CSS_TRY(ws_get(ctx, "no_part", css_lanczos_part_doubles(N, b, nc) * 2, &part));
+  CSS_TRY(ws_get(ctx, "no_small", css_lanczos_small_doubles(b, nc), &small));
+  CSS_TRY(ws_get(ctx, "no_Z", (size_t)nc * nmax * b, &Z));
+  CSS_CU(ctx, cudaMemsetAsync(Vc, 0, sizeof(double) * nc * nmax * b, st));
+  std::vector<int64_t> no_pairs((size_t)nc + 1, 0);  // nothing is sampled: X comes from whole rows
+  LzArgs la;
+  la.fp32 = f32;
+  la.n_brow = n_brow;
+  la.b = b;
+  la.m = m;
+  la.w = nc * b;
+  la.ws = ws;
+  la.row_ptr = Hp->row_ptr;
+  la.col_idx = Hp->col_idx;
+  la.Hval = hpv;
+  la.Hlo_diag = hplo;
+  la.max_row_blocks = max_row;
+  la.colour = colour;
+  la.sign = sign;
+  la.inv_sqrt_cnt = isq;
+  la.cb0 = 0;
+  la.ncb = nc;
+  la.Q0 = Q0;
+  la.Q1 = Q1;
+  la.W = Wv;
+  la.Ablk = Ablk;
+  la.Bblk = Bblk;
+  la.Bblk_prev = Bprev;
+  la.nblk = nblk;
+  la.done = done;
+  la.part = part;
+  la.small = small;
+  la.tau = f32 ? 1e-5 : 1e-10;
+  la.shift_rel = f32 ? 1e-5 : 1e-12;
+  la.flags = f32 ? (flags | CSS_REORTH_LOCAL) : flags;
+  la.mode = 0;
+  la.Z = Z;
+  la.ldz = nmax;
+  la.pair_off_h = no_pairs.data();
+  la.start = R0;
+  la.B0 = B0;
+  la.ucol = U;
+  la.Vc = Vc;
+  CSS_TRY(css_lanczos_pass(ctx, la, st));
+
+  // ------------------------------ eigen-data with B_0, kappa, mu and Z_c
+  EigArgs ea;
+  ea.n_col = nc;
+  ea.b = b;
+  ea.m = m;
+  ea.Ablk = Ablk;
+  ea.Bblk = Bblk;
+  ea.nblk = nblk;
+  ea.cnt = cnt;
+  ea.B0 = B0;
+  ea.rcap = nmax * (nmax / b + 2);
+  CSS_TRY(ws_get(ctx, "e_AB", (size_t)nc * nmax * (2 * b + 1), &ea.AB));
+  CSS_TRY(ws_get(ctx, "e_RV", (size_t)nc * ea.rcap * b, &ea.RV));
+  CSS_TRY(ws_get(ctx, "e_RT", (size_t)nc * ea.rcap, &ea.RT));
+  CSS_TRY(ws_get(ctx, "e_RR0", (size_t)nc * ea.rcap, &ea.RR0));
+  CSS_TRY(ws_get(ctx, "e_so", (size_t)nc * (nmax + 1), &ea.sweep_off));
+  CSS_TRY(ws_get(ctx, "e_d", (size_t)nc * nmax, &ea.d));
+  CSS_TRY(ws_get(ctx, "e_e", (size_t)nc * nmax, &ea.e));
+  CSS_TRY(ws_get(ctx, "e_l32", (size_t)nc * nmax, &ea.lam32));
+  CSS_TRY(ws_get(ctx, "e_tn", (size_t)nc, &ea.tnorm));
+  CSS_TRY(ws_get(ctx, "e_U", (size_t)nc * nmax * nmax, &ea.U));
+  CSS_TRY(ws_get(ctx, "e_F", (size_t)nc * 5 * nmax * nmax, &ea.F));
+  CSS_TRY(ws_get(ctx, "e_lam", (size_t)nc * nmax, &ea.lam));
+  CSS_TRY(ws_get(ctx, "e_X0", (size_t)nc * nmax * b, &ea.X0));
+  CSS_TRY(ws_get(ctx, "e_Y", (size_t)nc * nmax * b, &ea.Y));
+  CSS_TRY(ws_get(ctx, "e_w", (size_t)nc * nmax, &ea.wgt));
+  CSS_TRY(ws_get(ctx, "e_st", (size_t)nc, &ea.status));
+  CSS_TRY(ws_get(ctx, "e_flag", (size_t)nc * nmax, &ea.flag));
+  CSS_TRY(css_eigen_ritz(ctx, ea, st));
+  double *YV, *scratch, *kap;
+  CSS_TRY(ws_get(ctx, "no_YV", (size_t)nc * nmax * b, &YV));
+  CSS_TRY(ws_get(ctx, "no_wsc", (size_t)nc * nmax, &scratch));
+  CSS_TRY(ws_get(ctx, "no_kap", (size_t)nc * nmax, &kap));
+  CSS_TRY(css_eigen_project(ctx, ea, Vc, YV, scratch, st));
+  k_kappa<<<(unsigned)css_ceil_div((int64_t)nc * nmax, T), T, 0, st>>>(nc, b, nmax, nblk, YV, ea.Y, kap);
+  CSS_LAUNCHED(ctx);
+  double *dmu, *dkT, *dhalf, *dmu_in, *dtol, *mupart;
+  int32_t* dsolve;
+  unsigned* bar;
+  CSS_TRY(ws_get(ctx, "no_mu", 8, &dmu));
+  CSS_TRY(ws_get(ctx, "no_fermi", 8, &dkT));
+  dhalf = dkT + 1;
+  dmu_in = dkT + 2;
+  dtol = dkT + 3;
+  CSS_TRY(ws_get(ctx, "no_solve", 8, &dsolve));
+  CSS_TRY(ws_get(ctx, "no_bar", 8, &bar));
+  {
+    double* hp;
+    CSS_TRY(css_pinned(ctx, 256, (void**)&hp));
+    hp[0] = fermi->kT;
+    hp[1] = 0.5 * fermi->n_elec;
+    hp[2] = fermi->mu;
+    hp[3] = fermi->ne_tol > 0.0 ? fermi->ne_tol : 1e-6 * std::max(1.0, 0.5 * fermi->n_elec);
+    ((int32_t*)(hp + 4))[0] = fermi->solve_mu ? 1 : 0;
+    CSS_CU(ctx, cudaMemcpyAsync(dkT, hp, 4 * sizeof(double), cudaMemcpyHostToDevice, st));
+    CSS_CU(ctx, cudaMemcpyAsync(dsolve, hp + 4, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CSS_CU(ctx, cudaMemsetAsync(bar, 0, 8 * sizeof(unsigned), st));
+    CSS_CU(ctx, cudaStreamSynchronize(st));  // the pinned staging is reused below
+  }
+  int occ = 0;
+  CSS_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mu, MU_T, 0));
+  unsigned G = (unsigned)std::max(1, std::min(ctx->n_sm * std::max(occ, 1), std::max(nc, 1)));
+  if (G > (unsigned)ctx->n_sm) G = (unsigned)ctx->n_sm;
+  CSS_TRY(ws_get(ctx, "no_mu_part", (size_t)4 * G + 16, &mupart));
+  {
+    int32_t n_sys_ = 1, n_col_ = nc, nmax_ = nmax, b_ = b;
+    const int32_t* nblk_ = nblk;
+    const int32_t* soc_ = soc;
+    const double* lam_ = ea.lam;
+    const double* w_ = kap;  // the electron count is Tr(rho S)
+    const double* kT_ = dkT;
+    const double* h_ = dhalf;
+    const double* tl_ = dtol;
+    const int32_t* sv_ = dsolve;
+    const double* mi_ = dmu_in;
+    double* mo_ = dmu;
+    double* pp_ = mupart;
+    unsigned* bar_ = bar;
+    int32_t* err_ = misc + 8;
+    void* args[] = {&n_sys_, &n_col_, &nmax_, &nblk_, &b_, &soc_, &lam_, &w_, &kT_, &h_, &tl_, &sv_, &mi_, &mo_, &pp_,
+                    &bar_, &err_};
+    CSS_CU(ctx, cudaLaunchCooperativeKernel((void*)k_mu, dim3(G), dim3(MU_T), args, 0, st));
+    ++ctx->kernel_launches;
+  }
+  CSS_TRY(css_eigen_z(ctx, ea, soc, dmu, dkT, Z, st, 0));
+
+  // ------------- pass 2: X~ = Phi Z over all rows, X = S~^(-1/2) X~, extraction
+  void* Xt = R;  // the probe blocks are no longer needed
+  void* X = SR;
+  CSS_CU(ctx, cudaMemsetAsync(Xt, 0, vbytes, st));
+  CSS_CU(ctx, cudaMemsetAsync(done, 0, nc * sizeof(int32_t), st));
+  k_inv_sqrt<<<(unsigned)css_ceil_div(nc, T), T, 0, st>>>(nc, cnt, isq, nblk, done, m);
+  CSS_LAUNCHED(ctx);
+  double* B0b;  // pass 2 recomputes B_0 (bitwise the same) into a scratch copy
+  CSS_TRY(ws_get(ctx, "no_B0b", (size_t)nc * bb, &B0b));
+  la.mode = 2;
+  la.Yfull = Xt;
+  la.ldy = ws;
+  la.ucol = nullptr;
+  la.Vc = nullptr;
+  la.B0 = B0b;
+  CSS_TRY(css_lanczos_pass(ctx, la, st));
+  CSS_TRY(spmm_with(S, siv, silo, Xt, X));
+  double *tpart, *tpart2, *tout;
+  const int64_t nh = (int64_t)Hp->nnzb * bb, ns = (int64_t)S->nnzb * bb;
+  const unsigned xblocks = (unsigned)css_ceil_div(nh, EX_T);
+  const unsigned tblocks = (unsigned)css_ceil_div(std::max(nh, ns), EX_T);
+  CSS_TRY(ws_get(ctx, "no_tpart", 2 * (size_t)xblocks + 2, &tpart));
+  CSS_TRY(ws_get(ctx, "no_tpart2", 2 * (size_t)tblocks + 2, &tpart2));
+  CSS_TRY(ws_get(ctx, "no_tout", 4, &tout));
+  const int sym = (flags & CSS_SYMMETRIZE) ? 1 : 0;
+  if (f32)
+    k_hp_extract<float><<<xblocks, EX_T, 0, st>>>(Hp->nnzb, b, hbrow, Hp->col_idx, colour, sign, (const float*)X, ws,
+                                                  sym, P_val, tpart);
+  else
+    k_hp_extract<double><<<xblocks, EX_T, 0, st>>>(Hp->nnzb, b, hbrow, Hp->col_idx, colour, sign, (const double*)X,
+                                                   ws, sym, P_val, tpart);
+  CSS_LAUNCHED(ctx);
+  k_trace_hs<<<tblocks, EX_T, 0, st>>>(nh, ns, b, P_val, H_val, Hp->row_ptr, Hp->col_idx, sbrow, S->col_idx, S->val,
+                                       tpart2, misc + 20);
+  CSS_LAUNCHED(ctx);
+  k_trace_sum<<<1, 1024, 0, st>>>((int32_t)tblocks, tpart2, tout);
+  CSS_LAUNCHED(ctx);
+  k_count_breakdown<<<(unsigned)css_ceil_div(nc, T), T, 0, st>>>(nc, m, nblk, cnt, misc + 16);
+  CSS_LAUNCHED(ctx);
+  k_status_or<<<(unsigned)css_ceil_div(nc, T), T, 0, st>>>(nc, ea.status, misc + 17);
+  CSS_LAUNCHED(ctx);
+
+  // -------------------------------------------------------------- read back
+  double* hres;
+  CSS_TRY(css_pinned(ctx, 256, (void**)&hres));
+  CSS_CU(ctx, cudaMemcpyAsync(hres, tout, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CSS_CU(ctx, cudaMemcpyAsync(hres + 2, dmu, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CSS_CU(ctx, cudaMemcpyAsync(hres + 4, misc, 24 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CSS_CU(ctx, cudaStreamSynchronize(st));
+  const int32_t* hm = (const int32_t*)(hres + 4);
+  if (trPH) *trPH = hres[0];
+  if (trPS) *trPS = hres[1];
+  if (mu_out) *mu_out = hres[2];
+  ctx->last_lam = ea.lam;
+  ctx->last_wgt = kap;
+  ctx->last_nblk = nblk;
+  ctx->last_ncol = nc;
+  ctx->last_b = b;
+  ctx->last_nmax = nmax;
+  ctx->last_A = Ablk;
+  ctx->last_B = Bblk;
+  ctx->last_m = m;
+  ctx->info.n_colours = nc;
+  ctx->info.n_breakdown = hm[16];
+  ctx->info.m = m;
+  if (hm[8]) {
+    ctx->last_error = "css_density_nonorth: grid barrier of the mu bisection timed out";
+    return CSS_ERR_TIMEOUT;
+  }
+  if (hm[17] & 2) {
+    ctx->last_error = "css_density_nonorth: a wait between pipelined band-reduction sweeps timed out";
+    return CSS_ERR_TIMEOUT;
+  }
+  if (hm[20]) return css_set_arg_error(ctx, "css_density_nonorth: S has a block outside H's pattern");
+  if (!std::isfinite(hres[0]) || !std::isfinite(hres[1]) || !std::isfinite(hres[2])) {
+    ctx->last_error = "css_density_nonorth: non-finite trace or mu";
+    return CSS_ERR_NUMERIC;
+  }
+  return hm[16] > 0 ? CSS_WARN_BREAKDOWN : CSS_OK;
 }
 
 }  // extern "C"

@@ -314,6 +314,15 @@ __global__ void k_apply_refl(int32_t kd, int32_t b, int32_t nmax, int32_t rcap, 
   }
 }
 
+// X0 = E_1 B_0 = [B_0; 0] for a general start factor B_0 [c][b][b]
+__global__ void k_x0_b0(int32_t b, int32_t nmax, const double* __restrict__ B0, double* __restrict__ X) {
+  const int32_t c = blockIdx.x;
+  for (int32_t t = threadIdx.x; t < nmax * b; t += blockDim.x) {
+    const int32_t i = t / b, k = t % b;
+    X[(size_t)c * nmax * b + t] = (i < b) ? B0[((size_t)c * b + i) * b + k] : 0.0;
+  }
+}
+
 // X0 = E_1 B_0 = sqrt|c| [I_b; 0]
 __global__ void k_x0(int32_t b, int32_t nmax, const int32_t* __restrict__ cnt, double* __restrict__ X) {
   const int32_t c = blockIdx.x;
@@ -977,7 +986,10 @@ css_status css_eigen_ritz(css_ctx* ctx, const EigArgs& a, cudaStream_t st) {
   k_band_to_tri<<<nc, 1024, 0, st>>>(b, nmax, ldb, a.rcap, a.nblk, a.AB, a.RV, a.RT, a.RR0, a.sweep_off, a.d, a.e,
                                      a.status);
   CSS_LAUNCHED(ctx);
-  k_x0<<<nc, 256, 0, st>>>(b, nmax, a.cnt, a.X0);
+  if (a.B0)
+    k_x0_b0<<<nc, 256, 0, st>>>(b, nmax, a.B0, a.X0);
+  else
+    k_x0<<<nc, 256, 0, st>>>(b, nmax, a.cnt, a.X0);
   CSS_LAUNCHED(ctx);
   k_apply_refl<true><<<nc, 1024, 0, st>>>(b, b, nmax, a.rcap, a.nblk, a.RV, a.RT, a.RR0, a.sweep_off, a.X0);
   CSS_LAUNCHED(ctx);
@@ -1009,6 +1021,16 @@ css_status css_eigen_z(css_ctx* ctx, const EigArgs& a, const int32_t* sys_of_col
                                                  fn);
   CSS_LAUNCHED(ctx);
   k_apply_refl<false><<<nc, 1024, 0, st>>>(b, b, nmax, a.rcap, a.nblk, a.RV, a.RT, a.RR0, a.sweep_off, Z);
+  CSS_LAUNCHED(ctx);
+  return CSS_OK;
+}
+
+css_status css_eigen_project(css_ctx* ctx, const EigArgs& a, double* V, double* YV, double* scratch, cudaStream_t st) {
+  const int32_t nc = a.n_col, b = a.b, nmax = a.m * b;
+  k_apply_refl<true><<<nc, 1024, 0, st>>>(b, b, nmax, a.rcap, a.nblk, a.RV, a.RT, a.RR0, a.sweep_off, V);
+  CSS_LAUNCHED(ctx);
+  dim3 g((unsigned)css_ceil_div(nmax, 128), (unsigned)nc);
+  k_ritz_y<<<g, 128, 64 * b * sizeof(double), st>>>(b, b, nmax, a.nblk, a.U, V, YV, scratch);
   CSS_LAUNCHED(ctx);
   return CSS_OK;
 }

@@ -20,6 +20,7 @@ struct EigArgs {
   const double* Bblk = nullptr;        // [c][m][b][b]
   const int32_t* nblk = nullptr;       // [c] blocks in use (0 for an empty colour)
   const int32_t* cnt = nullptr;        // [c] molecules of the colour
+  const double* B0 = nullptr;          // [c][b][b] general start factor (nullptr: B_0 = sqrt|c| I)
   int32_t rcap = 0;                    // reflector slots per colour
   double* AB = nullptr;                // [c][nmax][2b+1]
   double* RV = nullptr;                // [c][rcap][b]
@@ -42,3 +43,7 @@ struct EigArgs {
 css_status css_eigen_ritz(css_ctx* ctx, const EigArgs& a, cudaStream_t st);
 css_status css_eigen_z(css_ctx* ctx, const EigArgs& a, const int32_t* sys_of_colour, const double* mu,
                        const double* kT, double* Z, cudaStream_t st, int fn = 0);
+// after css_eigen_ritz: YV = U^T Q_band^T V for another n x b block per colour ([c][nmax][b], V is
+// overwritten by Q_band^T V), in the same order of operations that gives Y from E_1 B_0; scratch
+// receives the row norms
+css_status css_eigen_project(css_ctx* ctx, const EigArgs& a, double* V, double* YV, double* scratch, cudaStream_t st);

@@ -775,6 +775,32 @@ __global__ void k_chol(int32_t ncb, int32_t b, int32_t cb0, int32_t m, int32_t j
   }
 }
 
+// M[lc] = I_b for the colours of the batch
+__global__ void k_eye(int32_t ncb, int32_t b, double* __restrict__ M) {
+  const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ncb * b * b) return;
+  const int32_t e = t % (b * b);
+  M[t] = (e / b == e % b) ? 1.0 : 0.0;
+}
+
+// hq2[lc] = trace of the Gram G[lc] = ||W_c||_F^2 (breakdown scale of a start block)
+__global__ void k_gtrace(int32_t ncb, int32_t b, const double* __restrict__ G, double* __restrict__ hq2) {
+  const int32_t lc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (lc >= ncb) return;
+  double s = 0.0;
+  for (int32_t k = 0; k < b; ++k) s += G[((size_t)lc * b + k) * b + k];
+  hq2[lc] = s;
+}
+
+// Vc[cb0 + lc][j b + k][l] = P[lc][k][l]
+__global__ void k_store_v(int32_t ncb, int32_t b, int32_t cb0, int32_t nmax, int32_t j, const double* __restrict__ P,
+                          double* __restrict__ Vc) {
+  const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ncb * b * b) return;
+  const int32_t lc = t / (b * b), e = t % (b * b), k = e / b, l = e % b;
+  Vc[((size_t)(cb0 + lc) * nmax + (size_t)j * b + k) * b + l] = P[t];
+}
+
 // Q_1 = R_c / sqrt|c| for the colours of the batch (the rest of Q is zeroed by the caller)
 template <typename T>
 __global__ void k_init_q1(int32_t n_brow, int32_t b, int32_t ws, int32_t cb0, int32_t ncb,
@@ -956,6 +982,7 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
   double* sR2i = sR2 + (size_t)ncb * bb;
   double* sC1 = sR2i + (size_t)ncb * bb;
   double* sKp = sC1 + (size_t)ncb * bb;
+  double* sV = sKp + (size_t)ncb * bb;  // Q_j^T u of the running step (the tenth small matrix)
   const unsigned rblocks_bb = (unsigned)css_ceil_div((int64_t)ncb * bb, 256);
   const int64_t pb = a.pair_off_h[a.cb0], pe = a.pair_off_h[a.cb0 + ncb];
   const unsigned sblocks = (unsigned)css_ceil_div((pe - pb) * bb, 256);
@@ -965,11 +992,57 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
   CSS_TRY(smem_optin(ctx, s3, sm_s3));
   CSS_TRY(smem_optin(ctx, k_tri<T, BP, true>, sm_tri));
   CSS_TRY(smem_optin(ctx, k_tri<T, BP, false>, sm_tri));
+  if (a.ucol) CSS_TRY(smem_optin(ctx, k_s1<T, BP, false>, sm_s1));
   CSS_CU(ctx, cudaMemsetAsync(Qp, 0, vec_bytes, st));
   CSS_CU(ctx, cudaMemsetAsync(Qc, 0, vec_bytes, st));
-  k_init_q1<T><<<(unsigned)css_ceil_div(N, 256), 256, 0, st>>>(a.n_brow, b, a.ws, a.cb0, ncb, a.colour, a.sign,
-                                                                a.inv_sqrt_cnt, Qc);
-  CSS_LAUNCHED(ctx);
+  if (a.start) {
+    // Q_1 B_0 = start by the shifted CholeskyQR3 of the steps below: the start block is copied
+    // into W (times the identity) with its Gram, and B_0 is the product of the three factors
+    k_eye<<<rblocks_bb, 256, 0, st>>>(ncb, b, sR1i);
+    CSS_LAUNCHED(ctx);
+    k_tri<T, BP, true><<<rgrid, row_threads<T, BP>(b), sm_tri, st>>>(N, b, a.ws, ncb, (const T*)a.start, W, sR1i,
+                                                                     partKq);
+    CSS_LAUNCHED(ctx);
+    k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
+    CSS_LAUNCHED(ctx);
+    k_gtrace<<<(unsigned)css_ceil_div(ncb, 128), 128, 0, st>>>(ncb, b, sG, sH);
+    CSS_LAUNCHED(ctx);
+    const unsigned gb = (unsigned)css_ceil_div(ncb, 4);
+    k_chol<0><<<gb, 128, 0, st>>>(ncb, b, a.cb0, 1, 0, sG, sH, a.tau, a.shift_rel, sR1, sR1i, sC1, a.B0, a.done,
+                                  a.nblk);
+    CSS_LAUNCHED(ctx);
+    CSS_CU(ctx, cudaMemcpyAsync(sC1, sR1, sizeof(double) * ncb * bb, cudaMemcpyDeviceToDevice, st));
+    k_tri<T, BP, true><<<rgrid, row_threads<T, BP>(b), sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
+    CSS_LAUNCHED(ctx);
+    k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
+    CSS_LAUNCHED(ctx);
+    k_chol<1><<<gb, 128, 0, st>>>(ncb, b, a.cb0, 1, 0, sG, sH, a.tau, 0.0, sR1, sR1i, sC1, a.B0, a.done, a.nblk);
+    CSS_LAUNCHED(ctx);
+    k_tri<T, BP, true><<<rgrid, row_threads<T, BP>(b), sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
+    CSS_LAUNCHED(ctx);
+    k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
+    CSS_LAUNCHED(ctx);
+    k_chol<2><<<gb, 128, 0, st>>>(ncb, b, a.cb0, 1, 0, sG, sH, a.tau, 0.0, sR2, sR2i, sC1, a.B0, a.done, a.nblk);
+    CSS_LAUNCHED(ctx);
+    k_tri<T, BP, false><<<rgrid, row_threads<T, BP>(b), sm_tri, st>>>(N, b, a.ws, ncb, W, Qc, sR2i, nullptr);
+    CSS_LAUNCHED(ctx);
+  } else {
+    k_init_q1<T><<<(unsigned)css_ceil_div(N, 256), 256, 0, st>>>(a.n_brow, b, a.ws, a.cb0, ncb, a.colour, a.sign,
+                                                                  a.inv_sqrt_cnt, Qc);
+    CSS_LAUNCHED(ctx);
+  }
+  // Vc[c][j] = Q_j^T u (the u block is only read: the first-step form of the three-term kernel)
+  auto project_u = [&](const T* Qj, int32_t j) -> css_status {
+    if (!a.ucol) return CSS_OK;
+    k_s1<T, BP, false><<<rgrid, RW, sm_s1, st>>>(N, b, a.ws, ncb, a.cb0, nullptr, Qj, (T*)a.ucol, nullptr, 1,
+                                                  partKq, nullptr);
+    CSS_LAUNCHED(ctx);
+    k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sV);
+    CSS_LAUNCHED(ctx);
+    k_store_v<<<rblocks_bb, 256, 0, st>>>(ncb, b, a.cb0, m * b, j, sV, a.Vc);
+    CSS_LAUNCHED(ctx);
+    return CSS_OK;
+  };
   auto sampled = [&](const T* Qj, int32_t j) -> css_status {
     if (a.mode == 2 && a.Yfull) {
       k_accum_full<T><<<(unsigned)((int64_t)a.n_brow * b), 128, 0, st>>>(b, a.ws, a.ncb, a.cb0, a.ldz, j, a.nblk,
@@ -1002,6 +1075,7 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
     return CSS_OK;
   };
   CSS_TRY(sampled(Qc, 0));
+  CSS_TRY(project_u(Qc, 0));
   for (int32_t j = 0; j < m; ++j) {
     if (a.ev_spmm) CSS_CU(ctx, cudaEventRecord(a.ev_spmm[2 * j], st));
     CSS_TRY(launch_spmm<T>(ctx, a, Qc, W, st));
@@ -1043,6 +1117,7 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
     k_tri<T, BP, false><<<rgrid, row_threads<T, BP>(b), sm_tri, st>>>(N, b, a.ws, ncb, W, Qp, sR2i, nullptr);
     CSS_LAUNCHED(ctx);
     CSS_TRY(sampled(Qp, j + 1));
+    CSS_TRY(project_u(Qp, j + 1));
     // B_{j} for the next step's three-term update, in the batch's local layout
     CSS_CU(ctx, cudaMemcpy2DAsync(a.Bblk_prev + (size_t)a.cb0 * bb, bb * sizeof(double),
                                   a.Bblk + ((size_t)a.cb0 * m + j) * bb, (size_t)m * bb * sizeof(double),
@@ -1083,6 +1158,54 @@ size_t css_lanczos_part_doubles(int64_t N, int32_t b, int32_t ncb) {
 size_t css_lanczos_small_doubles(int32_t b, int32_t ncb) { return (size_t)ncb * b * b * 10 + ncb + 64; }
 
 int32_t css_spmm_bm(int32_t b) { return b <= 8 ? 8 : b <= 12 ? 12 : b <= 16 ? 16 : b <= 24 ? 24 : 32; }
+
+css_status css_spmm_prepare_as(css_ctx* ctx, const char* tag, bool fp32, int32_t b, int32_t n_brow, int32_t nnzb,
+                               const int32_t* row_ptr, const int32_t* col_idx, const double* H, const void** Hpad,
+                               const void** Hlo_pad, cudaStream_t st) {
+  const int32_t BM = css_spmm_bm(b);
+  const int64_t bb = (int64_t)BM * BM;
+  constexpr int T = 256;
+  char n1[64], n2[64];
+  snprintf(n1, sizeof(n1), "%s_pad%d", tag, fp32 ? 32 : 64);
+  snprintf(n2, sizeof(n2), "%s_lopad32", tag);
+  if (fp32) {
+    float *hp, *lp;
+    CSS_TRY(css_ws(ctx, n1, (size_t)nnzb * bb * sizeof(float), (void**)&hp));
+    CSS_TRY(css_ws(ctx, n2, (size_t)n_brow * bb * sizeof(float), (void**)&lp));
+    k_hpad<float, false><<<(unsigned)css_ceil_div((int64_t)nnzb * bb, T), T, 0, st>>>(nnzb, b, BM, H, row_ptr,
+                                                                                       col_idx, hp);
+    CSS_LAUNCHED(ctx);
+    k_hpad<float, true><<<(unsigned)css_ceil_div((int64_t)n_brow * bb, T), T, 0, st>>>(n_brow, b, BM, H, row_ptr,
+                                                                                       col_idx, lp);
+    CSS_LAUNCHED(ctx);
+    *Hpad = hp;
+    *Hlo_pad = lp;
+  } else {
+    double* hp;
+    CSS_TRY(css_ws(ctx, n1, (size_t)nnzb * bb * sizeof(double), (void**)&hp));
+    k_hpad<double, false><<<(unsigned)css_ceil_div((int64_t)nnzb * bb, T), T, 0, st>>>(nnzb, b, BM, H, row_ptr,
+                                                                                        col_idx, hp);
+    CSS_LAUNCHED(ctx);
+    *Hpad = hp;
+    *Hlo_pad = nullptr;
+  }
+  return CSS_OK;
+}
+
+css_status css_probe_block(css_ctx* ctx, bool fp32, int32_t n_brow, int32_t b, int32_t ws, int32_t cb0, int32_t ncb,
+                           const int32_t* colour, const int8_t* sign, const double* scale, void* out,
+                           cudaStream_t st) {
+  const int64_t N = (int64_t)n_brow * b;
+  CSS_CU(ctx, cudaMemsetAsync(out, 0, (size_t)N * ws * (fp32 ? sizeof(float) : sizeof(double)), st));
+  if (fp32)
+    k_init_q1<float><<<(unsigned)css_ceil_div(N, 256), 256, 0, st>>>(n_brow, b, ws, cb0, ncb, colour, sign, scale,
+                                                                      (float*)out);
+  else
+    k_init_q1<double><<<(unsigned)css_ceil_div(N, 256), 256, 0, st>>>(n_brow, b, ws, cb0, ncb, colour, sign, scale,
+                                                                       (double*)out);
+  CSS_LAUNCHED(ctx);
+  return CSS_OK;
+}
 
 css_status css_spmm_prepare(css_ctx* ctx, bool fp32, int32_t b, int32_t n_brow, int32_t nnzb,
                             const int32_t* row_ptr, const int32_t* col_idx, const double* H, const void** Hpad,

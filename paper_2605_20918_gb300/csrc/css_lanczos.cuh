@@ -40,6 +40,14 @@ struct LzArgs {
   cudaEvent_t* ev_spmm = nullptr;    // when set: 2 events per step bracket each H*V launch
   void* Yfull = nullptr;             // mode 2 only: also Y += Q_j Z_c[j] over ALL rows, [N][ldy] in the
   int32_t ldy = 0;                   //   vector precision, colour c at columns [c b, c b + b)
+  // general start block (non-orthogonal basis): when set, Q_1 B_0 = start (N x ws, the batch's
+  // colours in their columns) by shifted CholeskyQR3 instead of Q_1 = R_c / sqrt|c|, and B_0 goes
+  // to B0 [colour][b][b]
+  const void* start = nullptr;
+  double* B0 = nullptr;
+  // when set: Vc[colour][j b + k][l] = (Q_j^T u)[k][l] for every block j (u: N x ws)
+  const void* ucol = nullptr;
+  double* Vc = nullptr;
 };
 
 css_status css_lanczos_pass(css_ctx* ctx, const LzArgs& a, cudaStream_t st);
@@ -55,3 +63,13 @@ int32_t css_spmm_bm(int32_t b);
 css_status css_spmm_prepare(css_ctx* ctx, bool fp32, int32_t b, int32_t n_brow, int32_t nnzb,
                             const int32_t* row_ptr, const int32_t* col_idx, const double* H, const void** Hpad,
                             const void** Hlo_pad, cudaStream_t st);
+// the same into workspace buffers of their own (named after `tag`), so that several matrices can
+// be prepared at once
+css_status css_spmm_prepare_as(css_ctx* ctx, const char* tag, bool fp32, int32_t b, int32_t n_brow, int32_t nnzb,
+                               const int32_t* row_ptr, const int32_t* col_idx, const double* H, const void** Hpad,
+                               const void** Hlo_pad, cudaStream_t st);
+// probe block: out (N x ws, zeroed here) holds scale[c] * sign on orbital k of every molecule of
+// colour c in column c b + k, for the colours [cb0, cb0 + ncb)
+css_status css_probe_block(css_ctx* ctx, bool fp32, int32_t n_brow, int32_t b, int32_t ws, int32_t cb0, int32_t ncb,
+                           const int32_t* colour, const int8_t* sign, const double* scale, void* out,
+                           cudaStream_t st);
