@@ -94,3 +94,18 @@ def test_hprime_pbuild_eigen_refuse_wrong_sizes(sys64):
     A = torch.zeros((3, 4, b, b), dtype=torch.float64)
     with pytest.raises(ValueError, match="nblk has"):
         css.css_eigen_blocks(None, A, A, _i32(2), _i32(3))
+
+
+def test_density_nonorth_refuses_wrong_sizes(sys64):
+    _, H, Hd = sys64
+    n, b = H.n_brow, H.b
+    col, sign = _i32(n), torch.ones(n * b, dtype=torch.int8)
+    P = torch.zeros((H.nnzb, b, b), dtype=torch.float64)
+    with pytest.raises(ValueError, match="Sinv has"):
+        css.css_density_nonorth(None, Hd, P[:-1], Hd, P, col, sign, 4, P)
+    with pytest.raises(ValueError, match="H_val has"):
+        css.css_density_nonorth(None, Hd, P, Hd, P[:-1], col, sign, 4, P)
+    with pytest.raises(ValueError, match="P has"):
+        css.css_density_nonorth(None, Hd, P, Hd, P, col, sign, 4, P[:-1])
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        css.css_density_nonorth(None, Hd, P, Hd, P, col, sign, 4, P)
