@@ -857,3 +857,22 @@ def test_solve_mu_on_ritz_lists_is_the_density_rule(O):
             assert np.array_equal(sub[c][0], full[c][0]) and np.array_equal(sub[c][1], full[c][1])
         else:
             assert sub[c][0].size == 0
+
+
+def test_nonorth_idempotent_in_the_overlap_metric(O):
+    """Full patterns, one molecule per colour, full Krylov spaces and a small kT: the density
+    matrix of the non-orthogonal basis is a projector in the S metric, rho S rho = rho, and
+    holds N_e/2 electrons in Tr(rho S)."""
+    g = synth.water_box(6, box=6.0)
+    S = synth.overlap(g, r_cut=20.0)
+    H = synth.hamiltonian(g, r_cut=20.0)
+    col, nc = O.color(g.pos, g.box, 100.0, 1004)
+    s = O.probes(col, S.b, 1005)
+    hp = O.hprime(S, H, col, s, nc, m=6)
+    ne = synth.n_electrons(6)
+    r = O.density_nonorth(S, hp["Sinv"], H, hp["Hp"], col, s, nc, kT=1e-3, n_elec=ne, m=6)
+    rho = _dense_from_blocks(H, r["P"])
+    Sd = S.dense()
+    assert np.abs(rho @ Sd @ rho - rho).max() < 1e-9
+    assert abs(np.trace(rho @ Sd) - 0.5 * ne) < 1e-9
+    assert abs(r["trPS"] - 0.5 * ne) < 1e-9
