@@ -99,8 +99,9 @@ typedef struct {
  * function.  solve_mu != 0: mu is taken from the Ritz quadrature N(mu) = sum_c sum_k
  * f(lambda_ck) w_ck of Tr P (P per spin): it is the midpoint of the set of mu where
  * |N(mu) - n_elec/2| <= ne_tol (each end by bisection), i.e. the root for a metal and
- * mid-gap for an insulator; ne_tol <= 0 selects 1e-6 * n_elec/2.  Otherwise `mu` is used
- * as given. */
+ * mid-gap for an insulator; ne_tol <= 0 selects 1e-4 * n_elec/2 (above the spurious Ritz
+ * weight that a truncated Krylov projection leaves inside a gap, so that the ends of the set
+ * are the band edges).  Otherwise `mu` is used as given. */
 typedef struct {
   double mu, kT, n_elec, ne_tol;
   int32_t solve_mu;
@@ -147,7 +148,9 @@ CSS_API css_status css_color(css_ctx* ctx, const css_geom* geom, double r_col, u
                      int32_t* n_colours, void* stream);
 
 /* Same colouring rule on an explicit graph: device CSR adj_ptr[n+1], adj[adj_ptr[n]]
- * (symmetric, no self loops; neighbour order irrelevant). */
+ * (symmetric, no self loops; neighbour order irrelevant).  The pattern is checked on the device
+ * before the rounds: adj_ptr[0] != 0, a decreasing adj_ptr or a neighbour outside [0, n) gives
+ * CSS_ERR_INVALID_ARG (adj must hold adj_ptr[n] entries; the call cannot check that). */
 CSS_API css_status css_color_graph(css_ctx* ctx, int32_t n, const int32_t* adj_ptr, const int32_t* adj, uint64_t seed,
                            int32_t* colour, int32_t* n_colours, void* stream);
 
@@ -296,7 +299,10 @@ CSS_API css_status css_eigen_blocks(css_ctx* ctx, int32_t n_col, int32_t b, int3
  *   array: calls that overlap on the GPU (several streams or host threads at once) race and
  *   must be serialised by the caller.
  *   The first call on a device looks the array's device address up (cudaGetSymbolAddress, with
- *   that device current) and caches it; make that first call before any stream capture.
+ *   that device current) and caches it for the life of the process; make that first call before
+ *   any stream capture.  The cached address does not survive cudaDeviceReset (or any other
+ *   teardown of the device's primary context): do not call this entry point after one.
+ *   The graph is checked as in css_color_graph (CSS_ERR_INVALID_ARG for a malformed pattern).
  *   adj_ptr, adj, colour: device arrays as in css_color_graph (colour int32[n], written);
  *   n_colours: host int32*, written; the call synchronises `stream`. */
 #define CSS_NOALLOC_MAX_VERTICES 262144

@@ -233,6 +233,26 @@ __global__ void k_jp_round(int32_t n, const int32_t* __restrict__ adj_ptr, const
   }
 }
 
+// An explicit graph must have adj_ptr[0] = 0, non-decreasing adj_ptr and every neighbour in
+// [0, n): vertex i checks its own row and sets *bad otherwise (its entries are then not read)
+__global__ void k_graph_check(int32_t n, const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
+                              int32_t* __restrict__ bad) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t s = adj_ptr[i], e = adj_ptr[i + 1];
+  if ((i == 0 && s != 0) || e < s) {
+    atomicOr(bad, 1);
+    return;
+  }
+  for (int32_t k = s; k < e; ++k) {
+    const int32_t u = adj[k];
+    if (u < 0 || u >= n) {
+      atomicOr(bad, 1);
+      return;
+    }
+  }
+}
+
 __global__ void k_max_colour(int32_t n, const int32_t* __restrict__ colour, int32_t* __restrict__ maxc) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   int32_t c = i < n ? colour[i] : -1;
@@ -398,6 +418,15 @@ css_status css_color_impl(css_ctx* ctx, int32_t n, const double* xyz, double box
   CSS_TRY(css_ws(ctx, "jp_deg", sizeof(int32_t) * n, (void**)&deg));
   CSS_TRY(css_ws(ctx, "jp_key", sizeof(uint64_t) * n, (void**)&key));
   CSS_TRY(css_ws(ctx, "jp_counters", sizeof(int32_t) * 64, (void**)&counters));
+  if (!xyz) {  // a caller's graph: refuse a malformed pattern before any round reads through it
+    CSS_CU(ctx, cudaMemsetAsync(counters + 40, 0, sizeof(int32_t), st));
+    k_graph_check<<<nbk, T, 0, st>>>(n, adj_ptr, adj, counters + 40);
+    CSS_LAUNCHED(ctx);
+    CSS_CU(ctx, cudaMemcpyAsync(hbuf, counters + 40, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CSS_CU(ctx, cudaStreamSynchronize(st));
+    if (hbuf[0] != 0)
+      return css_set_arg_error(ctx, "css_color_graph: adj_ptr not non-decreasing from 0 or a neighbour outside [0, n)");
+  }
   k_jp_init<<<nbk, T, 0, st>>>(n, adj_ptr, seed, deg, key, colour);
   CSS_LAUNCHED(ctx);
   // rounds, checked in groups; every round colours at least the highest-priority uncoloured

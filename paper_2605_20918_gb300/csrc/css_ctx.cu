@@ -85,6 +85,11 @@ css_status css_create(css_ctx** out, int device) {
   if (sv && sv[0] >= '0' && sv[0] <= '4' && sv[1] == 0) ctx->spmm_variant = sv[0] - '0';
   const char* de = getenv("CSS_DEBUG_EIG");
   ctx->debug_eig = de ? atoi(de) : 0;
+  const char* tb = getenv("CSS_TEST_MU_BARRIER_EXTRA");
+  const int extra = tb ? atoi(tb) : 0;
+  ctx->test_mu_barrier_extra = extra > 0 && extra < 64 ? extra : 0;
+  const char* tc = getenv("CSS_HV_TC");
+  ctx->hv_tc = !(tc && tc[0] == '0');
   *out = ctx;
   return CSS_OK;
 }

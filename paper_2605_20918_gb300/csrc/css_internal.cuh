@@ -61,6 +61,13 @@ struct css_ctx {
   // H * V autotuner: launch variant chosen per (precision, block width, column count, rows)
   std::vector<std::pair<uint64_t, int>> spmm_tune;
   int spmm_variant = -1;  // env CSS_SPMM_VARIANT = 0..4 fixes the variant (no tuning)
+  // failure injection for tests (env CSS_TEST_MU_BARRIER_EXTRA = k at css_create): the grid
+  // barrier of the mu bisection waits for k CTAs more than the launch has, so its bounded wait
+  // runs out and the call returns CSS_ERR_TIMEOUT; 0 (the default) is the normal barrier
+  int32_t test_mu_barrier_extra = 0;
+  // FP32 H * V on the tensor cores where the block width allows it (env CSS_HV_TC=0 at
+  // css_create selects the CUDA-core kernel instead)
+  bool hv_tc = true;
 };
 
 // CUDA events owned by the holder: destroyed when it goes out of scope, early returns included

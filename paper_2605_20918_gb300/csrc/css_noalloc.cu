@@ -79,6 +79,26 @@ __global__ void k_na_round(int32_t n, const int32_t* __restrict__ adj_ptr, const
   }
 }
 
+// adj_ptr[0] = 0, adj_ptr non-decreasing and every neighbour in [0, n), else counters[40] != 0
+__global__ void k_na_check(int32_t n, const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
+                           unsigned char* scratch) {
+  int32_t* counters = reinterpret_cast<int32_t*>(scratch);
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t s = adj_ptr[i], e = adj_ptr[i + 1];
+  if ((i == 0 && s != 0) || e < s) {
+    atomicOr(&counters[40], 1);
+    return;
+  }
+  for (int32_t k = s; k < e; ++k) {
+    const int32_t u = adj[k];
+    if (u < 0 || u >= n) {
+      atomicOr(&counters[40], 1);
+      return;
+    }
+  }
+}
+
 __global__ void k_na_max(int32_t n, const int32_t* __restrict__ colour, unsigned char* scratch) {
   int32_t* counters = reinterpret_cast<int32_t*>(scratch);
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -115,6 +135,16 @@ css_status css_color_graph_noalloc(int32_t n, const int32_t* adj_ptr, const int3
   cudaStream_t st = (cudaStream_t)stream;
   const unsigned nbk = (unsigned)((n + 255) / 256);
   int32_t* counters = reinterpret_cast<int32_t*>(scratch);
+  // a malformed graph is refused before any round reads through it (the flag keeps the previous
+  // call's value, so it is cleared first)
+  int32_t bad = 0;
+  if ((e = cudaMemsetAsync(counters + 40, 0, sizeof(int32_t), st)) != cudaSuccess) return na_error(e);
+  k_na_check<<<nbk, 256, 0, st>>>(n, adj_ptr, adj, scratch);
+  if ((e = cudaGetLastError()) != cudaSuccess) return na_error(e);
+  if ((e = cudaMemcpyAsync(&bad, counters + 40, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return na_error(e);
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return na_error(e);
+  if (bad) return CSS_ERR_INVALID_ARG;
   k_na_init<<<nbk, 256, 0, st>>>(n, adj_ptr, seed, scratch, colour);
   if ((e = cudaGetLastError()) != cudaSuccess) return na_error(e);
   const int group = 8;

@@ -69,8 +69,56 @@ def test_two_calls_in_a_row_match_the_regular_entry_point(torch, lib):
     for n, p, seed in [(3000, 0.01, 5), (600, 0.2, 9)]:
         ptr, adj = _graph(n, p, seed)
         ref, nref = _regular(torch, ptr, adj, 1004)
-        got, ng = _noalloc(torch, lib, ptr, adj, 1004)
-        assert ng == nref and np.array_equal(got, ref)
+        for _ in range(2):  # the second call starts from the first call's leftover scratch
+            got, ng = _noalloc(torch, lib, ptr, adj, 1004)
+            assert ng == nref and np.array_equal(got, ref)
+
+
+def test_a_warm_call_allocates_no_device_memory(torch, lib):
+    """The property the entry point exists for: once its inputs and outputs exist, a call takes
+    no device memory (free bytes as the driver reports them, and torch's caching allocator)."""
+    ptr, adj = _graph(2000, 0.02, 3)
+    dp = torch.as_tensor(ptr, device="cuda")
+    da = torch.as_tensor(adj, device="cuda")
+    col = torch.empty(2000, dtype=torch.int32, device="cuda")
+    nc = C.c_int32()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def call():
+        return lib.css_color_graph_noalloc(2000, C.c_void_p(dp.data_ptr()), C.c_void_p(da.data_ptr()),
+                                           C.c_uint64(11), C.c_void_p(col.data_ptr()), C.byref(nc), stream)
+
+    assert call() == 0  # warm: the library is loaded and the scratch address looked up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    for _ in range(3):
+        assert call() == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert torch.cuda.memory_reserved() == reserved0
+
+
+def test_refuses_a_malformed_graph(torch, lib):
+    """A neighbour outside [0, n) or a decreasing adj_ptr is refused on the device before any
+    round reads through it, and the next call on a good graph is unaffected."""
+    ptr, adj = _graph(500, 0.05, 4)
+    ref, nref = _regular(torch, ptr, adj, 21)
+    bad_adj = adj.copy()
+    bad_adj[len(bad_adj) // 2] = 500  # one past the last vertex
+    bad_ptr = ptr.copy()
+    bad_ptr[100] = bad_ptr[101] + 1  # decreasing
+    for p_, a_ in ((ptr, bad_adj), (bad_ptr, adj)):
+        dp = torch.as_tensor(p_, device="cuda")
+        da = torch.as_tensor(a_, device="cuda")
+        col = torch.empty(500, dtype=torch.int32, device="cuda")
+        nc = C.c_int32()
+        st = lib.css_color_graph_noalloc(500, C.c_void_p(dp.data_ptr()), C.c_void_p(da.data_ptr()), C.c_uint64(21),
+                                         C.c_void_p(col.data_ptr()), C.byref(nc), None)
+        assert st == 1  # CSS_ERR_INVALID_ARG
+    got, ng = _noalloc(torch, lib, ptr, adj, 21)
+    assert ng == nref and np.array_equal(got, ref)
 
 
 def test_geometric_graph_and_repeat(torch, lib):
