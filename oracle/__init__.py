@@ -226,7 +226,7 @@ def density(H, colour, sign, n_colours: int, *, mu: float = 0.0, kT: float = 0.0
             ne_tol: float = 0.0):
     """CSS density matrix on H's pattern.
 
-    ne_tol: electron-count tolerance of the mu rule (<= 0: 1e-6 N_e/2).
+    ne_tol: electron-count tolerance of the mu rule (<= 0: 1e-4 N_e/2).
     Returns dict(P=(nnzb, b, b), trP, trPH, mu, n_breakdown)."""
     colour = np.ascontiguousarray(colour, dtype=np.int32)
     sign = np.ascontiguousarray(sign, dtype=np.int8)

@@ -31,10 +31,13 @@
  *   - probe signs s[J*b+k] = -1 if bit 0 of h(sign_seed, J*b+k) is set, else +1;
  *   - Fermi-Dirac f(x) = (1 - tanh((x - mu) / (2 kT))) / 2, step function at kT = 0;
  *   - mu: the Ritz quadrature N(mu) = sum_c sum_j f(lambda_cj) w_cj of Tr P must match N_e/2;
- *     mu is the midpoint of the set where |N(mu) - N_e/2| <= ne_tol (default 1e-6 N_e/2),
+ *     mu is the midpoint of the set where |N(mu) - N_e/2| <= ne_tol (default 1e-4 N_e/2),
  *     each end found by bisection on [min lambda - 1, max lambda + 1] until
  *     hi - lo <= 1e-13 max(1, |mid|) or 200 halvings (mid-gap for an insulator, the root for
- *     a metal; the paper works at T = 0 and does not state how mu is fixed);
+ *     a metal; the paper works at T = 0 and does not state how mu is fixed).  The quadrature
+ *     of a truncated, contaminated Krylov projection puts a thin spread of spurious Ritz weight
+ *     inside the gap; ne_tol must exceed its total so that the ends of the set are the band
+ *     edges, not points inside that spread;
  *   - breakdown: stop the colour's recurrence at step j when min_k R_kk of the QR of the
  *     new block is <= 1e-10 ||H Q_j||_F; its projected matrix then has j blocks;
  *   - no reorthogonalisation unless CSS_REF_REORTH_LOCAL (one more pass against Q_j, Q_j-1);
@@ -640,7 +643,7 @@ static double ref_solve_mu(int32_t nwork, const int32_t* nj, int32_t nmax, const
 int css_ref_solve_mu(int32_t n_lists, const int32_t* n_per, int32_t nmax, const double* lam, const double* wgt,
                      double kT, double n_elec, double ne_tol, double* mu) {
   if (n_lists < 1 || nmax < 1 || !n_per || !lam || !wgt || !mu || kT < 0.0) return REF_ERR_ARG;
-  if (!(ne_tol > 0.0)) ne_tol = 1e-6 * fmax(1.0, 0.5 * n_elec);
+  if (!(ne_tol > 0.0)) ne_tol = 1e-4 * fmax(1.0, 0.5 * n_elec);
   *mu = ref_solve_mu(n_lists, n_per, nmax, lam, wgt, kT, n_elec, ne_tol);
   return isfinite(*mu) ? REF_OK : REF_ERR_NUMERIC;
 }
@@ -656,7 +659,7 @@ int css_ref_density(int32_t n_brow, int32_t b, int32_t nnzb, const int32_t* row_
   if (n_brow < 1 || b < 1 || m < 1 || n_colours < 1 || nnzb < n_brow || !P_val) return REF_ERR_ARG;
   if (colour_subset && solve_mu) return REF_ERR_ARG;
   if (kT < 0.0) return REF_ERR_ARG;
-  if (!(ne_tol > 0.0)) ne_tol = 1e-6 * fmax(1.0, 0.5 * n_elec);
+  if (!(ne_tol > 0.0)) ne_tol = 1e-4 * fmax(1.0, 0.5 * n_elec);
   ref_h H = {n_brow, b, row_ptr, col_idx, val};
   const int64_t N = (int64_t)n_brow * b;
   const int32_t nmax = m * b;
@@ -907,7 +910,7 @@ int css_ref_density_nonorth(int32_t n_brow, int32_t b, int32_t nnzb_s, const int
                             double mu, double kT, double n_elec, double ne_tol, int solve_mu, int32_t m, int flags,
                             double* P_val, double* trPS, double* trPH, double* mu_out, int32_t* n_breakdown) {
   if (n_brow < 1 || b < 1 || m < 1 || n_colours < 1 || nnzb_h < n_brow || !P_val || kT < 0.0) return REF_ERR_ARG;
-  if (!(ne_tol > 0.0)) ne_tol = 1e-6 * fmax(1.0, 0.5 * n_elec);
+  if (!(ne_tol > 0.0)) ne_tol = 1e-4 * fmax(1.0, 0.5 * n_elec);
   const int64_t N = (int64_t)n_brow * b;
   const int32_t nmax = m * b, bb = b * b;
   ref_h Hp = {n_brow, b, h_row_ptr, h_col_idx, hp_val};

@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(MU_T) k_mu(int32_t n_sys, int32_t n_col, int32
                                              const double* __restrict__ tol, const int32_t* __restrict__ solve,
                                              const double* __restrict__ mu_in, double* __restrict__ mu_out,
                                              double* __restrict__ part, unsigned* __restrict__ bar,
-                                             int32_t* __restrict__ err) {
+                                             int32_t* __restrict__ err, int32_t nb_extra) {
   __shared__ double acc[2][MU_MAXSYS];
   __shared__ double lo[2][MU_MAXSYS], hi[2][MU_MAXSYS];
   __shared__ int conv[MU_MAXSYS];
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(MU_T) k_mu(int32_t n_sys, int32_t n_col, int32
     pbuf[0][(size_t)s * G + blockIdx.x] = lo[0][s];
     pbuf[0][(size_t)(n_sys + s) * G + blockIdx.x] = hi[0][s];
   }
-  if (!grid_sync(bar, bar + 1, G, err)) return;
+  if (!grid_sync(bar, bar + 1, G + (unsigned)nb_extra, err)) return;
   for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) {
     double a = 1e300, z = -1e300;
     for (unsigned g = 0; g < G; ++g) {
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(MU_T) k_mu(int32_t n_sys, int32_t n_col, int32
       pb[(size_t)s * G + blockIdx.x] = acc[0][s];
       pb[(size_t)(n_sys + s) * G + blockIdx.x] = acc[1][s];
     }
-    if (!grid_sync(bar, bar + 1, G, err)) return;
+    if (!grid_sync(bar, bar + 1, G + (unsigned)nb_extra, err)) return;
     if (threadIdx.x == 0) all_done = 1;
     __syncthreads();
     for (int32_t s = threadIdx.x; s < n_sys; s += blockDim.x) {
@@ -945,7 +945,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
       // no chemical potential for the inverse square root of an overlap matrix
       ((int32_t*)(hp + 3 * n_sys))[s] = (sys[s].fermi.solve_mu && !(flags & CSS_INV_SQRT)) ? 1 : 0;
       const double tl = sys[s].fermi.ne_tol;
-      hp[4 * n_sys + s] = tl > 0.0 ? tl : 1e-6 * std::max(1.0, 0.5 * sys[s].fermi.n_elec);
+      hp[4 * n_sys + s] = tl > 0.0 ? tl : 1e-4 * std::max(1.0, 0.5 * sys[s].fermi.n_elec);
     }
     CSS_CU(ctx, cudaMemcpyAsync(dtol, hp + 4 * n_sys, sizeof(double) * n_sys, cudaMemcpyHostToDevice, st));
     CSS_CU(ctx, cudaMemcpyAsync(dkT, hp, sizeof(double) * n_sys, cudaMemcpyHostToDevice, st));
@@ -975,8 +975,9 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     double* pp_ = mupart;
     unsigned* bar_ = bar;
     int32_t* err_ = misc + 8;
+    int32_t extra_ = ctx->test_mu_barrier_extra;
     void* args[] = {&n_sys_, &n_col_, &nmax_, &nblk_, &b_, &soc_, &lam_, &w_, &kT_, &h_, &tl_, &sv_, &mi_, &mo_, &pp_,
-                    &bar_, &err_};
+                    &bar_, &err_, &extra_};
     CSS_CU(ctx, cudaLaunchCooperativeKernel((void*)k_mu, dim3(G), dim3(MU_T), args, 0, st));
     ++ctx->kernel_launches;
   }
@@ -1647,7 +1648,7 @@ css_status css_density_nonorth(css_ctx* ctx, const css_bsr* S, const double* Sin
     hp[0] = fermi->kT;
     hp[1] = 0.5 * fermi->n_elec;
     hp[2] = fermi->mu;
-    hp[3] = fermi->ne_tol > 0.0 ? fermi->ne_tol : 1e-6 * std::max(1.0, 0.5 * fermi->n_elec);
+    hp[3] = fermi->ne_tol > 0.0 ? fermi->ne_tol : 1e-4 * std::max(1.0, 0.5 * fermi->n_elec);
     ((int32_t*)(hp + 4))[0] = fermi->solve_mu ? 1 : 0;
     CSS_CU(ctx, cudaMemcpyAsync(dkT, hp, 4 * sizeof(double), cudaMemcpyHostToDevice, st));
     CSS_CU(ctx, cudaMemcpyAsync(dsolve, hp + 4, sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -1674,8 +1675,9 @@ css_status css_density_nonorth(css_ctx* ctx, const css_bsr* S, const double* Sin
     double* pp_ = mupart;
     unsigned* bar_ = bar;
     int32_t* err_ = misc + 8;
+    int32_t extra_ = ctx->test_mu_barrier_extra;
     void* args[] = {&n_sys_, &n_col_, &nmax_, &nblk_, &b_, &soc_, &lam_, &w_, &kT_, &h_, &tl_, &sv_, &mi_, &mo_, &pp_,
-                    &bar_, &err_};
+                    &bar_, &err_, &extra_};
     CSS_CU(ctx, cudaLaunchCooperativeKernel((void*)k_mu, dim3(G), dim3(MU_T), args, 0, st));
     ++ctx->kernel_launches;
   }

