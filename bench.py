@@ -34,10 +34,33 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "P build s/step at 10k H2O"
 SPMM_KERNEL_VERSION = "k_spmm-f32x2-v4"  # profiles/spmm_traffic.json must name the kernel measured
-FP32_PEAK_NOTE = "FP32 FFMA peak derived from 152 SMs x 128 lanes x 2 flop x 2070 MHz max SM clock"
 FP64_PEAK_NOTE = "FP64 peak: 1.25 TFLOP/s nominal GB300 FP64 rate"
-FP32_PEAK = 152 * 128 * 2 * 2070e6 / 1e12       # TFLOP/s
 FP64_PEAK = 1.25                                 # TFLOP/s
+
+
+def measured_peaks():
+    """HBM GB/s, dense BF16 TF/s (burst, sustained) and the maximum SM clock from
+    MEASURED_PEAKS.json, else the fallback figures of an earlier GB300 measurement."""
+    p = ROOT / "MEASURED_PEAKS.json"
+    try:
+        d = json.loads(p.read_text())
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16": float(d["bf16_tflops"]),
+                "bf16_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)), "source": "of measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "sm_max_mhz": 2070.0,
+                "source": "of fallback"}
+
+
+def fp32_peak_tflops(n_sm: int, sm_max_mhz: float) -> float:
+    """FFMA peak: SMs x 128 FP32 lanes x 2 flop x maximum SM clock."""
+    return n_sm * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+
+
+def tf32_peak_tflops(pk) -> float:
+    """Dense TF32 tensor peak: the measured sustained BF16 rate x the nominal TF32 / BF16 ratio
+    (1.1 / 2.25 PFLOP/s dense)."""
+    return pk["bf16_sustained"] * 1.1 / 2.25
 
 
 def parse():
@@ -56,6 +79,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-modes", action="store_true", help="skip the energy-weighted and S^-1/2 timings")
+    ap.add_argument("--oracle-full", action="store_true",
+                    help="reference arm: time complete oracle builds instead of the scaled sample")
     return ap.parse_args()
 
 
@@ -156,27 +181,139 @@ def colour_reuse(ctx, xyz_seq, box, r_col, colour, skins=(0.0, 0.25), seed=1004)
     return out
 
 
-SAMPLE_STEPS = 3  # block-Lanczos steps of one colour per oracle sample
+SAMPLE_M = 2  # block-Lanczos steps per pass in the oracle sample
 
 
-def oracle_sample(H, col, sign, c, a):
-    """Seconds per block-Lanczos step of colour c on the full matrix (oracle, host cores)."""
+def oracle_sample(H, col, sign, nc, a):
+    """A bounded sample of one oracle P build on the host cores, scaled to the whole build.
+
+    The oracle runs colours in parallel (OpenMP, one thread per colour, each colour's two
+    block-Lanczos passes and two exact diagonalisations of its m b x m b projected matrix on one
+    thread).  The sample runs the same schedule on its first `threads` colours with depth
+    SAMPLE_M instead of m (a fixed mu, so no colour waits for the others), and times one exact
+    diagonalisation of an m b x m b symmetric matrix; the build is then
+        t_lanczos x (m / SAMPLE_M) x ceil(nc / threads) + 2 x ceil(nc / threads) x t_eig.
+    mu, the extraction and the symmetrisation (a few percent of a build) are not in it."""
     import oracle
+    threads = oracle.num_threads()
     flags = oracle.REORTH_LOCAL if a.precision == "mixed" else 0
+    sub = list(range(min(threads, nc)))
     t0 = time.perf_counter()
-    oracle.lanczos(H, col, sign, c, SAMPLE_STEPS, flags=flags)
-    return (time.perf_counter() - t0) / SAMPLE_STEPS
+    oracle.density(H, col, sign, nc, mu=-4.0, kT=0.05, solve_mu=False, m=SAMPLE_M, flags=flags, colour_subset=sub)
+    t_l = time.perf_counter() - t0
+    n = a.m * H.b
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((n, n))
+    t0 = time.perf_counter()
+    oracle.eigh(A + A.T)
+    t_e = time.perf_counter() - t0
+    rounds = -(-nc // threads)
+    est = t_l * (a.m / SAMPLE_M) * rounds + 2 * rounds * t_e
+    return est, {"t_lanczos_s": t_l, "t_eig_s": t_e, "threads": threads, "colours": nc, "rounds": rounds}
 
 
-def sample_note(a, nc):
+def sample_note(a, parts):
     reo = ", local reorthogonalisation" if a.precision == "mixed" else ""
-    return (f"{SAMPLE_STEPS} block-Lanczos steps of one colour (FP64 oracle{reo}) on the full {a.n_mol}-molecule "
-            f"matrix, geometry 0; seconds per step x {a.m} steps x 2 passes x {nc} colours = one P build "
-            f"(the eigen stage, mu and the extraction, a few percent of the oracle's time, are not in the sample)")
+    return (f"oracle (FP64{reo}) on geometry 0 of the {a.n_mol}-molecule workload, its own schedule (OpenMP over "
+            f"colours, one thread per colour): {parts['threads']} colours at Krylov depth {SAMPLE_M} "
+            f"({parts['t_lanczos_s']:.2f} s) and one exact diagonalisation of a {a.m * 23 if a.kind == 'dzp' else a.m * 6}"
+            f"-square projected matrix ({parts['t_eig_s']:.2f} s), scaled to depth {a.m} and {parts['colours']} "
+            f"colours ({parts['rounds']} rounds of {parts['threads']} threads, two passes); mu and the extraction "
+            f"are not in the sample")
+
+
+def oracle_full_build(H, col, sign, nc, a):
+    """Wall time of one complete oracle P build (mu solved), for checking the sample's scaling."""
+    import oracle
+    from paper_2605_20918_gb300 import synth
+    flags = oracle.SYMMETRIZE | (oracle.REORTH_LOCAL if a.precision == "mixed" else 0)
+    t0 = time.perf_counter()
+    oracle.density(H, col, sign, nc, kT=0.05, n_elec=synth.n_electrons(H.n_brow), m=a.m, flags=flags)
+    return time.perf_counter() - t0
+
+
+def mode_4096(a, ctx, css, synth, dev, stream):
+    """The 4,096-molecule, 23-orbital workload (N = 94,208, R_col = 10 A, m = 40): FP64 and mixed P
+    builds side by side, each timed with CUDA events, with errors against the oracle's stored
+    unsymmetrised columns of two colours at mu = -4 eV (tests/golden/make_fullsize_golden.py
+    --n-mol 4096) and mixed against FP64 with mu solved in each."""
+    import torch
+    gold = ROOT / "tests" / "golden" / "fullsize_4096_colours.npz"
+    g = synth.water_box(4096)
+    H = synth.hamiltonian(g, "dzp")
+    Hd = css.DeviceBSR.from_host(H, dev)
+    xyz = torch.as_tensor(g.pos, device=dev)
+    col = torch.empty(4096, dtype=torch.int32, device=dev)
+    sign = torch.empty(4096 * H.b, dtype=torch.int8, device=dev)
+    ne = synth.n_electrons(4096)
+    out, P = {}, {}
+    for pname, p in (("fp64", css.CSS_FP64), ("mixed", css.CSS_MIXED_FP32)):
+        P[pname] = torch.empty((H.nnzb, H.b, H.b), dtype=torch.float64, device=dev)
+        nc = ctx.color(xyz, g.box, a.r_col, 1004, col)
+        ctx.probes(col, H.b, 1005, sign)
+        ctx.density(Hd, col, sign, nc, P[pname], kT=0.05, n_elec=ne, m=a.m, precision=p)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 1 if p == css.CSS_FP64 else 3
+        e0.record(stream)
+        for _ in range(reps):
+            nc = ctx.color(xyz, g.box, a.r_col, 1004, col)
+            ctx.probes(col, H.b, 1005, sign)
+            r = ctx.density(Hd, col, sign, nc, P[pname], kT=0.05, n_elec=ne, m=a.m, precision=p)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[pname] = {"s_per_pbuild": e0.elapsed_time(e1) / 1e3 / reps, "mu": r["mu"], "trP": r["trP"],
+                      "dTrP_vs_ne2": r["trP"] - ne / 2, "n_colours": nc, "trPH": r["trPH"]}
+    out["mixed_vs_fp64_mu_solved"] = {
+        "max_abs_dP": float((P["mixed"] - P["fp64"]).abs().max().item()),
+        "dE_band_eV_per_molecule": abs(2 * (out["mixed"]["trPH"] - out["fp64"]["trPH"])) / 4096,
+        "dmu_eV": out["mixed"]["mu"] - out["fp64"]["mu"]}
+    if gold.exists():
+        gd = np.load(gold)
+        ch = col.cpu().numpy()
+        rows = np.repeat(np.arange(H.n_brow), np.diff(H.row_ptr))
+        for pname, p in (("fp64", css.CSS_FP64), ("mixed", css.CSS_MIXED_FP32)):
+            ctx.density(Hd, col, sign, nc, P[pname], mu=float(gd["mu"]), kT=0.05, solve_mu=False, m=a.m,
+                        precision=p, flags=0)
+            Ph = None
+            e = {}
+            for c in gd["colours"]:
+                c = int(c)
+                got = P[pname][torch.as_tensor(gd[f"blocks_{c}"], device=dev)].cpu().numpy()
+                if Ph is None:
+                    Ph = P[pname].cpu().numpy()
+                mask = ch[H.col_idx] == c
+                diag = mask & (rows == H.col_idx)
+                e[f"colour_{c}"] = {
+                    "max_abs_dP_sampled": float(np.abs(got - gd[f"P_{c}"]).max()),
+                    "dTrP_colour": float(np.trace(Ph[diag], axis1=1, axis2=2).sum()) - float(gd[f"trP_{c}"]),
+                    "dE_band_colour_eV_per_molecule": abs(2 * (float((Ph[mask] * H.val[mask]).sum()) -
+                                                             float(gd[f"trPH_{c}"]))) / 4096}
+            out[pname]["vs_oracle_fixed_mu"] = e
+        out["oracle_note"] = ("oracle's unsymmetrised columns of the first and last colour at mu = -4 eV: 32 sampled "
+                              "blocks each, and the colour's share of Tr P and Tr(PH) over all its blocks")
+    del P, Hd
+    return out
+
+
+def row_roofline(a, H, nc, rows_ms, fp32, pk):
+    """Row work of one Lanczos step (everything between two H*V launches) against HBM: the
+    algorithmic minimum is reading Q_{j-1}, Q_j and W = H Q_j and writing Q_{j+1} once (four
+    N x w passes); the FP32 row passes of b <= 24 stream eleven (the CholeskyQR3 Grams re-read W1)."""
+    w = nc * H.b
+    s = 4 if fp32 else 8
+    alg = 4.0 * H.n_brow * H.b * w * s
+    achieved = alg / (rows_ms * 1e-3) / 1e9 if rows_ms > 0 else None
+    return {"kernel": "Lanczos row work per step (three-term update, reorthogonalisation, CholeskyQR3, sampled rows)",
+            "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"] if achieved else None, "ms_per_step": rows_ms,
+            "alg_bytes_per_step": alg, "streamed_bytes_per_step": (11 if fp32 and 16 < H.b <= 24 else 14) / 4 * alg,
+            "peak_source": f"HBM copy bandwidth {pk['source']}"}
 
 
 def run_reference(a):
-    """Oracle on host cores; each step one bounded sample of the P build, scaled to a whole build."""
+    """Oracle on host cores; each step one bounded sample of the P build, scaled to a whole build
+    (with --oracle-full: one complete oracle build per step)."""
     import oracle
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -187,32 +324,40 @@ def run_reference(a):
     col, nc = oracle.color(g.pos, g.box, a.r_col, 1004)
     sign = oracle.probes(col, H.b, 1005)
     threads = oracle.num_threads()
-    times = []
+    times, parts = [], None
     for i in range(a.warmup + a.steps):
-        per_step = oracle_sample(H, col, sign, i % nc, a)
+        if a.oracle_full:
+            t = oracle_full_build(H, col, sign, nc, a)
+        else:
+            t, parts = oracle_sample(H, col, sign, nc, a)
         if i >= a.warmup:
-            times.append(per_step * a.m * 2 * nc)
+            times.append(t)
     value = statistics.mean(times)
     cfg = workload_config(a)
     cfg["l2"] = l2_note(H)
+    cfg["precision"] = "fp64 (CPU oracle" + (", local reorthogonalisation as the mixed GPU path)" if a.precision == "mixed"
+                                             else ")")
+    note = (f"one complete oracle P build of the {a.n_mol}-molecule workload per step" if a.oracle_full
+            else sample_note(a, parts))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s/P-build",
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": value * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": cfg,
             "cpu_baseline": {"value": value, "unit": "s/P-build", "cores": threads, "kind": "oracle",
-                             "sample": sample_note(a, nc)},
+                             "sample": note},
             "e2e": {"value": value, "unit": "s/P-build", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def cpu_baseline(a, g, H):
+    """The reference arm's sample (the same colours, depth and scaling), on geometry 0."""
     import oracle
     oracle.build()
     col, nc = oracle.color(g.pos, g.box, a.r_col, 1004)
     sign = oracle.probes(col, H.b, 1005)
-    per_step = oracle_sample(H, col, sign, 0, a)
-    return {"value": per_step * a.m * 2 * nc, "unit": "s/P-build", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": sample_note(a, nc) + f"; {per_step:.2f} s per step"}
+    est, parts = oracle_sample(H, col, sign, nc, a)
+    return {"value": est, "unit": "s/P-build", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": sample_note(a, parts)}
 
 
 def main():
@@ -267,7 +412,7 @@ def main():
     if ws > 1:
         dist.barrier()
     launches0 = ctx.info()["kernel_launches"]
-    spmm_ms, results = [], []
+    spmm_ms, rows_ms, results = [], [], []
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk:
         torch.cuda.synchronize()
@@ -275,6 +420,7 @@ def main():
         for i in range(a.warmup, n_steps):
             r, nc, inf = step(i)
             spmm_ms.append(inf["ms_spmm"])
+            rows_ms.append(inf["ms_rows"])
             results.append((r, nc, inf))
         ev1.record(stream)
         torch.cuda.synchronize()
@@ -286,8 +432,14 @@ def main():
     value = shard.seconds_per_build(elapsed, a.steps, ws)
     last_r, last_nc, last_inf = results[-1]
     spmm_avg = statistics.mean(spmm_ms)
+    rows_avg = statistics.mean(rows_ms)
     achieved = last_inf["spmm_flops"] / (spmm_avg * 1e-3) / 1e12
-    peak = FP32_PEAK if prec == css.CSS_MIXED_FP32 else FP64_PEAK
+    pk = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = fp32_peak_tflops(n_sm, pk["sm_max_mhz"])
+    tf32_peak = tf32_peak_tflops(pk)
+    tc = os.environ.get("CSS_HV_TC") == "1" and prec == css.CSS_MIXED_FP32 and H0.b > 16
+    peak = (tf32_peak if tc else fp32_peak) if prec == css.CSS_MIXED_FP32 else FP64_PEAK
     traffic = None
     tf = ROOT / "profiles" / "spmm_traffic.json"
     if tf.exists():
@@ -304,13 +456,19 @@ def main():
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": elapsed / a.steps * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == css.CSS_MIXED_FP32 else "f64",
             "data": "synthetic", "config": cfg,
-            "roofline": {"kernel": "k_spmm (H*V, all colours of the system as columns)",
-                         "bound": "alu" if prec == css.CSS_MIXED_FP32 else "alu_fp64",
+            "roofline": {"kernel": ("k_hv_tc (H*V on tcgen05, 3xTF32)" if tc else
+                                    "k_spmm (H*V on the FP32 FMA pipe, all colours of the system as columns)"),
+                         "bound": "tensor" if tc else ("alu" if prec == css.CSS_MIXED_FP32 else "alu_fp64"),
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": traffic,
-                         "peak_source": FP32_PEAK_NOTE if prec == css.CSS_MIXED_FP32 else FP64_PEAK_NOTE,
+                         "traffic": None if tc else traffic,
+                         "peak_source": (f"dense TF32 tensor peak: measured sustained BF16 {pk['bf16_sustained']:.0f} "
+                                         f"TF/s x 1.1/2.25 ({pk['source']})" if tc else
+                                         f"FP32 FFMA (CUDA-core) ceiling: {n_sm} SMs x 128 lanes x 2 flop x "
+                                         f"{pk['sm_max_mhz']:.0f} MHz" if prec == css.CSS_MIXED_FP32 else FP64_PEAK_NOTE),
+                         "frac_vs_tf32_tensor_peak": achieved / tf32_peak if prec == css.CSS_MIXED_FP32 else None,
                          "launch_ms": spmm_avg, "flops_per_launch": last_inf["spmm_flops"],
                          "alg_bytes_per_launch": last_inf["spmm_bytes"]},
+            "roofline_rows": row_roofline(a, H0, last_nc, rows_avg, prec == css.CSS_MIXED_FP32, pk),
             "clocks": clk.summary(), "gpu_launches": int(launches),
             "phases_ms": {k: last_inf[k] for k in ("ms_setup", "ms_lanczos", "ms_eigen", "ms_mu", "ms_extract",
                                                    "ms_total")},
@@ -322,11 +480,20 @@ def main():
         nc = ctx.color(xyz, geoms[t][0].box, a.r_col, 1004, colour)
         ctx.probes(colour, Hd.b, 1005, sign)
         P64 = torch.empty_like(P[t])
+        # FP64 P builds of the same geometry: one untimed (workspace, tuning), then two timed with
+        # CUDA events on the stream (colour + probes + density, as a timed step of the mixed arm)
+        ctx.density(Hd, colour, sign, nc, P64, kT=0.05, n_elec=ne, m=a.m, precision=css.CSS_FP64)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r64 = ctx.density(Hd, colour, sign, nc, P64, kT=0.05, n_elec=ne, m=a.m, precision=css.CSS_FP64)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            nc = ctx.color(xyz, geoms[t][0].box, a.r_col, 1004, colour)
+            ctx.probes(colour, Hd.b, 1005, sign)
+            r64 = ctx.density(Hd, colour, sign, nc, P64, kT=0.05, n_elec=ne, m=a.m, precision=css.CSS_FP64)
+        e1.record(stream)
         torch.cuda.synchronize()
-        t64 = time.perf_counter() - t0
+        t64 = e0.elapsed_time(e1) / 2e3
+        inf64 = ctx.info()
         dP = float((P64 - P[t]).abs().max().item())
         # FP64 at the mixed run's mu: the error of the mixed arithmetic alone, without the
         # change of mu (any mu in the gap satisfies the electron count)
@@ -334,6 +501,9 @@ def main():
                            mu=last_r["mu"], solve_mu=False)
         dPf = float((P64 - P[t]).abs().max().item())
         line["fp64_compare"] = {"fp64_s_per_pbuild": t64, "mixed_s_per_pbuild": value,
+                                "fp64_timed_builds": 2, "fp64_spmm_ms_per_launch": inf64["ms_spmm"],
+                                "fp64_spmm_tflops": inf64["spmm_flops"] / (inf64["ms_spmm"] * 1e-3) / 1e12
+                                if inf64["ms_spmm"] > 0 else None,
                                 "speedup_mixed_vs_fp64": t64 / value, "max_abs_dP": dP,
                                 "max_abs_dP_same_mu": dPf,
                                 "dE_band_eV_per_molecule_same_mu": abs(2 * (last_r["trPH"] - r64f["trPH"])) / a.n_mol,
@@ -400,13 +570,13 @@ def main():
                          torch.empty(int(n_i) * Hi.b, dtype=torch.int8, device=dev),
                          torch.empty((Hi.nnzb, Hi.b, Hi.b), dtype=torch.float64, device=dev)))
 
-        def batched():
+        def batched(p=prec):
             ncs = [ctx.color(x, gi.box, 10.0, 1004, ci) for gi, Hd_i, x, ci, si, Pi in sysd]
             for (gi, Hd_i, x, ci, si, Pi) in sysd:
                 ctx.probes(ci, Hd_i.b, 1005, si)
             fs = [{"kT": 0.05, "n_elec": synth.n_electrons(gi.n_mol), "solve_mu": True} for gi, *_ in sysd]
-            ctx.density_batch([d[1] for d in sysd], [d[3] for d in sysd], [d[4] for d in sysd], ncs,
-                              [d[5] for d in sysd], fs, m=30, precision=prec)
+            return ctx.density_batch([d[1] for d in sysd], [d[3] for d in sysd], [d[4] for d in sysd], ncs,
+                                     [d[5] for d in sysd], fs, m=30, precision=p)
 
         def one_by_one():
             for gi, Hd_i, x, ci, si, Pi in sysd:
@@ -430,11 +600,35 @@ def main():
         cr["note"] = ("css_color_update along the MD-like sequence: keep the colouring while no same-coloured "
                       "pair is closer than R_col, else recolour at R_col + skin")
         line["modes"]["md_colour_reuse"] = cr
-        line["modes"]["batch_32_systems"] = {
-            "batched_s": times["batched"], "one_by_one_s": times["one_by_one"],
-            "molecules": int(sizes.sum()), "sizes_min_max": [int(sizes.min()), int(sizes.max())],
-            "note": "32 systems, 6 orbitals, R_col 10 A, m 30: css_density_batch vs css_density per system"}
+        batch = {"batched_s": times["batched"], "one_by_one_s": times["one_by_one"],
+                 "molecules": int(sizes.sum()), "sizes_min_max": [int(sizes.min()), int(sizes.max())],
+                 "note": "32 systems, 6 orbitals, R_col 10 A, m 30: css_density_batch vs css_density per system"}
+        # both precisions side by side against the oracle (stored oracle values of the smallest and
+        # the largest system: tests/golden/make_batch_golden.py)
+        gold = ROOT / "tests" / "golden" / "batch32_systems.npz"
+        if gold.exists():
+            gb = np.load(gold)
+            for pname, p in (("fp64", css.CSS_FP64), ("mixed", css.CSS_MIXED_FP32)):
+                batched(p)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rb = batched(p)
+                torch.cuda.synchronize()
+                err = {"batched_s": time.perf_counter() - t0}
+                for i in gb["systems"]:
+                    i = int(i)
+                    gi, Pi = sysd[i][0], sysd[i][5]
+                    got = Pi[torch.as_tensor(gb[f"blocks_{i}"], device=dev)].cpu().numpy()
+                    err[f"system_{i}_{gi.n_mol}_molecules"] = {
+                        "max_abs_dP_sampled": float(np.abs(got - gb[f"P_{i}"]).max()),
+                        "dE_band_eV_per_molecule": abs(2 * (rb["trPH"][i] - float(gb[f"trPH_{i}"]))) / gi.n_mol,
+                        "dTrP": rb["trP"][i] - float(gb[f"trP_{i}"]), "dmu_eV": rb["mu"][i] - float(gb[f"mu_{i}"])}
+                batch[pname] = err
+            batch["oracle_note"] = ("errors against the oracle's density matrix (mu solved, symmetrised) of the smallest "
+                                    "and the largest system: 256 sampled blocks each, Tr(PH) and Tr P")
+        line["modes"]["batch_32_systems"] = batch
         del sysd
+        line["modes"]["n4096_23_orbitals"] = mode_4096(a, ctx, css, synth, dev, stream)
     if not a.no_e2e:
         # end to end through css_pbuild with host buffers: pinned host inputs in, P out per step
         pin = {}

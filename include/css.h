@@ -73,6 +73,10 @@ typedef enum {
  * S~^(-1/2) on S's pattern, trP Tr S~^(-1/2), trPH Tr(S~^(-1/2) S).  A non-positive Ritz
  * value (S not positive definite) gives CSS_ERR_NUMERIC. */
 #define CSS_INV_SQRT 32u
+/* Stop after the exact diagonalisation of the projected matrices (paper, Eq. 7): css_ritz then
+ * returns every colour's Ritz values and weights; mu, Z and P are not computed (P_val, trP, trPH
+ * and mu_out are left untouched).  The first phase of a colour-partitioned build. */
+#define CSS_RITZ_ONLY 64u
 /* css_probes flags */
 #define CSS_SIGNS_ONES 1u   /* all probe entries +1 instead of seeded random signs             */
 
@@ -116,6 +120,8 @@ typedef struct {
   double spmm_flops;     /* algorithmic flops of one H*V launch: 2 nnzb b^2 w               */
   double spmm_bytes;     /* algorithmic bytes of one H*V launch: H once, V in, W out        */
   int64_t kernel_launches; /* kernels launched by this context since css_create            */
+  double ms_rows;          /* row work of one Lanczos step between two H*V launches (three-term
+                              update, reorthogonalisation, CholeskyQR3, sampled rows), averaged */
 } css_info;
 
 /* ------------------------------------------------------------------ context */
@@ -256,6 +262,45 @@ CSS_API css_status css_density_batch(css_ctx* ctx, int32_t n_sys, const css_bsr*
                              const int8_t* const* sign, const int32_t* n_colours, const css_fermi* fermi, int32_t m,
                              css_precision prec, uint32_t flags, double* const* P_val, double* trP, double* trPH,
                              double* mu_out, void* stream);
+
+/* Colour-partitioned build of one system (paper: each colour's probe block is an independent
+ * right-hand side of the shifted systems, paragraph after Eq. 4, so its block-Lanczos problem and
+ * its columns of P~ need no other colour).  Only the colours with owned[c] != 0 are worked on; they
+ * are renumbered 0, 1, ... in increasing c for css_ritz, and every other molecule is in no probe
+ * block of this call.  A build split over ranks:
+ *   1. each rank: css_density_colours(..., flags | CSS_RITZ_ONLY) for its colours, then css_ritz;
+ *   2. all ranks' Ritz lists gathered in increasing colour order; css_solve_mu gives mu (the same
+ *      mu, bit for bit, as one css_density call over all colours);
+ *   3. each rank: css_density_colours(..., fermi->mu = that mu) writes P~_IJ = [Q_c Z_c]_I diag(s_J)
+ *      for the blocks whose column molecule J has an owned colour, and ZERO for every other block;
+ *   4. the ranks' P_val arrays are summed (disjoint blocks) and symmetrised by the caller.
+ * Each owned colour's arithmetic is that of css_density, so the sum of the parts equals the
+ * unsymmetrised P of one css_density call with the same mu bit for bit.
+ *   colour, sign, H  as in css_density (colour in [0, n_colours))
+ *   owned            HOST uint8[n_colours]
+ *   fermi            host struct; solve_mu must be 0 (mu is an input here)
+ *   flags            CSS_TWO_PASS, CSS_REORTH_LOCAL, CSS_ENERGY_WEIGHTED, CSS_RITZ_ONLY (no
+ *                    CSS_SYMMETRIZE: the output is unsymmetrised)
+ *   P_val, trP, trPH as in css_density (the traces cover the owned columns only)
+ * Errors: INVALID_ARG for solve_mu != 0, CSS_SYMMETRIZE, no owned colour, or a colour out of range
+ * (checked on the device).  Synchronises `stream`. */
+CSS_API css_status css_density_colours(css_ctx* ctx, const css_bsr* H, const int32_t* colour, const int8_t* sign,
+                                       int32_t n_colours, const uint8_t* owned, const css_fermi* fermi, int32_t m,
+                                       css_precision prec, uint32_t flags, double* P_val, double* trP, double* trPH,
+                                       void* stream);
+
+/* mu from Ritz lists gathered from several calls (the rule of css_fermi with solve_mu: the midpoint
+ * of {mu : |N(mu) - n_elec/2| <= ne_tol}, N(mu) = sum over lists t and pairs k of
+ * f(lam_tk) wgt_tk; ne_tol <= 0 selects 1e-4 n_elec/2), on the GPU with the kernel of css_density.
+ * Lists given in the colour order of one css_density call over all colours give exactly that call's
+ * mu.
+ *   n_per   HOST int32[n_lists] (pairs per list);  lam, wgt  HOST doubles, the lists concatenated
+ *   mu_out  HOST double, written.  Synchronises `stream`.
+ * Errors: INVALID_ARG for n_lists < 1, a negative length or kT < 0; TIMEOUT if the bounded grid
+ * barrier runs out; NUMERIC for a non-finite mu. */
+CSS_API css_status css_solve_mu(css_ctx* ctx, int32_t n_lists, const int32_t* n_per, const double* lam,
+                                const double* wgt, double kT, double n_elec, double ne_tol, double* mu_out,
+                                void* stream);
 
 /* Ritz data of the last css_density / css_density_batch call (paper, Eq. 7: eigenvalues of
  * each colour's projected matrix and their weights w = ||Y_k||^2, Y = U^T E_1 B_0, whose

@@ -19,13 +19,15 @@ __all__ = [
     "CSSError", "Context", "DeviceBSR", "load_library", "library_path", "css_create", "css_destroy", "css_color",
     "css_color_graph", "css_color_check", "css_color_update", "css_probes", "css_density", "css_density_nonorth", "css_density_batch", "css_pbuild", "css_get_info", "css_ritz", "css_projected", "css_eigen_blocks",
     "CSS_OK", "CSS_WARN_BREAKDOWN", "CSS_FP64", "CSS_MIXED_FP32", "CSS_SYMMETRIZE", "CSS_TWO_PASS",
-    "CSS_REORTH_LOCAL", "CSS_HOST_IO", "CSS_SIGNS_ONES", "CSS_ENERGY_WEIGHTED", "CSS_INV_SQRT",
+    "CSS_REORTH_LOCAL", "CSS_HOST_IO", "CSS_SIGNS_ONES", "CSS_ENERGY_WEIGHTED", "CSS_INV_SQRT", "CSS_RITZ_ONLY",
+    "css_density_colours", "css_solve_mu",
 ]
 
 CSS_OK, CSS_ERR_INVALID_ARG, CSS_ERR_NOMEM, CSS_ERR_CUDA, CSS_ERR_TIMEOUT, CSS_ERR_NUMERIC = 0, 1, 2, 3, 4, 5
 CSS_WARN_BREAKDOWN, CSS_ERR_UNSUPPORTED = 6, 7
 CSS_FP64, CSS_MIXED_FP32 = 0, 1
 CSS_SYMMETRIZE, CSS_TWO_PASS, CSS_REORTH_LOCAL, CSS_HOST_IO, CSS_ENERGY_WEIGHTED, CSS_INV_SQRT = 1, 2, 4, 8, 16, 32
+CSS_RITZ_ONLY = 64
 CSS_SIGNS_ONES = 1
 
 _PKG = Path(__file__).resolve().parent
@@ -55,7 +57,7 @@ class _Info(C.Structure):
                [(k, C.c_double) for k in ("ms_color", "ms_probes", "ms_setup", "ms_lanczos", "ms_spmm", "ms_eigen",
                                           "ms_mu", "ms_extract", "ms_total")] + \
                [("spmm_launches", C.c_int64), ("spmm_flops", C.c_double), ("spmm_bytes", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("ms_rows", C.c_double)]
 
 
 _lib = None
@@ -116,6 +118,11 @@ def load_library(path: str | Path | None = None):
     lib.css_density_nonorth.argtypes = [v, C.POINTER(_BSR), v, C.POINTER(_BSR), v, v, v, i32, C.POINTER(_Fermi), i32,
                                         st, u32, v, C.POINTER(f64), C.POINTER(f64), C.POINTER(f64), v]
     lib.css_density_nonorth.restype = st
+    lib.css_density_colours.argtypes = [v, C.POINTER(_BSR), v, v, i32, v, C.POINTER(_Fermi), i32, st, u32, v,
+                                        C.POINTER(f64), C.POINTER(f64), v]
+    lib.css_density_colours.restype = st
+    lib.css_solve_mu.argtypes = [v, i32, v, v, v, f64, f64, f64, C.POINTER(f64), v]
+    lib.css_solve_mu.restype = st
     lib.css_ritz.restype = st
     _lib = lib
     return lib
@@ -351,6 +358,42 @@ def css_density_nonorth(ctx, S: DeviceBSR, Sinv, Hp: DeviceBSR, H_val, colour, s
     return {"trPS": tps.value, "trPH": tph.value, "mu": mo.value, "status": st}
 
 
+def css_density_colours(ctx, H: DeviceBSR, colour, sign, n_colours: int, owned, P, *, mu, kT=0.05, m=30,
+                        precision=CSS_FP64, flags=0, stream=None) -> dict:
+    """Colours with owned[c] != 0 only (host sequence of n_colours flags): unsymmetrised columns
+    of P at the given mu into P (other blocks zero), or with CSS_RITZ_ONLY their Ritz data only."""
+    torch = _torch()
+    lib = load_library()
+    _need(colour, H.n_brow, "colour")
+    _need(sign, H.n_brow * H.b, "sign")
+    _need(P, H.nnzb * H.b * H.b, "P")
+    ow = np.ascontiguousarray(np.asarray(owned, dtype=np.uint8))
+    _need(ow, n_colours, "owned")
+    hb = H._c()
+    f = _fermi(mu, kT, 0.0, False)
+    tp, tph = C.c_double(), C.c_double()
+    st = _check(lib, ctx, lib.css_density_colours(ctx, C.byref(hb), _dev(colour, torch.int32, "colour"),
+                                                  _dev(sign, torch.int8, "sign"), int(n_colours),
+                                                  ow.ctypes.data_as(C.c_void_p), C.byref(f), int(m), int(precision),
+                                                  int(flags), _dev(P, torch.float64, "P"), C.byref(tp), C.byref(tph),
+                                                  _stream(stream)), "css_density_colours")
+    return {"trP": tp.value, "trPH": tph.value, "status": st}
+
+
+def css_solve_mu(ctx, ritz_lists, *, kT=0.05, n_elec=0.0, ne_tol=0.0, stream=None) -> float:
+    """mu from gathered Ritz lists [(lam, w), ...] (host arrays) with the rule of css_density."""
+    lib = load_library()
+    n = len(ritz_lists)
+    n_per = np.array([len(l) for l, _ in ritz_lists], dtype=np.int32)
+    lam = np.ascontiguousarray(np.concatenate([np.asarray(l, np.float64) for l, _ in ritz_lists] + [np.zeros(1)]))
+    wgt = np.ascontiguousarray(np.concatenate([np.asarray(w, np.float64) for _, w in ritz_lists] + [np.zeros(1)]))
+    mu = C.c_double()
+    _check(lib, ctx, lib.css_solve_mu(ctx, n, n_per.ctypes.data_as(C.c_void_p), lam.ctypes.data_as(C.c_void_p),
+                                      wgt.ctypes.data_as(C.c_void_p), float(kT), float(n_elec), float(ne_tol),
+                                      C.byref(mu), _stream(stream)), "css_solve_mu")
+    return mu.value
+
+
 def css_density_batch(ctx, Hs, colours, signs, n_colours, Ps, fermis, *, m=30, precision=CSS_FP64,
                       flags=CSS_SYMMETRIZE, stream=None) -> dict:
     """Several systems in one call.  fermis: list of dicts(mu, kT, n_elec, solve_mu)."""
@@ -524,6 +567,12 @@ class Context:
 
     def density_batch(self, *a, **k):
         return css_density_batch(self.handle, *a, **k)
+
+    def density_colours(self, *a, **k):
+        return css_density_colours(self.handle, *a, **k)
+
+    def solve_mu(self, *a, **k):
+        return css_solve_mu(self.handle, *a, **k)
 
     def pbuild(self, *a, **k):
         return css_pbuild(self.handle, *a, **k)

@@ -89,7 +89,9 @@ css_status css_create(css_ctx** out, int device) {
   const int extra = tb ? atoi(tb) : 0;
   ctx->test_mu_barrier_extra = extra > 0 && extra < 64 ? extra : 0;
   const char* tc = getenv("CSS_HV_TC");
-  ctx->hv_tc = !(tc && tc[0] == '0');
+  ctx->hv_tc = tc && tc[0] == '1';
+  const char* rs = getenv("CSS_ROWS_STREAM");
+  ctx->rows_stream = rs && rs[0] == '1';
   *out = ctx;
   return CSS_OK;
 }

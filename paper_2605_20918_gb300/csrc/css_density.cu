@@ -30,17 +30,22 @@ __global__ void k_offset_i32(int64_t n, const int32_t* __restrict__ src, int32_t
   if (i < n) dst[i] = src[i] + off;
 }
 
+// colour -1 marks a molecule that is in no probe block of this call (a colour owned by another
+// rank of a colour-partitioned build); allowed only when `partial` is set
 __global__ void k_rows(int32_t n_brow, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
                        const int32_t* __restrict__ colour, int32_t n_col, int32_t* __restrict__ brow,
                        int32_t* __restrict__ trans, int32_t* __restrict__ cnt, int32_t* __restrict__ maxrow,
-                       int32_t* __restrict__ err) {
+                       int32_t* __restrict__ err, int partial = 0) {
   int32_t I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= n_brow) return;
   const int32_t s = row_ptr[I], e = row_ptr[I + 1];
   atomicMax(maxrow, e - s);
   const int32_t cI = colour[I];
-  if (cI < 0 || cI >= n_col) atomicOr(err, ERR_COLOUR);
-  else atomicAdd(&cnt[cI], 1);
+  if (cI < 0 || cI >= n_col) {
+    if (!(partial && cI == -1)) atomicOr(err, ERR_COLOUR);
+  } else {
+    atomicAdd(&cnt[cI], 1);
+  }
   bool diag = false;
   for (int32_t k = s; k < e; ++k) {
     brow[k] = I;
@@ -90,6 +95,7 @@ __global__ void k_pair_count(int32_t n_brow, const int32_t* __restrict__ row_ptr
   int32_t n = 0;
   for (int32_t k = s; k < e; ++k) {
     const int32_t c = colour[col_idx[k]];
+    if (c < 0) continue;  // not probed in this call
     bool seen = false;
     for (int32_t k2 = s; k2 < k; ++k2)
       if (colour[col_idx[k2]] == c) {
@@ -111,6 +117,10 @@ __global__ void k_pair_fill(int32_t n_brow, const int32_t* __restrict__ row_ptr,
   const int32_t base = pstart[I];
   for (int32_t k = s; k < e; ++k) {
     const int32_t c = colour[col_idx[k]];
+    if (c < 0) {  // not probed in this call: the block gets no column
+      bpr[k] = -1;
+      continue;
+    }
     int32_t found = -1;
     for (int32_t t = 0; t < n; ++t)
       if (pr_c[base + t] == c) {
@@ -144,7 +154,7 @@ __global__ void k_pair_place(int32_t n_brow, const int32_t* __restrict__ pstart,
 __global__ void k_pob(int32_t nnzb, const int32_t* __restrict__ bpr, const int32_t* __restrict__ perm,
                       int32_t* __restrict__ pob) {
   int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < nnzb) pob[k] = perm[bpr[k]];
+  if (k < nnzb) pob[k] = bpr[k] < 0 ? -1 : perm[bpr[k]];
 }
 
 // ----------------------------------------------------------- chemical potential
@@ -509,7 +519,8 @@ __global__ void __launch_bounds__(EX_T) k_extract(int32_t k0, int32_t k1, int32_
   if (t < (int64_t)k1 * bb) {
     const int32_t k = (int32_t)(t / bb), e = (int32_t)(t % bb), a = e / b, kk = e % b;
     const int32_t I = brow[k], J = col_idx[k];
-    double v = X[(size_t)pob[k] * bb + e] * (double)sign[(size_t)J * b + kk];
+    const int32_t pk = pob[k];  // -1: column J is not probed in this call (written as zero)
+    double v = pk < 0 ? 0.0 : X[(size_t)pk * bb + e] * (double)sign[(size_t)J * b + kk];
     if (sym) {
       const int32_t kt = trans[k];
       const double w = X[(size_t)pob[kt] * bb + kk * b + a] * (double)sign[(size_t)I * b + a];
@@ -613,12 +624,14 @@ struct Timer {
 
 css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys, int32_t m, css_precision prec,
                             uint32_t flags, double* trP, double* trPH, double* mu_out, cudaStream_t st,
-                            void* yfull, int32_t ldy) {
+                            void* yfull, int32_t ldy, bool partial) {
   // ------------------------------------------------------------ validation
   if (n_sys < 1 || n_sys > MU_MAXSYS) return css_set_arg_error(ctx, "css_density: n_sys out of range");
   if (prec != CSS_FP64 && prec != CSS_MIXED_FP32) return css_set_arg_error(ctx, "css_density: unknown precision");
-  if (flags & ~(CSS_SYMMETRIZE | CSS_TWO_PASS | CSS_REORTH_LOCAL | CSS_ENERGY_WEIGHTED | CSS_INV_SQRT))
+  if (flags & ~(CSS_SYMMETRIZE | CSS_TWO_PASS | CSS_REORTH_LOCAL | CSS_ENERGY_WEIGHTED | CSS_INV_SQRT | CSS_RITZ_ONLY))
     return css_set_arg_error(ctx, "css_density: unknown flag");
+  if (partial && (n_sys != 1 || (flags & CSS_SYMMETRIZE)))
+    return css_set_arg_error(ctx, "css_density_colours: one system, unsymmetrised output");
   const int32_t b = sys[0].H.b;
   if (b < 1) return css_set_arg_error(ctx, "css_density: b < 1");
   if (b > CSS_MAX_B) {
@@ -647,6 +660,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   const int32_t bb = b * b, nmax = m * b;
   const bool f32 = prec == CSS_MIXED_FP32;
   const bool two_pass = (flags & CSS_TWO_PASS) != 0 || yfull != nullptr;
+  const bool ritz_only = (flags & CSS_RITZ_ONLY) != 0;  // stop after the exact diagonalisation
   const int T = 256;
   Timer tm(ctx, st);
   tm.mark();  // 0
@@ -738,7 +752,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   CSS_CU(ctx, cudaMemsetAsync(ccount, 0, (n_col + 1) * sizeof(int32_t), st));
   CSS_CU(ctx, cudaMemsetAsync(cfill, 0, (n_col + 1) * sizeof(int32_t), st));
   const unsigned gb = (unsigned)css_ceil_div(n_brow, T);
-  k_rows<<<gb, T, 0, st>>>(n_brow, row_ptr, col_idx, colour, n_col, brow, trans, cnt, misc + 1, misc);
+  k_rows<<<gb, T, 0, st>>>(n_brow, row_ptr, col_idx, colour, n_col, brow, trans, cnt, misc + 1, misc, partial ? 1 : 0);
   CSS_LAUNCHED(ctx);
   k_inv_sqrt<<<(unsigned)css_ceil_div(n_col, T), T, 0, st>>>(n_col, cnt, isq, nblk, done, m);
   CSS_LAUNCHED(ctx);
@@ -776,7 +790,13 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   }
   const void* Hv = nullptr;
   const void* Hlo = nullptr;
-  CSS_TRY(css_spmm_prepare(ctx, f32, b, n_brow, nnzb, row_ptr, col_idx, Hval, &Hv, &Hlo, st));
+  const void* Htc = nullptr;
+  const void* Hd3 = nullptr;
+  const bool use_tc = ctx->hv_tc && css_hv_tc_supported(f32, b, max_row);
+  if (use_tc)
+    CSS_TRY(css_hv_tc_prepare(ctx, b, n_brow, nnzb, row_ptr, col_idx, Hval, &Htc, &Hd3, st));
+  else
+    CSS_TRY(css_spmm_prepare(ctx, f32, b, n_brow, nnzb, row_ptr, col_idx, Hval, &Hv, &Hlo, st));
   tm.mark();  // 1
 
   // ----------------------------------------------------------- memory plan
@@ -787,7 +807,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   CSS_TRY(ws_get(ctx, "Bprev", (size_t)n_col * bb, &Bprev));
   CSS_TRY(ws_get(ctx, "X", (size_t)n_pairs * bb, &X));
   void* Qs = nullptr;
-  if (!two_pass) CSS_TRY(css_ws(ctx, "Qs", (size_t)n_pairs * m * bb * s_vec, &Qs));
+  if (!two_pass && !ritz_only) CSS_TRY(css_ws(ctx, "Qs", (size_t)n_pairs * m * bb * s_vec, &Qs));
   // eigen workspace (all colours at once)
   EigArgs ea;
   ea.n_col = n_col;
@@ -854,6 +874,9 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   la.col_idx = col_idx;
   la.Hval = Hv;
   la.Hlo_diag = Hlo;
+  la.use_tc = use_tc;
+  la.tc_H = Htc;
+  la.tc_Hd3 = Hd3;
   la.max_row_blocks = max_row;
   la.colour = colour;
   la.sign = sign;
@@ -888,7 +911,8 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   if (ctx->timing) {
     CSS_CU(ctx, evs.create(2 * (size_t)m));
   }
-  double spmm_ms = 0.0;
+  double spmm_ms = 0.0, rows_ms = 0.0;
+  int64_t n_rows = 0;
   const int32_t BMh = css_spmm_bm(b);
   auto run_batches = [&](int mode) -> css_status {
     la.mode = mode;
@@ -913,18 +937,51 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
               spmm_ms += t;
               ++n_spmm;
             }
+            // the row work of step j: from the end of its H * V to the start of the next one
+            if (j + 1 < m && cudaEventElapsedTime(&t, evs[2 * j + 1], evs[2 * j + 2]) == cudaSuccess) {
+              rows_ms += t;
+              ++n_rows;
+            }
           }
         }
       }
     }
     return CSS_OK;
   };
-  CSS_TRY(run_batches(two_pass ? 0 : 1));
+  CSS_TRY(run_batches((two_pass || ritz_only) ? 0 : 1));
   tm.mark();  // 2
 
   // ---------------------------------------------------------- eigen + mu + Z
   CSS_TRY(css_eigen_ritz(ctx, ea, st));
   tm.mark();  // 3
+  if (ritz_only) {  // Ritz values and weights only (css_ritz); mu, Z and P are not computed
+    k_count_breakdown<<<(unsigned)css_ceil_div(n_col, T), T, 0, st>>>(n_col, m, nblk, cnt, misc + 16);
+    CSS_LAUNCHED(ctx);
+    k_status_or<<<(unsigned)css_ceil_div(n_col, T), T, 0, st>>>(n_col, ea.status, misc + 17);
+    CSS_LAUNCHED(ctx);
+    int32_t* hm;
+    CSS_TRY(css_pinned(ctx, 64 * sizeof(int32_t), (void**)&hm));
+    CSS_CU(ctx, cudaMemcpyAsync(hm, misc + 16, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CSS_CU(ctx, cudaStreamSynchronize(st));
+    ctx->last_lam = ea.lam;
+    ctx->last_wgt = ea.wgt;
+    ctx->last_nblk = nblk;
+    ctx->last_ncol = n_col;
+    ctx->last_b = b;
+    ctx->last_nmax = nmax;
+    ctx->last_A = Ablk;
+    ctx->last_B = Bblk;
+    ctx->last_m = m;
+    ctx->info.n_colours = n_col;
+    ctx->info.n_breakdown = hm[0];
+    const int32_t st_bits = hm[1];
+    if (use_tc) CSS_TRY(css_hv_tc_check(ctx, st));
+    if (st_bits & 2) {
+      ctx->last_error = "css_density: a wait between pipelined band-reduction sweeps timed out";
+      return CSS_ERR_TIMEOUT;
+    }
+    return hm[0] > 0 ? CSS_WARN_BREAKDOWN : CSS_OK;
+  }
   double *dmu, *dkT, *dhalf, *dmu_in, *dtol, *mupart;
   int32_t* dsolve;
   unsigned* bar;
@@ -1079,6 +1136,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   ctx->info.spmm_flops = 2.0 * nnzb * (double)bb * (double)wcols;
   ctx->info.spmm_bytes = (double)nnzb * bb * s_vec + 2.0 * (double)N * wcols * s_vec;
   ctx->info.ms_spmm = n_spmm ? spmm_ms / n_spmm : 0.0;
+  ctx->info.ms_rows = n_rows ? rows_ms / n_rows : 0.0;
   if (ctx->timing) {
     ctx->info.ms_setup = tm.ms(0, 1);
     ctx->info.ms_lanczos = tm.ms(1, 2);
@@ -1087,6 +1145,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     ctx->info.ms_extract = tm.ms(4, 6);
     ctx->info.ms_total = tm.ms(0, 6);
   }
+  if (use_tc) CSS_TRY(css_hv_tc_check(ctx, st));
   if (mu_err) {
     ctx->last_error = "css_density: grid barrier of the mu bisection timed out";
     return CSS_ERR_TIMEOUT;
@@ -1328,6 +1387,147 @@ css_status css_density(css_ctx* ctx, const css_bsr* H, const int32_t* colour, co
   CSS_CU(ctx, cudaSetDevice(ctx->device));
   css_sys_desc d{*H, colour, sign, n_colours, *fermi, P_val};
   return css_density_impl(ctx, 1, &d, m, prec, flags, trP, trPH, mu_out, (cudaStream_t)stream);
+}
+
+// colour'(J) = map[colour(J)]: the owned colours renumbered 0.. in increasing order, -1 for the rest
+__global__ void k_colour_map(int32_t n, const int32_t* __restrict__ colour, int32_t n_col, const int32_t* __restrict__ map,
+                             int32_t* __restrict__ out, int32_t* __restrict__ err) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t c = colour[i];
+  if (c < 0 || c >= n_col) {
+    atomicOr(err, 1);
+    out[i] = -1;
+    return;
+  }
+  out[i] = map[c];
+}
+
+css_status css_density_colours(css_ctx* ctx, const css_bsr* H, const int32_t* colour, const int8_t* sign,
+                               int32_t n_colours, const uint8_t* owned, const css_fermi* fermi, int32_t m,
+                               css_precision prec, uint32_t flags, double* P_val, double* trP, double* trPH,
+                               void* stream) {
+  if (!ctx || !H || !colour || !sign || !owned || !fermi || !P_val || n_colours < 1)
+    return css_set_arg_error(ctx, "css_density_colours: null pointer or n_colours < 1");
+  if (fermi->solve_mu) return css_set_arg_error(ctx, "css_density_colours: mu must be given (solve_mu = 0)");
+  if (flags & CSS_SYMMETRIZE) return css_set_arg_error(ctx, "css_density_colours: the output is unsymmetrised");
+  CSS_CU(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int32_t> map(n_colours);
+  int32_t n_own = 0;
+  for (int32_t c = 0; c < n_colours; ++c) map[c] = owned[c] ? n_own++ : -1;
+  if (n_own < 1) return css_set_arg_error(ctx, "css_density_colours: no colour owned");
+  int32_t *dmap, *dcol, *derr, *h;
+  CSS_TRY(css_ws(ctx, "part_map", sizeof(int32_t) * (n_colours + 64), (void**)&dmap));
+  CSS_TRY(css_ws(ctx, "part_colour", sizeof(int32_t) * H->n_brow, (void**)&dcol));
+  derr = dmap + n_colours;
+  CSS_TRY(css_pinned(ctx, sizeof(int32_t) * (n_colours + 64), (void**)&h));
+  std::memcpy(h, map.data(), sizeof(int32_t) * n_colours);
+  CSS_CU(ctx, cudaMemcpyAsync(dmap, h, sizeof(int32_t) * n_colours, cudaMemcpyHostToDevice, st));
+  CSS_CU(ctx, cudaMemsetAsync(derr, 0, sizeof(int32_t), st));
+  k_colour_map<<<(unsigned)css_ceil_div(H->n_brow, 256), 256, 0, st>>>(H->n_brow, colour, n_colours, dmap, dcol, derr);
+  CSS_LAUNCHED(ctx);
+  CSS_CU(ctx, cudaMemcpyAsync(h + n_colours, derr, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CSS_CU(ctx, cudaStreamSynchronize(st));  // the pinned staging is reused below
+  if (h[n_colours]) return css_set_arg_error(ctx, "css_density_colours: colour outside [0, n_colours)");
+  css_sys_desc d{*H, dcol, sign, n_own, *fermi, P_val};
+  double mu = 0.0;
+  return css_density_impl(ctx, 1, &d, m, prec, flags, trP, trPH, &mu, st, nullptr, 0, true);
+}
+
+css_status css_solve_mu(css_ctx* ctx, int32_t n_lists, const int32_t* n_per, const double* lam, const double* wgt,
+                        double kT, double n_elec, double ne_tol, double* mu_out, void* stream) {
+  if (!ctx || !n_per || !lam || !wgt || !mu_out || n_lists < 1)
+    return css_set_arg_error(ctx, "css_solve_mu: null pointer or n_lists < 1");
+  if (!(kT >= 0.0) || !std::isfinite(kT) || !std::isfinite(n_elec))
+    return css_set_arg_error(ctx, "css_solve_mu: kT must be finite and >= 0, n_elec finite");
+  CSS_CU(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t total = 0;
+  int32_t nmax = 1;
+  for (int32_t t = 0; t < n_lists; ++t) {
+    if (n_per[t] < 0) return css_set_arg_error(ctx, "css_solve_mu: negative list length");
+    total += n_per[t];
+    nmax = std::max(nmax, n_per[t]);
+  }
+  // the lists as the colours of one system (stride nmax, block width 1), solved by the kernel
+  // and the rule of css_density
+  double *dl, *dw, *dpar, *dmu;
+  int32_t *dn, *dsoc, *dsolve, *derr;
+  unsigned* bar;
+  const size_t nn = (size_t)n_lists * nmax;
+  CSS_TRY(css_ws(ctx, "smu_lam", sizeof(double) * nn, (void**)&dl));
+  CSS_TRY(css_ws(ctx, "smu_wgt", sizeof(double) * nn, (void**)&dw));
+  CSS_TRY(css_ws(ctx, "smu_i", sizeof(int32_t) * (2 * (size_t)n_lists + 64), (void**)&dn));
+  dsoc = dn + n_lists;
+  dsolve = dsoc + n_lists;
+  derr = dsolve + 8;
+  bar = reinterpret_cast<unsigned*>(derr + 8);
+  CSS_TRY(css_ws(ctx, "smu_d", sizeof(double) * 16, (void**)&dpar));
+  dmu = dpar + 8;
+  double* hp;
+  const size_t hbytes = sizeof(double) * 2 * nn + sizeof(int32_t) * 2 * (size_t)n_lists + 256;
+  CSS_TRY(css_pinned(ctx, hbytes, (void**)&hp));
+  double* hl = hp;
+  double* hw = hl + nn;
+  int32_t* hi = reinterpret_cast<int32_t*>(hw + nn);
+  double* hd = reinterpret_cast<double*>(hi + 2 * (size_t)n_lists + 2);
+  size_t o = 0;
+  for (int32_t t = 0; t < n_lists; ++t) {
+    for (int32_t k = 0; k < nmax; ++k) {
+      hl[(size_t)t * nmax + k] = k < n_per[t] ? lam[o + k] : 0.0;
+      hw[(size_t)t * nmax + k] = k < n_per[t] ? wgt[o + k] : 0.0;
+    }
+    o += n_per[t];
+    hi[t] = n_per[t];
+    hi[n_lists + t] = 0;
+  }
+  hd[0] = kT;
+  hd[1] = 0.5 * n_elec;
+  hd[2] = ne_tol > 0.0 ? ne_tol : 1e-4 * std::max(1.0, 0.5 * n_elec);
+  hd[3] = 0.0;
+  CSS_CU(ctx, cudaMemcpyAsync(dl, hl, sizeof(double) * nn, cudaMemcpyHostToDevice, st));
+  CSS_CU(ctx, cudaMemcpyAsync(dw, hw, sizeof(double) * nn, cudaMemcpyHostToDevice, st));
+  CSS_CU(ctx, cudaMemcpyAsync(dn, hi, sizeof(int32_t) * 2 * (size_t)n_lists, cudaMemcpyHostToDevice, st));
+  CSS_CU(ctx, cudaMemcpyAsync(dpar, hd, sizeof(double) * 4, cudaMemcpyHostToDevice, st));
+  const int32_t one = 1;
+  CSS_CU(ctx, cudaMemcpyAsync(dsolve, &one, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  CSS_CU(ctx, cudaMemsetAsync(derr, 0, sizeof(int32_t) * 8 + 8 * sizeof(unsigned), st));
+  int occ = 0;
+  CSS_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mu, MU_T, 0));
+  unsigned G = (unsigned)std::max(1, std::min(ctx->n_sm * std::max(occ, 1), n_lists));
+  if (G > (unsigned)ctx->n_sm) G = (unsigned)ctx->n_sm;
+  double* mupart;
+  CSS_TRY(css_ws(ctx, "smu_part", sizeof(double) * (4 * (size_t)G + 16), (void**)&mupart));
+  {
+    int32_t n_sys_ = 1, n_col_ = n_lists, nmax_ = nmax, b_ = 1, extra_ = 0;
+    const int32_t* nblk_ = dn;
+    const int32_t* soc_ = dsoc;
+    const double* lam_ = dl;
+    const double* w_ = dw;
+    const double* kT_ = dpar;
+    const double* h_ = dpar + 1;
+    const double* tl_ = dpar + 2;
+    const int32_t* sv_ = dsolve;
+    const double* mi_ = dpar + 3;
+    double* mo_ = dmu;
+    double* pp_ = mupart;
+    unsigned* bar_ = bar;
+    int32_t* err_ = derr;
+    void* args[] = {&n_sys_, &n_col_, &nmax_, &nblk_, &b_, &soc_, &lam_, &w_, &kT_, &h_, &tl_, &sv_, &mi_, &mo_, &pp_,
+                    &bar_, &err_, &extra_};
+    CSS_CU(ctx, cudaLaunchCooperativeKernel((void*)k_mu, dim3(G), dim3(MU_T), args, 0, st));
+    ++ctx->kernel_launches;
+  }
+  CSS_CU(ctx, cudaMemcpyAsync(hd + 4, dmu, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CSS_CU(ctx, cudaMemcpyAsync(hi, derr, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CSS_CU(ctx, cudaStreamSynchronize(st));
+  if (hi[0]) {
+    ctx->last_error = "css_solve_mu: grid barrier of the mu bisection timed out";
+    return CSS_ERR_TIMEOUT;
+  }
+  *mu_out = hd[4];
+  return std::isfinite(*mu_out) ? CSS_OK : CSS_ERR_NUMERIC;
 }
 
 css_status css_density_batch(css_ctx* ctx, int32_t n_sys, const css_bsr* H, const int32_t* const* colour,

@@ -65,9 +65,12 @@ struct css_ctx {
   // barrier of the mu bisection waits for k CTAs more than the launch has, so its bounded wait
   // runs out and the call returns CSS_ERR_TIMEOUT; 0 (the default) is the normal barrier
   int32_t test_mu_barrier_extra = 0;
-  // FP32 H * V on the tensor cores where the block width allows it (env CSS_HV_TC=0 at
-  // css_create selects the CUDA-core kernel instead)
-  bool hv_tc = true;
+  // FP32 H * V on the tensor cores where the block width allows it (env CSS_HV_TC=1 at
+  // css_create; the default is the CUDA-core kernel)
+  bool hv_tc = false;
+  // env CSS_ROWS_STREAM=1 at css_create: the streaming FP32 row passes of css_rows.cu (11
+  // passes per step) instead of the tiled row kernels (14 passes, faster as measured)
+  bool rows_stream = false;
 };
 
 // CUDA events owned by the holder: destroyed when it goes out of scope, early returns included
@@ -124,6 +127,8 @@ struct css_sys_desc {
 };
 // yfull (optional, device, [N][ldy] in the vector precision, zeroed by the caller): forces the
 // regenerating second pass and accumulates Y = Q_c Z_c of every colour over all rows into it
+// partial: colour -1 marks molecules in no probe block (colour-partitioned builds; one system,
+// unsymmetrised output, the blocks of unprobed columns written as zero)
 css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys, int32_t m, css_precision prec,
                             uint32_t flags, double* trP, double* trPH, double* mu_out, cudaStream_t st,
-                            void* yfull = nullptr, int32_t ldy = 0);
+                            void* yfull = nullptr, int32_t ldy = 0, bool partial = false);

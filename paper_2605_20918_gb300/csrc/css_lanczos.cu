@@ -922,6 +922,8 @@ css_status launch_spmm_v(css_ctx* ctx, const LzArgs& a, const T* V, T* W, int v,
 // same W), and the fastest is kept.  Shapes: precision, b, columns in buckets of 256, rows.
 template <typename T>
 css_status launch_spmm(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4)
+    if (a.use_tc) return css_hv_tc(ctx, a, V, W, st);
   const uint64_t key = ((uint64_t)sizeof(T) << 60) ^ ((uint64_t)a.b << 48) ^ ((uint64_t)(a.w / 256) << 24) ^
                        (uint64_t)(a.n_brow >= (1 << 24) ? (1 << 24) - 1 : a.n_brow);
   if (ctx->spmm_variant >= 0) return launch_spmm_v<T>(ctx, a, V, W, ctx->spmm_variant, st);
@@ -953,7 +955,9 @@ css_status launch_spmm(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaStre
 }
 
 template <typename T, int BP>
-css_status run_pass_bp(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
+css_status run_pass_bp(css_ctx* ctx, const LzArgs& a_in, cudaStream_t st) {
+  LzArgs a = a_in;
+  if (a.use_tc) CSS_TRY(css_hv_tc_schedule(ctx, a, st));
   const int32_t b = a.b, bb = b * b, ncb = a.ncb, m = a.m;
   const int64_t N = (int64_t)a.n_brow * b;
   const int32_t nch = (int32_t)css_ceil_div(N, RCHK);
@@ -983,6 +987,11 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
   double* sC1 = sR2i + (size_t)ncb * bb;
   double* sKp = sC1 + (size_t)ncb * bb;
   double* sV = sKp + (size_t)ncb * bb;  // Q_j^T u of the running step (the tenth small matrix)
+  double* sRi10 = sV + (size_t)ncb * bb;     // R0^-1 R1^-1 (FP32 row passes)
+  double* sRi210 = sRi10 + (size_t)ncb * bb;  // R0^-1 R1^-1 R2^-1
+  // FP32, 16 < b <= 24, env CSS_ROWS_STREAM=1: the streaming row passes of css_rows.cu
+  constexpr bool kF32 = sizeof(T) == 4;
+  const bool rp = kF32 && BP == 24 && css_rowpass_supported(true, b) && ctx->rows_stream;
   const unsigned rblocks_bb = (unsigned)css_ceil_div((int64_t)ncb * bb, 256);
   const int64_t pb = a.pair_off_h[a.cb0], pe = a.pair_off_h[a.cb0 + ncb];
   const unsigned sblocks = (unsigned)css_ceil_div((pe - pb) * bb, 256);
@@ -1080,6 +1089,57 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
     if (a.ev_spmm) CSS_CU(ctx, cudaEventRecord(a.ev_spmm[2 * j], st));
     CSS_TRY(launch_spmm<T>(ctx, a, Qc, W, st));
     if (a.ev_spmm) CSS_CU(ctx, cudaEventRecord(a.ev_spmm[2 * j + 1], st));
+    if (rp) {
+      const int first = j == 0 ? 1 : 0, ro = reorth ? 1 : 0;
+      const float *q = (const float*)Qc, *qp = (const float*)Qp;
+      float* wv = (float*)W;
+      // Kq = Q_j^T W0, Kp = Q_{j-1}^T W0 with W0 = W - Q_{j-1} B_{j-1}^T
+      CSS_TRY(css_rowpass(ctx, 0, N, b, a.ws, ncb, a.cb0, first, ro, q, qp, wv, nullptr, a.Bblk_prev, nullptr, nullptr,
+                          partKq, partKp, st));
+      k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sA);
+      CSS_LAUNCHED(ctx);
+      if (reorth && !first) {
+        k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKp, sKp);
+        CSS_LAUNCHED(ctx);
+      }
+      k_store_A<<<rblocks_bb, 256, 0, st>>>(ncb, b, a.cb0, m, j, sA, a.Ablk);
+      CSS_LAUNCHED(ctx);
+      if (j + 1 == m) break;
+      // W1 = W - Q_j Kq - Q_{j-1} (B_{j-1}^T + Kp) over W, and its Gram
+      CSS_TRY(css_rowpass(ctx, 1, N, b, a.ws, ncb, a.cb0, first, ro, q, qp, wv, wv, sA, a.Bblk_prev,
+                          (reorth && !first) ? sKp : nullptr, partKq, nullptr, st));
+      k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
+      CSS_LAUNCHED(ctx);
+      k_hnorm<<<(unsigned)css_ceil_div(ncb, 8), 256, 0, st>>>(ncb, b, a.cb0, j, sA, a.Bblk_prev, sG, sH);
+      CSS_LAUNCHED(ctx);
+      // shifted CholeskyQR3 on W1 without storing the intermediates: the Grams of W1 R0^-1 and
+      // W1 R0^-1 R1^-1 are taken from W1 itself, and Q_{j+1} = W1 R0^-1 R1^-1 R2^-1
+      CSS_TRY(chol(0, j, sR1, sR1i, a.shift_rel));
+      CSS_CU(ctx, cudaMemcpyAsync(sC1, sR1, sizeof(double) * ncb * bb, cudaMemcpyDeviceToDevice, st));
+      CSS_TRY(css_rowpass(ctx, 2, N, b, a.ws, ncb, a.cb0, first, ro, nullptr, nullptr, wv, nullptr, sR1i, nullptr,
+                          nullptr, partKq, nullptr, st));
+      k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
+      CSS_LAUNCHED(ctx);
+      CSS_TRY(chol(1, j, sR2, sR2i, 0.0));
+      CSS_TRY(css_small_mm(ctx, ncb, b, sR1i, sR2i, sRi10, st));
+      CSS_TRY(css_rowpass(ctx, 2, N, b, a.ws, ncb, a.cb0, first, ro, nullptr, nullptr, wv, nullptr, sRi10, nullptr,
+                          nullptr, partKq, nullptr, st));
+      k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
+      CSS_LAUNCHED(ctx);
+      CSS_TRY(chol(2, j, sR1, sR1i, 0.0));
+      CSS_TRY(css_small_mm(ctx, ncb, b, sRi10, sR1i, sRi210, st));
+      CSS_TRY(css_rowpass(ctx, 3, N, b, a.ws, ncb, a.cb0, first, ro, nullptr, nullptr, wv, (float*)Qp, sRi210, nullptr,
+                          nullptr, nullptr, nullptr, st));
+      CSS_TRY(sampled(Qp, j + 1));
+      CSS_TRY(project_u(Qp, j + 1));
+      CSS_CU(ctx, cudaMemcpy2DAsync(a.Bblk_prev + (size_t)a.cb0 * bb, bb * sizeof(double),
+                                    a.Bblk + ((size_t)a.cb0 * m + j) * bb, (size_t)m * bb * sizeof(double),
+                                    bb * sizeof(double), ncb, cudaMemcpyDeviceToDevice, st));
+      T* t = Qp;
+      Qp = Qc;
+      Qc = t;
+      continue;
+    }
     // three-term update and the projections onto Q_j (and Q_{j-1})
     s1<<<rgrid, reorth ? 2 * RW : RW, sm_s1, st>>>(N, b, a.ws, ncb, a.cb0, Qp, Qc, W, a.Bblk_prev, j == 0 ? 1 : 0,
                                                    partKq, partKp);
@@ -1155,7 +1215,7 @@ size_t css_lanczos_part_doubles(int64_t N, int32_t b, int32_t ncb) {
   return (size_t)nch * ncb * b * b * 2 + (size_t)nch * ncb + 64;
 }
 
-size_t css_lanczos_small_doubles(int32_t b, int32_t ncb) { return (size_t)ncb * b * b * 10 + ncb + 64; }
+size_t css_lanczos_small_doubles(int32_t b, int32_t ncb) { return (size_t)ncb * b * b * 12 + ncb + 64; }
 
 int32_t css_spmm_bm(int32_t b) { return b <= 8 ? 8 : b <= 12 ? 12 : b <= 16 ? 16 : b <= 24 ? 24 : 32; }
 

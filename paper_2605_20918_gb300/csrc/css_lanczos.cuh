@@ -48,9 +48,34 @@ struct LzArgs {
   // when set: Vc[colour][j b + k][l] = (Q_j^T u)[k][l] for every block j (u: N x ws)
   const void* ucol = nullptr;
   double* Vc = nullptr;
+  // FP32 H * V on the tensor cores (css_hv_tc.cu) when use_tc: TF32 parts of H (tc_H: every
+  // block, tc_Hd3: third part of the diagonal blocks, rows numbered as in the combined matrix)
+  // and the pass's group schedule (filled by css_hv_tc_schedule)
+  bool use_tc = false;
+  const void* tc_H = nullptr;
+  const void* tc_Hd3 = nullptr;
+  const int32_t* tc_cnt = nullptr;
+  const int32_t* tc_sJ = nullptr;
+  const int32_t* tc_sp = nullptr;
+  int32_t tc_cap = 0, tc_groups = 0;
 };
 
 css_status css_lanczos_pass(css_ctx* ctx, const LzArgs& a, cudaStream_t st);
+// tensor-core H * V (css_hv_tc.cu): FP32 mode with 16 < b <= 24
+bool css_hv_tc_supported(bool fp32, int32_t b, int32_t max_row_blocks);
+css_status css_hv_tc_prepare(css_ctx* ctx, int32_t b, int32_t n_brow, int32_t nnzb, const int32_t* row_ptr,
+                             const int32_t* col_idx, const double* H, const void** Htc, const void** Hd3,
+                             cudaStream_t st);
+css_status css_hv_tc_schedule(css_ctx* ctx, LzArgs& a, cudaStream_t st);
+css_status css_hv_tc(css_ctx* ctx, const LzArgs& a, const float* V, float* W, cudaStream_t st);
+css_status css_hv_tc_check(css_ctx* ctx, cudaStream_t st);
+// FP32 row passes of a Lanczos step for 16 < b <= 24 (css_rows.cu); mode 0 S1, 1 S3, 2 TRIG, 3 TRI
+bool css_rowpass_supported(bool fp32, int32_t b);
+css_status css_rowpass(css_ctx* ctx, int mode, int64_t N, int32_t b, int32_t ws, int32_t ncb, int32_t cb0, int first,
+                       int reorth, const float* Q, const float* Qp, const float* W, float* OUT, const double* M1,
+                       const double* Bprev, const double* Kp, double* part1, double* part2, cudaStream_t st);
+css_status css_small_mm(css_ctx* ctx, int32_t ncb, int32_t b, const double* A, const double* B, double* Cm,
+                        cudaStream_t st);
 // W = M V for a BSR matrix prepared by css_spmm_prepare (a.Hval, a.Hlo_diag, a.row_ptr,
 // a.col_idx, a.n_brow, a.b) and N x a.w blocks V, W of row stride a.ws in the vector precision
 css_status css_spmm(css_ctx* ctx, const LzArgs& a, const void* V, void* W, cudaStream_t st);

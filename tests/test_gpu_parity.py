@@ -206,6 +206,36 @@ def test_density_mixed_within_tolerance(torch, css, ctx, n, kind, r_col, m, solv
     assert abs(got["trP"] - ref["trP"]) < 1e-4
 
 
+@pytest.mark.parametrize("env", ["CSS_HV_TC", "CSS_ROWS_STREAM"])
+@pytest.mark.parametrize("n,r_col,m,solve", [(125, 10.0, 40, True), (64, 10.0, 8, False)])
+def test_alternative_fp32_kernels_match_oracle(torch, css, n, r_col, m, solve, env):
+    """The opt-in FP32 kernels for 17 <= b <= 24 (selected by an environment variable at
+    css_create): H*V on the tensor cores (tcgen05, 3xTF32 with the on-site blocks in three parts)
+    and the streaming row passes; each against the oracle like the default mixed path, with the
+    stored sampled rows and with the regenerating second pass."""
+    import os
+    g, H, col, s, nc = _system(n, "dzp", r_col)
+    ne = synth.n_electrons(n)
+    ref = oracle.density(H, col, s, nc, kT=0.05, n_elec=ne, m=m, mu=-4.0, solve_mu=solve)
+    os.environ[env] = "1"
+    try:
+        c2 = css.Context(0)
+    finally:
+        del os.environ[env]
+    try:
+        got = gpu_density(torch, css, c2, H, col, s, nc, kT=0.05, n_elec=ne, m=m, mu=-4.0, solve_mu=solve,
+                          precision=css.CSS_MIXED_FP32)
+        two = gpu_density(torch, css, c2, H, col, s, nc, kT=0.05, n_elec=ne, m=m, mu=-4.0, solve_mu=solve,
+                          precision=css.CSS_MIXED_FP32, flags=css.CSS_SYMMETRIZE | css.CSS_TWO_PASS)
+    finally:
+        c2.close()
+    dP = float(np.abs(got["P"] - ref["P"]).max())
+    assert dP < MIXED_P_TOL, dP
+    assert abs(2 * got["trPH"] - 2 * ref["trPH"]) / n < MIXED_E_TOL
+    assert abs(got["trP"] - ref["trP"]) < 1e-4
+    assert float(np.abs(two["P"] - ref["P"]).max()) < MIXED_P_TOL
+
+
 # ------------------------------------------- energy-weighted density matrix (forces)
 @pytest.mark.parametrize("n,kind,r_col,m,flags", [(64, "minimal", 8.0, 10, 1), (125, "minimal", 8.0, 12, 0),
                                                   (27, "dzp", 6.0, 6, 1), (64, "minimal", 8.0, 10, 1 | 2)])
