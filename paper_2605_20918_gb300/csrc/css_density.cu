@@ -624,7 +624,7 @@ struct Timer {
 
 css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys, int32_t m, css_precision prec,
                             uint32_t flags, double* trP, double* trPH, double* mu_out, cudaStream_t st,
-                            void* yfull, int32_t ldy, bool partial) {
+                            void* yfull, int32_t ldy, bool partial, const int32_t* colour_ids) {
   // ------------------------------------------------------------ validation
   if (n_sys < 1 || n_sys > MU_MAXSYS) return css_set_arg_error(ctx, "css_density: n_sys out of range");
   if (prec != CSS_FP64 && prec != CSS_MIXED_FP32) return css_set_arg_error(ctx, "css_density: unknown precision");
@@ -817,6 +817,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   ea.Bblk = Bblk;
   ea.nblk = nblk;
   ea.cnt = cnt;
+  ea.gid = colour_ids;
   ea.rcap = nmax * (nmax / b + 2);
   CSS_TRY(ws_get(ctx, "e_AB", (size_t)n_col * nmax * (2 * b + 1), &ea.AB));
   CSS_TRY(ws_get(ctx, "e_RV", (size_t)n_col * ea.rcap * b, &ea.RV));
@@ -1417,13 +1418,17 @@ css_status css_density_colours(css_ctx* ctx, const css_bsr* H, const int32_t* co
   int32_t n_own = 0;
   for (int32_t c = 0; c < n_colours; ++c) map[c] = owned[c] ? n_own++ : -1;
   if (n_own < 1) return css_set_arg_error(ctx, "css_density_colours: no colour owned");
-  int32_t *dmap, *dcol, *derr, *h;
-  CSS_TRY(css_ws(ctx, "part_map", sizeof(int32_t) * (n_colours + 64), (void**)&dmap));
+  int32_t *dmap, *dcol, *derr, *dids, *h;
+  CSS_TRY(css_ws(ctx, "part_map", sizeof(int32_t) * (2 * (size_t)n_colours + 64), (void**)&dmap));
   CSS_TRY(css_ws(ctx, "part_colour", sizeof(int32_t) * H->n_brow, (void**)&dcol));
   derr = dmap + n_colours;
-  CSS_TRY(css_pinned(ctx, sizeof(int32_t) * (n_colours + 64), (void**)&h));
+  dids = derr + 64;  // the owned colours' ids in the full numbering (their eigen-stage seeds)
+  CSS_TRY(css_pinned(ctx, sizeof(int32_t) * (2 * (size_t)n_colours + 64), (void**)&h));
   std::memcpy(h, map.data(), sizeof(int32_t) * n_colours);
+  for (int32_t c = 0, t = 0; c < n_colours; ++c)
+    if (owned[c]) h[n_colours + 64 + t++] = c;
   CSS_CU(ctx, cudaMemcpyAsync(dmap, h, sizeof(int32_t) * n_colours, cudaMemcpyHostToDevice, st));
+  CSS_CU(ctx, cudaMemcpyAsync(dids, h + n_colours + 64, sizeof(int32_t) * n_own, cudaMemcpyHostToDevice, st));
   CSS_CU(ctx, cudaMemsetAsync(derr, 0, sizeof(int32_t), st));
   k_colour_map<<<(unsigned)css_ceil_div(H->n_brow, 256), 256, 0, st>>>(H->n_brow, colour, n_colours, dmap, dcol, derr);
   CSS_LAUNCHED(ctx);
@@ -1432,7 +1437,7 @@ css_status css_density_colours(css_ctx* ctx, const css_bsr* H, const int32_t* co
   if (h[n_colours]) return css_set_arg_error(ctx, "css_density_colours: colour outside [0, n_colours)");
   css_sys_desc d{*H, dcol, sign, n_own, *fermi, P_val};
   double mu = 0.0;
-  return css_density_impl(ctx, 1, &d, m, prec, flags, trP, trPH, &mu, st, nullptr, 0, true);
+  return css_density_impl(ctx, 1, &d, m, prec, flags, trP, trPH, &mu, st, nullptr, 0, true, dids);
 }
 
 css_status css_solve_mu(css_ctx* ctx, int32_t n_lists, const int32_t* n_per, const double* lam, const double* wgt,

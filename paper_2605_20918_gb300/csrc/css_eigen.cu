@@ -422,8 +422,9 @@ __global__ void __launch_bounds__(128) k_inviter_p1(int32_t kd, int32_t nmax, co
                                                     const float* __restrict__ lam32, const double* __restrict__ tnorm,
                                                     double rel_cluster, double* __restrict__ U,
                                                     double* __restrict__ F, double* __restrict__ lam,
-                                                    int32_t* __restrict__ flag) {
+                                                    int32_t* __restrict__ flag, const int32_t* __restrict__ gid) {
   const int32_t c = blockIdx.y;
+  const uint64_t cseed = gid ? (uint64_t)gid[c] : (uint64_t)c;  // the colour's own id seeds its start vectors
   const int32_t n = nblk[c] * kd;
   const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (blockIdx.x * blockDim.x >= n) return;  // whole block beyond this colour's size
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(128) k_inviter_p1(int32_t kd, int32_t nmax, co
   // start vector, normalised
   double nrm = 0.0;
   for (int32_t i = 0; i < n; ++i) {
-    const double x = work ? hash_unit((uint64_t)c * 1000003ull + (uint64_t)k, (uint64_t)i) : 0.0;
+    const double x = work ? hash_unit(cseed * 1000003ull + (uint64_t)k, (uint64_t)i) : 0.0;
     if (work) f_x[(size_t)i * nmax + k] = x;
     nrm += x * x;
   }
@@ -651,11 +652,12 @@ __global__ void __launch_bounds__(256) k_inviter_cl(int32_t kd, int32_t nmax, co
                                                     const double* __restrict__ tnorm, double rel_cluster,
                                                     double* __restrict__ U, double* __restrict__ F,
                                                     double* __restrict__ lam, int32_t* __restrict__ status,
-                                                    const int32_t* __restrict__ flag) {
+                                                    const int32_t* __restrict__ flag, const int32_t* __restrict__ gid) {
   __shared__ double sC[8][kMaxCluster][kMaxCluster + 1];
   __shared__ double sV[8][kMaxCluster][kMaxCluster + 1];
   constexpr unsigned FULL = 0xffffffffu;
   const int32_t c = blockIdx.x;
+  const uint64_t cseed = gid ? (uint64_t)gid[c] : (uint64_t)c;
   const int32_t n = nblk[c] * kd;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const float* l32 = lam32 + (size_t)c * nmax;
@@ -711,7 +713,7 @@ __global__ void __launch_bounds__(256) k_inviter_cl(int32_t kd, int32_t nmax, co
           for (int q = 0; q < kCB; ++q) {
             const int32_t i = i0 + q;
             if (i < n) {
-              const double x = hash_unit((uint64_t)c * 1000003ull + (uint64_t)col + 7919ull * attempt, (uint64_t)i);
+              const double x = hash_unit(cseed * 1000003ull + (uint64_t)col + 7919ull * attempt, (uint64_t)i);
               if (act) m.x[(size_t)i * nmax + col] = x;
               nrm += x * x;
             }
@@ -998,10 +1000,10 @@ css_status css_eigen_ritz(css_ctx* ctx, const EigArgs& a, cudaStream_t st) {
   k_bisect32<<<nc, 256, sh, st>>>(b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm);
   CSS_LAUNCHED(ctx);
   k_inviter_p1<<<dim3((unsigned)css_ceil_div(nmax, 128), (unsigned)nc), 128, 0, st>>>(
-      b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm, 1e-4, a.U, a.F, a.lam, a.flag);
+      b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm, 1e-4, a.U, a.F, a.lam, a.flag, a.gid);
   CSS_LAUNCHED(ctx);
   k_inviter_cl<<<dim3((unsigned)nc, 4), 256, 0, st>>>(b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm, 1e-4, a.U, a.F, a.lam, a.status,
-                                   a.flag);
+                                   a.flag, a.gid);
   CSS_LAUNCHED(ctx);
   if (ctx->debug_eig == 1) {
     k_shifts_out<<<nc, 256, 0, st>>>(nmax, a.lam32, a.lam);

@@ -38,6 +38,9 @@ struct EigArgs {
   double* wgt = nullptr;               // [c][nmax] ||Y_k||^2
   int32_t* status = nullptr;           // [c]
   int32_t* flag = nullptr;             // [c][nmax] eigenvalues left to the sequential phase
+  const int32_t* gid = nullptr;        // [c] the colour's id for its inverse-iteration start vectors
+                                       // (nullptr: its index here; a colour subset passes the full
+                                       // call's numbering so that its results do not change)
 };
 
 css_status css_eigen_ritz(css_ctx* ctx, const EigArgs& a, cudaStream_t st);

@@ -131,4 +131,5 @@ struct css_sys_desc {
 // unsymmetrised output, the blocks of unprobed columns written as zero)
 css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys, int32_t m, css_precision prec,
                             uint32_t flags, double* trP, double* trPH, double* mu_out, cudaStream_t st,
-                            void* yfull = nullptr, int32_t ldy = 0, bool partial = false);
+                            void* yfull = nullptr, int32_t ldy = 0, bool partial = false,
+                            const int32_t* colour_ids = nullptr);
