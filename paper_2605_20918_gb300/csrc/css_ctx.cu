@@ -102,6 +102,8 @@ void css_destroy(css_ctx* ctx) {
   cudaDeviceSynchronize();
   for (auto& kv : ctx->bufs)
     if (kv.second.p) cudaFree(kv.second.p);
+  for (cudaStream_t s : ctx->side) cudaStreamDestroy(s);
+  for (cudaEvent_t e : ctx->side_ev) cudaEventDestroy(e);
   if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
   delete ctx;
 }

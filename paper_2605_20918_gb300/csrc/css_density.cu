@@ -6,6 +6,7 @@
 // "Pairs": for every block row I the distinct colours of its pattern columns.  X is needed
 // exactly on those (I, c) pairs; they are stored sorted by colour, so the pairs of a colour
 // batch are one contiguous range.
+#include <algorithm>
 #include <cmath>
 
 #include "css_eigen.cuh"
@@ -915,8 +916,97 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   double spmm_ms = 0.0, rows_ms = 0.0;
   int64_t n_rows = 0;
   const int32_t BMh = css_spmm_bm(b);
+  // A batch of systems runs its per-system passes concurrently on up to kSide side streams, each
+  // with its own Krylov workspace (the passes of different systems touch disjoint rows, colours
+  // and sampled pairs); the call's stream waits for all of them before the eigen stage.  The
+  // tensor-core H*V keeps one schedule per call, so it runs the passes in turn.
+  constexpr int kSide = 8;
+  int nside = (n_sys > 1 && !use_tc) ? std::min(n_sys, kSide) : 0;
+  if (nside > 0) {
+    // each side stream needs one more Krylov set; take only as many as fit beside the
+    // reserve (sets already held from an earlier call count as free)
+    size_t free2 = 0, total2 = 0, held = 0;
+    CSS_CU(ctx, cudaMemGetInfo(&free2, &total2));
+    static const char* const kSideNames[] = {"sQ0_", "sQ1_", "sW_", "spart_", "ssmall_"};
+    for (auto& kv : ctx->bufs)
+      for (const char* pre : kSideNames)
+        if (kv.first.rfind(pre, 0) == 0) held += kv.second.bytes;
+    const size_t avail = free2 + held > reserve ? free2 + held - reserve : 0;
+    nside = (int)std::min<size_t>((size_t)nside, avail / vec_need(ncb));
+    if (nside < 2) nside = 0;
+  }
+  struct SideWs {
+    void *Q0, *Q1, *W;
+    double *part, *small;
+  };
+  std::vector<SideWs> sws(nside);
+  if (nside > 0) {
+    while ((int)ctx->side.size() < nside) {
+      cudaStream_t s2;
+      CSS_CU(ctx, cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+      ctx->side.push_back(s2);
+    }
+    while ((int)ctx->side_ev.size() < nside + 1) {
+      cudaEvent_t e2;
+      CSS_CU(ctx, cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+      ctx->side_ev.push_back(e2);
+    }
+    for (int k = 0; k < nside; ++k) {
+      char nm[32];
+      snprintf(nm, sizeof(nm), "sQ0_%d", k);
+      CSS_TRY(css_ws(ctx, nm, (size_t)Nmax * ws * s_vec, &sws[k].Q0));
+      snprintf(nm, sizeof(nm), "sQ1_%d", k);
+      CSS_TRY(css_ws(ctx, nm, (size_t)Nmax * ws * s_vec, &sws[k].Q1));
+      snprintf(nm, sizeof(nm), "sW_%d", k);
+      CSS_TRY(css_ws(ctx, nm, (size_t)Nmax * ws * s_vec, &sws[k].W));
+      snprintf(nm, sizeof(nm), "spart_%d", k);
+      CSS_TRY(ws_get(ctx, nm, css_lanczos_part_doubles(Nmax, b, ncb) * 2, &sws[k].part));
+      snprintf(nm, sizeof(nm), "ssmall_%d", k);
+      CSS_TRY(ws_get(ctx, nm, css_lanczos_small_doubles(b, ncb), &sws[k].small));
+    }
+  }
+  // systems by decreasing size, dealt round-robin to the side streams
+  std::vector<int32_t> sys_order(n_sys);
+  for (int32_t s = 0; s < n_sys; ++s) sys_order[s] = s;
+  std::stable_sort(sys_order.begin(), sys_order.end(),
+                   [&](int32_t x, int32_t y) { return sys[x].H.n_brow > sys[y].H.n_brow; });
   auto run_batches = [&](int mode) -> css_status {
     la.mode = mode;
+    if (nside > 0) {
+      CSS_CU(ctx, cudaEventRecord(ctx->side_ev[nside], st));
+      for (int k = 0; k < nside; ++k) CSS_CU(ctx, cudaStreamWaitEvent(ctx->side[k], ctx->side_ev[nside], 0));
+      css_status rs = CSS_OK;
+      for (int32_t i = 0; i < n_sys; ++i) {
+        const int32_t s = sys_order[i];
+        const int k = i % nside;
+        LzArgs lb = la;
+        lb.Q0 = sws[k].Q0;
+        lb.Q1 = sws[k].Q1;
+        lb.W = sws[k].W;
+        lb.part = sws[k].part;
+        lb.small = sws[k].small;
+        lb.row0 = row_off[s];
+        lb.n_brow = sys[s].H.n_brow;
+        lb.row_ptr = row_ptr + row_off[s];
+        lb.colour = colour + row_off[s];
+        lb.sign = sign + (size_t)row_off[s] * b;
+        lb.Hlo_diag = Hlo ? (const void*)((const char*)Hlo + (size_t)row_off[s] * BMh * BMh * s_vec) : nullptr;
+        lb.ev_spmm = nullptr;
+        for (int32_t cb0 = col_off[s]; cb0 < col_off[s + 1] && rs == CSS_OK; cb0 += ncb) {
+          lb.cb0 = cb0;
+          lb.ncb = min(ncb, col_off[s + 1] - cb0);
+          lb.w = lb.ncb * b;
+          rs = css_lanczos_pass(ctx, lb, ctx->side[k]);
+        }
+        if (rs != CSS_OK) break;
+      }
+      // joined on every path, so that no side stream still writes the workspace after return
+      for (int k = 0; k < nside; ++k) {
+        CSS_CU(ctx, cudaEventRecord(ctx->side_ev[k], ctx->side[k]));
+        CSS_CU(ctx, cudaStreamWaitEvent(st, ctx->side_ev[k], 0));
+      }
+      return rs;
+    }
     for (int32_t s = 0; s < n_sys; ++s) {
       la.row0 = row_off[s];
       la.n_brow = sys[s].H.n_brow;

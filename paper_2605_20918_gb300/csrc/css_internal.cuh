@@ -71,6 +71,10 @@ struct css_ctx {
   // env CSS_ROWS_STREAM=1 at css_create: the streaming FP32 row passes of css_rows.cu (11
   // passes per step) instead of the tiled row kernels (14 passes, faster as measured)
   bool rows_stream = false;
+  // side streams (and their fork / join events) on which the per-system block-Lanczos passes
+  // of a batch run concurrently; created on first use, destroyed with the context
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> side_ev;
 };
 
 // CUDA events owned by the holder: destroyed when it goes out of scope, early returns included
