@@ -30,8 +30,11 @@
 #include <mutex>
 
 #include "css_lanczos.cuh"
+#include "css_pipe.cuh"
 
 namespace {
+
+using namespace css_pipe;
 
 constexpr int TC_BK = 24;         // K per block: b <= 24, padded to 3 steps of 8
 constexpr int TC_BN = 32;         // N of the MMA (rows of W_I; b <= 24 of them are kept)
@@ -54,68 +57,14 @@ constexpr int TC_ACOL(int slot, int tile, int part) { return TC_DCOL + ((slot * 
 static_assert(TC_ACOL(1, 1, 2) + TC_BK <= 512, "tensor memory budget");
 constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
                               ((uint32_t)(128 >> 4) << 24);  // F32 += TF32 x TF32, K-major, M=128, N=32
-constexpr uint64_t TC_WAIT_NS = 2000000000ull;  // 2 s per wait
 
 // ------------------------------------------------------------------ PTX wrappers
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ uint64_t gtime() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t n) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
-}
-__device__ __forceinline__ void bar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool bar_test(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-      : "=r"(ok)
-      : "r"(su32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait for the phase of `parity`; gives up when the CTA's abort flag is set or after
-// TC_WAIT_NS (then sets the abort flag and the error flag)
-__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, int* err) {
-  if (bar_test(b, parity)) return true;
-  const uint64_t t0 = gtime();
-  for (uint32_t it = 1;; ++it) {
-    if (bar_test(b, parity)) return true;
-    if ((it & 255) == 0) {
-      if (*abort_flag) return false;
-      if (gtime() - t0 > TC_WAIT_NS) {
-        *abort_flag = 1;
-        atomicOr(err, 1);
-        return false;
-      }
-    }
-  }
-}
-// the same without abort: used at tear-down for copies and MMAs that are already in flight
-__device__ __forceinline__ void bar_drain(uint64_t* b, uint32_t parity) {
-  const uint64_t t0 = gtime();
-  while (!bar_test(b, parity))
-    if (gtime() - t0 > TC_WAIT_NS) return;
-}
 __device__ __forceinline__ void tma_v(void* dst, const CUtensorMap* map, int x, int y, uint64_t* b) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
           su32(dst)),
       "l"(map), "r"(x), "r"(y), "r"(su32(b))
       : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   su32(dst)),
-               "l"(src), "r"(bytes), "r"(su32(b))
-               : "memory");
 }
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
   uint32_t r;
