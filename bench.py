@@ -33,7 +33,19 @@ ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 METRIC = "P build s/step at 10k H2O"
-SPMM_KERNEL_VERSION = "k_spmm-f32x2-v4"  # profiles/spmm_traffic.json must name the kernel measured
+SPMM_KERNEL_VERSION = "k_spmm_dup-v1"  # profiles/spmm_traffic.json must name the kernel measured
+
+
+def hv_kernel(mixed, b):
+    """(name, version tag) of the H*V kernel a build runs: the tensor-core one when asked for, the
+    exact-width FP32 kernel for b = 6 and 23, else the padded FFMA/DFMA kernel."""
+    if mixed and os.environ.get("CSS_HV_TC") == "1" and 16 < b <= 24:
+        return "k_hv_tc (H*V on tcgen05, 3xTF32)", "k_hv_tc"
+    if mixed and b in (6, 23) and not os.environ.get("CSS_SPMM_VARIANT"):
+        return ("k_spmm_dup (exact-width H*V on the FP32 FMA pipe, packed column pairs, all colours of the "
+                "system as columns)", SPMM_KERNEL_VERSION)
+    return ("k_spmm (padded H*V on the " + ("FP32 FMA" if mixed else "FP64 DFMA") +
+            " pipe, all colours of the system as columns)", "k_spmm-padded")
 FP64_PEAK_NOTE = "FP64 peak: 1.25 TFLOP/s nominal GB300 FP64 rate"
 FP64_PEAK = 1.25                                 # TFLOP/s
 
@@ -418,7 +430,7 @@ def run_million(a):
                                    "two-pass block-Lanczos", "n_mol": n, "orbitals_per_molecule": 6,
                        "krylov_blocks_m": 30, "r_col_A": 10.0, "coupling_cutoff_A": 6.0, "kT_eV": 0.05,
                        "precision": "mixed", "l2": l2_note(H)},
-            "roofline": {"kernel": "k_spmm (H*V on the FP32 FMA pipe)", "bound": "alu", "achieved": achieved,
+            "roofline": {"kernel": hv_kernel(True, 6)[0], "bound": "alu", "achieved": achieved,
                          "peak": fp32_peak_tflops(n_sm, pk["sm_max_mhz"]), "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak_tflops(n_sm, pk["sm_max_mhz"]) if achieved else None,
                          "launch_ms": inf["ms_spmm"], "launches_per_build": inf["spmm_launches"]},
@@ -517,14 +529,15 @@ def main():
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = fp32_peak_tflops(n_sm, pk["sm_max_mhz"])
     tf32_peak = tf32_peak_tflops(pk)
-    tc = os.environ.get("CSS_HV_TC") == "1" and prec == css.CSS_MIXED_FP32 and H0.b > 16
+    tc = os.environ.get("CSS_HV_TC") == "1" and prec == css.CSS_MIXED_FP32 and 16 < H0.b <= 24
+    hv_name, hv_version = hv_kernel(prec == css.CSS_MIXED_FP32, H0.b)
     peak = (tf32_peak if tc else fp32_peak) if prec == css.CSS_MIXED_FP32 else FP64_PEAK
     traffic = None
     tf = ROOT / "profiles" / "spmm_traffic.json"
     if tf.exists():
         try:
             d = json.loads(tf.read_text())
-            if d.get("kernel_version") == SPMM_KERNEL_VERSION and d.get("precision") == a.precision and \
+            if d.get("kernel_version") == hv_version and d.get("precision") == a.precision and \
                     d.get("n_mol") == a.n_mol:
                 traffic = d.get("bytes_per_launch")
         except Exception:
@@ -535,8 +548,7 @@ def main():
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": elapsed / a.steps * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == css.CSS_MIXED_FP32 else "f64",
             "data": "synthetic", "config": cfg,
-            "roofline": {"kernel": ("k_hv_tc (H*V on tcgen05, 3xTF32)" if tc else
-                                    "k_spmm (H*V on the FP32 FMA pipe, all colours of the system as columns)"),
+            "roofline": {"kernel": hv_name,
                          "bound": "tensor" if tc else ("alu" if prec == css.CSS_MIXED_FP32 else "alu_fp64"),
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": None if tc else traffic,

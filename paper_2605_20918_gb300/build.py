@@ -18,7 +18,7 @@ SRC = PKG / "csrc"
 INC = ROOT / "include"
 OUT = PKG / "libcss.so"
 BUILD = PKG / "_build"
-UNITS = ["css_ctx", "css_color", "css_lanczos", "css_rows", "css_hv_tc", "css_eigen", "css_density", "css_pbuild",
+UNITS = ["css_ctx", "css_color", "css_lanczos", "css_rows", "css_hv_tc", "css_spmm", "css_eigen", "css_density", "css_pbuild",
          "css_noalloc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

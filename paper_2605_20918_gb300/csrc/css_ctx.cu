@@ -83,11 +83,16 @@ css_status css_create(css_ctx** out, int device) {
   ctx->timing = t && t[0] == '1';
   const char* sv = getenv("CSS_SPMM_VARIANT");
   if (sv && sv[0] >= '0' && sv[0] <= '4' && sv[1] == 0) ctx->spmm_variant = sv[0] - '0';
+  const char* dv = getenv("CSS_SPMM_DUP_VARIANT");
+  if (dv && dv[0] >= '0' && dv[0] <= '3' && dv[1] == 0) ctx->spmm_dup_variant = dv[0] - '0';
   const char* de = getenv("CSS_DEBUG_EIG");
   ctx->debug_eig = de ? atoi(de) : 0;
   const char* tb = getenv("CSS_TEST_MU_BARRIER_EXTRA");
   const int extra = tb ? atoi(tb) : 0;
   ctx->test_mu_barrier_extra = extra > 0 && extra < 64 ? extra : 0;
+  const char* te = getenv("CSS_TEST_SPMM_EMPTY_EXTRA");
+  const int eextra = te ? atoi(te) : 0;
+  ctx->test_spmm_empty_extra = eextra > 0 && eextra < 4 ? eextra : 0;
   const char* tc = getenv("CSS_HV_TC");
   ctx->hv_tc = tc && tc[0] == '1';
   const char* rs = getenv("CSS_ROWS_STREAM");

@@ -793,9 +793,15 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   const void* Hlo = nullptr;
   const void* Htc = nullptr;
   const void* Hd3 = nullptr;
+  const void* Hdup = nullptr;
+  const void* Hlodup = nullptr;
   const bool use_tc = ctx->hv_tc && css_hv_tc_supported(f32, b, max_row);
+  // FP32 with b = 6 or 23: the exact-width H * V unless a padded variant is asked for
+  const bool use_dup = !use_tc && ctx->spmm_variant < 0 && css_spmm_dup_supported(f32, b);
   if (use_tc)
     CSS_TRY(css_hv_tc_prepare(ctx, b, n_brow, nnzb, row_ptr, col_idx, Hval, &Htc, &Hd3, st));
+  else if (use_dup)
+    CSS_TRY(css_spmm_dup_prepare(ctx, b, n_brow, nnzb, row_ptr, col_idx, Hval, &Hdup, &Hlodup, st));
   else
     CSS_TRY(css_spmm_prepare(ctx, f32, b, n_brow, nnzb, row_ptr, col_idx, Hval, &Hv, &Hlo, st));
   tm.mark();  // 1
@@ -876,6 +882,8 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   la.col_idx = col_idx;
   la.Hval = Hv;
   la.Hlo_diag = Hlo;
+  la.Hdup = Hdup;
+  la.Hlo_dup = Hlodup;
   la.use_tc = use_tc;
   la.tc_H = Htc;
   la.tc_Hd3 = Hd3;
@@ -916,6 +924,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   double spmm_ms = 0.0, rows_ms = 0.0;
   int64_t n_rows = 0;
   const int32_t BMh = css_spmm_bm(b);
+  const size_t dup_row = (size_t)b * (b + (b & 1)) * 8;  // bytes of one row's low-part block (exact width)
   // A batch of systems runs its per-system passes concurrently on up to kSide side streams, each
   // with its own Krylov workspace (the passes of different systems touch disjoint rows, colours
   // and sampled pairs); the call's stream waits for all of them before the eigen stage.  The
@@ -991,6 +1000,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
         lb.colour = colour + row_off[s];
         lb.sign = sign + (size_t)row_off[s] * b;
         lb.Hlo_diag = Hlo ? (const void*)((const char*)Hlo + (size_t)row_off[s] * BMh * BMh * s_vec) : nullptr;
+        lb.Hlo_dup = Hlodup ? (const void*)((const char*)Hlodup + (size_t)row_off[s] * dup_row) : nullptr;
         lb.ev_spmm = nullptr;
         for (int32_t cb0 = col_off[s]; cb0 < col_off[s + 1] && rs == CSS_OK; cb0 += ncb) {
           lb.cb0 = cb0;
@@ -1014,6 +1024,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
       la.colour = colour + row_off[s];
       la.sign = sign + (size_t)row_off[s] * b;
       la.Hlo_diag = Hlo ? (const void*)((const char*)Hlo + (size_t)row_off[s] * BMh * BMh * s_vec) : nullptr;
+      la.Hlo_dup = Hlodup ? (const void*)((const char*)Hlodup + (size_t)row_off[s] * dup_row) : nullptr;
       for (int32_t cb0 = col_off[s]; cb0 < col_off[s + 1]; cb0 += ncb) {
         la.cb0 = cb0;
         la.ncb = min(ncb, col_off[s + 1] - cb0);
@@ -1067,6 +1078,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     ctx->info.n_breakdown = hm[0];
     const int32_t st_bits = hm[1];
     if (use_tc) CSS_TRY(css_hv_tc_check(ctx, st));
+    if (use_dup) CSS_TRY(css_spmm_dup_check(ctx, st));
     if (st_bits & 2) {
       ctx->last_error = "css_density: a wait between pipelined band-reduction sweeps timed out";
       return CSS_ERR_TIMEOUT;
@@ -1237,6 +1249,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     ctx->info.ms_total = tm.ms(0, 6);
   }
   if (use_tc) CSS_TRY(css_hv_tc_check(ctx, st));
+  if (use_dup) CSS_TRY(css_spmm_dup_check(ctx, st));
   if (mu_err) {
     ctx->last_error = "css_density: grid barrier of the mu bisection timed out";
     return CSS_ERR_TIMEOUT;

@@ -60,7 +60,13 @@ struct css_ctx {
   size_t host_pinned_bytes = 0;
   // H * V autotuner: launch variant chosen per (precision, block width, column count, rows)
   std::vector<std::pair<uint64_t, int>> spmm_tune;
-  int spmm_variant = -1;  // env CSS_SPMM_VARIANT = 0..4 fixes the variant (no tuning)
+  // env CSS_SPMM_VARIANT = 0..4: the padded FP32 kernel (also for b = 6 and 23) with that variant
+  int spmm_variant = -1;
+  int spmm_dup_variant = -1;  // env CSS_SPMM_DUP_VARIANT = 0..3 fixes the exact-width kernel's variant
+  // failure injection for tests (env CSS_TEST_SPMM_EMPTY_EXTRA = k at css_create): the "empty"
+  // barriers of the exact-width H * V wait for k warps more than a CTA has, so the copying
+  // thread's bounded wait runs out and the call returns CSS_ERR_TIMEOUT; 0 is the normal kernel
+  int test_spmm_empty_extra = 0;
   // failure injection for tests (env CSS_TEST_MU_BARRIER_EXTRA = k at css_create): the grid
   // barrier of the mu bisection waits for k CTAs more than the launch has, so its bounded wait
   // runs out and the call returns CSS_ERR_TIMEOUT; 0 (the default) is the normal barrier

@@ -922,26 +922,37 @@ css_status launch_spmm_v(css_ctx* ctx, const LzArgs& a, const T* V, T* W, int v,
 // same W), and the fastest is kept.  Shapes: precision, b, columns in buckets of 256, rows.
 template <typename T>
 css_status launch_spmm(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaStream_t st) {
-  if constexpr (sizeof(T) == 4)
+  bool dup = false;
+  if constexpr (sizeof(T) == 4) {
     if (a.use_tc) return css_hv_tc(ctx, a, V, W, st);
-  const uint64_t key = ((uint64_t)sizeof(T) << 60) ^ ((uint64_t)a.b << 48) ^ ((uint64_t)(a.w / 256) << 24) ^
-                       (uint64_t)(a.n_brow >= (1 << 24) ? (1 << 24) - 1 : a.n_brow);
-  if (ctx->spmm_variant >= 0) return launch_spmm_v<T>(ctx, a, V, W, ctx->spmm_variant, st);
+    dup = a.Hdup != nullptr;
+  }
+  // the exact-width kernel (css_spmm.cu) when H was prepared for it, else the padded one
+  auto run = [&](int v) -> css_status {
+    if constexpr (sizeof(T) == 4)
+      if (dup) return css_spmm_dup(ctx, a, V, W, v, st);
+    return launch_spmm_v<T>(ctx, a, V, W, v, st);
+  };
+  const int nv = dup ? css_spmm_dup_variants() : kSpmmVariants;
+  const uint64_t key = ((uint64_t)sizeof(T) << 60) ^ ((uint64_t)dup << 59) ^ ((uint64_t)a.b << 48) ^
+                       ((uint64_t)(a.w / 256) << 24) ^ (uint64_t)(a.n_brow >= (1 << 24) ? (1 << 24) - 1 : a.n_brow);
+  if (!dup && ctx->spmm_variant >= 0) return run(ctx->spmm_variant);
+  if (dup && ctx->spmm_dup_variant >= 0) return run(ctx->spmm_dup_variant);
   for (const auto& kv : ctx->spmm_tune)
-    if (kv.first == key) return launch_spmm_v<T>(ctx, a, V, W, kv.second, st);
+    if (kv.first == key) return run(kv.second);
   css_events ev;
-  CSS_CU(ctx, ev.create(kSpmmVariants + 1));
+  CSS_CU(ctx, ev.create((size_t)nv + 1));
   css_status rc = CSS_OK;
-  for (int v = 0; v < kSpmmVariants && rc == CSS_OK; ++v) rc = launch_spmm_v<T>(ctx, a, V, W, v, st);
+  for (int v = 0; v < nv && rc == CSS_OK; ++v) rc = run(v);
   if (rc == CSS_OK) CSS_CU(ctx, cudaEventRecord(ev[0], st));
-  for (int v = 0; v < kSpmmVariants && rc == CSS_OK; ++v) {
-    rc = launch_spmm_v<T>(ctx, a, V, W, v, st);
+  for (int v = 0; v < nv && rc == CSS_OK; ++v) {
+    rc = run(v);
     if (rc == CSS_OK) rc = cudaEventRecord(ev[v + 1], st) == cudaSuccess ? CSS_OK : CSS_ERR_CUDA;
   }
   int best = 0;
-  if (rc == CSS_OK && cudaEventSynchronize(ev[kSpmmVariants]) == cudaSuccess) {
+  if (rc == CSS_OK && cudaEventSynchronize(ev[nv]) == cudaSuccess) {
     float tbest = 0.0f;
-    for (int v = 0; v < kSpmmVariants; ++v) {
+    for (int v = 0; v < nv; ++v) {
       float ms = 0.0f;
       cudaEventElapsedTime(&ms, ev[v], ev[v + 1]);
       if (v == 0 || ms < tbest) {

@@ -51,6 +51,10 @@ struct LzArgs {
   // FP32 H * V on the tensor cores (css_hv_tc.cu) when use_tc: TF32 parts of H (tc_H: every
   // block, tc_Hd3: third part of the diagonal blocks, rows numbered as in the combined matrix)
   // and the pass's group schedule (filled by css_hv_tc_schedule)
+  // FP32 H * V with exact block width (css_spmm.cu) when Hdup is set: duplicated FP32 pairs of
+  // every block and of the low parts of the diagonal blocks (rows as in Hlo_diag)
+  const void* Hdup = nullptr;
+  const void* Hlo_dup = nullptr;
   bool use_tc = false;
   const void* tc_H = nullptr;
   const void* tc_Hd3 = nullptr;
@@ -69,6 +73,14 @@ css_status css_hv_tc_prepare(css_ctx* ctx, int32_t b, int32_t n_brow, int32_t nn
 css_status css_hv_tc_schedule(css_ctx* ctx, LzArgs& a, cudaStream_t st);
 css_status css_hv_tc(css_ctx* ctx, const LzArgs& a, const float* V, float* W, cudaStream_t st);
 css_status css_hv_tc_check(css_ctx* ctx, cudaStream_t st);
+// exact-width FP32 H * V (css_spmm.cu): b = 6 and b = 23
+bool css_spmm_dup_supported(bool fp32, int32_t b);
+int css_spmm_dup_variants();
+css_status css_spmm_dup_prepare(css_ctx* ctx, int32_t b, int32_t n_brow, int32_t nnzb, const int32_t* row_ptr,
+                                const int32_t* col_idx, const double* H, const void** Hd, const void** Hlod,
+                                cudaStream_t st);
+css_status css_spmm_dup(css_ctx* ctx, const LzArgs& a, const float* V, float* W, int variant, cudaStream_t st);
+css_status css_spmm_dup_check(css_ctx* ctx, cudaStream_t st);
 // FP32 row passes of a Lanczos step for 16 < b <= 24 (css_rows.cu); mode 0 S1, 1 S3, 2 TRIG, 3 TRI
 bool css_rowpass_supported(bool fp32, int32_t b);
 css_status css_rowpass(css_ctx* ctx, int mode, int64_t N, int32_t b, int32_t ws, int32_t ncb, int32_t cb0, int first,

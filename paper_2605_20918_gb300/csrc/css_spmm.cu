@@ -1,0 +1,346 @@
+// FP32 H * V for the block widths of the two molecular bases (b = 6, minimal; b = 23, DZP-like):
+// W = H V for the BSR matrix H and the Krylov blocks V of every colour of a batch (paper: the
+// SpMMs that make up the whole cost of the method, paragraph after Eq. 10).
+//
+// The padded kernel of css_lanczos.cu multiplies BM x BM blocks (BM = 8 for b = 6, 24 for
+// b = 23: 78% and 9% more FMAs than the blocks hold) and stages V through shared memory behind
+// two CTA barriers per neighbour block.  This one
+//  * pairs adjacent COLUMNS in the packed FMA fma.rn.f32x2: a thread owns 2 TCP = 4 consecutive
+//    columns of the b rows of W_I, each 64-bit accumulator one row and two columns, and H enters
+//    as the duplicated pair {h, h}, stored that way once per call (Hd[p][k][r] = {H_p[r][k],
+//    H_p[r][k]}, r padded to an even count), so a k costs exactly b * TCP packed FMAs;
+//  * reads each thread's own 8 TCP bytes of the b rows of V_J straight from L2 into registers,
+//    DEPTH rows ahead of their use: V needs neither shared memory nor a barrier;
+//  * keeps only the H blocks in shared memory, in a ring of NS stages that one thread fills with
+//    bulk copies (cp.async.bulk) completing on mbarriers.  The warps of a CTA wait on a stage's
+//    "full" barrier and release it on its "empty" barrier; only the copying thread waits for the
+//    other warps, one stage behind.
+// Each output is the same sum in the same order as in the padded kernel (neighbours in CSR
+// order, k ascending, then the low FP32 part of the diagonal block), every term the same IEEE
+// FMA, so both kernels give bitwise equal W.  Every wait is bounded: on time-out the CTA sets the
+// error flag, waits for its own copies in flight, writes zeros to its part of W and returns.
+#include <algorithm>
+
+#include "css_lanczos.cuh"
+#include "css_pipe.cuh"
+
+namespace {
+
+using namespace css_pipe;
+
+constexpr int SD_NS = 4;     // H stages
+constexpr int SD_DEPTH = 4;  // rows of V in flight per thread
+
+template <int B, int TCP, int NW>
+struct SdCfg {
+  static constexpr int BA = B + (B & 1);  // rows of a duplicated block (even)
+  static constexpr int HQ = B * BA;       // 8-byte pairs per block
+  static constexpr int HB = HQ * 8;       // bytes per block, a multiple of 16
+  static constexpr int NT = NW * 32;
+  static constexpr int CPT = 2 * TCP;     // columns per thread
+  static constexpr int CW = 32 * CPT;     // columns per warp
+  static constexpr int CT = NW * CW;      // columns per CTA
+  static constexpr size_t smem = (size_t)SD_NS * HB + 2 * SD_NS * sizeof(uint64_t) + 16;
+  // four columns per thread only: with eight (TCP = 4) the batched build, whose systems run on
+  // concurrent side streams, gave run-to-run different W for a few systems although every
+  // single-system call matched the padded kernel bit for bit; the cause was not found
+  static_assert(B >= SD_DEPTH && TCP == 2, "shape");
+};
+
+struct SdArgs {
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const unsigned long long* Hd;    // [nnzb][B][BA] duplicated pairs
+  const unsigned long long* Hlod;  // [n_brow][B][BA] low parts of the diagonal blocks, or null
+  const float* V;
+  float* W;
+  int32_t ws, w, jbase;
+  int32_t empty_extra;  // 0; a test sets k > 0 so that the ring's waits run out
+  int* err;
+};
+
+template <int TCP>
+struct VRow {
+  unsigned long long x[TCP];  // TCP pairs of adjacent columns
+};
+
+template <int TCP>
+__device__ __forceinline__ VRow<TCP> v_load(const float* p) {
+  VRow<TCP> r;
+#pragma unroll
+  for (int i = 0; i < TCP; i += 2) {
+    const ulonglong2 t = __ldcg(reinterpret_cast<const ulonglong2*>(p) + i / 2);
+    r.x[i] = t.x;
+    r.x[i + 1] = t.y;
+  }
+  return r;
+}
+
+__device__ __forceinline__ void fma2(unsigned long long& d, unsigned long long h, unsigned long long v) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(h), "l"(v));
+}
+// grid (n_brow, column tiles of CT); rows without blocks (and no low part) give W_I = 0
+template <int B, int TCP, int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) k_spmm_dup(SdArgs a) {
+  using C = SdCfg<B, TCP, NW>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned long long* ring = reinterpret_cast<unsigned long long*>(smem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + SD_NS * C::HB);
+  uint64_t* empty = full + SD_NS;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + SD_NS);
+  const int32_t I = blockIdx.x;
+  const int32_t tile0 = blockIdx.y * C::CT;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int live = min(NW, (a.w - tile0 + C::CW - 1) / C::CW);  // warps with a column below w
+  const int32_t p0 = a.row_ptr[I], nnz = a.row_ptr[I + 1] - p0;
+  const int32_t nsteps = nnz + (a.Hlod ? 1 : 0);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < SD_NS; ++s) {
+      bar_init(&full[s], 1);
+      bar_init(&empty[s], (uint32_t)(live + a.empty_extra));
+    }
+    // after a time-out anywhere in this call the remaining CTAs return at once (the call fails)
+    *abort_flag = *(volatile int*)a.err ? 1 : 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp >= live) return;  // no barrier below involves these warps
+  const int32_t col = tile0 + (warp * 32 + lane) * C::CPT;
+  float* Wr = a.W + (size_t)I * B * a.ws + col;
+  // a failed call leaves zeros (finite values) in W for the rest of the pass
+  auto zero_w = [&]() {
+    if (col < a.w)
+      for (int r = 0; r < B; ++r)
+        for (int u = 0; u < C::CPT && col + u < a.w; ++u) Wr[(size_t)r * a.ws + u] = 0.0f;
+  };
+  if (*abort_flag) {
+    zero_w();
+    return;
+  }
+
+  const bool producer = warp == 0 && lane == 0;
+  auto issue = [&](int32_t q) {
+    const int s = q % SD_NS;
+    const unsigned long long* src = q < nnz ? a.Hd + (size_t)(p0 + q) * C::HQ : a.Hlod + (size_t)I * C::HQ;
+    bar_expect(&full[s], C::HB);
+    bulk_g2s(ring + (size_t)s * C::HQ, src, C::HB, &full[s]);
+  };
+  int32_t issued = 0;
+  if (producer)
+    for (; issued < nsteps && issued < SD_NS - 1; ++issued) issue(issued);
+
+  const float* Vc = a.V + (col < a.w ? col : 0);  // lanes past w read column 0 and store nothing
+  auto jof = [&](int32_t q) -> int32_t { return q < nnz ? a.col_idx[p0 + q] - a.jbase : I; };
+  auto vrow = [&](int32_t J, int k) { return v_load<TCP>(Vc + ((size_t)J * B + k) * a.ws); };
+
+  unsigned long long acc[B][TCP];
+#pragma unroll
+  for (int r = 0; r < B; ++r)
+#pragma unroll
+    for (int u = 0; u < TCP; ++u) acc[r][u] = 0ull;
+  bool ok = true;
+  int32_t q = 0;
+  if (nsteps > 0) {
+    VRow<TCP> vr[B];
+    VRow<TCP> vn[SD_DEPTH];
+    int32_t Jc = jof(0);
+#pragma unroll
+    for (int k = 0; k < SD_DEPTH; ++k) vr[k] = vrow(Jc, k);
+    for (; q < nsteps; ++q) {
+      const int s = q % SD_NS;
+      const bool more = q + 1 < nsteps;
+      const int32_t Jn = more ? jof(q + 1) : Jc;
+      bool good = true;
+      if (producer && issued < nsteps) {
+        // the stage of step `issued` was last read by step issued - NS (= q - 1)
+        if (issued >= SD_NS)
+          good = bar_wait(&empty[issued % SD_NS], (uint32_t)((issued / SD_NS - 1) & 1), abort_flag, a.err);
+        if (good) {
+          issue(issued);
+          ++issued;
+        }
+      }
+      if (good) good = bar_wait(&full[s], (uint32_t)((q / SD_NS) & 1), abort_flag, a.err);
+      if (!__all_sync(0xffffffffu, good)) {
+        ok = false;
+        break;
+      }
+      const unsigned long long* hs = ring + (size_t)s * C::HQ;
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        if (k + SD_DEPTH < B)
+          vr[k + SD_DEPTH] = vrow(Jc, k + SD_DEPTH);
+        else if (more)
+          vn[k + SD_DEPTH - B] = vrow(Jn, k + SD_DEPTH - B);
+#pragma unroll
+        for (int r2 = 0; r2 < C::BA / 2; ++r2) {
+          const ulonglong2 h = *reinterpret_cast<const ulonglong2*>(hs + k * C::BA + 2 * r2);
+#pragma unroll
+          for (int u = 0; u < TCP; ++u) fma2(acc[2 * r2][u], h.x, vr[k].x[u]);
+          if (2 * r2 + 1 < B) {
+#pragma unroll
+            for (int u = 0; u < TCP; ++u) fma2(acc[2 * r2 + 1][u], h.y, vr[k].x[u]);
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) bar_arrive(&empty[s]);
+#pragma unroll
+      for (int k = 0; k < SD_DEPTH; ++k) vr[k] = vn[k];
+      Jc = Jn;
+    }
+  }
+  if (!ok) {
+    // bulk copies issued and not yet waited for are steps [q, issued): let them land first
+    if (producer)
+      for (int32_t n = q; n < issued; ++n) bar_drain(&full[n % SD_NS], (uint32_t)((n / SD_NS) & 1));
+    zero_w();
+    return;
+  }
+  if (col >= a.w) return;
+  const bool whole = col + C::CPT <= a.w;
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    if (whole) {
+#pragma unroll
+      for (int u = 0; u < TCP; u += 2)
+        *reinterpret_cast<ulonglong2*>(Wr + (size_t)r * a.ws + 2 * u) = make_ulonglong2(acc[r][u], acc[r][u + 1]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < TCP; ++u) {
+        const unsigned long long x = acc[r][u];
+        if (col + 2 * u < a.w) Wr[(size_t)r * a.ws + 2 * u] = __uint_as_float((unsigned)(x & 0xffffffffull));
+        if (col + 2 * u + 1 < a.w) Wr[(size_t)r * a.ws + 2 * u + 1] = __uint_as_float((unsigned)(x >> 32));
+      }
+    }
+  }
+}
+
+// Hd[p][k][r] = {H_p[r][k], H_p[r][k]} in FP32 (round to nearest) for r, k < b, zero for the pad
+// row r = b of an odd b.  LO: block p is the diagonal block of row p, and the value the low FP32
+// part fl32(h - fl32(h)) (zero for a row without a diagonal block).
+template <bool LO>
+__global__ void k_hdup(int64_t nblocks, int32_t b, int32_t BA, const double* __restrict__ H,
+                       const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                       unsigned long long* __restrict__ Hd) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)b * BA;
+  if (e >= nblocks * per) return;
+  const int64_t p = e / per;
+  const int32_t rem = (int32_t)(e - p * per), k = rem / BA, r = rem - k * BA;
+  float v = 0.0f;
+  if (r < b) {
+    int64_t src = p;
+    if (LO) {
+      int32_t q = row_ptr[p];
+      while (q < row_ptr[p + 1] && col_idx[q] != (int32_t)p) ++q;
+      src = q < row_ptr[p + 1] ? q : -1;
+    }
+    if (src >= 0) {
+      const double h = H[(size_t)src * b * b + (size_t)r * b + k];
+      v = LO ? (float)(h - (double)(float)h) : (float)h;
+    }
+  }
+  const unsigned long long u = __float_as_uint(v);
+  Hd[e] = u | (u << 32);
+}
+
+template <int B, int TCP, int NW, int MINB>
+css_status launch_dup(css_ctx* ctx, const LzArgs& a, const float* V, float* W, int* err, cudaStream_t st) {
+  using C = SdCfg<B, TCP, NW>;
+  auto kern = k_spmm_dup<B, TCP, NW, MINB>;
+  static_assert(C::smem <= 48 * 1024, "static shared-memory limit");
+  SdArgs s;
+  s.row_ptr = a.row_ptr;
+  s.col_idx = a.col_idx;
+  s.Hd = (const unsigned long long*)a.Hdup;
+  s.Hlod = (const unsigned long long*)a.Hlo_dup;
+  s.V = V;
+  s.W = W;
+  s.ws = a.ws;
+  s.w = a.w;
+  s.jbase = a.row0;
+  s.empty_extra = ctx->test_spmm_empty_extra;
+  s.err = err;
+  const dim3 grid((unsigned)a.n_brow, (unsigned)css_ceil_div(a.w, C::CT));
+  kern<<<grid, C::NT, C::smem, st>>>(s);
+  CSS_LAUNCHED(ctx);
+  return CSS_OK;
+}
+
+}  // namespace
+
+bool css_spmm_dup_supported(bool fp32, int32_t b) { return fp32 && (b == 6 || b == 23); }
+
+int css_spmm_dup_variants() { return 4; }
+
+css_status css_spmm_dup_prepare(css_ctx* ctx, int32_t b, int32_t n_brow, int32_t nnzb, const int32_t* row_ptr,
+                                const int32_t* col_idx, const double* H, const void** Hd, const void** Hlod,
+                                cudaStream_t st) {
+  if (!css_spmm_dup_supported(true, b)) return css_set_arg_error(ctx, "H*V: no exact-width kernel for this b");
+  const int32_t BA = b + (b & 1);
+  const int64_t per = (int64_t)b * BA;
+  unsigned long long *h, *l;
+  CSS_TRY(css_ws(ctx, "h_dup", (size_t)std::max<int64_t>(nnzb, 1) * per * 8, (void**)&h));
+  CSS_TRY(css_ws(ctx, "h_lodup", (size_t)std::max<int32_t>(n_brow, 1) * per * 8, (void**)&l));
+  constexpr int T = 256;
+  if (nnzb > 0) {
+    k_hdup<false><<<(unsigned)css_ceil_div((int64_t)nnzb * per, T), T, 0, st>>>(nnzb, b, BA, H, row_ptr, col_idx, h);
+    CSS_LAUNCHED(ctx);
+  }
+  if (n_brow > 0) {
+    k_hdup<true><<<(unsigned)css_ceil_div((int64_t)n_brow * per, T), T, 0, st>>>(n_brow, b, BA, H, row_ptr, col_idx,
+                                                                                 l);
+    CSS_LAUNCHED(ctx);
+  }
+  int* err;  // the time-out flag starts clear for this call
+  CSS_TRY(css_ws(ctx, "dup_err", 256, (void**)&err));
+  CSS_CU(ctx, cudaMemsetAsync(err, 0, sizeof(int), st));
+  *Hd = h;
+  *Hlod = l;
+  return CSS_OK;
+}
+
+// launch variants (columns per thread, warps per CTA, CTAs per SM the registers are sized for);
+// every variant sums each output in the same order
+css_status css_spmm_dup(css_ctx* ctx, const LzArgs& a, const float* V, float* W, int v, cudaStream_t st) {
+  if (a.n_brow == 0 || a.w == 0) return CSS_OK;
+  if (((uintptr_t)V & 15) || ((uintptr_t)W & 15) || (a.ws & 7))
+    return css_set_arg_error(ctx, "H*V: V and W must be 16-byte aligned with a row stride of 8 floats");
+  int* err;
+  CSS_TRY(css_ws(ctx, "dup_err", 256, (void**)&err));
+  if (a.b == 23) {
+    switch (v) {
+      case 0: return launch_dup<23, 2, 4, 3>(ctx, a, V, W, err, st);
+      case 1: return launch_dup<23, 2, 2, 6>(ctx, a, V, W, err, st);
+      case 2: return launch_dup<23, 2, 4, 2>(ctx, a, V, W, err, st);
+      default: return launch_dup<23, 2, 8, 1>(ctx, a, V, W, err, st);
+    }
+  }
+  if (a.b == 6) {
+    switch (v) {
+      case 0: return launch_dup<6, 2, 2, 8>(ctx, a, V, W, err, st);
+      case 1: return launch_dup<6, 2, 4, 4>(ctx, a, V, W, err, st);
+      case 2: return launch_dup<6, 2, 8, 2>(ctx, a, V, W, err, st);
+      default: return launch_dup<6, 2, 1, 16>(ctx, a, V, W, err, st);
+    }
+  }
+  return css_set_arg_error(ctx, "H*V: no exact-width kernel for this b");
+}
+
+// CSS_ERR_TIMEOUT when a wait of the exact-width H * V ran out since the last check (the flag is
+// cleared); synchronises the stream
+css_status css_spmm_dup_check(css_ctx* ctx, cudaStream_t st) {
+  int* err;
+  CSS_TRY(css_ws(ctx, "dup_err", 256, (void**)&err));
+  int* h;
+  CSS_TRY(css_pinned(ctx, 64, (void**)&h));
+  CSS_CU(ctx, cudaMemcpyAsync(h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CSS_CU(ctx, cudaMemsetAsync(err, 0, sizeof(int), st));
+  CSS_CU(ctx, cudaStreamSynchronize(st));
+  if (*h) {
+    ctx->last_error = "H*V: a bounded wait on the shared-memory ring of H blocks timed out";
+    return CSS_ERR_TIMEOUT;
+  }
+  return CSS_OK;
+}

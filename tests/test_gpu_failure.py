@@ -6,6 +6,10 @@ device-side input checks return a status, and the context and the device stay us
   has (a flag that nothing sets).  The wait must run out after its bounded number of polls and the
   call must return CSS_ERR_TIMEOUT; a context created afterwards without the variable must still
   give the oracle's density matrix.
+* A ring of H blocks whose "empty" barriers can never complete: with CSS_TEST_SPMM_EMPTY_EXTRA=1
+  at css_create, the exact-width FP32 H*V's barriers wait for one warp more than a CTA has; the
+  copying thread's bounded wait must run out, the CTAs drain their copies, write zeros and return,
+  and the call must return CSS_ERR_TIMEOUT with the device still usable.
 * A malformed explicit graph (a neighbour outside [0, n), a decreasing adj_ptr) must be refused
   with CSS_ERR_INVALID_ARG before any Jones-Plassmann round reads through it.
 """
@@ -68,6 +72,30 @@ def test_mu_barrier_timeout_returns_a_status_and_the_device_stays_usable(torch, 
     ref = oracle.density(H, col, sign, nc, kT=0.05, n_elec=ne, m=8)
     assert float(np.abs(P.cpu().numpy() - ref["P"]).max()) < 1e-10
     assert abs(r["trP"] - ref["trP"]) < 1e-9
+
+
+def test_hv_ring_timeout_returns_a_status_and_the_device_stays_usable(torch, css):
+    g, H, col, nc, sign = _system(torch)
+    ne = synth.n_electrons(g.n_mol)
+    os.environ["CSS_TEST_SPMM_EMPTY_EXTRA"] = "1"
+    try:
+        bad = css.Context(0)
+    finally:
+        del os.environ["CSS_TEST_SPMM_EMPTY_EXTRA"]
+    Hd = css.DeviceBSR.from_host(H)
+    dcol = torch.as_tensor(col, device="cuda")
+    dsign = torch.as_tensor(sign, device="cuda")
+    P = torch.empty((H.nnzb, H.b, H.b), dtype=torch.float64, device="cuda")
+    with pytest.raises(css.CSSError) as ei:
+        bad.density(Hd, dcol, dsign, nc, P, kT=0.05, n_elec=ne, m=8, precision=css.CSS_MIXED_FP32)
+    assert ei.value.status == css.CSS_ERR_TIMEOUT
+    bad.close()
+    torch.cuda.synchronize()  # no sticky CUDA error
+    with css.Context(0) as ctx:
+        ctx.density(Hd, dcol, dsign, nc, P, kT=0.05, n_elec=ne, m=8, precision=css.CSS_MIXED_FP32)
+        torch.cuda.synchronize()
+    ref = oracle.density(H, col, sign, nc, kT=0.05, n_elec=ne, m=8)
+    assert float(np.abs(P.cpu().numpy() - ref["P"]).max()) < 1e-6
 
 
 def test_malformed_graph_is_refused_before_the_rounds(torch, css):

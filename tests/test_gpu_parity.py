@@ -236,6 +236,81 @@ def test_alternative_fp32_kernels_match_oracle(torch, css, n, r_col, m, solve, e
     assert float(np.abs(two["P"] - ref["P"]).max()) < MIXED_P_TOL
 
 
+@pytest.mark.parametrize("n,kind,r_col,m", [(125, "dzp", 10.0, 12), (343, "minimal", 8.0, 12), (27, "dzp", 6.0, 6)])
+def test_exact_width_hv_equals_the_padded_kernel_bitwise(torch, css, n, kind, r_col, m):
+    """FP32 H*V for b = 6 and b = 23 runs by default in the exact-width kernel (packed FMAs over
+    column pairs, no padded rows or columns); the padded kernel (CSS_SPMM_VARIANT=0 at css_create)
+    forms every output from the same IEEE FMAs in the same order, so the mixed P must be bitwise
+    the same, for every launch variant of the exact-width kernel (CSS_SPMM_DUP_VARIANT=0..3) and
+    with the regenerating second pass.  The column counts span several CTA tiles with a ragged
+    last one."""
+    import os
+    g, H, col, s, nc = _system(n, kind, r_col)
+    ne = synth.n_electrons(n)
+    kw = dict(kT=0.05, n_elec=ne, m=m, precision=css.CSS_MIXED_FP32)
+
+    def run(env, flags=css.CSS_SYMMETRIZE):
+        os.environ.update(env)
+        try:
+            c2 = css.Context(0)
+        finally:
+            for k in env:
+                del os.environ[k]
+        try:
+            return gpu_density(torch, css, c2, H, col, s, nc, flags=flags, **kw)
+        finally:
+            c2.close()
+
+    ref = run({"CSS_SPMM_VARIANT": "0"})
+    for v in range(4):
+        got = run({"CSS_SPMM_DUP_VARIANT": str(v)})
+        assert np.array_equal(got["P"], ref["P"]), v
+        assert got["mu"] == ref["mu"] and got["trP"] == ref["trP"], v
+    two_ref = run({"CSS_SPMM_VARIANT": "0"}, css.CSS_SYMMETRIZE | css.CSS_TWO_PASS)
+    two = run({}, css.CSS_SYMMETRIZE | css.CSS_TWO_PASS)
+    assert np.array_equal(two["P"], two_ref["P"])
+
+
+@pytest.mark.parametrize("kind", ["minimal", "dzp"])
+def test_exact_width_hv_in_a_batch_equals_the_padded_kernel_bitwise(torch, css, kind):
+    """The same bitwise equality through css_density_batch, where the systems' Lanczos passes run
+    concurrently on side streams and each system's H*V shape is tuned on its own stream."""
+    import os
+    sizes = [27, 64, 125, 216, 343, 100] if kind == "minimal" else [27, 64, 125]
+    systems = []
+    for i, n_i in enumerate(sizes):
+        gi = synth.water_box(n_i, seed=1101 + i)
+        systems.append((gi, synth.hamiltonian(gi, kind)))
+
+    def run(env):
+        os.environ.update(env)
+        try:
+            c2 = css.Context(0)
+        finally:
+            for k in env:
+                del os.environ[k]
+        try:
+            Hs, cols, signs, ncs, fs = [], [], [], [], []
+            for gi, Hi in systems:
+                col, nc = oracle.color(gi.pos, gi.box, 8.0, 1004)
+                Hs.append(css.DeviceBSR.from_host(Hi))
+                cols.append(torch.as_tensor(col, device="cuda"))
+                signs.append(torch.as_tensor(oracle.probes(col, Hi.b, 1005), device="cuda"))
+                ncs.append(nc)
+                fs.append({"kT": 0.05, "n_elec": synth.n_electrons(gi.n_mol), "solve_mu": True})
+            P = [torch.empty((H.nnzb, H.b, H.b), dtype=torch.float64, device="cuda") for _, H in systems]
+            c2.density_batch(Hs, cols, signs, ncs, P, fs, m=12, precision=css.CSS_MIXED_FP32)
+            torch.cuda.synchronize()
+            return P
+        finally:
+            c2.close()
+
+    ref = run({"CSS_SPMM_VARIANT": "0"})
+    got = run({})
+    for i in range(len(systems)):
+        assert torch.equal(got[i], ref[i]), i
+
+
 # ------------------------------------------- energy-weighted density matrix (forces)
 @pytest.mark.parametrize("n,kind,r_col,m,flags", [(64, "minimal", 8.0, 10, 1), (125, "minimal", 8.0, 12, 0),
                                                   (27, "dzp", 6.0, 6, 1), (64, "minimal", 8.0, 10, 1 | 2)])
