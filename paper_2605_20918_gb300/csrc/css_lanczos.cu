@@ -309,6 +309,48 @@ __device__ __forceinline__ void tile_mul(const RowCtx<T, BP>& c, const T* X, con
   constexpr int CS = ColStride<BP>::CS;
   constexpr int CB = BP / 4;
   const int32_t nblk = (rtl / 4) * c.G * CB;
+  if constexpr (sizeof(T) == 4) {
+    // FP32: the four columns of a row in two packed pairs, fma.rn.f32x2 against the row's x
+    // duplicated into both halves: element by element the same IEEE FMAs in the same order as
+    // the scalar loop below (4-column blocks start on 16-byte boundaries: CS, BP, pitch and MS
+    // are multiples of 4)
+    for (int32_t t = threadIdx.x; t < nblk; t += blockDim.x) {
+      const int32_t rb = t / (c.G * CB), rem = t - rb * c.G * CB, g = rem / CB, cb = rem - g * CB;
+      const int32_t r0 = rb * 4, col = g * CS + cb * 4;
+      unsigned long long acc[4][2];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (SUB) {
+          const ulonglong2 o = *reinterpret_cast<const ulonglong2*>(OUT + (r0 + i) * c.pitch + col);
+          acc[i][0] = o.x;
+          acc[i][1] = o.y;
+        } else {
+          acc[i][0] = acc[i][1] = 0ull;
+        }
+      }
+      auto accumulate = [&](const T* Xs, const T* Ms) {
+        const T* xm = Xs + g * CS;
+        const T* mm = Ms + (size_t)g * ColStride<BP>::MS + cb * 4;
+        for (int32_t l = 0; l < c.b; ++l) {
+          const ulonglong2 m = *reinterpret_cast<const ulonglong2*>(mm + l * BP);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float x = SUB ? -(float)xm[(r0 + i) * c.pitch + l] : (float)xm[(r0 + i) * c.pitch + l];
+            unsigned long long xx;
+            asm("mov.b64 %0, {%1, %1};" : "=l"(xx) : "f"(x));
+            asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[i][0]) : "l"(xx), "l"(m.x));
+            asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc[i][1]) : "l"(xx), "l"(m.y));
+          }
+        }
+      };
+      accumulate(X, M);
+      if (TWO) accumulate(X2, M2);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<ulonglong2*>(OUT + (r0 + i) * c.pitch + col) = make_ulonglong2(acc[i][0], acc[i][1]);
+    }
+    return;
+  }
   for (int32_t t = threadIdx.x; t < nblk; t += blockDim.x) {
     const int32_t rb = t / (c.G * CB), rem = t - rb * c.G * CB, g = rem / CB, cb = rem - g * CB;
     const int32_t r0 = rb * 4, col = g * CS + cb * 4;
@@ -403,16 +445,59 @@ __device__ __forceinline__ bool gram_block(int32_t t, int32_t G, int32_t& g, int
   return true;
 }
 
+// A symmetric Gram has CB (CB + 1) / 2 blocks per colour, fewer than a CTA's threads: when the
+// CTA has twice as many threads as blocks, two threads share a block, the first summing the
+// first half of every tile's rows and the second the second half (gram_store adds the two sums
+// in FP64, in that order).
+template <int CB, bool SYM>
+__device__ __forceinline__ bool gram_split(int32_t G) {
+  return SYM && (int32_t)blockDim.x >= 2 * G * (CB * (CB + 1) / 2);
+}
+
 // acc[i][j] += sum_r X[r][g][4bi+i] Y[r][g][4bj+j] for this thread's block (g, bi, bj)
 template <typename T, int BP, bool SYM = false>
 __device__ __forceinline__ void tile_gram(const RowCtx<T, BP>& c, const T* X, const T* Y, int32_t rtl,
                                           GramAcc<T>& acc, int32_t t) {
   constexpr int CS = ColStride<BP>::CS;
   constexpr int CB = BP / 4;
+  int32_t r_beg = 0;
+  if (gram_split<CB, SYM>(c.G)) {
+    const int32_t nbt = c.G * (CB * (CB + 1) / 2), half = t / nbt;
+    if (half >= 2) return;
+    t -= half * nbt;
+    rtl /= 2;
+    r_beg = half * rtl;
+  }
   int32_t g, bi, bj;
   if (!gram_block<CB, SYM>(t, c.G, g, bi, bj)) return;
+  X += r_beg * c.pitch;
+  Y += r_beg * c.pitch;
   const T* xp = X + g * CS + bi * 4;
   const T* yp = Y + g * CS + bj * 4;
+  if constexpr (sizeof(T) == 4) {
+    // FP32: packed pairs over j, the same IEEE FMAs in the same order as the scalar loop below
+    unsigned long long a2[4][2] = {};
+    for (int32_t r = 0; r < rtl; ++r) {
+      const float4 x = *reinterpret_cast<const float4*>(xp + r * c.pitch);
+      const ulonglong2 y = *reinterpret_cast<const ulonglong2*>(yp + r * c.pitch);
+      const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        unsigned long long xx;
+        asm("mov.b64 %0, {%1, %1};" : "=l"(xx) : "f"(xv[i]));
+        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a2[i][0]) : "l"(xx), "l"(y.x));
+        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a2[i][1]) : "l"(xx), "l"(y.y));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const unsigned long long p = a2[i][j >> 1];
+        acc.add(i * 4 + j, __uint_as_float((unsigned)((j & 1) ? (p >> 32) : (p & 0xffffffffull))));
+      }
+    return;
+  }
   T a[4][4] = {};
   for (int32_t r = 0; r < rtl; ++r) {
     T x[4], y[4];
@@ -432,10 +517,22 @@ __device__ __forceinline__ void tile_gram(const RowCtx<T, BP>& c, const T* X, co
     for (int j = 0; j < 4; ++j) acc.add(i * 4 + j, a[i][j]);
 }
 
+// every thread of the CTA calls this (a split Gram synchronises the CTA once; `scratch`: 16
+// doubles per Gram block of shared memory no longer in use)
 template <typename T, int BP, bool SYM = false>
 __device__ __forceinline__ void gram_store(const RowCtx<T, BP>& c, const GramAcc<T>& acc, double* part,
-                                           int32_t t) {
+                                           int32_t t, double* scratch = nullptr) {
   constexpr int CB = BP / 4;
+  const bool split = gram_split<CB, SYM>(c.G);
+  if (split) {
+    const int32_t nbt = c.G * (CB * (CB + 1) / 2), half = t / nbt;
+    t -= half * nbt;
+    if (half == 1)
+#pragma unroll
+      for (int i = 0; i < 16; ++i) scratch[t * 16 + i] = acc.get(i);
+    __syncthreads();
+    if (half != 0) return;
+  }
   int32_t g, bi, bj;
   if (!gram_block<CB, SYM>(t, c.G, g, bi, bj)) return;
   if (g >= c.gcount) return;
@@ -446,7 +543,7 @@ __device__ __forceinline__ void gram_store(const RowCtx<T, BP>& c, const GramAcc
     for (int j = 0; j < 4; ++j) {
       const int32_t k = bi * 4 + i, l = bj * 4 + j;
       if (k < c.b && l < c.b) {
-        const double v = acc.get(i * 4 + j);
+        const double v = split ? acc.get(i * 4 + j) + scratch[t * 16 + i * 4 + j] : acc.get(i * 4 + j);
         o[k * c.b + l] = v;
         if (SYM && bi != bj) o[l * c.b + k] = v;  // the mirrored block of a symmetric Gram
       }
@@ -585,7 +682,8 @@ __global__ void __launch_bounds__(2 * RW, 1)
         c.store(W, sW, r0, nr);
         tile_gram<T, BP, true>(c, sW, sW, RTL, acc, threadIdx.x);
       });
-  gram_store<T, BP, true>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b, threadIdx.x);
+  gram_store<T, BP, true>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b, threadIdx.x,
+                          reinterpret_cast<double*>(smem_raw));
 }
 
 // OUT = W R^-1 (R^-1 upper triangular per colour); partial Gram of OUT when GRAM.  OUT may be W.
@@ -615,7 +713,9 @@ __global__ void __launch_bounds__(384, 2)
         c.store(OUT, sO, r0, nr);
         if (GRAM) tile_gram<T, BP, true>(c, sO, sO, RTL, acc, threadIdx.x);
       });
-  if (GRAM) gram_store<T, BP, true>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b, threadIdx.x);
+  if (GRAM)
+    gram_store<T, BP, true>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b, threadIdx.x,
+                            reinterpret_cast<double*>(smem_raw));
 }
 
 // out[lc][e] = sum over chunks of part[ch][lc][e], fixed order, FP64
