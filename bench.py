@@ -33,16 +33,16 @@ ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 METRIC = "P build s/step at 10k H2O"
-SPMM_KERNEL_VERSION = "k_spmm_dup-v1"  # profiles/spmm_traffic.json must name the kernel measured
+SPMM_KERNEL_VERSION = "k_spmm_dup-v2"  # profiles/spmm_traffic.json must name the kernel measured
 
 
-def hv_kernel(mixed, b):
+def hv_kernel(mixed, b, tc=False):
     """(name, version tag) of the H*V kernel a build runs: the tensor-core one when asked for, the
     exact-width FP32 kernel for b = 6 and 23, else the padded FFMA/DFMA kernel."""
-    if mixed and os.environ.get("CSS_HV_TC") == "1" and 16 < b <= 24:
+    if mixed and (tc or os.environ.get("CSS_HV_TC") == "1") and 16 < b <= 24:
         return "k_hv_tc (H*V on tcgen05, 3xTF32)", "k_hv_tc"
     if mixed and b in (6, 23) and not os.environ.get("CSS_SPMM_VARIANT"):
-        return ("k_spmm_dup (exact-width H*V on the FP32 FMA pipe, packed column pairs, all colours of the "
+        return ("k_spmm_dup (exact-width H*V on the FP32 FMA pipe, packed row pairs, all colours of the "
                 "system as columns)", SPMM_KERNEL_VERSION)
     return ("k_spmm (padded H*V on the " + ("FP32 FMA" if mixed else "FP64 DFMA") +
             " pipe, all colours of the system as columns)", "k_spmm-padded")
@@ -81,7 +81,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "fp64", "3xtf32"], default="mixed")
     ap.add_argument("--n-mol", type=int, default=10000)
     ap.add_argument("--kind", default="dzp")
     ap.add_argument("--m", type=int, default=40)
@@ -210,7 +210,7 @@ def oracle_sample(H, col, sign, nc, a):
     mu, the extraction and the symmetrisation (a few percent of a build) are not in it."""
     import oracle
     threads = oracle.num_threads()
-    flags = oracle.REORTH_LOCAL if a.precision == "mixed" else 0
+    flags = oracle.REORTH_LOCAL if a.precision != "fp64" else 0
     sub = list(range(min(threads, nc)))
     t0 = time.perf_counter()
     oracle.density(H, col, sign, nc, mu=-4.0, kT=0.05, solve_mu=False, m=SAMPLE_M, flags=flags, colour_subset=sub)
@@ -227,7 +227,7 @@ def oracle_sample(H, col, sign, nc, a):
 
 
 def sample_note(a, parts):
-    reo = ", local reorthogonalisation" if a.precision == "mixed" else ""
+    reo = ", local reorthogonalisation" if a.precision != "fp64" else ""
     return (f"oracle (FP64{reo}) on geometry 0 of the {a.n_mol}-molecule workload, its own schedule (OpenMP over "
             f"colours, one thread per colour): {parts['threads']} colours at Krylov depth {SAMPLE_M} "
             f"({parts['t_lanczos_s']:.2f} s) and one exact diagonalisation of a {a.m * 23 if a.kind == 'dzp' else a.m * 6}"
@@ -240,7 +240,7 @@ def oracle_full_build(H, col, sign, nc, a):
     """Wall time of one complete oracle P build (mu solved), for checking the sample's scaling."""
     import oracle
     from paper_2605_20918_gb300 import synth
-    flags = oracle.SYMMETRIZE | (oracle.REORTH_LOCAL if a.precision == "mixed" else 0)
+    flags = oracle.SYMMETRIZE | (oracle.REORTH_LOCAL if a.precision != "fp64" else 0)
     t0 = time.perf_counter()
     oracle.density(H, col, sign, nc, kT=0.05, n_elec=synth.n_electrons(H.n_brow), m=a.m, flags=flags)
     return time.perf_counter() - t0
@@ -349,7 +349,7 @@ def run_reference(a):
     value = statistics.mean(times)
     cfg = workload_config(a)
     cfg["l2"] = l2_note(H)
-    cfg["precision"] = "fp64 (CPU oracle" + (", local reorthogonalisation as the mixed GPU path)" if a.precision == "mixed"
+    cfg["precision"] = "fp64 (CPU oracle" + (", local reorthogonalisation as the mixed GPU path)" if a.precision != "fp64"
                                              else ")")
     note = (f"one complete oracle P build of the {a.n_mol}-molecule workload per step" if a.oracle_full
             else sample_note(a, parts))
@@ -471,7 +471,8 @@ def main():
     if ws > 1:
         dist.barrier()
     dev = torch.device("cuda", local)
-    prec = css.CSS_MIXED_FP32 if a.precision == "mixed" else css.CSS_FP64
+    prec = {"mixed": css.CSS_MIXED_FP32, "3xtf32": css.CSS_MIXED_3XTF32}.get(a.precision, css.CSS_FP64)
+    mixed = prec != css.CSS_FP64
     from paper_2605_20918_gb300 import shard
     n_steps = a.warmup + a.steps
     my = shard.rank_steps(rank, ws, n_steps)
@@ -529,9 +530,9 @@ def main():
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = fp32_peak_tflops(n_sm, pk["sm_max_mhz"])
     tf32_peak = tf32_peak_tflops(pk)
-    tc = os.environ.get("CSS_HV_TC") == "1" and prec == css.CSS_MIXED_FP32 and 16 < H0.b <= 24
-    hv_name, hv_version = hv_kernel(prec == css.CSS_MIXED_FP32, H0.b)
-    peak = (tf32_peak if tc else fp32_peak) if prec == css.CSS_MIXED_FP32 else FP64_PEAK
+    tc = (os.environ.get("CSS_HV_TC") == "1" or prec == css.CSS_MIXED_3XTF32) and mixed and 16 < H0.b <= 24
+    hv_name, hv_version = hv_kernel(mixed, H0.b, tc)
+    peak = (tf32_peak if tc else fp32_peak) if mixed else FP64_PEAK
     traffic = None
     tf = ROOT / "profiles" / "spmm_traffic.json"
     if tf.exists():
@@ -546,25 +547,25 @@ def main():
     cfg["l2"] = l2_note(H0)
     line = {"metric": METRIC, "value": value, "unit": "s/P-build", "n_gpus": ws,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": elapsed / a.steps * 1e3, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == css.CSS_MIXED_FP32 else "f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64",
             "data": "synthetic", "config": cfg,
             "roofline": {"kernel": hv_name,
-                         "bound": "tensor" if tc else ("alu" if prec == css.CSS_MIXED_FP32 else "alu_fp64"),
+                         "bound": "tensor" if tc else ("alu" if mixed else "alu_fp64"),
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": None if tc else traffic,
                          "peak_source": (f"dense TF32 tensor peak: measured sustained BF16 {pk['bf16_sustained']:.0f} "
                                          f"TF/s x 1.1/2.25 ({pk['source']})" if tc else
                                          f"FP32 FFMA (CUDA-core) ceiling: {n_sm} SMs x 128 lanes x 2 flop x "
-                                         f"{pk['sm_max_mhz']:.0f} MHz" if prec == css.CSS_MIXED_FP32 else FP64_PEAK_NOTE),
-                         "frac_vs_tf32_tensor_peak": achieved / tf32_peak if prec == css.CSS_MIXED_FP32 else None,
+                                         f"{pk['sm_max_mhz']:.0f} MHz" if mixed else FP64_PEAK_NOTE),
+                         "frac_vs_tf32_tensor_peak": achieved / tf32_peak if mixed else None,
                          "launch_ms": spmm_avg, "flops_per_launch": last_inf["spmm_flops"],
                          "alg_bytes_per_launch": last_inf["spmm_bytes"]},
-            "roofline_rows": row_roofline(a, H0, last_nc, rows_avg, prec == css.CSS_MIXED_FP32, pk),
+            "roofline_rows": row_roofline(a, H0, last_nc, rows_avg, mixed, pk),
             "clocks": clk.summary(), "gpu_launches": int(launches),
             "phases_ms": {k: last_inf[k] for k in ("ms_setup", "ms_lanczos", "ms_eigen", "ms_mu", "ms_extract",
                                                    "ms_total")},
             "n_colours": last_nc, "trP": last_r["trP"], "mu": last_r["mu"]}
-    if rank == 0 and not a.no_fp64_compare and prec == css.CSS_MIXED_FP32:
+    if rank == 0 and not a.no_fp64_compare and mixed:
         # mixed against FP64 on the last geometry (the FP64 path matches the oracle to ~1e-13)
         t = my[n_steps - 1] % a.geometries
         xyz, Hd = dev_in[t]

@@ -49,10 +49,15 @@ typedef enum {
 } css_status;
 
 typedef enum {
-  CSS_FP64 = 0,       /* everything in FP64                                               */
-  CSS_MIXED_FP32 = 1  /* H*V, Krylov vectors and block products in FP32 (FP32 accumulate); */
-                      /* recurrence coefficients, Cholesky, eigensolve, mu, Z and P in FP64; */
-                      /* implies CSS_REORTH_LOCAL (it removes an FP32-level bias of Tr P)   */
+  CSS_FP64 = 0,        /* everything in FP64                                               */
+  CSS_MIXED_FP32 = 1,  /* H*V, Krylov vectors and block products in FP32 (FP32 accumulate); */
+                       /* recurrence coefficients, Cholesky, eigensolve, mu, Z and P in FP64; */
+                       /* implies CSS_REORTH_LOCAL (it removes an FP32-level bias of Tr P)   */
+  CSS_MIXED_3XTF32 = 2 /* as CSS_MIXED_FP32, with the H*V of the block-Lanczos recurrence on  */
+                       /* the tensor cores: TF32 products of split operands (x = x1 + x2, the */
+                       /* on-site blocks in three parts) accumulated in FP32, for 17 <= b <= 24 */
+                       /* (other b: CSS_ERR_UNSUPPORTED); the other sparse products of        */
+                       /* css_hprime and css_density_nonorth stay on the FP32 FMA pipe        */
 } css_precision;
 
 /* css_density flags */
@@ -122,6 +127,9 @@ typedef struct {
   int64_t kernel_launches; /* kernels launched by this context since css_create            */
   double ms_rows;          /* row work of one Lanczos step between two H*V launches (three-term
                               update, reorthogonalisation, CholeskyQR3, sampled rows), averaged */
+  int64_t graph_launches;  /* CUDA-graph launches of the block-Lanczos phase since css_create  */
+  int64_t graph_instantiations; /* of those, graphs instantiated anew (the rest were updated in
+                                   place from the previous call's graph of the same mode)     */
 } css_info;
 
 /* ------------------------------------------------------------------ context */

@@ -97,6 +97,8 @@ css_status css_create(css_ctx** out, int device) {
   ctx->hv_tc = tc && tc[0] == '1';
   const char* rs = getenv("CSS_ROWS_STREAM");
   ctx->rows_stream = rs && rs[0] == '1';
+  const char* gr = getenv("CSS_GRAPH");
+  ctx->graph = !(gr && gr[0] == '0');
   *out = ctx;
   return CSS_OK;
 }
@@ -109,6 +111,10 @@ void css_destroy(css_ctx* ctx) {
     if (kv.second.p) cudaFree(kv.second.p);
   for (cudaStream_t s : ctx->side) cudaStreamDestroy(s);
   for (cudaEvent_t e : ctx->side_ev) cudaEventDestroy(e);
+  for (cudaGraphExec_t g : ctx->lz_exec)
+    if (g) cudaGraphExecDestroy(g);
+  for (cudaEvent_t e : ctx->lz_ev) cudaEventDestroy(e);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
   delete ctx;
 }
@@ -134,6 +140,8 @@ css_status css_get_info(const css_ctx* ctx, css_info* info) {
   *info = ctx->info;
   info->workspace_bytes = ctx->ws_bytes;
   info->kernel_launches = ctx->kernel_launches;
+  info->graph_launches = ctx->graph_launches;
+  info->graph_instantiations = ctx->graph_instantiations;
   return CSS_OK;
 }
 

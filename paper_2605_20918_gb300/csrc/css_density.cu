@@ -628,7 +628,8 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
                             void* yfull, int32_t ldy, bool partial, const int32_t* colour_ids) {
   // ------------------------------------------------------------ validation
   if (n_sys < 1 || n_sys > MU_MAXSYS) return css_set_arg_error(ctx, "css_density: n_sys out of range");
-  if (prec != CSS_FP64 && prec != CSS_MIXED_FP32) return css_set_arg_error(ctx, "css_density: unknown precision");
+  if (prec != CSS_FP64 && prec != CSS_MIXED_FP32 && prec != CSS_MIXED_3XTF32)
+    return css_set_arg_error(ctx, "css_density: unknown precision");
   if (flags & ~(CSS_SYMMETRIZE | CSS_TWO_PASS | CSS_REORTH_LOCAL | CSS_ENERGY_WEIGHTED | CSS_INV_SQRT | CSS_RITZ_ONLY))
     return css_set_arg_error(ctx, "css_density: unknown flag");
   if (partial && (n_sys != 1 || (flags & CSS_SYMMETRIZE)))
@@ -659,7 +660,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   const int32_t n_brow = (int32_t)nb_tot, nnzb = (int32_t)nnz_tot, n_col = (int32_t)nc_tot;
   const int64_t N = (int64_t)n_brow * b;
   const int32_t bb = b * b, nmax = m * b;
-  const bool f32 = prec == CSS_MIXED_FP32;
+  const bool f32 = prec != CSS_FP64;
   const bool two_pass = (flags & CSS_TWO_PASS) != 0 || yfull != nullptr;
   const bool ritz_only = (flags & CSS_RITZ_ONLY) != 0;  // stop after the exact diagonalisation
   const int T = 256;
@@ -795,7 +796,11 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   const void* Hd3 = nullptr;
   const void* Hdup = nullptr;
   const void* Hlodup = nullptr;
-  const bool use_tc = ctx->hv_tc && css_hv_tc_supported(f32, b, max_row);
+  const bool use_tc = (prec == CSS_MIXED_3XTF32 || ctx->hv_tc) && css_hv_tc_supported(f32, b, max_row);
+  if (prec == CSS_MIXED_3XTF32 && !use_tc) {
+    ctx->last_error = "css_density: CSS_MIXED_3XTF32 needs 17 <= b <= 24 (and rows of at most 128 blocks)";
+    return CSS_ERR_UNSUPPORTED;
+  }
   // FP32 with b = 6 or 23: the exact-width H * V unless a padded variant is asked for
   const bool use_dup = !use_tc && ctx->spmm_variant < 0 && css_spmm_dup_supported(f32, b);
   if (use_tc)
@@ -916,15 +921,14 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   la.pair_I = pair_I;
   la.pair_c = pair_c;
   la.pair_off_h = pair_off_h.data();
-  css_events evs;
+  // timing: two events per step of every pass of the one-stream path, read after the phase
+  int32_t n_pass = 0;
+  for (int32_t s = 0; s < n_sys; ++s) n_pass += (int32_t)css_ceil_div(col_off[s + 1] - col_off[s], ncb);
   int64_t n_spmm = 0;
-  if (ctx->timing) {
-    CSS_CU(ctx, evs.create(2 * (size_t)m));
-  }
   double spmm_ms = 0.0, rows_ms = 0.0;
   int64_t n_rows = 0;
   const int32_t BMh = css_spmm_bm(b);
-  const size_t dup_row = (size_t)b * (b + (b & 1)) * 8;  // bytes of one row's low-part block (exact width)
+  const size_t dup_row = (size_t)b * (b + (b & 1)) * 4;  // bytes of one row's low-part block (exact width)
   // A batch of systems runs its per-system passes concurrently on up to kSide side streams, each
   // with its own Krylov workspace (the passes of different systems touch disjoint rows, colours
   // and sampled pairs); the call's stream waits for all of them before the eigen stage.  The
@@ -979,11 +983,15 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   for (int32_t s = 0; s < n_sys; ++s) sys_order[s] = s;
   std::stable_sort(sys_order.begin(), sys_order.end(),
                    [&](int32_t x, int32_t y) { return sys[x].H.n_brow > sys[y].H.n_brow; });
-  auto run_batches = [&](int mode) -> css_status {
+  // tune == true: only choose the H * V launch variant of every pass (tuning new shapes), so that
+  // the passes themselves can then be captured
+  auto run_batches = [&](int mode, bool tune, cudaStream_t s0) -> css_status {
     la.mode = mode;
     if (nside > 0) {
-      CSS_CU(ctx, cudaEventRecord(ctx->side_ev[nside], st));
-      for (int k = 0; k < nside; ++k) CSS_CU(ctx, cudaStreamWaitEvent(ctx->side[k], ctx->side_ev[nside], 0));
+      if (!tune) {
+        CSS_CU(ctx, cudaEventRecord(ctx->side_ev[nside], s0));
+        for (int k = 0; k < nside; ++k) CSS_CU(ctx, cudaStreamWaitEvent(ctx->side[k], ctx->side_ev[nside], 0));
+      }
       css_status rs = CSS_OK;
       for (int32_t i = 0; i < n_sys; ++i) {
         const int32_t s = sys_order[i];
@@ -1006,17 +1014,19 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
           lb.cb0 = cb0;
           lb.ncb = min(ncb, col_off[s + 1] - cb0);
           lb.w = lb.ncb * b;
-          rs = css_lanczos_pass(ctx, lb, ctx->side[k]);
+          rs = tune ? css_lanczos_tune(ctx, lb, s0) : css_lanczos_pass(ctx, lb, ctx->side[k]);
         }
         if (rs != CSS_OK) break;
       }
+      if (tune) return rs;
       // joined on every path, so that no side stream still writes the workspace after return
       for (int k = 0; k < nside; ++k) {
         CSS_CU(ctx, cudaEventRecord(ctx->side_ev[k], ctx->side[k]));
-        CSS_CU(ctx, cudaStreamWaitEvent(st, ctx->side_ev[k], 0));
+        CSS_CU(ctx, cudaStreamWaitEvent(s0, ctx->side_ev[k], 0));
       }
       return rs;
     }
+    int32_t p = 0;
     for (int32_t s = 0; s < n_sys; ++s) {
       la.row0 = row_off[s];
       la.n_brow = sys[s].H.n_brow;
@@ -1025,32 +1035,92 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
       la.sign = sign + (size_t)row_off[s] * b;
       la.Hlo_diag = Hlo ? (const void*)((const char*)Hlo + (size_t)row_off[s] * BMh * BMh * s_vec) : nullptr;
       la.Hlo_dup = Hlodup ? (const void*)((const char*)Hlodup + (size_t)row_off[s] * dup_row) : nullptr;
-      for (int32_t cb0 = col_off[s]; cb0 < col_off[s + 1]; cb0 += ncb) {
+      for (int32_t cb0 = col_off[s]; cb0 < col_off[s + 1]; cb0 += ncb, ++p) {
         la.cb0 = cb0;
         la.ncb = min(ncb, col_off[s + 1] - cb0);
         la.w = la.ncb * b;
-        la.ev_spmm = ctx->timing ? evs.data() : nullptr;
-        CSS_TRY(css_lanczos_pass(ctx, la, st));
-        if (ctx->timing) {
-          CSS_CU(ctx, cudaStreamSynchronize(st));
-          for (int32_t j = 0; j < m; ++j) {
-            float t = 0.f;
-            if (cudaEventElapsedTime(&t, evs[2 * j], evs[2 * j + 1]) == cudaSuccess) {
-              spmm_ms += t;
-              ++n_spmm;
-            }
-            // the row work of step j: from the end of its H * V to the start of the next one
-            if (j + 1 < m && cudaEventElapsedTime(&t, evs[2 * j + 1], evs[2 * j + 2]) == cudaSuccess) {
-              rows_ms += t;
-              ++n_rows;
-            }
-          }
-        }
+        la.ev_spmm = (ctx->timing && !tune) ? ctx->lz_ev.data() + (size_t)p * 2 * m : nullptr;
+        CSS_TRY(tune ? css_lanczos_tune(ctx, la, s0) : css_lanczos_pass(ctx, la, s0));
       }
     }
     return CSS_OK;
   };
-  CSS_TRY(run_batches((two_pass || ritz_only) ? 0 : 1));
+  // H * V times and the row work between them, from the events of the one-stream path
+  auto read_timing = [&]() -> css_status {
+    if (!ctx->timing || nside > 0) return CSS_OK;
+    CSS_CU(ctx, cudaStreamSynchronize(st));
+    for (int32_t p = 0; p < n_pass; ++p) {
+      const cudaEvent_t* e = ctx->lz_ev.data() + (size_t)p * 2 * m;
+      for (int32_t j = 0; j < m; ++j) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, e[2 * j], e[2 * j + 1]) == cudaSuccess) {
+          spmm_ms += t;
+          ++n_spmm;
+        }
+        // the row work of step j: from the end of its H * V to the start of the next one
+        if (j + 1 < m && cudaEventElapsedTime(&t, e[2 * j + 1], e[2 * j + 2]) == cudaSuccess) {
+          rows_ms += t;
+          ++n_rows;
+        }
+      }
+    }
+    cudaGetLastError();  // steps a breakdown skipped leave unrecorded events
+    return CSS_OK;
+  };
+  // The block-Lanczos phase: every pass of every system (on the side streams of a batch) is
+  // captured on the context's capture stream into one CUDA graph, which replaces the previous
+  // call's graph of the same mode in place when the launch sequence has the same shape (else it is
+  // instantiated anew), and launched at once on the call's stream.  Not when the caller's stream
+  // is itself being captured: the kernels then go into the caller's graph one by one.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CSS_CU(ctx, cudaStreamIsCapturing(st, &cap));
+  const bool use_graph = ctx->graph && cap == cudaStreamCaptureStatusNone;
+  if (use_graph && !ctx->cap_stream) CSS_CU(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  auto run_lanczos = [&](int mode) -> css_status {
+    while (ctx->timing && nside == 0 && ctx->lz_ev.size() < 2 * (size_t)m * n_pass) {
+      cudaEvent_t e = nullptr;
+      CSS_CU(ctx, cudaEventCreate(&e));
+      ctx->lz_ev.push_back(e);
+    }
+    if (!use_graph) {
+      CSS_TRY(run_batches(mode, false, st));
+      return read_timing();
+    }
+    CSS_TRY(run_batches(mode, true, st));
+    CSS_CU(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
+    const css_status rs = run_batches(mode, false, ctx->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (rs != CSS_OK || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      if (rs != CSS_OK) return rs;
+      return css_set_cuda_error(ctx, ce, "cudaStreamEndCapture (block-Lanczos graph)", __FILE__, __LINE__);
+    }
+    cudaGraphExec_t& ex = ctx->lz_exec[mode];
+    if (ex) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(ex, g, &info) == cudaSuccess) {
+        ++ctx->graph_updates;
+      } else {
+        cudaGetLastError();
+        cudaGraphExecDestroy(ex);
+        ex = nullptr;
+      }
+    }
+    cudaError_t ie = cudaSuccess;
+    if (!ex) {
+      ie = cudaGraphInstantiate(&ex, g, 0);
+      if (ie == cudaSuccess) ++ctx->graph_instantiations;
+      else ex = nullptr;
+    }
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return css_set_cuda_error(ctx, ie, "cudaGraphInstantiate (block-Lanczos graph)", __FILE__, __LINE__);
+    CSS_CU(ctx, cudaGraphLaunch(ex, st));
+    ++ctx->graph_launches;
+    return read_timing();
+  };
+  CSS_TRY(run_lanczos((two_pass || ritz_only) ? 0 : 1));
   tm.mark();  // 2
 
   // ---------------------------------------------------------- eigen + mu + Z
@@ -1151,7 +1221,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     CSS_CU(ctx, cudaMemsetAsync(done, 0, n_col * sizeof(int32_t), st));
     k_inv_sqrt<<<(unsigned)css_ceil_div(n_col, T), T, 0, st>>>(n_col, cnt, isq, nblk, done, m);
     CSS_LAUNCHED(ctx);
-    CSS_TRY(run_batches(2));
+    CSS_TRY(run_lanczos(2));
   } else {
     float *zh = nullptr, *zl = nullptr;
     if (f32) {
@@ -1661,7 +1731,7 @@ css_status css_hprime(css_ctx* ctx, const css_bsr* S, const css_bsr* H, const in
   if (n_colours < 1) return css_set_arg_error(ctx, "css_hprime: n_colours < 1");
   CSS_CU(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
-  const bool f32 = prec == CSS_MIXED_FP32;
+  const bool f32 = prec != CSS_FP64;
   const int32_t b = S->b, n_brow = S->n_brow;
   const int64_t N = (int64_t)n_brow * b;
   const int32_t w = n_colours * b;
@@ -1739,7 +1809,8 @@ css_status css_density_nonorth(css_ctx* ctx, const css_bsr* S, const double* Sin
     return css_set_arg_error(ctx, "css_density_nonorth: S or H' without pattern or values");
   if (S->n_brow != Hp->n_brow || S->b != Hp->b || S->n_brow < 1 || S->nnzb < S->n_brow || Hp->nnzb < Hp->n_brow)
     return css_set_arg_error(ctx, "css_density_nonorth: S and H' need the same n_brow and b and a diagonal");
-  if (prec != CSS_FP64 && prec != CSS_MIXED_FP32) return css_set_arg_error(ctx, "css_density_nonorth: unknown precision");
+  if (prec != CSS_FP64 && prec != CSS_MIXED_FP32 && prec != CSS_MIXED_3XTF32)
+    return css_set_arg_error(ctx, "css_density_nonorth: unknown precision");
   if (flags & ~(CSS_SYMMETRIZE | CSS_REORTH_LOCAL)) return css_set_arg_error(ctx, "css_density_nonorth: unknown flag");
   const int32_t b = Hp->b;
   if (b < 1) return css_set_arg_error(ctx, "css_density_nonorth: b < 1");
@@ -1756,7 +1827,7 @@ css_status css_density_nonorth(css_ctx* ctx, const css_bsr* S, const double* Sin
     return css_set_arg_error(ctx, "css_density_nonorth: problem too large");
   CSS_CU(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
-  const bool f32 = prec == CSS_MIXED_FP32;
+  const bool f32 = prec != CSS_FP64;
   const int32_t n_brow = Hp->n_brow, nc = n_colours, bb = b * b, nmax = m * b;
   const int64_t N = (int64_t)n_brow * b;
   const size_t s_vec = f32 ? 4 : 8;

@@ -81,6 +81,17 @@ struct css_ctx {
   // of a batch run concurrently; created on first use, destroyed with the context
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> side_ev;
+  // the block-Lanczos phase of a css_density call (every system, colour batch and step) is
+  // captured from the stream into one CUDA graph and launched at once; the executable graph of
+  // each pass mode (0 no retention, 1 stored rows, 2 regenerating pass) is kept and updated in
+  // place by the next call's capture (env CSS_GRAPH=0 at css_create: launch the kernels one by one)
+  bool graph = true;
+  cudaStream_t cap_stream = nullptr;  // the stream the phase is captured on
+  cudaGraphExec_t lz_exec[3] = {nullptr, nullptr, nullptr};
+  int64_t graph_launches = 0, graph_instantiations = 0, graph_updates = 0;
+  // CSS_TIMING events of the block-Lanczos phase (two per step and pass), kept across calls so
+  // that a captured graph's event nodes stay the same
+  std::vector<cudaEvent_t> lz_ev;
 };
 
 // CUDA events owned by the holder: destroyed when it goes out of scope, early returns included

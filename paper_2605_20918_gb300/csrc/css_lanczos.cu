@@ -230,10 +230,24 @@ struct ColStride {
   static constexpr int MS = BP * BP + BP;
 };
 
-template <typename T>
+// Tiles, Gram partials and ring depths of the row kernels.  The Gram sums of GRP consecutive rows
+// are taken in the vector precision and then added into the running sum (FP32: the compensated
+// hi + lo pair; FP64: doubles).  The kernels that stage three arrays per tile (k_s1, k_s3) walk
+// tiles of RTL3 rows through NS3 stages, k_tri tiles of RTL1 rows through NS1 stages (row_pipeline:
+// two stages run the barrier-separated schedule, three or more the overlapped one).  The depths
+// are the fastest measured: FP32 with b = 23 (BP = 24) two stages of 32-row tiles, FP32 with
+// b <= 16 three, FP64 three (k_s1, k_s3) and four (k_tri) stages of 16-row tiles.  None of them
+// changes a result: every sum keeps its order.
+template <typename T, int BP>
 struct RowTile {
-  static constexpr int RTL = sizeof(T) == 4 ? 32 : 16;  // rows per tile
+  static constexpr bool f32 = sizeof(T) == 4;
+  static constexpr int GRP = f32 ? 32 : 16;
+  static constexpr int RTL3 = f32 ? 32 : 16;
+  static constexpr int NS3 = f32 && BP >= 24 ? 2 : 3;
+  static constexpr int RTL1 = f32 ? 32 : 16;
+  static constexpr int NS1 = f32 ? (BP >= 24 ? 2 : 3) : 4;
 };
+constexpr size_t kRowSmemMax = 227 * 1024;  // opt-in dynamic shared memory of one CTA
 
 template <int BP>
 __host__ __device__ constexpr int group_cap() {
@@ -241,24 +255,40 @@ __host__ __device__ constexpr int group_cap() {
 }
 
 // colours per CTA for block width b (runtime) padded to BP: at most group_cap (one Gram thread
-// per 4 x 4 block), at most 192 contiguous columns per row, and small enough that two stages of
-// three tiles plus two matrices fit in 216 KB of shared memory (rows x value size is 128 bytes
-// for both precisions; matrices counted at 8 bytes a value)
-template <int BP>
+// per 4 x 4 block), at most 192 contiguous columns per row, and small enough that the NS3-stage
+// ring of three tiles plus two per-colour matrices fits in one CTA's shared memory
+template <typename T, int BP>
 __host__ __device__ inline int colours_per_cta(int b) {
   int g = group_cap<BP>();
   if (g > 192 / b) g = 192 / b;
-  while (g > 1 && 6 * 128 * (g * (BP + 4) + 4) + 2 * g * (BP * BP + BP) * 8 > 216 * 1024) --g;
+  constexpr size_t row_bytes = (size_t)RowTile<T, BP>::RTL3 * sizeof(T);
+  while (g > 1 && (size_t)RowTile<T, BP>::NS3 * 3 * row_bytes * (g * (BP + 4) + 4) +
+                          2 * (size_t)g * (BP * BP + BP) * sizeof(T) >
+                      kRowSmemMax)
+    --g;
   return g < 1 ? 1 : g;
 }
 
-// threads of a row-kernel launch: one per 4 x 4 output block of a tile (every block in one
-// round), at least one per Gram block, rounded up to whole warps
+// A symmetric Gram has CB (CB + 1) / 2 blocks per colour.  Where twice that many threads are
+// no more than max(GRP / 4, CB) CB per colour, two threads share a block, the first summing the
+// first half of every GRP-row group and the second the second half (gram_store adds the two sums
+// in FP64, in that order).
 template <typename T, int BP>
+__host__ __device__ constexpr bool sym_split() {
+  constexpr int CB = BP / 4, a = (RowTile<T, BP>::GRP / 4) * CB, g = CB * CB;
+  return CB * (CB + 1) <= (a > g ? a : g);
+}
+
+// threads of a k_s3 / k_tri launch (tiles of RTL rows): one per 4 x 4 output block of a tile
+// (every block in one round), one per Gram block, two per block of a split symmetric Gram; whole
+// warps
+template <typename T, int BP, int RTL>
 __host__ __device__ inline int row_threads(int b) {
-  const int G = colours_per_cta<BP>(b);
-  const int items = (RowTile<T>::RTL / 4) * G * (BP / 4), gram = G * (BP / 4) * (BP / 4);
-  const int t = items > gram ? items : gram;
+  constexpr int CB = BP / 4;
+  const int G = colours_per_cta<T, BP>(b);
+  const int items = (RTL / 4) * G * CB, gram = G * CB * CB;
+  int t = items > gram ? items : gram;
+  if (sym_split<T, BP>() && G * CB * (CB + 1) > t) t = G * CB * (CB + 1);
   return (t + 31) / 32 * 32;
 }
 
@@ -445,107 +475,162 @@ __device__ __forceinline__ bool gram_block(int32_t t, int32_t G, int32_t& g, int
   return true;
 }
 
-// A symmetric Gram has CB (CB + 1) / 2 blocks per colour, fewer than a CTA's threads: when the
-// CTA has twice as many threads as blocks, two threads share a block, the first summing the
-// first half of every tile's rows and the second the second half (gram_store adds the two sums
-// in FP64, in that order).
-template <int CB, bool SYM>
-__device__ __forceinline__ bool gram_split(int32_t G) {
-  return SYM && (int32_t)blockDim.x >= 2 * G * (CB * (CB + 1) / 2);
+// One thread's Gram block: (g, bi, bj) and, for a split symmetric Gram, its half of every
+// GRP-row group (0 or 1); inactive threads hold none.
+struct GramRole {
+  bool active;
+  int32_t t, g, bi, bj, half;  // t: index of the block among the CTA's Gram blocks
+};
+
+template <typename T, int BP, bool SYM>
+__device__ __forceinline__ GramRole gram_role(int32_t G, int32_t t) {
+  constexpr int CB = BP / 4;
+  GramRole r;
+  r.half = 0;
+  if (SYM && sym_split<T, BP>()) {
+    const int32_t nbt = G * (CB * (CB + 1) / 2);
+    r.half = t / nbt;
+    if (r.half >= 2) {
+      r.active = false;
+      r.t = r.g = r.bi = r.bj = 0;
+      return r;
+    }
+    t -= r.half * nbt;
+  }
+  r.t = t;
+  r.active = gram_block<CB, SYM>(t, G, r.g, r.bi, r.bj);
+  return r;
 }
 
-// acc[i][j] += sum_r X[r][g][4bi+i] Y[r][g][4bj+j] for this thread's block (g, bi, bj)
-template <typename T, int BP, bool SYM = false>
-__device__ __forceinline__ void tile_gram(const RowCtx<T, BP>& c, const T* X, const T* Y, int32_t rtl,
-                                          GramAcc<T>& acc, int32_t t) {
-  constexpr int CS = ColStride<BP>::CS;
-  constexpr int CB = BP / 4;
-  int32_t r_beg = 0;
-  if (gram_split<CB, SYM>(c.G)) {
-    const int32_t nbt = c.G * (CB * (CB + 1) / 2), half = t / nbt;
-    if (half >= 2) return;
-    t -= half * nbt;
-    rtl /= 2;
-    r_beg = half * rtl;
+// The running Gram partial of one 4 x 4 block over the rows since its last flush, in the vector
+// precision: FP32 as packed pairs (columns j, j + 1 of row i in one 64-bit register, summed with
+// fma.rn.f32x2: element by element the IEEE FMAs of a scalar loop), FP64 as plain values.
+template <typename T>
+struct GramPart {
+  T a[4][4];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a[i][j] = T(0);
   }
-  int32_t g, bi, bj;
-  if (!gram_block<CB, SYM>(t, c.G, g, bi, bj)) return;
-  X += r_beg * c.pitch;
-  Y += r_beg * c.pitch;
-  const T* xp = X + g * CS + bi * 4;
-  const T* yp = Y + g * CS + bj * 4;
-  if constexpr (sizeof(T) == 4) {
-    // FP32: packed pairs over j, the same IEEE FMAs in the same order as the scalar loop below
-    unsigned long long a2[4][2] = {};
-    for (int32_t r = 0; r < rtl; ++r) {
-      const float4 x = *reinterpret_cast<const float4*>(xp + r * c.pitch);
-      const ulonglong2 y = *reinterpret_cast<const ulonglong2*>(yp + r * c.pitch);
-      const float xv[4] = {x.x, x.y, x.z, x.w};
+  // a[i][j] += sum over n rows of x[r][i] y[r][j] (x, y: the block's first column, row stride p)
+  __device__ __forceinline__ void rows(const T* x, const T* y, int32_t p, int32_t n) {
+    for (int32_t r = 0; r < n; ++r) {
+      T xv[4], yv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        xv[i] = x[r * p + i];
+        yv[i] = y[r * p + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[i][j] = fma(xv[i], yv[j], a[i][j]);
+    }
+  }
+  __device__ __forceinline__ void flush(GramAcc<T>& acc) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc.add(i * 4 + j, a[i][j]);
+    zero();
+  }
+};
+template <>
+struct GramPart<float> {
+  unsigned long long a2[4][2];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a2[i][0] = a2[i][1] = 0ull;
+  }
+  __device__ __forceinline__ void rows(const float* x, const float* y, int32_t p, int32_t n) {
+    for (int32_t r = 0; r < n; ++r) {
+      const float4 xq = *reinterpret_cast<const float4*>(x + r * p);
+      const ulonglong2 yq = *reinterpret_cast<const ulonglong2*>(y + r * p);
+      const float xv[4] = {xq.x, xq.y, xq.z, xq.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         unsigned long long xx;
         asm("mov.b64 %0, {%1, %1};" : "=l"(xx) : "f"(xv[i]));
-        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a2[i][0]) : "l"(xx), "l"(y.x));
-        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a2[i][1]) : "l"(xx), "l"(y.y));
+        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a2[i][0]) : "l"(xx), "l"(yq.x));
+        asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a2[i][1]) : "l"(xx), "l"(yq.y));
       }
     }
+  }
+  __device__ __forceinline__ void flush(GramAcc<float>& acc) {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const unsigned long long p = a2[i][j >> 1];
-        acc.add(i * 4 + j, __uint_as_float((unsigned)((j & 1) ? (p >> 32) : (p & 0xffffffffull))));
+        const unsigned long long q = a2[i][j >> 1];
+        acc.add(i * 4 + j, __uint_as_float((unsigned)((j & 1) ? (q >> 32) : (q & 0xffffffffull))));
       }
-    return;
+    zero();
   }
-  T a[4][4] = {};
-  for (int32_t r = 0; r < rtl; ++r) {
-    T x[4], y[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      x[i] = xp[r * c.pitch + i];
-      y[i] = yp[r * c.pitch + i];
+};
+
+// Gram rows of tile i (0-based within the CTA's chunk; `last`: the chunk's last tile) for this
+// thread's block: part += X^T Y over the tile's rows (its half of them for a split Gram), then
+// into acc at the end of each GRP-row group (of each half-group when split).  Rows past the
+// end of the matrix are zero in the tile and add nothing.
+template <typename T, int BP, bool SYM, int RTL>
+__device__ __forceinline__ void gram_tile(const RowCtx<T, BP>& c, const GramRole& role, const T* X, const T* Y,
+                                          int32_t i, bool last, GramPart<T>& part, GramAcc<T>& acc) {
+  constexpr int CS = ColStride<BP>::CS;
+  constexpr int GRP = RowTile<T, BP>::GRP, SEG = GRP / 2;
+  static_assert(GRP % RTL == 0 && (RTL <= SEG || RTL == GRP), "tiles must tile the Gram groups");
+  if (!role.active) return;
+  const int32_t pos = (i * RTL) % GRP;  // offset of the tile in its GRP-row group
+  int32_t lo = 0, n = RTL;
+  bool flush = pos + RTL == GRP || last;
+  if (SYM && sym_split<T, BP>()) {
+    if constexpr (RTL <= SEG) {  // the tile lies in one half of its group
+      if (pos / SEG != role.half) return;
+      flush = (pos + RTL) % SEG == 0 || last;
+    } else {  // the thread's half of the tile
+      lo = role.half * SEG;
+      n = SEG;
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) a[i][j] = fma(x[i], y[j], a[i][j]);
   }
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc.add(i * 4 + j, a[i][j]);
+  const T* xp = X + lo * c.pitch + role.g * CS + role.bi * 4;
+  const T* yp = Y + lo * c.pitch + role.g * CS + role.bj * 4;
+  if constexpr (RTL == GRP) {  // every tile closes its group: the partial lives in this call only
+    GramPart<T> local;
+    local.zero();
+    local.rows(xp, yp, c.pitch, n);
+    local.flush(acc);
+  } else {
+    part.rows(xp, yp, c.pitch, n);
+    if (flush) part.flush(acc);
+  }
 }
 
 // every thread of the CTA calls this (a split Gram synchronises the CTA once; `scratch`: 16
 // doubles per Gram block of shared memory no longer in use)
 template <typename T, int BP, bool SYM = false>
-__device__ __forceinline__ void gram_store(const RowCtx<T, BP>& c, const GramAcc<T>& acc, double* part,
-                                           int32_t t, double* scratch = nullptr) {
-  constexpr int CB = BP / 4;
-  const bool split = gram_split<CB, SYM>(c.G);
+__device__ __forceinline__ void gram_store(const RowCtx<T, BP>& c, const GramRole& role, const GramAcc<T>& acc,
+                                           double* part, double* scratch = nullptr) {
+  constexpr bool split = SYM && sym_split<T, BP>();
+  const int32_t t = role.t;
   if (split) {
-    const int32_t nbt = c.G * (CB * (CB + 1) / 2), half = t / nbt;
-    t -= half * nbt;
-    if (half == 1)
+    if (role.active && role.half == 1)
 #pragma unroll
       for (int i = 0; i < 16; ++i) scratch[t * 16 + i] = acc.get(i);
     __syncthreads();
-    if (half != 0) return;
+    if (role.half != 0) return;
   }
-  int32_t g, bi, bj;
-  if (!gram_block<CB, SYM>(t, c.G, g, bi, bj)) return;
-  if (g >= c.gcount) return;
-  double* o = part + (size_t)(c.cg0 + g) * c.b * c.b;
+  if (!role.active || role.g >= c.gcount) return;
+  double* o = part + (size_t)(c.cg0 + role.g) * c.b * c.b;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int32_t k = bi * 4 + i, l = bj * 4 + j;
+      const int32_t k = role.bi * 4 + i, l = role.bj * 4 + j;
       if (k < c.b && l < c.b) {
         const double v = split ? acc.get(i * 4 + j) + scratch[t * 16 + i * 4 + j] : acc.get(i * 4 + j);
         o[k * c.b + l] = v;
-        if (SYM && bi != bj) o[l * c.b + k] = v;  // the mirrored block of a symmetric Gram
+        if (SYM && role.bi != role.bj) o[l * c.b + k] = v;  // the mirrored block of a symmetric Gram
       }
     }
 }
@@ -556,7 +641,7 @@ __device__ __forceinline__ RowCtx<T, BP> make_ctx(int32_t b, int32_t ws, int32_t
   RowCtx<T, BP> c;
   c.b = b;
   c.ws = ws;
-  c.G = colours_per_cta<BP>(b);
+  c.G = colours_per_cta<T, BP>(b);
   c.cg0 = blockIdx.y * c.G;
   c.gcount = min(c.G, ncb - c.cg0);
   c.pitch = c.G * CS + 4;
@@ -571,10 +656,9 @@ __device__ __forceinline__ RowCtx<T, BP> make_ctx(int32_t b, int32_t ws, int32_t
   return c;
 }
 
-// The row kernels below walk their chunk of RCHK rows in tiles of RTL rows through a
-// two-stage shared-memory ring: the cp.async copies of tile i+1 are in flight while tile i is
-// processed.  Padding columns of a stage are zeroed once and never written by a copy; rows past
-// the end of the matrix are zero-filled by the copies themselves.
+// The row kernels below walk their chunk of RCHK rows in tiles of RTL rows through an NS-stage
+// shared-memory ring filled by cp.async.  Padding columns of a stage are zeroed once and never
+// written by a copy; rows past the end of the matrix are zero-filled by the copies themselves.
 template <typename T, int BP>
 struct RowRing {
   T* base;
@@ -582,28 +666,64 @@ struct RowRing {
   __device__ __forceinline__ T* at(int s, int a) const { return base + ((size_t)s * na + a) * tile; }
 };
 
-// tiles of this CTA's row chunk: fn_issue(stage, r0, nr) issues and commits the copies of one
-// tile, fn_tile(stage, r0, nr) consumes it (with its own barriers where it needs them)
-template <typename Issue, typename Body>
-__device__ __forceinline__ void row_pipeline(int64_t N, int32_t rtl, Issue fn_issue, Body fn_tile) {
+// Tiles of this CTA's chunk.  fn_issue(stage, tile, r0, nr) issues (does not commit) the copies
+// of a tile, fn_mul(stage, tile, r0, nr) is its first phase (a block product in place in its
+// stage), fn_fin(stage, tile, r0, nr, last) its second (stores and Gram sums of that product).
+// Two stages: the barrier-separated schedule, per tile wait, barrier, first phase, barrier, second
+// phase, with the next tile's copies in flight.  NS >= 3 stages: one barrier per tile; the copies
+// run NS - 2 tiles ahead, and in the iteration of tile i the CTA works on two tiles at once, the
+// first phase of tile i + 1 and the second phase of tile i (different stages, so no barrier
+// separates them).
+template <int NS, typename Issue, typename Mul, typename Fin>
+__device__ __forceinline__ void row_pipeline(int64_t N, int32_t rtl, Issue fn_issue, Mul fn_mul, Fin fn_fin) {
+  static_assert(NS >= 2, "the ring needs a stage in flight besides the one being worked on");
   const int64_t rbeg = (int64_t)blockIdx.x * RCHK, rend = min(N, rbeg + RCHK);
   if (rbeg >= rend) return;
   const int32_t ntile = (int32_t)((rend - rbeg + rtl - 1) / rtl);
-  fn_issue(0, rbeg, (int32_t)min((int64_t)rtl, rend - rbeg));
-  for (int32_t it = 0; it < ntile; ++it) {
-    const int s = it & 1;
-    const int64_t r0 = rbeg + (int64_t)it * rtl;
-    const int32_t nr = (int32_t)min((int64_t)rtl, rend - r0);
-    if (it + 1 < ntile) {
-      const int64_t r1 = r0 + rtl;
-      fn_issue(s ^ 1, r1, (int32_t)min((int64_t)rtl, rend - r1));
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
+  auto r0_of = [&](int32_t i) { return rbeg + (int64_t)i * rtl; };
+  auto nr_of = [&](int32_t i) { return (int32_t)min((int64_t)rtl, rend - r0_of(i)); };
+  if constexpr (NS == 2) {
+    fn_issue(0, 0, r0_of(0), nr_of(0));
+    cp_async_commit();
+#pragma unroll 1
+    for (int32_t it = 0; it < ntile; ++it) {
+      const int s = it & 1;
+      if (it + 1 < ntile) {
+        fn_issue(s ^ 1, it + 1, r0_of(it + 1), nr_of(it + 1));
+        cp_async_commit();
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();  // tile it is in shared memory for every thread
+      fn_mul(s, it, r0_of(it), nr_of(it));
+      __syncthreads();
+      fn_fin(s, it, r0_of(it), nr_of(it), it + 1 == ntile);
+      __syncthreads();  // stage s is free for tile it + 2
     }
-    __syncthreads();  // tile it is in shared memory for every thread
-    fn_tile(s, r0, nr);
-    __syncthreads();  // stage s is free for tile it + 2
+    return;
+  } else {
+#pragma unroll 1
+    for (int32_t i = 0; i < NS - 1; ++i) {  // one commit group per tile (empty past the end)
+      if (i < ntile) fn_issue(i, i, r0_of(i), nr_of(i));
+      cp_async_commit();
+    }
+    cp_async_wait<NS - 2>();  // this thread's copies of tile 0
+    __syncthreads();
+    fn_mul(0, 0, r0_of(0), nr_of(0));
+#pragma unroll 1
+    for (int32_t it = 0; it < ntile; ++it) {
+      cp_async_wait<NS - 3>();  // this thread's copies of tile it + 1
+      // every thread's copies of tile it + 1 and products of tile it are done, and tile it - 1
+      // (finished in the previous iteration) has left its stage
+      __syncthreads();
+      const int32_t nx = it + NS - 1;
+      if (nx < ntile) fn_issue(nx % NS, nx, r0_of(nx), nr_of(nx));
+      cp_async_commit();
+      if (it + 1 < ntile) fn_mul((it + 1) % NS, it + 1, r0_of(it + 1), nr_of(it + 1));
+      fn_fin(it % NS, it, r0_of(it), nr_of(it), it + 1 == ntile);
+    }
+    __syncthreads();  // the stages are free (gram_store may reuse them as scratch)
   }
 }
 
@@ -615,39 +735,36 @@ __global__ void __launch_bounds__(REORTH ? 2 * RW : RW, 1)
     k_s1(int64_t N, int32_t b, int32_t ws, int32_t ncb, int32_t cb0, const T* __restrict__ Qp,
          const T* __restrict__ Q, T* __restrict__ W, const double* __restrict__ Bprev, int first,
          double* __restrict__ partKq, double* __restrict__ partKp) {
-  constexpr int RTL = RowTile<T>::RTL;
+  constexpr int RTL = RowTile<T, BP>::RTL3, NS = RowTile<T, BP>::NS3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const RowCtx<T, BP> c = make_ctx<T, BP>(b, ws, ncb);
   const bool usep = REORTH || !first;
   RowRing<T, BP> ring{reinterpret_cast<T*>(smem_raw), RTL * c.pitch, 3};  // Q, Q_{j-1}, W
-  T* sB = ring.at(2, 0);                                                    // [G][BP][BP] B_{j-1}^T
+  T* sB = ring.at(NS, 0);                                                   // [G][BP][BP] B_{j-1}^T
   GramAcc<T> acc;                                   // Kq (first RW threads) or Kp (second RW)
+  GramPart<T> gp;
+  gp.zero();
   const bool second = REORTH && threadIdx.x >= RW;
-  const int32_t tg = threadIdx.x - (second ? RW : 0);  // index of the thread's Gram block
+  const GramRole role = gram_role<T, BP, false>(c.G, threadIdx.x - (second ? RW : 0));
   if (!first) c.load_mat(sB, Bprev, cb0 + c.cg0, true);
-  c.zero(ring.at(0, 0), 6 * RTL);
+  c.zero(ring.at(0, 0), 3 * NS * RTL);
   __syncthreads();
-  row_pipeline(
+  row_pipeline<NS>(
       N, RTL,
-      [&](int s, int64_t r0, int32_t nr) {
+      [&](int s, int32_t, int64_t r0, int32_t nr) {
         c.template load<RTL>(ring.at(s, 0), Q, r0, nr);
         c.template load<RTL>(ring.at(s, 2), W, r0, nr);
         if (usep) c.template load<RTL>(ring.at(s, 1), Qp, r0, nr);
-        cp_async_commit();
       },
-      [&](int s, int64_t r0, int32_t nr) {
-        T* sQ = ring.at(s, 0);
-        T* sP = ring.at(s, 1);
-        T* sW = ring.at(s, 2);
-        if (!first) {
-          tile_mul<T, BP, true, false>(c, sP, sB, sW, RTL, nullptr, nullptr);
-          __syncthreads();
-          c.store(W, sW, r0, nr);
-        }
-        tile_gram<T, BP>(c, second ? sP : sQ, sW, RTL, acc, tg);
+      [&](int s, int32_t, int64_t, int32_t) {
+        if (!first) tile_mul<T, BP, true, false>(c, ring.at(s, 1), sB, ring.at(s, 2), RTL, nullptr, nullptr);
+      },
+      [&](int s, int32_t i, int64_t r0, int32_t nr, bool last) {
+        if (!first) c.store(W, ring.at(s, 2), r0, nr);
+        gram_tile<T, BP, false, RTL>(c, role, ring.at(s, second ? 1 : 0), ring.at(s, 2), i, last, gp, acc);
       });
   const size_t o = (size_t)blockIdx.x * ncb;
-  gram_store<T, BP>(c, acc, (second ? partKp : partKq) + o * b * b, tg);
+  gram_store<T, BP>(c, role, acc, (second ? partKp : partKq) + o * b * b);
 }
 
 // S3: W1 = W0 - Q_j M1 (- Q_{j-1} M2), stored; partial Gram W1^T W1
@@ -656,69 +773,74 @@ __global__ void __launch_bounds__(2 * RW, 1)
     k_s3(int64_t N, int32_t b, int32_t ws, int32_t ncb, const T* __restrict__ Q, const T* __restrict__ Qp,
          T* __restrict__ W, const double* __restrict__ M1, const double* __restrict__ M2,
          double* __restrict__ partG) {
-  constexpr int RTL = RowTile<T>::RTL;
+  constexpr int RTL = RowTile<T, BP>::RTL3, NS = RowTile<T, BP>::NS3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const RowCtx<T, BP> c = make_ctx<T, BP>(b, ws, ncb);
   RowRing<T, BP> ring{reinterpret_cast<T*>(smem_raw), RTL * c.pitch, 3};  // Q, Q_{j-1}, W
-  T* sM1 = ring.at(2, 0);
+  T* sM1 = ring.at(NS, 0);
   T* sM2 = sM1 + c.G * ColStride<BP>::MS;
   GramAcc<T> acc;
+  GramPart<T> gp;
+  gp.zero();
+  const GramRole role = gram_role<T, BP, true>(c.G, threadIdx.x);
   c.load_mat(sM1, M1, c.cg0, false);
   if (REORTH) c.load_mat(sM2, M2, c.cg0, false);
-  c.zero(ring.at(0, 0), 6 * RTL);
+  c.zero(ring.at(0, 0), 3 * NS * RTL);
   __syncthreads();
-  row_pipeline(
+  row_pipeline<NS>(
       N, RTL,
-      [&](int s, int64_t r0, int32_t nr) {
+      [&](int s, int32_t, int64_t r0, int32_t nr) {
         c.template load<RTL>(ring.at(s, 0), Q, r0, nr);
         c.template load<RTL>(ring.at(s, 2), W, r0, nr);
         if (REORTH) c.template load<RTL>(ring.at(s, 1), Qp, r0, nr);
-        cp_async_commit();
       },
-      [&](int s, int64_t r0, int32_t nr) {
-        T* sW = ring.at(s, 2);
-        tile_mul<T, BP, true, REORTH>(c, ring.at(s, 0), sM1, sW, RTL, ring.at(s, 1), sM2);
-        __syncthreads();
-        c.store(W, sW, r0, nr);
-        tile_gram<T, BP, true>(c, sW, sW, RTL, acc, threadIdx.x);
+      [&](int s, int32_t, int64_t, int32_t) {
+        tile_mul<T, BP, true, REORTH>(c, ring.at(s, 0), sM1, ring.at(s, 2), RTL, ring.at(s, 1), sM2);
+      },
+      [&](int s, int32_t i, int64_t r0, int32_t nr, bool last) {
+        c.store(W, ring.at(s, 2), r0, nr);
+        gram_tile<T, BP, true, RTL>(c, role, ring.at(s, 2), ring.at(s, 2), i, last, gp, acc);
       });
-  gram_store<T, BP, true>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b, threadIdx.x,
+  gram_store<T, BP, true>(c, role, acc, partG + (size_t)blockIdx.x * ncb * b * b,
                           reinterpret_cast<double*>(smem_raw));
 }
 
 // OUT = W R^-1 (R^-1 upper triangular per colour); partial Gram of OUT when GRAM.  OUT may be W.
+// With three or more stages the products of consecutive tiles alternate between two output tiles.
 template <typename T, int BP, bool GRAM>
 __global__ void __launch_bounds__(384, 2)
     k_tri(int64_t N, int32_t b, int32_t ws, int32_t ncb, const T* __restrict__ W, T* __restrict__ OUT,
           const double* __restrict__ Rinv, double* __restrict__ partG) {
-  constexpr int RTL = RowTile<T>::RTL;
+  constexpr int RTL = RowTile<T, BP>::RTL1, NS = RowTile<T, BP>::NS1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const RowCtx<T, BP> c = make_ctx<T, BP>(b, ws, ncb);
+  constexpr int NO = NS == 2 ? 1 : 2;  // output tiles (the overlapped schedule alternates two)
   RowRing<T, BP> ring{reinterpret_cast<T*>(smem_raw), RTL * c.pitch, 1};  // W
-  T* sO = ring.at(2, 0);
-  T* sR = sO + RTL * c.pitch;
+  T* sO = ring.at(NS, 0);
+  T* sR = sO + NO * RTL * c.pitch;
   GramAcc<T> acc;
+  GramPart<T> gp;
+  gp.zero();
+  const GramRole role = gram_role<T, BP, true>(c.G, threadIdx.x);
   c.load_mat(sR, Rinv, c.cg0, false);
-  c.zero(ring.at(0, 0), 3 * RTL);
+  c.zero(ring.at(0, 0), (NS + NO) * RTL);
   __syncthreads();
-  row_pipeline(
+  row_pipeline<NS>(
       N, RTL,
-      [&](int s, int64_t r0, int32_t nr) {
-        c.template load<RTL>(ring.at(s, 0), W, r0, nr);
-        cp_async_commit();
+      [&](int s, int32_t, int64_t r0, int32_t nr) { c.template load<RTL>(ring.at(s, 0), W, r0, nr); },
+      [&](int s, int32_t i, int64_t, int32_t) {
+        tile_mul<T, BP, false, false>(c, ring.at(s, 0), sR, sO + (i & (NO - 1)) * RTL * c.pitch, RTL, nullptr, nullptr);
       },
-      [&](int s, int64_t r0, int32_t nr) {
-        tile_mul<T, BP, false, false>(c, ring.at(s, 0), sR, sO, RTL, nullptr, nullptr);
-        __syncthreads();
-        c.store(OUT, sO, r0, nr);
-        if (GRAM) tile_gram<T, BP, true>(c, sO, sO, RTL, acc, threadIdx.x);
+      [&](int, int32_t i, int64_t r0, int32_t nr, bool last) {
+        const T* o = sO + (i & (NO - 1)) * RTL * c.pitch;
+        c.store(OUT, o, r0, nr);
+        if (GRAM) gram_tile<T, BP, true, RTL>(c, role, o, o, i, last, gp, acc);
       });
   if (GRAM)
-    gram_store<T, BP, true>(c, acc, partG + (size_t)blockIdx.x * ncb * b * b, threadIdx.x,
+    gram_store<T, BP, true>(c, role, acc, partG + (size_t)blockIdx.x * ncb * b * b,
                             reinterpret_cast<double*>(smem_raw));
 }
 
-// out[lc][e] = sum over chunks of part[ch][lc][e], fixed order, FP64
 __global__ void k_reduce(int32_t nch, int32_t ncb, int32_t E, const double* __restrict__ part,
                          double* __restrict__ out) {
   int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1020,11 +1142,13 @@ css_status launch_spmm_v(css_ctx* ctx, const LzArgs& a, const T* V, T* W, int v,
 // W = H V with the variant tuned for this shape: the first time a shape is seen, every variant
 // runs once untimed (first-launch costs) and once timed on the call's own data (each writes the
 // same W), and the fastest is kept.  Shapes: precision, b, columns in buckets of 256, rows.
+// With tune_only the call only makes sure the shape's variant is chosen (tuning it on V and W
+// when it is new) and launches nothing else, so that a later pass can be captured in a graph.
 template <typename T>
-css_status launch_spmm(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaStream_t st) {
+css_status launch_spmm(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaStream_t st, bool tune_only = false) {
   bool dup = false;
   if constexpr (sizeof(T) == 4) {
-    if (a.use_tc) return css_hv_tc(ctx, a, V, W, st);
+    if (a.use_tc) return tune_only ? CSS_OK : css_hv_tc(ctx, a, V, W, st);
     dup = a.Hdup != nullptr;
   }
   // the exact-width kernel (css_spmm.cu) when H was prepared for it, else the padded one
@@ -1036,10 +1160,10 @@ css_status launch_spmm(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaStre
   const int nv = dup ? css_spmm_dup_variants() : kSpmmVariants;
   const uint64_t key = ((uint64_t)sizeof(T) << 60) ^ ((uint64_t)dup << 59) ^ ((uint64_t)a.b << 48) ^
                        ((uint64_t)(a.w / 256) << 24) ^ (uint64_t)(a.n_brow >= (1 << 24) ? (1 << 24) - 1 : a.n_brow);
-  if (!dup && ctx->spmm_variant >= 0) return run(ctx->spmm_variant);
-  if (dup && ctx->spmm_dup_variant >= 0) return run(ctx->spmm_dup_variant);
+  if (!dup && ctx->spmm_variant >= 0) return tune_only ? CSS_OK : run(ctx->spmm_variant);
+  if (dup && ctx->spmm_dup_variant >= 0) return tune_only ? CSS_OK : run(ctx->spmm_dup_variant);
   for (const auto& kv : ctx->spmm_tune)
-    if (kv.first == key) return run(kv.second);
+    if (kv.first == key) return tune_only ? CSS_OK : run(kv.second);
   css_events ev;
   CSS_CU(ctx, ev.create((size_t)nv + 1));
   css_status rc = CSS_OK;
@@ -1072,7 +1196,7 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a_in, cudaStream_t st) {
   const int32_t b = a.b, bb = b * b, ncb = a.ncb, m = a.m;
   const int64_t N = (int64_t)a.n_brow * b;
   const int32_t nch = (int32_t)css_ceil_div(N, RCHK);
-  const int32_t G = colours_per_cta<BP>(b);
+  const int32_t G = colours_per_cta<T, BP>(b);
   const int32_t ngr = (int32_t)css_ceil_div(ncb, G);
   const bool reorth = (a.flags & CSS_REORTH_LOCAL) != 0;
   T* Qp = (T*)a.Q0;
@@ -1080,12 +1204,13 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a_in, cudaStream_t st) {
   T* W = (T*)a.W;
   const size_t vec_bytes = (size_t)N * a.ws * sizeof(T);
   const dim3 rgrid((unsigned)nch, (unsigned)ngr);
-  constexpr int RTL = RowTile<T>::RTL;
-  const size_t tile = (size_t)RTL * (G * (BP + 4) + 4) * sizeof(T);
+  constexpr int RTL3 = RowTile<T, BP>::RTL3, NS3 = RowTile<T, BP>::NS3, RTL1 = RowTile<T, BP>::RTL1, NS1 = RowTile<T, BP>::NS1;
+  const size_t pitch_bytes = (size_t)(G * (BP + 4) + 4) * sizeof(T);
   const size_t mat = (size_t)G * ColStride<BP>::MS * sizeof(T);
-  const size_t sm_s1 = 6 * tile + mat;
-  const size_t sm_s3 = 6 * tile + 2 * mat;
-  const size_t sm_tri = 3 * tile + mat;
+  const size_t sm_s1 = 3 * NS3 * RTL3 * pitch_bytes + mat;
+  const size_t sm_s3 = 3 * NS3 * RTL3 * pitch_bytes + 2 * mat;
+  const size_t sm_tri = (NS1 + (NS1 == 2 ? 1 : 2)) * RTL1 * pitch_bytes + mat;
+  const int th3 = row_threads<T, BP, RTL3>(b), th1 = row_threads<T, BP, RTL1>(b);
   double* partKq = a.part;
   double* partKp = a.part + (size_t)nch * ncb * bb;
   double* sA = a.small;                          // [2][ncb][bb]: raw, symmetrised
@@ -1120,7 +1245,7 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a_in, cudaStream_t st) {
     // into W (times the identity) with its Gram, and B_0 is the product of the three factors
     k_eye<<<rblocks_bb, 256, 0, st>>>(ncb, b, sR1i);
     CSS_LAUNCHED(ctx);
-    k_tri<T, BP, true><<<rgrid, row_threads<T, BP>(b), sm_tri, st>>>(N, b, a.ws, ncb, (const T*)a.start, W, sR1i,
+    k_tri<T, BP, true><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, (const T*)a.start, W, sR1i,
                                                                      partKq);
     CSS_LAUNCHED(ctx);
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
@@ -1132,19 +1257,19 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a_in, cudaStream_t st) {
                                   a.nblk);
     CSS_LAUNCHED(ctx);
     CSS_CU(ctx, cudaMemcpyAsync(sC1, sR1, sizeof(double) * ncb * bb, cudaMemcpyDeviceToDevice, st));
-    k_tri<T, BP, true><<<rgrid, row_threads<T, BP>(b), sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
+    k_tri<T, BP, true><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
     CSS_LAUNCHED(ctx);
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
     CSS_LAUNCHED(ctx);
     k_chol<1><<<gb, 128, 0, st>>>(ncb, b, a.cb0, 1, 0, sG, sH, a.tau, 0.0, sR1, sR1i, sC1, a.B0, a.done, a.nblk);
     CSS_LAUNCHED(ctx);
-    k_tri<T, BP, true><<<rgrid, row_threads<T, BP>(b), sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
+    k_tri<T, BP, true><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
     CSS_LAUNCHED(ctx);
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
     CSS_LAUNCHED(ctx);
     k_chol<2><<<gb, 128, 0, st>>>(ncb, b, a.cb0, 1, 0, sG, sH, a.tau, 0.0, sR2, sR2i, sC1, a.B0, a.done, a.nblk);
     CSS_LAUNCHED(ctx);
-    k_tri<T, BP, false><<<rgrid, row_threads<T, BP>(b), sm_tri, st>>>(N, b, a.ws, ncb, W, Qc, sR2i, nullptr);
+    k_tri<T, BP, false><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, Qc, sR2i, nullptr);
     CSS_LAUNCHED(ctx);
   } else {
     k_init_q1<T><<<(unsigned)css_ceil_div(N, 256), 256, 0, st>>>(a.n_brow, b, a.ws, a.cb0, ncb, a.colour, a.sign,
@@ -1196,10 +1321,18 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a_in, cudaStream_t st) {
   };
   CSS_TRY(sampled(Qc, 0));
   CSS_TRY(project_u(Qc, 0));
+  // timing events: inside a stream capture they are recorded as external event nodes of the graph
+  // (real records each time the graph runs); that flag is refused outside a capture
+  unsigned ev_flags = cudaEventRecordDefault;
+  if (a.ev_spmm) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CSS_CU(ctx, cudaStreamIsCapturing(st, &cap));
+    if (cap == cudaStreamCaptureStatusActive) ev_flags = cudaEventRecordExternal;
+  }
   for (int32_t j = 0; j < m; ++j) {
-    if (a.ev_spmm) CSS_CU(ctx, cudaEventRecord(a.ev_spmm[2 * j], st));
+    if (a.ev_spmm) CSS_CU(ctx, cudaEventRecordWithFlags(a.ev_spmm[2 * j], st, ev_flags));
     CSS_TRY(launch_spmm<T>(ctx, a, Qc, W, st));
-    if (a.ev_spmm) CSS_CU(ctx, cudaEventRecord(a.ev_spmm[2 * j + 1], st));
+    if (a.ev_spmm) CSS_CU(ctx, cudaEventRecordWithFlags(a.ev_spmm[2 * j + 1], st, ev_flags));
     if (rp) {
       const int first = j == 0 ? 1 : 0, ro = reorth ? 1 : 0;
       const float *q = (const float*)Qc, *qp = (const float*)Qp;
@@ -1265,7 +1398,7 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a_in, cudaStream_t st) {
     CSS_LAUNCHED(ctx);
     if (j + 1 == m) break;
     // W1 = W0 - Q_j Kq (- Q_{j-1} Kp) and its Gram
-    s3<<<rgrid, row_threads<T, BP>(b), sm_s3, st>>>(N, b, a.ws, ncb, Qc, Qp, W, sA, sKp, partKq);
+    s3<<<rgrid, th3, sm_s3, st>>>(N, b, a.ws, ncb, Qc, Qp, W, sA, sKp, partKq);
     CSS_LAUNCHED(ctx);
     // shifted CholeskyQR3 of W: R0 from G + sI, then two plain CholeskyQR passes
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
@@ -1274,18 +1407,18 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a_in, cudaStream_t st) {
     CSS_LAUNCHED(ctx);
     CSS_TRY(chol(0, j, sR1, sR1i, a.shift_rel));
     CSS_CU(ctx, cudaMemcpyAsync(sC1, sR1, sizeof(double) * ncb * bb, cudaMemcpyDeviceToDevice, st));
-    k_tri<T, BP, true><<<rgrid, row_threads<T, BP>(b), sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
+    k_tri<T, BP, true><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
     CSS_LAUNCHED(ctx);
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
     CSS_LAUNCHED(ctx);
     CSS_TRY(chol(1, j, sR1, sR1i, 0.0));
-    k_tri<T, BP, true><<<rgrid, row_threads<T, BP>(b), sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
+    k_tri<T, BP, true><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
     CSS_LAUNCHED(ctx);
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
     CSS_LAUNCHED(ctx);
     CSS_TRY(chol(2, j, sR2, sR2i, 0.0));
     // Q_{j+1} = W R2^-1 overwrites Q_{j-1}
-    k_tri<T, BP, false><<<rgrid, row_threads<T, BP>(b), sm_tri, st>>>(N, b, a.ws, ncb, W, Qp, sR2i, nullptr);
+    k_tri<T, BP, false><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, Qp, sR2i, nullptr);
     CSS_LAUNCHED(ctx);
     CSS_TRY(sampled(Qp, j + 1));
     CSS_TRY(project_u(Qp, j + 1));
@@ -1311,6 +1444,15 @@ css_status run_pass(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
 }  // namespace
 
 // Bblk_prev is indexed by global colour; the three-term kernel reads [cb0 + lc]
+css_status css_lanczos_tune(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
+  if (a.use_tc) {  // sizes the schedule's workspace before any capture
+    LzArgs t = a;
+    return css_hv_tc_schedule(ctx, t, st);
+  }
+  if (a.fp32) return launch_spmm<float>(ctx, a, (const float*)a.Q1, (float*)a.W, st, true);
+  return launch_spmm<double>(ctx, a, (const double*)a.Q1, (double*)a.W, st, true);
+}
+
 css_status css_lanczos_pass(css_ctx* ctx, const LzArgs& a, cudaStream_t st) {
   if (a.fp32) return run_pass<float>(ctx, a, st);
   return run_pass<double>(ctx, a, st);

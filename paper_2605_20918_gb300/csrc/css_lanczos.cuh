@@ -65,6 +65,8 @@ struct LzArgs {
 };
 
 css_status css_lanczos_pass(css_ctx* ctx, const LzArgs& a, cudaStream_t st);
+// choose (tune, when the shape is new) the H * V launch variant of a pass without running it
+css_status css_lanczos_tune(css_ctx* ctx, const LzArgs& a, cudaStream_t st);
 // tensor-core H * V (css_hv_tc.cu): FP32 mode with 16 < b <= 24
 bool css_hv_tc_supported(bool fp32, int32_t b, int32_t max_row_blocks);
 css_status css_hv_tc_prepare(css_ctx* ctx, int32_t b, int32_t n_brow, int32_t nnzb, const int32_t* row_ptr,

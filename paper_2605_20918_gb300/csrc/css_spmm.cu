@@ -5,11 +5,13 @@
 // The padded kernel of css_lanczos.cu multiplies BM x BM blocks (BM = 8 for b = 6, 24 for
 // b = 23: 78% and 9% more FMAs than the blocks hold) and stages V through shared memory behind
 // two CTA barriers per neighbour block.  This one
-//  * pairs adjacent COLUMNS in the packed FMA fma.rn.f32x2: a thread owns 2 TCP = 4 consecutive
-//    columns of the b rows of W_I, each 64-bit accumulator one row and two columns, and H enters
-//    as the duplicated pair {h, h}, stored that way once per call (Hd[p][k][r] = {H_p[r][k],
-//    H_p[r][k]}, r padded to an even count), so a k costs exactly b * TCP packed FMAs;
-//  * reads each thread's own 8 TCP bytes of the b rows of V_J straight from L2 into registers,
+//  * pairs adjacent ROWS of W_I in the packed FMA fma.rn.f32x2: a thread owns CPT = 4 consecutive
+//    columns and all b rows of W_I for them, each 64-bit accumulator two rows (2i, 2i + 1) of one
+//    column; H enters as the natural pair {H_p[2i][k], H_p[2i+1][k]} of its transposed block
+//    (Ht[p][k][r] = H_p[r][k], r padded to an even count RA, stored once per call) and V as the
+//    duplicated pair {v, v} formed in registers, so a k costs (RA / 2) CPT packed FMAs and RA / 4
+//    broadcast 16-byte shared loads (RA / 2 eight-byte ones when RA is not a multiple of 4);
+//  * reads each thread's own 16 bytes of the b rows of V_J straight from L2 into registers,
 //    DEPTH rows ahead of their use: V needs neither shared memory nor a barrier;
 //  * keeps only the H blocks in shared memory, in a ring of NS stages that one thread fills with
 //    bulk copies (cp.async.bulk) completing on mbarriers.  The warps of a CTA wait on a stage's
@@ -31,27 +33,25 @@ using namespace css_pipe;
 constexpr int SD_NS = 4;     // H stages
 constexpr int SD_DEPTH = 4;  // rows of V in flight per thread
 
-template <int B, int TCP, int NW>
+template <int B, int NW>
 struct SdCfg {
-  static constexpr int BA = B + (B & 1);  // rows of a duplicated block (even)
-  static constexpr int HQ = B * BA;       // 8-byte pairs per block
-  static constexpr int HB = HQ * 8;       // bytes per block, a multiple of 16
+  static constexpr int RA = B + (B & 1);  // rows of a stored block (even)
+  static constexpr int RP = RA / 2;       // row pairs
+  static constexpr int HF = B * RA;       // floats per block
+  static constexpr int HB = HF * 4;       // bytes per block, a multiple of 16 for b = 6 and 23
   static constexpr int NT = NW * 32;
-  static constexpr int CPT = 2 * TCP;     // columns per thread
+  static constexpr int CPT = 4;           // columns per thread
   static constexpr int CW = 32 * CPT;     // columns per warp
   static constexpr int CT = NW * CW;      // columns per CTA
   static constexpr size_t smem = (size_t)SD_NS * HB + 2 * SD_NS * sizeof(uint64_t) + 16;
-  // four columns per thread only: with eight (TCP = 4) the batched build, whose systems run on
-  // concurrent side streams, gave run-to-run different W for a few systems although every
-  // single-system call matched the padded kernel bit for bit; the cause was not found
-  static_assert(B >= SD_DEPTH && TCP == 2, "shape");
+  static_assert(B >= SD_DEPTH && HB % 16 == 0, "shape");
 };
 
 struct SdArgs {
   const int32_t* row_ptr;
   const int32_t* col_idx;
-  const unsigned long long* Hd;    // [nnzb][B][BA] duplicated pairs
-  const unsigned long long* Hlod;  // [n_brow][B][BA] low parts of the diagonal blocks, or null
+  const float* Ht;    // [nnzb][B][RA] transposed blocks
+  const float* Hlot;  // [n_brow][B][RA] low parts of the diagonal blocks, or null
   const float* V;
   float* W;
   int32_t ws, w, jbase;
@@ -59,32 +59,22 @@ struct SdArgs {
   int* err;
 };
 
-template <int TCP>
-struct VRow {
-  unsigned long long x[TCP];  // TCP pairs of adjacent columns
-};
-
-template <int TCP>
-__device__ __forceinline__ VRow<TCP> v_load(const float* p) {
-  VRow<TCP> r;
-#pragma unroll
-  for (int i = 0; i < TCP; i += 2) {
-    const ulonglong2 t = __ldcg(reinterpret_cast<const ulonglong2*>(p) + i / 2);
-    r.x[i] = t.x;
-    r.x[i + 1] = t.y;
-  }
-  return r;
+__device__ __forceinline__ float4 v_load(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ unsigned long long dup2(float x) {
+  unsigned long long d;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(d) : "f"(x));
+  return d;
 }
-
 __device__ __forceinline__ void fma2(unsigned long long& d, unsigned long long h, unsigned long long v) {
   asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(h), "l"(v));
 }
 // grid (n_brow, column tiles of CT); rows without blocks (and no low part) give W_I = 0
-template <int B, int TCP, int NW, int MINB>
+template <int B, int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) k_spmm_dup(SdArgs a) {
-  using C = SdCfg<B, TCP, NW>;
+  using C = SdCfg<B, NW>;
+  constexpr int RP = C::RP, CPT = C::CPT;
   extern __shared__ __align__(128) unsigned char smem[];
-  unsigned long long* ring = reinterpret_cast<unsigned long long*>(smem);
+  float* ring = reinterpret_cast<float*>(smem);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + SD_NS * C::HB);
   uint64_t* empty = full + SD_NS;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + SD_NS);
@@ -93,7 +83,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_spmm_dup(SdArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int live = min(NW, (a.w - tile0 + C::CW - 1) / C::CW);  // warps with a column below w
   const int32_t p0 = a.row_ptr[I], nnz = a.row_ptr[I + 1] - p0;
-  const int32_t nsteps = nnz + (a.Hlod ? 1 : 0);
+  const int32_t nsteps = nnz + (a.Hlot ? 1 : 0);
   if (threadIdx.x == 0) {
     for (int s = 0; s < SD_NS; ++s) {
       bar_init(&full[s], 1);
@@ -105,13 +95,13 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_spmm_dup(SdArgs a) {
   }
   __syncthreads();
   if (warp >= live) return;  // no barrier below involves these warps
-  const int32_t col = tile0 + (warp * 32 + lane) * C::CPT;
+  const int32_t col = tile0 + (warp * 32 + lane) * CPT;
   float* Wr = a.W + (size_t)I * B * a.ws + col;
   // a failed call leaves zeros (finite values) in W for the rest of the pass
   auto zero_w = [&]() {
     if (col < a.w)
       for (int r = 0; r < B; ++r)
-        for (int u = 0; u < C::CPT && col + u < a.w; ++u) Wr[(size_t)r * a.ws + u] = 0.0f;
+        for (int u = 0; u < CPT && col + u < a.w; ++u) Wr[(size_t)r * a.ws + u] = 0.0f;
   };
   if (*abort_flag) {
     zero_w();
@@ -121,9 +111,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_spmm_dup(SdArgs a) {
   const bool producer = warp == 0 && lane == 0;
   auto issue = [&](int32_t q) {
     const int s = q % SD_NS;
-    const unsigned long long* src = q < nnz ? a.Hd + (size_t)(p0 + q) * C::HQ : a.Hlod + (size_t)I * C::HQ;
+    const float* src = q < nnz ? a.Ht + (size_t)(p0 + q) * C::HF : a.Hlot + (size_t)I * C::HF;
     bar_expect(&full[s], C::HB);
-    bulk_g2s(ring + (size_t)s * C::HQ, src, C::HB, &full[s]);
+    bulk_g2s(ring + (size_t)s * C::HF, src, C::HB, &full[s]);
   };
   int32_t issued = 0;
   if (producer)
@@ -131,18 +121,19 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_spmm_dup(SdArgs a) {
 
   const float* Vc = a.V + (col < a.w ? col : 0);  // lanes past w read column 0 and store nothing
   auto jof = [&](int32_t q) -> int32_t { return q < nnz ? a.col_idx[p0 + q] - a.jbase : I; };
-  auto vrow = [&](int32_t J, int k) { return v_load<TCP>(Vc + ((size_t)J * B + k) * a.ws); };
+  auto vrow = [&](int32_t J, int k) { return v_load(Vc + ((size_t)J * B + k) * a.ws); };
 
-  unsigned long long acc[B][TCP];
+  // acc[i][u]: rows 2i (low half) and 2i + 1 (high half) of column col + u
+  unsigned long long acc[RP][CPT];
 #pragma unroll
-  for (int r = 0; r < B; ++r)
+  for (int i = 0; i < RP; ++i)
 #pragma unroll
-    for (int u = 0; u < TCP; ++u) acc[r][u] = 0ull;
+    for (int u = 0; u < CPT; ++u) acc[i][u] = 0ull;
   bool ok = true;
   int32_t q = 0;
   if (nsteps > 0) {
-    VRow<TCP> vr[B];
-    VRow<TCP> vn[SD_DEPTH];
+    float4 vr[B];
+    float4 vn[SD_DEPTH];
     int32_t Jc = jof(0);
 #pragma unroll
     for (int k = 0; k < SD_DEPTH; ++k) vr[k] = vrow(Jc, k);
@@ -165,21 +156,31 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_spmm_dup(SdArgs a) {
         ok = false;
         break;
       }
-      const unsigned long long* hs = ring + (size_t)s * C::HQ;
+      const float* hs = ring + (size_t)s * C::HF;
 #pragma unroll
       for (int k = 0; k < B; ++k) {
         if (k + SD_DEPTH < B)
           vr[k + SD_DEPTH] = vrow(Jc, k + SD_DEPTH);
         else if (more)
           vn[k + SD_DEPTH - B] = vrow(Jn, k + SD_DEPTH - B);
+        const unsigned long long v2[CPT] = {dup2(vr[k].x), dup2(vr[k].y), dup2(vr[k].z), dup2(vr[k].w)};
+        const float* hk = hs + k * C::RA;
+        if constexpr (RP % 2 == 0) {
 #pragma unroll
-        for (int r2 = 0; r2 < C::BA / 2; ++r2) {
-          const ulonglong2 h = *reinterpret_cast<const ulonglong2*>(hs + k * C::BA + 2 * r2);
+          for (int i = 0; i < RP; i += 2) {
+            const ulonglong2 h = *reinterpret_cast<const ulonglong2*>(hk + 2 * i);
 #pragma unroll
-          for (int u = 0; u < TCP; ++u) fma2(acc[2 * r2][u], h.x, vr[k].x[u]);
-          if (2 * r2 + 1 < B) {
+            for (int u = 0; u < CPT; ++u) {
+              fma2(acc[i][u], h.x, v2[u]);
+              fma2(acc[i + 1][u], h.y, v2[u]);
+            }
+          }
+        } else {
 #pragma unroll
-            for (int u = 0; u < TCP; ++u) fma2(acc[2 * r2 + 1][u], h.y, vr[k].x[u]);
+          for (int i = 0; i < RP; ++i) {
+            const unsigned long long h = *reinterpret_cast<const unsigned long long*>(hk + 2 * i);
+#pragma unroll
+            for (int u = 0; u < CPT; ++u) fma2(acc[i][u], h, v2[u]);
           }
         }
       }
@@ -198,36 +199,34 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_spmm_dup(SdArgs a) {
     return;
   }
   if (col >= a.w) return;
-  const bool whole = col + C::CPT <= a.w;
+  const bool whole = col + CPT <= a.w;
+  auto half = [](unsigned long long x, int h) { return __uint_as_float((unsigned)(h ? (x >> 32) : (x & 0xffffffffull))); };
 #pragma unroll
   for (int r = 0; r < B; ++r) {
+    const int i = r >> 1, h = r & 1;
     if (whole) {
-#pragma unroll
-      for (int u = 0; u < TCP; u += 2)
-        *reinterpret_cast<ulonglong2*>(Wr + (size_t)r * a.ws + 2 * u) = make_ulonglong2(acc[r][u], acc[r][u + 1]);
+      *reinterpret_cast<float4*>(Wr + (size_t)r * a.ws) =
+          make_float4(half(acc[i][0], h), half(acc[i][1], h), half(acc[i][2], h), half(acc[i][3], h));
     } else {
 #pragma unroll
-      for (int u = 0; u < TCP; ++u) {
-        const unsigned long long x = acc[r][u];
-        if (col + 2 * u < a.w) Wr[(size_t)r * a.ws + 2 * u] = __uint_as_float((unsigned)(x & 0xffffffffull));
-        if (col + 2 * u + 1 < a.w) Wr[(size_t)r * a.ws + 2 * u + 1] = __uint_as_float((unsigned)(x >> 32));
-      }
+      for (int u = 0; u < CPT; ++u)
+        if (col + u < a.w) Wr[(size_t)r * a.ws + u] = half(acc[i][u], h);
     }
   }
 }
 
-// Hd[p][k][r] = {H_p[r][k], H_p[r][k]} in FP32 (round to nearest) for r, k < b, zero for the pad
-// row r = b of an odd b.  LO: block p is the diagonal block of row p, and the value the low FP32
-// part fl32(h - fl32(h)) (zero for a row without a diagonal block).
+// Ht[p][k][r] = H_p[r][k] in FP32 (round to nearest) for r, k < b, zero for the pad row r = b of
+// an odd b.  LO: block p is the diagonal block of row p, and the value the low FP32 part
+// fl32(h - fl32(h)) (zero for a row without a diagonal block).
 template <bool LO>
-__global__ void k_hdup(int64_t nblocks, int32_t b, int32_t BA, const double* __restrict__ H,
+__global__ void k_hdup(int64_t nblocks, int32_t b, int32_t RA, const double* __restrict__ H,
                        const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
-                       unsigned long long* __restrict__ Hd) {
+                       float* __restrict__ Ht) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t per = (int64_t)b * BA;
+  const int64_t per = (int64_t)b * RA;
   if (e >= nblocks * per) return;
   const int64_t p = e / per;
-  const int32_t rem = (int32_t)(e - p * per), k = rem / BA, r = rem - k * BA;
+  const int32_t rem = (int32_t)(e - p * per), k = rem / RA, r = rem - k * RA;
   float v = 0.0f;
   if (r < b) {
     int64_t src = p;
@@ -241,20 +240,19 @@ __global__ void k_hdup(int64_t nblocks, int32_t b, int32_t BA, const double* __r
       v = LO ? (float)(h - (double)(float)h) : (float)h;
     }
   }
-  const unsigned long long u = __float_as_uint(v);
-  Hd[e] = u | (u << 32);
+  Ht[e] = v;
 }
 
-template <int B, int TCP, int NW, int MINB>
+template <int B, int NW, int MINB>
 css_status launch_dup(css_ctx* ctx, const LzArgs& a, const float* V, float* W, int* err, cudaStream_t st) {
-  using C = SdCfg<B, TCP, NW>;
-  auto kern = k_spmm_dup<B, TCP, NW, MINB>;
+  using C = SdCfg<B, NW>;
+  auto kern = k_spmm_dup<B, NW, MINB>;
   static_assert(C::smem <= 48 * 1024, "static shared-memory limit");
   SdArgs s;
   s.row_ptr = a.row_ptr;
   s.col_idx = a.col_idx;
-  s.Hd = (const unsigned long long*)a.Hdup;
-  s.Hlod = (const unsigned long long*)a.Hlo_dup;
+  s.Ht = (const float*)a.Hdup;
+  s.Hlot = (const float*)a.Hlo_dup;
   s.V = V;
   s.W = W;
   s.ws = a.ws;
@@ -278,18 +276,18 @@ css_status css_spmm_dup_prepare(css_ctx* ctx, int32_t b, int32_t n_brow, int32_t
                                 const int32_t* col_idx, const double* H, const void** Hd, const void** Hlod,
                                 cudaStream_t st) {
   if (!css_spmm_dup_supported(true, b)) return css_set_arg_error(ctx, "H*V: no exact-width kernel for this b");
-  const int32_t BA = b + (b & 1);
-  const int64_t per = (int64_t)b * BA;
-  unsigned long long *h, *l;
-  CSS_TRY(css_ws(ctx, "h_dup", (size_t)std::max<int64_t>(nnzb, 1) * per * 8, (void**)&h));
-  CSS_TRY(css_ws(ctx, "h_lodup", (size_t)std::max<int32_t>(n_brow, 1) * per * 8, (void**)&l));
+  const int32_t RA = b + (b & 1);
+  const int64_t per = (int64_t)b * RA;
+  float *h, *l;
+  CSS_TRY(css_ws(ctx, "h_dup", (size_t)std::max<int64_t>(nnzb, 1) * per * 4, (void**)&h));
+  CSS_TRY(css_ws(ctx, "h_lodup", (size_t)std::max<int32_t>(n_brow, 1) * per * 4, (void**)&l));
   constexpr int T = 256;
   if (nnzb > 0) {
-    k_hdup<false><<<(unsigned)css_ceil_div((int64_t)nnzb * per, T), T, 0, st>>>(nnzb, b, BA, H, row_ptr, col_idx, h);
+    k_hdup<false><<<(unsigned)css_ceil_div((int64_t)nnzb * per, T), T, 0, st>>>(nnzb, b, RA, H, row_ptr, col_idx, h);
     CSS_LAUNCHED(ctx);
   }
   if (n_brow > 0) {
-    k_hdup<true><<<(unsigned)css_ceil_div((int64_t)n_brow * per, T), T, 0, st>>>(n_brow, b, BA, H, row_ptr, col_idx,
+    k_hdup<true><<<(unsigned)css_ceil_div((int64_t)n_brow * per, T), T, 0, st>>>(n_brow, b, RA, H, row_ptr, col_idx,
                                                                                  l);
     CSS_LAUNCHED(ctx);
   }
@@ -311,18 +309,18 @@ css_status css_spmm_dup(css_ctx* ctx, const LzArgs& a, const float* V, float* W,
   CSS_TRY(css_ws(ctx, "dup_err", 256, (void**)&err));
   if (a.b == 23) {
     switch (v) {
-      case 0: return launch_dup<23, 2, 4, 3>(ctx, a, V, W, err, st);
-      case 1: return launch_dup<23, 2, 2, 6>(ctx, a, V, W, err, st);
-      case 2: return launch_dup<23, 2, 4, 2>(ctx, a, V, W, err, st);
-      default: return launch_dup<23, 2, 8, 1>(ctx, a, V, W, err, st);
+      case 0: return launch_dup<23, 4, 3>(ctx, a, V, W, err, st);
+      case 1: return launch_dup<23, 2, 6>(ctx, a, V, W, err, st);
+      case 2: return launch_dup<23, 4, 2>(ctx, a, V, W, err, st);
+      default: return launch_dup<23, 8, 1>(ctx, a, V, W, err, st);
     }
   }
   if (a.b == 6) {
     switch (v) {
-      case 0: return launch_dup<6, 2, 2, 8>(ctx, a, V, W, err, st);
-      case 1: return launch_dup<6, 2, 4, 4>(ctx, a, V, W, err, st);
-      case 2: return launch_dup<6, 2, 8, 2>(ctx, a, V, W, err, st);
-      default: return launch_dup<6, 2, 1, 16>(ctx, a, V, W, err, st);
+      case 0: return launch_dup<6, 2, 8>(ctx, a, V, W, err, st);
+      case 1: return launch_dup<6, 4, 4>(ctx, a, V, W, err, st);
+      case 2: return launch_dup<6, 8, 2>(ctx, a, V, W, err, st);
+      default: return launch_dup<6, 1, 16>(ctx, a, V, W, err, st);
     }
   }
   return css_set_arg_error(ctx, "H*V: no exact-width kernel for this b");

@@ -236,6 +236,41 @@ def test_alternative_fp32_kernels_match_oracle(torch, css, n, r_col, m, solve, e
     assert float(np.abs(two["P"] - ref["P"]).max()) < MIXED_P_TOL
 
 
+@pytest.mark.parametrize("n,r_col,m,solve", [(125, 10.0, 40, True), (216, 10.0, 12, False)])
+def test_3xtf32_precision_matches_oracle(torch, css, ctx, n, r_col, m, solve):
+    """CSS_MIXED_3XTF32: the recurrence's H*V on the tensor cores (TF32 products of split
+    operands, FP32 accumulation), everything else as in the FP32 mode; against the oracle at the
+    mixed-precision tolerances, single system and a batch of two."""
+    g, H, col, s, nc = _system(n, "dzp", r_col)
+    ne = synth.n_electrons(n)
+    ref = oracle.density(H, col, s, nc, kT=0.05, n_elec=ne, m=m, mu=-4.0, solve_mu=solve)
+    got = gpu_density(torch, css, ctx, H, col, s, nc, kT=0.05, n_elec=ne, m=m, mu=-4.0, solve_mu=solve,
+                      precision=css.CSS_MIXED_3XTF32)
+    dP = float(np.abs(got["P"] - ref["P"]).max())
+    assert dP < MIXED_P_TOL, dP
+    assert abs(2 * got["trPH"] - 2 * ref["trPH"]) / n < MIXED_E_TOL
+    assert abs(got["trP"] - ref["trP"]) < 1e-4
+    dev = torch.device("cuda:0")
+    Hd = css.DeviceBSR.from_host(H, dev)
+    cd = torch.as_tensor(col, device=dev)
+    sd = torch.as_tensor(s, device=dev)
+    Ps = [torch.empty((H.nnzb, H.b, H.b), dtype=torch.float64, device=dev) for _ in range(2)]
+    f = dict(mu=-4.0, kT=0.05, n_elec=ne, solve_mu=solve)
+    ctx.density_batch([Hd, Hd], [cd, cd], [sd, sd], [nc, nc], Ps, [f, f], m=m, precision=css.CSS_MIXED_3XTF32)
+    for p in Ps:
+        assert float(np.abs(p.cpu().numpy() - ref["P"]).max()) < MIXED_P_TOL
+
+
+def test_3xtf32_precision_refuses_other_block_widths(torch, css, ctx):
+    """The tensor-core H*V covers 17 <= b <= 24; CSS_MIXED_3XTF32 with the 6-orbital basis is
+    refused with CSS_ERR_UNSUPPORTED rather than run on another kernel."""
+    g, H, col, s, nc = _system(27, "minimal", 8.0)
+    with pytest.raises(css.CSSError) as e:
+        gpu_density(torch, css, ctx, H, col, s, nc, kT=0.05, n_elec=synth.n_electrons(27), m=6,
+                    precision=css.CSS_MIXED_3XTF32)
+    assert e.value.status == 7
+
+
 @pytest.mark.parametrize("n,kind,r_col,m", [(125, "dzp", 10.0, 12), (343, "minimal", 8.0, 12), (27, "dzp", 6.0, 6)])
 def test_exact_width_hv_equals_the_padded_kernel_bitwise(torch, css, n, kind, r_col, m):
     """FP32 H*V for b = 6 and b = 23 runs by default in the exact-width kernel (packed FMAs over
