@@ -98,7 +98,7 @@ css_status css_create(css_ctx** out, int device) {
   const char* rs = getenv("CSS_ROWS_STREAM");
   ctx->rows_stream = rs && rs[0] == '1';
   const char* gr = getenv("CSS_GRAPH");
-  ctx->graph = !(gr && gr[0] == '0');
+  ctx->graph = gr && gr[0] == '0' ? 0 : (gr && gr[0] == '1' ? 1 : -1);
   *out = ctx;
   return CSS_OK;
 }

@@ -1070,11 +1070,12 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   // The block-Lanczos phase: every pass of every system (on the side streams of a batch) is
   // captured on the context's capture stream into one CUDA graph, which replaces the previous
   // call's graph of the same mode in place when the launch sequence has the same shape (else it is
-  // instantiated anew), and launched at once on the call's stream.  Not when the caller's stream
-  // is itself being captured: the kernels then go into the caller's graph one by one.
+  // instantiated anew), and launched at once on the call's stream: by default for a single system,
+  // on request for a batch (ctx->graph).  Not when the caller's stream is itself being captured:
+  // the kernels then go into the caller's graph one by one.
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   CSS_CU(ctx, cudaStreamIsCapturing(st, &cap));
-  const bool use_graph = ctx->graph && cap == cudaStreamCaptureStatusNone;
+  const bool use_graph = (ctx->graph == 1 || (ctx->graph < 0 && n_sys == 1)) && cap == cudaStreamCaptureStatusNone;
   if (use_graph && !ctx->cap_stream) CSS_CU(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
   auto run_lanczos = [&](int mode) -> css_status {
     while (ctx->timing && nside == 0 && ctx->lz_ev.size() < 2 * (size_t)m * n_pass) {

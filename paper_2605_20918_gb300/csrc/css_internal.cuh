@@ -84,8 +84,10 @@ struct css_ctx {
   // the block-Lanczos phase of a css_density call (every system, colour batch and step) is
   // captured from the stream into one CUDA graph and launched at once; the executable graph of
   // each pass mode (0 no retention, 1 stored rows, 2 regenerating pass) is kept and updated in
-  // place by the next call's capture (env CSS_GRAPH=0 at css_create: launch the kernels one by one)
-  bool graph = true;
+  // place by the next call's capture.  graph: 1 always, 0 never (the kernels one by one), -1 (the
+  // default) for a single system only: a batch's thousands of small launches on the side streams
+  // cost less to enqueue than to capture anew each call (env CSS_GRAPH=0 / 1 at css_create)
+  int graph = -1;
   cudaStream_t cap_stream = nullptr;  // the stream the phase is captured on
   cudaGraphExec_t lz_exec[3] = {nullptr, nullptr, nullptr};
   int64_t graph_launches = 0, graph_instantiations = 0, graph_updates = 0;

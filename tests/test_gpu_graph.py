@@ -1,7 +1,8 @@
-"""The block-Lanczos phase as one CUDA graph per call: results bitwise equal to launching the
-kernels one by one (env CSS_GRAPH=0 at css_create), for a single system with the stored
-sampled rows, with the regenerating second pass, and for a batch whose systems run on side
-streams; a second call of the same shape updates the previous call's graph in place."""
+"""The block-Lanczos phase as one CUDA graph per call (env CSS_GRAPH=1 at css_create; the
+default for a single system): results bitwise equal to launching the kernels one by one
+(CSS_GRAPH=0), for a single system with the stored sampled rows, with the regenerating second
+pass, and for a batch whose systems run on side streams; a second call of the same shape updates
+the previous call's graph in place; by default a batch runs its kernels one by one."""
 import os
 
 import numpy as np
@@ -30,8 +31,7 @@ def css(torch):
 
 
 def _ctx(css, graph):
-    if not graph:
-        os.environ["CSS_GRAPH"] = "0"
+    os.environ["CSS_GRAPH"] = "1" if graph else "0"
     try:
         return css.Context(0)
     finally:
@@ -98,3 +98,15 @@ def test_graph_batch_on_side_streams_equals_eager(torch, css):
         assert np.array_equal(a, b)
     assert res[False][1] == res[True][1]
     assert res[False][2] == 0 and res[True][2] == 1
+    os.environ.pop("CSS_GRAPH", None)
+    c = css.Context(0)
+    try:
+        Ps = [torch.empty((x[4].nnzb, 6, 6), dtype=torch.float64, device="cuda") for x in systems]
+        c.density_batch([x[0] for x in systems], [x[1] for x in systems], [x[2] for x in systems],
+                        [x[3] for x in systems], Ps, [dict(kT=0.05, n_elec=x[5]) for x in systems], m=20,
+                        precision=css.CSS_MIXED_FP32)
+        assert c.info()["graph_launches"] == 0  # the default for a batch
+        for a, p in zip(res[False][0], Ps):
+            assert np.array_equal(a, p.cpu().numpy())
+    finally:
+        c.close()
