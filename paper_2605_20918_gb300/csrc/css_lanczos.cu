@@ -807,13 +807,31 @@ __global__ void __launch_bounds__(2 * RW, 1)
 
 // OUT = W R^-1 (R^-1 upper triangular per colour); partial Gram of OUT when GRAM.  OUT may be W.
 // With three or more stages the products of consecutive tiles alternate between two output tiles.
+// need3 (optional): the per-colour flags of k_chol<1>.  The second CholeskyQR pass (OUT2 set)
+// writes the columns of a colour whose flag is clear to OUT2 (Q_{j+1}) instead of OUT; the third
+// pass (OUT2 null) writes only the columns of colours whose flag is set, and a CTA none of whose
+// colours needs it returns at once.
 template <typename T, int BP, bool GRAM>
 __global__ void __launch_bounds__(384, 2)
-    k_tri(int64_t N, int32_t b, int32_t ws, int32_t ncb, const T* __restrict__ W, T* __restrict__ OUT,
-          const double* __restrict__ Rinv, double* __restrict__ partG) {
+    k_tri(int64_t N, int32_t b, int32_t ws, int32_t ncb, const T* __restrict__ W, T* OUT,
+          const double* __restrict__ Rinv, double* __restrict__ partG, const int32_t* __restrict__ need3,
+          T* OUT2) {
   constexpr int RTL = RowTile<T, BP>::RTL1, NS = RowTile<T, BP>::NS1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const RowCtx<T, BP> c = make_ctx<T, BP>(b, ws, ncb);
+  bool store_mine = true;  // this thread's column is stored (to OUT)
+  if (need3) {
+    if (!OUT2) {
+      bool any = false;
+      for (int32_t g = 0; g < c.gcount; ++g) any = any || need3[c.cg0 + g] != 0;
+      if (!any) return;  // uniform over the CTA
+    }
+    if (c.my_col >= 0) {
+      const bool n3 = need3[c.cg0 + c.my_col / b] != 0;
+      if (OUT2 && !n3) OUT = OUT2;
+      if (!OUT2 && !n3) store_mine = false;
+    }
+  }
   constexpr int NO = NS == 2 ? 1 : 2;  // output tiles (the overlapped schedule alternates two)
   RowRing<T, BP> ring{reinterpret_cast<T*>(smem_raw), RTL * c.pitch, 1};  // W
   T* sO = ring.at(NS, 0);
@@ -833,7 +851,7 @@ __global__ void __launch_bounds__(384, 2)
       },
       [&](int, int32_t i, int64_t r0, int32_t nr, bool last) {
         const T* o = sO + (i & (NO - 1)) * RTL * c.pitch;
-        c.store(OUT, o, r0, nr);
+        if (store_mine) c.store(OUT, o, r0, nr);
         if (GRAM) gram_tile<T, BP, true, RTL>(c, role, o, o, i, last, gp, acc);
       });
   if (GRAM)
@@ -894,11 +912,17 @@ __global__ void k_hnorm(int32_t ncb, int32_t b, int32_t cb0, int32_t j, const do
   if (lane == 0) hq2[lc] = s;
 }
 
+// need3 (optional, one flag per colour of the pass): MODE 1 sets a colour's flag when the Gram
+// of its W R0^-1 is not within kQr2Dev of the identity (max entry), clears it otherwise; MODE 2
+// with the flag clear takes R2 = I, so that B_j = R1 R0 (that colour's third CholeskyQR pass is
+// then skipped: its second pass has written Q_{j+1}).  Each colour decides on its own Gram, so
+// its result does not depend on the other colours of the pass.
+constexpr double kQr2Dev = 1e-2;
 template <int MODE>
 __global__ void k_chol(int32_t ncb, int32_t b, int32_t cb0, int32_t m, int32_t j, const double* __restrict__ G,
                        const double* __restrict__ hq2, double tau, double shift_rel, double* __restrict__ R,
                        double* __restrict__ Rinv, double* __restrict__ Rprod, double* __restrict__ Bblk,
-                       int32_t* __restrict__ done, int32_t* __restrict__ nblk) {
+                       int32_t* __restrict__ done, int32_t* __restrict__ nblk, int32_t* __restrict__ need3) {
   __shared__ double sR[4][CSS_MAX_B][CSS_MAX_B + 1];
   const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t lc = blockIdx.x * 4 + warp;
@@ -920,7 +944,18 @@ __global__ void k_chol(int32_t ncb, int32_t b, int32_t cb0, int32_t m, int32_t j
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     shift = shift_rel * t;
   }
-  if (!broken) {
+  const bool two_pass = MODE == 2 && need3 && need3[lc] == 0;
+  if (MODE == 1 && need3) {
+    double dev = broken ? 1.0 : 0.0;
+    if (lane < b && !broken)
+      for (int32_t i = 0; i < b; ++i) dev = fmax(dev, fabs(g[i * b + lane] - (i == lane ? 1.0 : 0.0)));
+    for (int o = 16; o > 0; o >>= 1) dev = fmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    if (lane == 0) need3[lc] = dev <= kQr2Dev ? 0 : 1;
+  }
+  if (two_pass) {
+    if (lane < b)
+      for (int32_t i = 0; i < b; ++i) r[i][lane] = i == lane ? 1.0 : 0.0;
+  } else if (!broken) {
     for (int32_t k = 0; k < b && !broken; ++k) {
       double sv = 0.0;
       if (lane < b && lane >= k) {
@@ -1225,6 +1260,8 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a_in, cudaStream_t st) {
   double* sV = sKp + (size_t)ncb * bb;  // Q_j^T u of the running step (the tenth small matrix)
   double* sRi10 = sV + (size_t)ncb * bb;     // R0^-1 R1^-1 (FP32 row passes)
   double* sRi210 = sRi10 + (size_t)ncb * bb;  // R0^-1 R1^-1 R2^-1
+  // per colour: "a third CholeskyQR pass is needed" in the running step (after the matrices)
+  int32_t* need3 = reinterpret_cast<int32_t*>(sRi210 + (size_t)ncb * bb);
   // FP32, 16 < b <= 24, env CSS_ROWS_STREAM=1: the streaming row passes of css_rows.cu
   constexpr bool kF32 = sizeof(T) == 4;
   const bool rp = kF32 && BP == 24 && css_rowpass_supported(true, b) && ctx->rows_stream;
@@ -1246,7 +1283,7 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a_in, cudaStream_t st) {
     k_eye<<<rblocks_bb, 256, 0, st>>>(ncb, b, sR1i);
     CSS_LAUNCHED(ctx);
     k_tri<T, BP, true><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, (const T*)a.start, W, sR1i,
-                                                                     partKq);
+                                                                     partKq, nullptr, nullptr);
     CSS_LAUNCHED(ctx);
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
     CSS_LAUNCHED(ctx);
@@ -1254,22 +1291,24 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a_in, cudaStream_t st) {
     CSS_LAUNCHED(ctx);
     const unsigned gb = (unsigned)css_ceil_div(ncb, 4);
     k_chol<0><<<gb, 128, 0, st>>>(ncb, b, a.cb0, 1, 0, sG, sH, a.tau, a.shift_rel, sR1, sR1i, sC1, a.B0, a.done,
-                                  a.nblk);
+                                  a.nblk, nullptr);
     CSS_LAUNCHED(ctx);
     CSS_CU(ctx, cudaMemcpyAsync(sC1, sR1, sizeof(double) * ncb * bb, cudaMemcpyDeviceToDevice, st));
-    k_tri<T, BP, true><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
+    k_tri<T, BP, true><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq, nullptr, nullptr);
     CSS_LAUNCHED(ctx);
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
     CSS_LAUNCHED(ctx);
-    k_chol<1><<<gb, 128, 0, st>>>(ncb, b, a.cb0, 1, 0, sG, sH, a.tau, 0.0, sR1, sR1i, sC1, a.B0, a.done, a.nblk);
+    k_chol<1><<<gb, 128, 0, st>>>(ncb, b, a.cb0, 1, 0, sG, sH, a.tau, 0.0, sR1, sR1i, sC1, a.B0, a.done, a.nblk,
+                                  nullptr);
     CSS_LAUNCHED(ctx);
-    k_tri<T, BP, true><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
+    k_tri<T, BP, true><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq, nullptr, nullptr);
     CSS_LAUNCHED(ctx);
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
     CSS_LAUNCHED(ctx);
-    k_chol<2><<<gb, 128, 0, st>>>(ncb, b, a.cb0, 1, 0, sG, sH, a.tau, 0.0, sR2, sR2i, sC1, a.B0, a.done, a.nblk);
+    k_chol<2><<<gb, 128, 0, st>>>(ncb, b, a.cb0, 1, 0, sG, sH, a.tau, 0.0, sR2, sR2i, sC1, a.B0, a.done, a.nblk,
+                                  nullptr);
     CSS_LAUNCHED(ctx);
-    k_tri<T, BP, false><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, Qc, sR2i, nullptr);
+    k_tri<T, BP, false><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, Qc, sR2i, nullptr, nullptr, nullptr);
     CSS_LAUNCHED(ctx);
   } else {
     k_init_q1<T><<<(unsigned)css_ceil_div(N, 256), 256, 0, st>>>(a.n_brow, b, a.ws, a.cb0, ncb, a.colour, a.sign,
@@ -1308,14 +1347,15 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a_in, cudaStream_t st) {
     CSS_LAUNCHED(ctx);
     return CSS_OK;
   };
-  auto chol = [&](int mode, int32_t j, double* R, double* Ri, double shift) -> css_status {
+  auto chol = [&](int mode, int32_t j, double* R, double* Ri, double shift, int32_t* n3) -> css_status {
     const unsigned gb = (unsigned)css_ceil_div(ncb, 4);
     if (mode == 0)
-      k_chol<0><<<gb, 128, 0, st>>>(ncb, b, a.cb0, m, j, sG, sH, a.tau, shift, R, Ri, sC1, a.Bblk, a.done, a.nblk);
+      k_chol<0><<<gb, 128, 0, st>>>(ncb, b, a.cb0, m, j, sG, sH, a.tau, shift, R, Ri, sC1, a.Bblk, a.done, a.nblk,
+                                    n3);
     else if (mode == 1)
-      k_chol<1><<<gb, 128, 0, st>>>(ncb, b, a.cb0, m, j, sG, sH, a.tau, 0.0, R, Ri, sC1, a.Bblk, a.done, a.nblk);
+      k_chol<1><<<gb, 128, 0, st>>>(ncb, b, a.cb0, m, j, sG, sH, a.tau, 0.0, R, Ri, sC1, a.Bblk, a.done, a.nblk, n3);
     else
-      k_chol<2><<<gb, 128, 0, st>>>(ncb, b, a.cb0, m, j, sG, sH, a.tau, 0.0, R, Ri, sC1, a.Bblk, a.done, a.nblk);
+      k_chol<2><<<gb, 128, 0, st>>>(ncb, b, a.cb0, m, j, sG, sH, a.tau, 0.0, R, Ri, sC1, a.Bblk, a.done, a.nblk, n3);
     CSS_LAUNCHED(ctx);
     return CSS_OK;
   };
@@ -1358,19 +1398,19 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a_in, cudaStream_t st) {
       CSS_LAUNCHED(ctx);
       // shifted CholeskyQR3 on W1 without storing the intermediates: the Grams of W1 R0^-1 and
       // W1 R0^-1 R1^-1 are taken from W1 itself, and Q_{j+1} = W1 R0^-1 R1^-1 R2^-1
-      CSS_TRY(chol(0, j, sR1, sR1i, a.shift_rel));
+      CSS_TRY(chol(0, j, sR1, sR1i, a.shift_rel, rp ? nullptr : need3));
       CSS_CU(ctx, cudaMemcpyAsync(sC1, sR1, sizeof(double) * ncb * bb, cudaMemcpyDeviceToDevice, st));
       CSS_TRY(css_rowpass(ctx, 2, N, b, a.ws, ncb, a.cb0, first, ro, nullptr, nullptr, wv, nullptr, sR1i, nullptr,
                           nullptr, partKq, nullptr, st));
       k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
       CSS_LAUNCHED(ctx);
-      CSS_TRY(chol(1, j, sR2, sR2i, 0.0));
+      CSS_TRY(chol(1, j, sR2, sR2i, 0.0, nullptr));
       CSS_TRY(css_small_mm(ctx, ncb, b, sR1i, sR2i, sRi10, st));
       CSS_TRY(css_rowpass(ctx, 2, N, b, a.ws, ncb, a.cb0, first, ro, nullptr, nullptr, wv, nullptr, sRi10, nullptr,
                           nullptr, partKq, nullptr, st));
       k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
       CSS_LAUNCHED(ctx);
-      CSS_TRY(chol(2, j, sR1, sR1i, 0.0));
+      CSS_TRY(chol(2, j, sR1, sR1i, 0.0, nullptr));
       CSS_TRY(css_small_mm(ctx, ncb, b, sRi10, sR1i, sRi210, st));
       CSS_TRY(css_rowpass(ctx, 3, N, b, a.ws, ncb, a.cb0, first, ro, nullptr, nullptr, wv, (float*)Qp, sRi210, nullptr,
                           nullptr, nullptr, nullptr, st));
@@ -1400,25 +1440,28 @@ css_status run_pass_bp(css_ctx* ctx, const LzArgs& a_in, cudaStream_t st) {
     // W1 = W0 - Q_j Kq (- Q_{j-1} Kp) and its Gram
     s3<<<rgrid, th3, sm_s3, st>>>(N, b, a.ws, ncb, Qc, Qp, W, sA, sKp, partKq);
     CSS_LAUNCHED(ctx);
-    // shifted CholeskyQR3 of W: R0 from G + sI, then two plain CholeskyQR passes
+    // shifted CholeskyQR3 of W: R0 from G + sI, then two plain CholeskyQR passes; the third is
+    // skipped (need3 clear) when the second pass's input W R0^-1 already has a Gram within
+    // kQr2Dev of the identity for every colour: one CholeskyQR pass of so well-conditioned a
+    // block gives orthonormal columns to the working precision, as the third pass would
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
     CSS_LAUNCHED(ctx);
     k_hnorm<<<(unsigned)css_ceil_div(ncb, 8), 256, 0, st>>>(ncb, b, a.cb0, j, sA, a.Bblk_prev, sG, sH);
     CSS_LAUNCHED(ctx);
-    CSS_TRY(chol(0, j, sR1, sR1i, a.shift_rel));
+    CSS_TRY(chol(0, j, sR1, sR1i, a.shift_rel, rp ? nullptr : need3));
     CSS_CU(ctx, cudaMemcpyAsync(sC1, sR1, sizeof(double) * ncb * bb, cudaMemcpyDeviceToDevice, st));
-    k_tri<T, BP, true><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
+    k_tri<T, BP, true><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq, nullptr, nullptr);
     CSS_LAUNCHED(ctx);
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
     CSS_LAUNCHED(ctx);
-    CSS_TRY(chol(1, j, sR1, sR1i, 0.0));
-    k_tri<T, BP, true><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq);
+    CSS_TRY(chol(1, j, sR1, sR1i, 0.0, need3));
+    k_tri<T, BP, true><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, W, sR1i, partKq, need3, Qp);
     CSS_LAUNCHED(ctx);
     k_reduce<<<rblocks_bb, 256, 0, st>>>(nch, ncb, bb, partKq, sG);
     CSS_LAUNCHED(ctx);
-    CSS_TRY(chol(2, j, sR2, sR2i, 0.0));
-    // Q_{j+1} = W R2^-1 overwrites Q_{j-1}
-    k_tri<T, BP, false><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, Qp, sR2i, nullptr);
+    CSS_TRY(chol(2, j, sR2, sR2i, 0.0, need3));
+    // Q_{j+1} = W R2^-1 overwrites Q_{j-1} (done by the second pass when two passes sufficed)
+    k_tri<T, BP, false><<<rgrid, th1, sm_tri, st>>>(N, b, a.ws, ncb, W, Qp, sR2i, nullptr, need3, nullptr);
     CSS_LAUNCHED(ctx);
     CSS_TRY(sampled(Qp, j + 1));
     CSS_TRY(project_u(Qp, j + 1));
@@ -1468,7 +1511,10 @@ size_t css_lanczos_part_doubles(int64_t N, int32_t b, int32_t ncb) {
   return (size_t)nch * ncb * b * b * 2 + (size_t)nch * ncb + 64;
 }
 
-size_t css_lanczos_small_doubles(int32_t b, int32_t ncb) { return (size_t)ncb * b * b * 12 + ncb + 64; }
+// twelve per-colour b x b matrices, the breakdown scales and the colours' CholeskyQR flags
+size_t css_lanczos_small_doubles(int32_t b, int32_t ncb) {
+  return (size_t)ncb * b * b * 12 + ncb + (ncb + 1) / 2 + 64;
+}
 
 int32_t css_spmm_bm(int32_t b) { return b <= 8 ? 8 : b <= 12 ? 12 : b <= 16 ? 16 : b <= 24 ? 24 : 32; }
 
