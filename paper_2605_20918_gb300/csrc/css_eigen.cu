@@ -474,8 +474,8 @@ __global__ void __launch_bounds__(128) k_inviter_p1(int32_t kd, int32_t nmax, co
       double u0, u1, u2, rhs_i, ncd, ncs, nx;
       if (fabs(cd) >= fabs(sub)) {
         if (fabs(cd) < pivmin) cd = cd >= 0 ? pivmin : -pivmin;
-        const double l = sub / cd;
-        u0 = cd;
+        u0 = 1.0 / cd;  // the pivot's reciprocal serves the multiplier and the back substitution
+        const double l = sub * u0;
         u1 = cs;
         u2 = 0.0;
         rhs_i = xc;
@@ -483,8 +483,8 @@ __global__ void __launch_bounds__(128) k_inviter_p1(int32_t kd, int32_t nmax, co
         ncs = sup;
         nx = xn - l * xc;
       } else {
-        const double l = cd / sub;
-        u0 = sub;
+        u0 = 1.0 / sub;
+        const double l = cd * u0;
         u1 = dg;
         u2 = sup;
         rhs_i = xn;
@@ -506,17 +506,17 @@ __global__ void __launch_bounds__(128) k_inviter_p1(int32_t kd, int32_t nmax, co
     // backward substitution U y = x, then the norm
     double y1 = 0.0, y2 = 0.0, ss = 0.0;
     for (int32_t i = n - 1; i >= 0; --i) {
-      double r, u0;
+      double r, u0;  // u0: the reciprocal of the row's pivot
       if (i == n - 1) {
         r = xc;
-        u0 = cd;
+        u0 = 1.0 / cd;
       } else {
         r = work ? f_x[(size_t)i * nmax + k] : 0.0;
         u0 = work ? f_u0[(size_t)i * nmax + k] : 1.0;
         if (work) r -= f_u1[(size_t)i * nmax + k] * y1;
         if (work && i + 2 < n) r -= f_u2[(size_t)i * nmax + k] * y2;
       }
-      const double y = work ? r / u0 : 0.0;
+      const double y = work ? r * u0 : 0.0;
       if (work) f_x[(size_t)i * nmax + k] = y;
       ss += y * y;
       y2 = y1;
@@ -586,8 +586,8 @@ __device__ double cl_solve(const ClusterCols& m, int32_t col, double sigma, doub
       double u0, u1, u2, rhs, ncd, ncs, nx;
       if (fabs(cd) >= fabs(sub[q])) {
         if (fabs(cd) < pivmin) cd = cd >= 0 ? pivmin : -pivmin;
-        const double l = sub[q] / cd;
-        u0 = cd;
+        u0 = 1.0 / cd;  // the pivot's reciprocal serves the multiplier and the back substitution
+        const double l = sub[q] * u0;
         u1 = cs;
         u2 = 0.0;
         rhs = xc;
@@ -595,8 +595,8 @@ __device__ double cl_solve(const ClusterCols& m, int32_t col, double sigma, doub
         ncs = sup[q];
         nx = xn[q] - l * xc;
       } else {
-        const double l = cd / sub[q];
-        u0 = sub[q];
+        u0 = 1.0 / sub[q];
+        const double l = cd * u0;
         u1 = dg[q];
         u2 = sup[q];
         rhs = xn[q];
@@ -636,7 +636,7 @@ __device__ double cl_solve(const ClusterCols& m, int32_t col, double sigma, doub
     for (int q = 0; q < kCB; ++q) {
       const int32_t i = i0 - q;
       if (i < 0) break;
-      const double y = (r[q] - a1[q] * y1 - a2[q] * y2) / a0[q];
+      const double y = (r[q] - a1[q] * y1 - a2[q] * y2) * a0[q];
       if (st) m.x[(size_t)i * nmax + col] = y;
       ss += y * y;
       y2 = y1;
@@ -646,20 +646,48 @@ __device__ double cl_solve(const ClusterCols& m, int32_t col, double sigma, doub
   return sqrt(ss);
 }
 
+// Work list of phase 2: (colour, first member, members) of every cluster of close shifts (runs
+// cut every kMaxCluster members) that holds a member phase 1 did not finish; one thread per shift,
+// the order of the list does not matter (every item writes only its own columns)
+__global__ void k_cl_items(int32_t kd, int32_t nmax, const int32_t* __restrict__ nblk,
+                           const float* __restrict__ lam32, const double* __restrict__ tnorm, double rel_cluster,
+                           const int32_t* __restrict__ flag, int32_t* __restrict__ count, int4* __restrict__ items) {
+  const int32_t c = blockIdx.y;
+  const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int32_t n = nblk[c] * kd;
+  if (k >= n) return;
+  const float* l32 = lam32 + (size_t)c * nmax;
+  const double tol = rel_cluster * tnorm[c];
+  int32_t s = k;
+  while (s > 0 && (double)l32[s] - (double)l32[s - 1] <= tol) --s;
+  if ((k - s) % kMaxCluster != 0) return;  // not the first member of a cluster
+  int32_t k1 = k;
+  while (k1 + 1 < n && (double)l32[k1 + 1] - (double)l32[k1] <= tol && k1 + 1 - k < kMaxCluster) ++k1;
+  bool any = false;
+  for (int32_t kk = k; kk <= k1; ++kk) any = any || flag[(size_t)c * nmax + kk] != 0;
+  if (!any) return;  // phase 1 finished every member
+  items[atomicAdd(count, 1)] = make_int4(c, k, k1 - k + 1, 0);
+}
+
+// one warp per work item of k_cl_items (warps past the list's length return)
 __global__ void __launch_bounds__(256) k_inviter_cl(int32_t kd, int32_t nmax, const int32_t* __restrict__ nblk,
                                                     const double* __restrict__ dd, const double* __restrict__ ee,
                                                     const float* __restrict__ lam32,
                                                     const double* __restrict__ tnorm, double rel_cluster,
                                                     double* __restrict__ U, double* __restrict__ F,
                                                     double* __restrict__ lam, int32_t* __restrict__ status,
-                                                    const int32_t* __restrict__ flag, const int32_t* __restrict__ gid) {
+                                                    const int32_t* __restrict__ gid, const int32_t* __restrict__ count,
+                                                    const int4* __restrict__ items) {
   __shared__ double sC[8][kMaxCluster][kMaxCluster + 1];
   __shared__ double sV[8][kMaxCluster][kMaxCluster + 1];
   constexpr unsigned FULL = 0xffffffffu;
-  const int32_t c = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int32_t item = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (item >= *count) return;  // uniform over the warp
+  const int4 it4 = items[item];
+  const int32_t c = it4.x, k0 = it4.y, kc = it4.z, k1 = k0 + kc - 1;
   const uint64_t cseed = gid ? (uint64_t)gid[c] : (uint64_t)c;
   const int32_t n = nblk[c] * kd;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const float* l32 = lam32 + (size_t)c * nmax;
   double* u = U + (size_t)c * nmax * nmax;
   ClusterCols m;
@@ -672,31 +700,11 @@ __global__ void __launch_bounds__(256) k_inviter_cl(int32_t kd, int32_t nmax, co
   m.n = n;
   m.nmax = nmax;
   const double tn = tnorm[c];
-  const double tol = rel_cluster * tn;
   const double pivmin = 2.2e-16 * tn;
   const double res_tol = kResTol * tn;
   int32_t failed = 0;
-  // the colour's shifts are dealt out in runs of 32 to the warps of gridDim.y CTAs
-  for (int32_t base = (blockIdx.y * nwarp + warp) * 32; base < n; base += gridDim.y * nwarp * 32) {
-    // cluster starts among this warp's 32 shifts: the gap to the previous shift exceeds tol,
-    // or a cluster longer than kMaxCluster is cut every kMaxCluster members
-    bool start = false;
-    const int32_t k = base + lane;
-    if (k < n) {
-      int32_t s = k;
-      while (s > 0 && (double)l32[s] - (double)l32[s - 1] <= tol) --s;
-      start = (k - s) % kMaxCluster == 0;
-    }
-    unsigned starts = __ballot_sync(FULL, start);
-    while (starts) {
-      const int32_t k0 = base + __ffs(starts) - 1;
-      starts &= starts - 1;
-      int32_t k1 = k0;
-      while (k1 + 1 < n && (double)l32[k1 + 1] - (double)l32[k1] <= tol && k1 + 1 - k0 < kMaxCluster) ++k1;
-      const int32_t kc = k1 - k0 + 1;
-      bool any = false;
-      for (int32_t kk = k0; kk <= k1; ++kk) any = any || flag[(size_t)c * nmax + kk] != 0;
-      if (!any) continue;  // phase 1 finished every member
+  {
+    {
       const bool act = lane < kc;
       const int32_t col = k0 + (act ? lane : 0);  // idle lanes shadow member 0 and store nothing
       const double g_lo = k0 > 0 ? (double)l32[k0] - (double)l32[k0 - 1] : tn;
@@ -1002,8 +1010,17 @@ css_status css_eigen_ritz(css_ctx* ctx, const EigArgs& a, cudaStream_t st) {
   k_inviter_p1<<<dim3((unsigned)css_ceil_div(nmax, 128), (unsigned)nc), 128, 0, st>>>(
       b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm, 1e-4, a.U, a.F, a.lam, a.flag, a.gid);
   CSS_LAUNCHED(ctx);
-  k_inviter_cl<<<dim3((unsigned)nc, 4), 256, 0, st>>>(b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm, 1e-4, a.U, a.F, a.lam, a.status,
-                                   a.flag, a.gid);
+  // phase 2 on a compact list: one warp per flagged cluster of any colour
+  int32_t* cl_count;
+  int4* cl_items;
+  CSS_TRY(css_ws(ctx, "e_cl_count", 256, (void**)&cl_count));
+  CSS_TRY(css_ws(ctx, "e_cl_items", (size_t)nc * nmax * sizeof(int4), (void**)&cl_items));
+  CSS_CU(ctx, cudaMemsetAsync(cl_count, 0, sizeof(int32_t), st));
+  k_cl_items<<<dim3((unsigned)css_ceil_div(nmax, 128), (unsigned)nc), 128, 0, st>>>(b, nmax, a.nblk, a.lam32, a.tnorm,
+                                                                                   1e-4, a.flag, cl_count, cl_items);
+  CSS_LAUNCHED(ctx);
+  k_inviter_cl<<<(unsigned)css_ceil_div((int64_t)nc * nmax, 8), 256, 0, st>>>(
+      b, nmax, a.nblk, a.d, a.e, a.lam32, a.tnorm, 1e-4, a.U, a.F, a.lam, a.status, a.gid, cl_count, cl_items);
   CSS_LAUNCHED(ctx);
   if (ctx->debug_eig == 1) {
     k_shifts_out<<<nc, 256, 0, st>>>(nmax, a.lam32, a.lam);
