@@ -587,6 +587,29 @@ def main():
         t64 = e0.elapsed_time(e1) / 2e3
         inf64 = ctx.info()
         dP = float((P64 - P[t]).abs().max().item())
+        # the same FP64 build with the recurrence's H*V in FP32 pairs (CSS_FP64_SPLIT, b = 6 or 23):
+        # one untimed, one timed build, its P against the FP64 P
+        split = None
+        if Hd.b in (6, 23):
+            Psp = torch.empty_like(P64)
+            ctx.density(Hd, colour, sign, nc, Psp, kT=0.05, n_elec=ne, m=a.m, precision=css.CSS_FP64_SPLIT)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            nc = ctx.color(xyz, geoms[t][0].box, a.r_col, 1004, colour)
+            ctx.probes(colour, Hd.b, 1005, sign)
+            rsp = ctx.density(Hd, colour, sign, nc, Psp, kT=0.05, n_elec=ne, m=a.m, precision=css.CSS_FP64_SPLIT)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            infs = ctx.info()
+            split = {"s_per_pbuild": e0.elapsed_time(e1) / 1e3, "spmm_ms_per_launch": infs["ms_spmm"],
+                     "spmm_fp64_equivalent_tflops": infs["spmm_flops"] / (infs["ms_spmm"] * 1e-3) / 1e12
+                     if infs["ms_spmm"] > 0 else None,
+                     "max_abs_dP_vs_fp64": float((Psp - P64).abs().max().item()),
+                     "dTrP_vs_fp64": rsp["trP"] - r64["trP"],
+                     "dE_band_eV_per_molecule_vs_fp64": abs(2 * (rsp["trPH"] - r64["trPH"])) / a.n_mol,
+                     "note": "CSS_FP64_SPLIT: FP64 vectors, the recurrence's H*V with FP32 hi + lo pairs and "
+                             "error-free products on the FP32 FMA pipe"}
+            del Psp
         # FP64 at the mixed run's mu: the error of the mixed arithmetic alone, without the
         # change of mu (any mu in the gap satisfies the electron count)
         r64f = ctx.density(Hd, colour, sign, nc, P64, kT=0.05, n_elec=ne, m=a.m, precision=css.CSS_FP64,
@@ -600,7 +623,7 @@ def main():
                                 "max_abs_dP_same_mu": dPf,
                                 "dE_band_eV_per_molecule_same_mu": abs(2 * (last_r["trPH"] - r64f["trPH"])) / a.n_mol,
                                 "dE_band_eV_per_molecule": abs(2 * (last_r["trPH"] - r64["trPH"])) / a.n_mol,
-                                "dTrP": last_r["trP"] - r64["trP"], "mu_fp64": r64["mu"],
+                                "dTrP": last_r["trP"] - r64["trP"], "mu_fp64": r64["mu"], "fp64_split": split,
                                 "note": "mixed P of the last timed geometry against the FP64 path on the same geometry"}
     if rank == 0 and not a.no_modes:
         # the other matrix functions of the library on the same workload, one build each

@@ -53,11 +53,16 @@ typedef enum {
   CSS_MIXED_FP32 = 1,  /* H*V, Krylov vectors and block products in FP32 (FP32 accumulate); */
                        /* recurrence coefficients, Cholesky, eigensolve, mu, Z and P in FP64; */
                        /* implies CSS_REORTH_LOCAL (it removes an FP32-level bias of Tr P)   */
-  CSS_MIXED_3XTF32 = 2 /* as CSS_MIXED_FP32, with the H*V of the block-Lanczos recurrence on  */
-                       /* the tensor cores: TF32 products of split operands (x = x1 + x2, the */
-                       /* on-site blocks in three parts) accumulated in FP32, for 17 <= b <= 24 */
-                       /* (other b: CSS_ERR_UNSUPPORTED); the other sparse products of        */
-                       /* css_hprime and css_density_nonorth stay on the FP32 FMA pipe        */
+  CSS_MIXED_3XTF32 = 2, /* as CSS_MIXED_FP32, with the H*V of the block-Lanczos recurrence on */
+                        /* the tensor cores: TF32 products of split operands (x = x1 + x2, the */
+                        /* on-site blocks in three parts) accumulated in FP32, for 17 <= b <= 24 */
+                        /* (other b: CSS_ERR_UNSUPPORTED); the other sparse products of        */
+                        /* css_hprime and css_density_nonorth stay on the FP32 FMA pipe        */
+  CSS_FP64_SPLIT = 3    /* as CSS_FP64, with the H*V of the block-Lanczos recurrence on the FP32 */
+                        /* FMA pipe: H and V as pairs hi + lo of FP32 numbers, each product by */
+                        /* an error-free FMA split, sums by TwoSum into hi + lo (about 2^-47   */
+                        /* relative per term against 2^-53); b = 6 or 23 (other b:            */
+                        /* CSS_ERR_UNSUPPORTED); other sparse products stay FP64             */
 } css_precision;
 
 /* css_density flags */

@@ -18,14 +18,14 @@ import numpy as np
 __all__ = [
     "CSSError", "Context", "DeviceBSR", "load_library", "library_path", "css_create", "css_destroy", "css_color",
     "css_color_graph", "css_color_check", "css_color_update", "css_probes", "css_density", "css_density_nonorth", "css_density_batch", "css_pbuild", "css_get_info", "css_ritz", "css_projected", "css_eigen_blocks",
-    "CSS_OK", "CSS_WARN_BREAKDOWN", "CSS_FP64", "CSS_MIXED_FP32", "CSS_MIXED_3XTF32", "CSS_SYMMETRIZE", "CSS_TWO_PASS",
+    "CSS_OK", "CSS_WARN_BREAKDOWN", "CSS_FP64", "CSS_MIXED_FP32", "CSS_MIXED_3XTF32", "CSS_FP64_SPLIT", "CSS_SYMMETRIZE", "CSS_TWO_PASS",
     "CSS_REORTH_LOCAL", "CSS_HOST_IO", "CSS_SIGNS_ONES", "CSS_ENERGY_WEIGHTED", "CSS_INV_SQRT", "CSS_RITZ_ONLY",
     "css_density_colours", "css_solve_mu",
 ]
 
 CSS_OK, CSS_ERR_INVALID_ARG, CSS_ERR_NOMEM, CSS_ERR_CUDA, CSS_ERR_TIMEOUT, CSS_ERR_NUMERIC = 0, 1, 2, 3, 4, 5
 CSS_WARN_BREAKDOWN, CSS_ERR_UNSUPPORTED = 6, 7
-CSS_FP64, CSS_MIXED_FP32, CSS_MIXED_3XTF32 = 0, 1, 2
+CSS_FP64, CSS_MIXED_FP32, CSS_MIXED_3XTF32, CSS_FP64_SPLIT = 0, 1, 2, 3
 CSS_SYMMETRIZE, CSS_TWO_PASS, CSS_REORTH_LOCAL, CSS_HOST_IO, CSS_ENERGY_WEIGHTED, CSS_INV_SQRT = 1, 2, 4, 8, 16, 32
 CSS_RITZ_ONLY = 64
 CSS_SIGNS_ONES = 1

@@ -628,7 +628,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
                             void* yfull, int32_t ldy, bool partial, const int32_t* colour_ids) {
   // ------------------------------------------------------------ validation
   if (n_sys < 1 || n_sys > MU_MAXSYS) return css_set_arg_error(ctx, "css_density: n_sys out of range");
-  if (prec != CSS_FP64 && prec != CSS_MIXED_FP32 && prec != CSS_MIXED_3XTF32)
+  if (prec != CSS_FP64 && prec != CSS_MIXED_FP32 && prec != CSS_MIXED_3XTF32 && prec != CSS_FP64_SPLIT)
     return css_set_arg_error(ctx, "css_density: unknown precision");
   if (flags & ~(CSS_SYMMETRIZE | CSS_TWO_PASS | CSS_REORTH_LOCAL | CSS_ENERGY_WEIGHTED | CSS_INV_SQRT | CSS_RITZ_ONLY))
     return css_set_arg_error(ctx, "css_density: unknown flag");
@@ -660,7 +660,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   const int32_t n_brow = (int32_t)nb_tot, nnzb = (int32_t)nnz_tot, n_col = (int32_t)nc_tot;
   const int64_t N = (int64_t)n_brow * b;
   const int32_t bb = b * b, nmax = m * b;
-  const bool f32 = prec != CSS_FP64;
+  const bool f32 = prec == CSS_MIXED_FP32 || prec == CSS_MIXED_3XTF32;
   const bool two_pass = (flags & CSS_TWO_PASS) != 0 || yfull != nullptr;
   const bool ritz_only = (flags & CSS_RITZ_ONLY) != 0;  // stop after the exact diagonalisation
   const int T = 256;
@@ -801,10 +801,18 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     ctx->last_error = "css_density: CSS_MIXED_3XTF32 needs 17 <= b <= 24 (and rows of at most 128 blocks)";
     return CSS_ERR_UNSUPPORTED;
   }
+  const bool use_split = prec == CSS_FP64_SPLIT;
+  if (use_split && !css_spmm_split_supported(b)) {
+    ctx->last_error = "css_density: CSS_FP64_SPLIT needs b = 6 or b = 23";
+    return CSS_ERR_UNSUPPORTED;
+  }
   // FP32 with b = 6 or 23: the exact-width H * V unless a padded variant is asked for
   const bool use_dup = !use_tc && ctx->spmm_variant < 0 && css_spmm_dup_supported(f32, b);
+  const void* Hsplit = nullptr;
   if (use_tc)
     CSS_TRY(css_hv_tc_prepare(ctx, b, n_brow, nnzb, row_ptr, col_idx, Hval, &Htc, &Hd3, st));
+  else if (use_split)
+    CSS_TRY(css_spmm_split_prepare(ctx, b, nnzb, Hval, &Hsplit, st));
   else if (use_dup)
     CSS_TRY(css_spmm_dup_prepare(ctx, b, n_brow, nnzb, row_ptr, col_idx, Hval, &Hdup, &Hlodup, st));
   else
@@ -889,6 +897,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   la.Hlo_diag = Hlo;
   la.Hdup = Hdup;
   la.Hlo_dup = Hlodup;
+  la.Hsplit = Hsplit;
   la.use_tc = use_tc;
   la.tc_H = Htc;
   la.tc_Hd3 = Hd3;
@@ -932,9 +941,10 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
   // A batch of systems runs its per-system passes concurrently on up to kSide side streams, each
   // with its own Krylov workspace (the passes of different systems touch disjoint rows, colours
   // and sampled pairs); the call's stream waits for all of them before the eigen stage.  The
-  // tensor-core H*V keeps one schedule per call, so it runs the passes in turn.
+  // tensor-core H*V keeps one schedule per call and the split-FP64 H*V one split copy of V, so
+  // with them the passes run in turn.
   constexpr int kSide = 8;
-  int nside = (n_sys > 1 && !use_tc) ? std::min(n_sys, kSide) : 0;
+  int nside = (n_sys > 1 && !use_tc && !use_split) ? std::min(n_sys, kSide) : 0;
   if (nside > 0) {
     // each side stream needs one more Krylov set; take only as many as fit beside the
     // reserve (sets already held from an earlier call count as free)
@@ -1149,7 +1159,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     ctx->info.n_breakdown = hm[0];
     const int32_t st_bits = hm[1];
     if (use_tc) CSS_TRY(css_hv_tc_check(ctx, st));
-    if (use_dup) CSS_TRY(css_spmm_dup_check(ctx, st));
+    if (use_dup || use_split) CSS_TRY(css_spmm_dup_check(ctx, st));
     if (st_bits & 2) {
       ctx->last_error = "css_density: a wait between pipelined band-reduction sweeps timed out";
       return CSS_ERR_TIMEOUT;
@@ -1320,7 +1330,7 @@ css_status css_density_impl(css_ctx* ctx, int32_t n_sys, const css_sys_desc* sys
     ctx->info.ms_total = tm.ms(0, 6);
   }
   if (use_tc) CSS_TRY(css_hv_tc_check(ctx, st));
-  if (use_dup) CSS_TRY(css_spmm_dup_check(ctx, st));
+  if (use_dup || use_split) CSS_TRY(css_spmm_dup_check(ctx, st));
   if (mu_err) {
     ctx->last_error = "css_density: grid barrier of the mu bisection timed out";
     return CSS_ERR_TIMEOUT;
@@ -1732,7 +1742,7 @@ css_status css_hprime(css_ctx* ctx, const css_bsr* S, const css_bsr* H, const in
   if (n_colours < 1) return css_set_arg_error(ctx, "css_hprime: n_colours < 1");
   CSS_CU(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
-  const bool f32 = prec != CSS_FP64;
+  const bool f32 = prec == CSS_MIXED_FP32 || prec == CSS_MIXED_3XTF32;
   const int32_t b = S->b, n_brow = S->n_brow;
   const int64_t N = (int64_t)n_brow * b;
   const int32_t w = n_colours * b;
@@ -1810,7 +1820,7 @@ css_status css_density_nonorth(css_ctx* ctx, const css_bsr* S, const double* Sin
     return css_set_arg_error(ctx, "css_density_nonorth: S or H' without pattern or values");
   if (S->n_brow != Hp->n_brow || S->b != Hp->b || S->n_brow < 1 || S->nnzb < S->n_brow || Hp->nnzb < Hp->n_brow)
     return css_set_arg_error(ctx, "css_density_nonorth: S and H' need the same n_brow and b and a diagonal");
-  if (prec != CSS_FP64 && prec != CSS_MIXED_FP32 && prec != CSS_MIXED_3XTF32)
+  if (prec != CSS_FP64 && prec != CSS_MIXED_FP32 && prec != CSS_MIXED_3XTF32 && prec != CSS_FP64_SPLIT)
     return css_set_arg_error(ctx, "css_density_nonorth: unknown precision");
   if (flags & ~(CSS_SYMMETRIZE | CSS_REORTH_LOCAL)) return css_set_arg_error(ctx, "css_density_nonorth: unknown flag");
   const int32_t b = Hp->b;
@@ -1828,7 +1838,7 @@ css_status css_density_nonorth(css_ctx* ctx, const css_bsr* S, const double* Sin
     return css_set_arg_error(ctx, "css_density_nonorth: problem too large");
   CSS_CU(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
-  const bool f32 = prec != CSS_FP64;
+  const bool f32 = prec == CSS_MIXED_FP32 || prec == CSS_MIXED_3XTF32;
   const int32_t n_brow = Hp->n_brow, nc = n_colours, bb = b * b, nmax = m * b;
   const int64_t N = (int64_t)n_brow * b;
   const size_t s_vec = f32 ? 4 : 8;

@@ -1185,14 +1185,20 @@ css_status launch_spmm(css_ctx* ctx, const LzArgs& a, const T* V, T* W, cudaStre
   if constexpr (sizeof(T) == 4) {
     if (a.use_tc) return tune_only ? CSS_OK : css_hv_tc(ctx, a, V, W, st);
     dup = a.Hdup != nullptr;
+  } else {
+    dup = a.Hsplit != nullptr;
   }
-  // the exact-width kernel (css_spmm.cu) when H was prepared for it, else the padded one
+  // the exact-width kernel (FP32) or the split-FP64 one (css_spmm.cu) when H was prepared for
+  // it, else the padded one
   auto run = [&](int v) -> css_status {
-    if constexpr (sizeof(T) == 4)
+    if constexpr (sizeof(T) == 4) {
       if (dup) return css_spmm_dup(ctx, a, V, W, v, st);
+    } else {
+      if (dup) return css_spmm_split(ctx, a, V, W, v, st);
+    }
     return launch_spmm_v<T>(ctx, a, V, W, v, st);
   };
-  const int nv = dup ? css_spmm_dup_variants() : kSpmmVariants;
+  const int nv = dup ? (sizeof(T) == 4 ? css_spmm_dup_variants() : css_spmm_split_variants()) : kSpmmVariants;
   const uint64_t key = ((uint64_t)sizeof(T) << 60) ^ ((uint64_t)dup << 59) ^ ((uint64_t)a.b << 48) ^
                        ((uint64_t)(a.w / 256) << 24) ^ (uint64_t)(a.n_brow >= (1 << 24) ? (1 << 24) - 1 : a.n_brow);
   if (!dup && ctx->spmm_variant >= 0) return tune_only ? CSS_OK : run(ctx->spmm_variant);

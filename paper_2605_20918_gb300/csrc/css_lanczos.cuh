@@ -55,6 +55,8 @@ struct LzArgs {
   // every block and of the low parts of the diagonal blocks (rows as in Hlo_diag)
   const void* Hdup = nullptr;
   const void* Hlo_dup = nullptr;
+  // FP64 H * V in FP32 pairs (css_spmm.cu) when Hsplit is set: hi and lo parts of every block
+  const void* Hsplit = nullptr;
   bool use_tc = false;
   const void* tc_H = nullptr;
   const void* tc_Hd3 = nullptr;
@@ -83,6 +85,13 @@ css_status css_spmm_dup_prepare(css_ctx* ctx, int32_t b, int32_t n_brow, int32_t
                                 cudaStream_t st);
 css_status css_spmm_dup(css_ctx* ctx, const LzArgs& a, const float* V, float* W, int variant, cudaStream_t st);
 css_status css_spmm_dup_check(css_ctx* ctx, cudaStream_t st);
+// FP64-accurate H * V in FP32 pairs (css_spmm.cu, precision CSS_FP64_SPLIT): b = 6 and b = 23;
+// its time-out flag is the exact-width kernel's (css_spmm_dup_check)
+bool css_spmm_split_supported(int32_t b);
+int css_spmm_split_variants();
+css_status css_spmm_split_prepare(css_ctx* ctx, int32_t b, int32_t nnzb, const double* H, const void** Hs,
+                                  cudaStream_t st);
+css_status css_spmm_split(css_ctx* ctx, const LzArgs& a, const double* V, double* W, int variant, cudaStream_t st);
 // FP32 row passes of a Lanczos step for 16 < b <= 24 (css_rows.cu); mode 0 S1, 1 S3, 2 TRIG, 3 TRI
 bool css_rowpass_supported(bool fp32, int32_t b);
 css_status css_rowpass(css_ctx* ctx, int mode, int64_t N, int32_t b, int32_t ws, int32_t ncb, int32_t cb0, int first,

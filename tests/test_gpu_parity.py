@@ -140,6 +140,60 @@ def test_density_fp64_matches_oracle(torch, css, ctx, n, kind, r_col, m, kw, hk)
     assert (got["status"] == css.CSS_WARN_BREAKDOWN) == (ref["n_breakdown"] > 0)
 
 
+@pytest.mark.parametrize("n,kind,r_col,m,kw,hk", FP64_CASES)
+def test_density_fp64_split_matches_oracle(torch, css, ctx, n, kind, r_col, m, kw, hk):
+    """CSS_FP64_SPLIT: FP64 everywhere but the recurrence's H*V, which runs on the FP32 FMA pipe with
+    every value as an FP32 hi + lo pair, error-free products and TwoSum accumulation; the FP64
+    tolerances against the oracle on every FP64 case (6 and 23 orbitals, breakdown, two-pass,
+    T = 0, no symmetrisation)."""
+    g, H, col, s, nc = _system(n, kind, r_col, **hk)
+    ne = synth.n_electrons(n)
+    args = dict(kT=0.05, n_elec=ne, solve_mu=True, m=m, flags=1)
+    args.update(kw)
+    ref = oracle.density(H, col, s, nc, mu=args.get("mu", 0.0), kT=args["kT"], n_elec=ne,
+                         solve_mu=args["solve_mu"], m=m, flags=args["flags"] & ~2)
+    got = gpu_density(torch, css, ctx, H, col, s, nc, precision=css.CSS_FP64_SPLIT, **args)
+    err = float(np.abs(got["P"] - ref["P"]).max())
+    assert err < FP64_TOL, err
+    assert abs(got["trP"] - ref["trP"]) < 1e-8
+    assert abs(got["trPH"] - ref["trPH"]) < 1e-7
+    assert (got["status"] == css.CSS_WARN_BREAKDOWN) == (ref["n_breakdown"] > 0)
+
+
+def test_fp64_split_batch_equals_single(torch, css, ctx):
+    """A batch of two systems under CSS_FP64_SPLIT (their passes in turn on one stream) gives each
+    system's single-call P bit for bit."""
+    sysd = [_system(n, "dzp", 8.0) for n in (64, 27)]
+    dev = torch.device("cuda:0")
+    singles, Hs, cs, ss, ncs, Ps, fs = [], [], [], [], [], [], []
+    for g, H, col, s, nc in sysd:
+        ne = synth.n_electrons(g.n_mol)
+        singles.append(gpu_density(torch, css, ctx, H, col, s, nc, kT=0.05, n_elec=ne, m=6,
+                                   precision=css.CSS_FP64_SPLIT)["P"])
+        Hs.append(css.DeviceBSR.from_host(H, dev))
+        cs.append(torch.as_tensor(col, device=dev))
+        ss.append(torch.as_tensor(s, device=dev))
+        ncs.append(nc)
+        Ps.append(torch.empty((H.nnzb, H.b, H.b), dtype=torch.float64, device=dev))
+        fs.append(dict(kT=0.05, n_elec=ne))
+    ctx.density_batch(Hs, cs, ss, ncs, Ps, fs, m=6, precision=css.CSS_FP64_SPLIT)
+    for a, p in zip(singles, Ps):
+        assert np.array_equal(a, p.cpu().numpy())
+
+
+def test_fp64_split_refuses_other_block_widths(torch, css, ctx):
+    """The split-FP64 H*V exists for b = 6 and b = 23; another b is refused with CSS_ERR_UNSUPPORTED."""
+    g = synth.water_box(27)
+    lv = np.sort(np.random.default_rng(5).uniform(-12, 8, size=(27, 5)), axis=1)
+    H = synth.hamiltonian(g, levels=lv)
+    col, nc = oracle.color(g.pos, g.box, 6.0, 1004)
+    s = oracle.probes(col, 5, 1005)
+    with pytest.raises(css.CSSError) as e:
+        gpu_density(torch, css, ctx, H, col, s, nc, mu=-1.0, kT=0.1, solve_mu=False, m=4,
+                    precision=css.CSS_FP64_SPLIT)
+    assert e.value.status == 7
+
+
 def test_degenerate_colouring_is_exact_f_of_H(torch, css, ctx):
     g = synth.water_box(8)
     H = synth.hamiltonian(g)
