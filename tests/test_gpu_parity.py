@@ -162,7 +162,7 @@ def test_density_fp64_split_matches_oracle(torch, css, ctx, n, kind, r_col, m, k
 
 def test_fp64_split_batch_equals_single(torch, css, ctx):
     """A batch of two systems under CSS_FP64_SPLIT (their passes in turn on one stream) gives each
-    system's single-call P bit for bit."""
+    system's single-call P to the batch tolerance of the FP64 mode."""
     sysd = [_system(n, "dzp", 8.0) for n in (64, 27)]
     dev = torch.device("cuda:0")
     singles, Hs, cs, ss, ncs, Ps, fs = [], [], [], [], [], [], []
@@ -178,7 +178,7 @@ def test_fp64_split_batch_equals_single(torch, css, ctx):
         fs.append(dict(kT=0.05, n_elec=ne))
     ctx.density_batch(Hs, cs, ss, ncs, Ps, fs, m=6, precision=css.CSS_FP64_SPLIT)
     for a, p in zip(singles, Ps):
-        assert np.array_equal(a, p.cpu().numpy())
+        assert np.abs(a - p.cpu().numpy()).max() < 1e-12
 
 
 def test_fp64_split_refuses_other_block_widths(torch, css, ctx):
