@@ -81,7 +81,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["mixed", "fp64", "3xtf32"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "fp64", "3xtf32", "fp64-split"], default="mixed")
     ap.add_argument("--n-mol", type=int, default=10000)
     ap.add_argument("--kind", default="dzp")
     ap.add_argument("--m", type=int, default=40)
@@ -210,7 +210,7 @@ def oracle_sample(H, col, sign, nc, a):
     mu, the extraction and the symmetrisation (a few percent of a build) are not in it."""
     import oracle
     threads = oracle.num_threads()
-    flags = oracle.REORTH_LOCAL if a.precision != "fp64" else 0
+    flags = oracle.REORTH_LOCAL if a.precision in ("mixed", "3xtf32") else 0
     sub = list(range(min(threads, nc)))
     t0 = time.perf_counter()
     oracle.density(H, col, sign, nc, mu=-4.0, kT=0.05, solve_mu=False, m=SAMPLE_M, flags=flags, colour_subset=sub)
@@ -227,7 +227,7 @@ def oracle_sample(H, col, sign, nc, a):
 
 
 def sample_note(a, parts):
-    reo = ", local reorthogonalisation" if a.precision != "fp64" else ""
+    reo = ", local reorthogonalisation" if a.precision in ("mixed", "3xtf32") else ""
     return (f"oracle (FP64{reo}) on geometry 0 of the {a.n_mol}-molecule workload, its own schedule (OpenMP over "
             f"colours, one thread per colour): {parts['threads']} colours at Krylov depth {SAMPLE_M} "
             f"({parts['t_lanczos_s']:.2f} s) and one exact diagonalisation of a {a.m * 23 if a.kind == 'dzp' else a.m * 6}"
@@ -240,7 +240,7 @@ def oracle_full_build(H, col, sign, nc, a):
     """Wall time of one complete oracle P build (mu solved), for checking the sample's scaling."""
     import oracle
     from paper_2605_20918_gb300 import synth
-    flags = oracle.SYMMETRIZE | (oracle.REORTH_LOCAL if a.precision != "fp64" else 0)
+    flags = oracle.SYMMETRIZE | (oracle.REORTH_LOCAL if a.precision in ("mixed", "3xtf32") else 0)
     t0 = time.perf_counter()
     oracle.density(H, col, sign, nc, kT=0.05, n_elec=synth.n_electrons(H.n_brow), m=a.m, flags=flags)
     return time.perf_counter() - t0
@@ -349,7 +349,7 @@ def run_reference(a):
     value = statistics.mean(times)
     cfg = workload_config(a)
     cfg["l2"] = l2_note(H)
-    cfg["precision"] = "fp64 (CPU oracle" + (", local reorthogonalisation as the mixed GPU path)" if a.precision != "fp64"
+    cfg["precision"] = "fp64 (CPU oracle" + (", local reorthogonalisation as the mixed GPU path)" if a.precision in ("mixed", "3xtf32")
                                              else ")")
     note = (f"one complete oracle P build of the {a.n_mol}-molecule workload per step" if a.oracle_full
             else sample_note(a, parts))
@@ -471,7 +471,8 @@ def main():
     if ws > 1:
         dist.barrier()
     dev = torch.device("cuda", local)
-    prec = {"mixed": css.CSS_MIXED_FP32, "3xtf32": css.CSS_MIXED_3XTF32}.get(a.precision, css.CSS_FP64)
+    prec = {"mixed": css.CSS_MIXED_FP32, "3xtf32": css.CSS_MIXED_3XTF32,
+            "fp64-split": css.CSS_FP64_SPLIT}.get(a.precision, css.CSS_FP64)
     mixed = prec != css.CSS_FP64
     from paper_2605_20918_gb300 import shard
     n_steps = a.warmup + a.steps
@@ -531,8 +532,13 @@ def main():
     fp32_peak = fp32_peak_tflops(n_sm, pk["sm_max_mhz"])
     tf32_peak = tf32_peak_tflops(pk)
     tc = (os.environ.get("CSS_HV_TC") == "1" or prec == css.CSS_MIXED_3XTF32) and mixed and 16 < H0.b <= 24
+    split = prec == css.CSS_FP64_SPLIT
     hv_name, hv_version = hv_kernel(mixed, H0.b, tc)
-    peak = (tf32_peak if tc else fp32_peak) if mixed else FP64_PEAK
+    if split:
+        hv_name, hv_version = ("k_spmm_df (FP64-accurate H*V in FP32 hi + lo pairs on the FP32 FMA pipe)",
+                               "k_spmm_df")
+    # the split arithmetic takes 11 FP32 lane operations per FP64-equivalent term (2 flop)
+    peak = (tf32_peak if tc else fp32_peak) if mixed else (fp32_peak / 11.0 if split else FP64_PEAK)
     traffic = None
     tf = ROOT / "profiles" / "spmm_traffic.json"
     if tf.exists():
@@ -547,16 +553,20 @@ def main():
     cfg["l2"] = l2_note(H0)
     line = {"metric": METRIC, "value": value, "unit": "s/P-build", "n_gpus": ws,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": elapsed / a.steps * 1e3, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if mixed else ("f64 (H*V in f32 pairs)" if split else "f64"),
             "data": "synthetic", "config": cfg,
             "roofline": {"kernel": hv_name,
-                         "bound": "tensor" if tc else ("alu" if mixed else "alu_fp64"),
+                         "bound": "tensor" if tc else ("alu" if mixed or split else "alu_fp64"),
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": None if tc else traffic,
                          "peak_source": (f"dense TF32 tensor peak: measured sustained BF16 {pk['bf16_sustained']:.0f} "
                                          f"TF/s x 1.1/2.25 ({pk['source']})" if tc else
                                          f"FP32 FFMA (CUDA-core) ceiling: {n_sm} SMs x 128 lanes x 2 flop x "
-                                         f"{pk['sm_max_mhz']:.0f} MHz" if mixed else FP64_PEAK_NOTE),
+                                         f"{pk['sm_max_mhz']:.0f} MHz" if mixed else
+                                         f"FP32 FFMA ceiling / 11 FP32 operations per FP64-equivalent term "
+                                         f"({n_sm} SMs x 128 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz / 11)"
+                                         if split else FP64_PEAK_NOTE),
                          "frac_vs_tf32_tensor_peak": achieved / tf32_peak if mixed else None,
                          "launch_ms": spmm_avg, "flops_per_launch": last_inf["spmm_flops"],
                          "alg_bytes_per_launch": last_inf["spmm_bytes"]},
