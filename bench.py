@@ -473,7 +473,7 @@ def main():
     dev = torch.device("cuda", local)
     prec = {"mixed": css.CSS_MIXED_FP32, "3xtf32": css.CSS_MIXED_3XTF32,
             "fp64-split": css.CSS_FP64_SPLIT}.get(a.precision, css.CSS_FP64)
-    mixed = prec != css.CSS_FP64
+    mixed = prec in (css.CSS_MIXED_FP32, css.CSS_MIXED_3XTF32)
     from paper_2605_20918_gb300 import shard
     n_steps = a.warmup + a.steps
     my = shard.rank_steps(rank, ws, n_steps)

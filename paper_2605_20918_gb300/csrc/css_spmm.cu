@@ -398,11 +398,11 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_spmm_df(DfArgs a) {
   bool ok = true;
   int32_t q = 0;
   if (nsteps > 0) {
-    float4 vr[B];
-    float4 vn[SD_DEPTH];
+    // the k loop is not unrolled (an unrolled block step is ≈ 7,000 instructions, past the
+    // instruction cache); V rows arrive three ahead of use through the registers v0, v1, v2,
+    // across the end of a block into the next neighbour's first rows
     int32_t Jc = a.col_idx[p0] - a.jbase;
-#pragma unroll
-    for (int k = 0; k < SD_DEPTH; ++k) vr[k] = vrow(Jc, k);
+    float4 v0 = vrow(Jc, 0), v1 = vrow(Jc, 1), v2 = vrow(Jc, 2);
     for (; q < nsteps; ++q) {
       const int s = q % SD_NS;
       const bool more = q + 1 < nsteps;
@@ -422,14 +422,16 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_spmm_df(DfArgs a) {
         break;
       }
       const float* hs = ring + (size_t)s * 2 * C::HF;
-#pragma unroll
+#pragma unroll 1
       for (int k = 0; k < B; ++k) {
-        if (k + SD_DEPTH < B)
-          vr[k + SD_DEPTH] = vrow(Jc, k + SD_DEPTH);
+        const int t = k + 3;  // the row this iteration prefetches
+        float4 v3 = v2;       // past the last block: a copy, never used
+        if (t < B)
+          v3 = vrow(Jc, t);
         else if (more)
-          vn[k + SD_DEPTH - B] = vrow(Jn, k + SD_DEPTH - B);
-        const unsigned long long vh[CPT] = {dup2(vr[k].x), dup2(vr[k].z)};
-        const unsigned long long vl[CPT] = {dup2(vr[k].y), dup2(vr[k].w)};
+          v3 = vrow(Jn, t - B);
+        const unsigned long long vh[CPT] = {dup2(v0.x), dup2(v0.z)};
+        const unsigned long long vl[CPT] = {dup2(v0.y), dup2(v0.w)};
         const float* hk = hs + k * C::RA;
         const float* lk = hk + C::HF;
         if constexpr (RP % 2 == 0) {
@@ -452,11 +454,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_spmm_df(DfArgs a) {
             for (int u = 0; u < CPT; ++u) df_term(sh[i][u], sl[i][u], h, l, vh[u], vl[u]);
           }
         }
+        v0 = v1;
+        v1 = v2;
+        v2 = v3;
       }
       __syncwarp();
       if (lane == 0) bar_arrive(&empty[s]);
-#pragma unroll
-      for (int k = 0; k < SD_DEPTH; ++k) vr[k] = vn[k];
       Jc = Jn;
     }
   }
