@@ -224,7 +224,12 @@ CSS_API css_status css_probes(css_ctx* ctx, const int32_t* colour, int32_t n_mol
  *   P_val      device double[nnzb*b*b], written (same block order as H->val)
  *   trP, trPH, mu_out   host doubles, written (Tr P, Tr(P H), chemical potential); may be NULL
  * Returns CSS_WARN_BREAKDOWN when a colour's recurrence stopped early (invariant Krylov
- * space: the result is exact for that colour).  Synchronises `stream`. */
+ * space: the result is exact for that colour).  Synchronises `stream`.
+ * The block-Lanczos phase of a single-system call runs as one CUDA graph, captured on a stream
+ * of the context and launched on `stream` (the previous call's graph is updated in place when
+ * the launch sequence has the same shape); the environment variable CSS_GRAPH=0 at css_create
+ * launches its kernels one by one, CSS_GRAPH=1 captures batches too.  The results are the
+ * same either way. */
 CSS_API css_status css_density(css_ctx* ctx, const css_bsr* H, const int32_t* colour, const int8_t* sign, int32_t n_colours,
                        const css_fermi* fermi, int32_t m, css_precision prec, uint32_t flags, double* P_val,
                        double* trP, double* trPH, double* mu_out, void* stream);
